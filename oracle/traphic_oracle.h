@@ -1,0 +1,110 @@
+/*
+ * traphic_oracle.h -- plain, slow FP64 CPU oracle of one TRAPHIC radiative-transfer
+ * step with transport of ionizing recombination radiation (Raicevic, Pawlik, Schaye &
+ * Rahmati, "The effect of recombination radiation on the temperature and ionization
+ * state of partially ionized gas", Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  It shares no source, header, table or
+ * constant generator with the CUDA library; both follow the same written readings of
+ * the paper.
+ *
+ * Units are cgs throughout.  Positions are given per box in [0, L_b) and quantised to
+ * ORC_Q = 2^20 integer cells per box side (a reading: the paper fixes no position
+ * arithmetic; integers make neighbour and cone decisions exact and reproducible).
+ */
+#ifndef TRAPHIC_ORACLE_H
+#define TRAPHIC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_HOP_LIMIT = 4 };
+enum { ORC_REC_TRANSPORT = 0, ORC_REC_OTS_CASE_B = 1, ORC_REC_CASE_A = 2 };
+/* cooling terms (bit flags): recombination, collisional excitation,
+   collisional ionisation, free-free */
+enum { ORC_COOL_REC = 1, ORC_COOL_CEX = 2, ORC_COOL_CION = 4, ORC_COOL_FF = 8 };
+
+typedef struct {
+    int n_ngb;            /* SPH neighbours per particle, 1..32 (Sec. 2.1) */
+    int n_ec, n_tc, n_rc; /* emission / transmission / reception cones (Sec. 2.1) */
+    int n_freq_src;       /* source frequency bins; one recombination bin is added */
+    double dt, dt_em;     /* RT step and emission step, s (Sec. 2.1) */
+    int rec_mode;         /* ORC_REC_* (Sec. 2.1 last paragraphs; Sec. 2.2) */
+    int evolve_T;         /* 0: temperature held fixed */
+    uint64_t seed;
+    int hop_cap;          /* maximum hops per RT step */
+    int sub_cap;          /* maximum chemistry subcycles per step */
+    int cool_flags;       /* ORC_COOL_* */
+    double T_floor;       /* K */
+    double eps_rr_fixed;  /* erg; < 0 selects kT of the emitting gas (Sec. 2.2) */
+    double sigma_rec;     /* grey cross-section of the recombination bin, cm^2 (Sec. 2.2) */
+} orc_config;
+
+typedef struct orc_sim orc_sim;
+
+/* --- building blocks, exposed for pinning tests ------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+uint64_t orc_mix64(uint64_t z);
+int orc_axis_set(int n, double *out /* [n*3] */);
+/* random rotation matrix (row-major) drawn from the counter-based generator */
+void orc_rotation(uint64_t seed, uint32_t purpose, uint32_t c0, uint32_t c1, uint32_t c2,
+                  double R[9]);
+int orc_in_cone(const int64_t delta[3], const double d[3], int n_tc);
+int orc_bin(const double R[9], const double *axes, int n_rc, const double d[3]);
+/* rate coefficients at T: alpha_A, alpha_B, beta_col, Lrec_A, Lrec_B, L_cex, L_cion, L_ff */
+void orc_rates(double T, double out[8]);
+/* one particle's chemistry update over dt.  On return x and T hold the new state;
+   out[0] = recombination photons to emit, out[1] = subcycles, out[2] = floor hits */
+void orc_chem_particle(const orc_config *cfg, double nH, double NH, double phot,
+                       double heat, double *x, double *T, double out[3]);
+/* exact k nearest neighbours of query points among points (integer coordinates).
+   self_offset >= 0: query q is point (self_offset + q) and is excluded. use_grid
+   selects the uniform-grid search instead of brute force. */
+int orc_knn(long long n_pts, const int64_t *pts /* [n*3] */, long long n_q,
+            const int64_t *qpts /* [n_q*3] */, long long self_offset, int k, int use_grid,
+            int32_t *out_idx /* [n_q*k] */, int64_t *out_d2 /* [n_q*k] */);
+
+/* --- the full step ------------------------------------------------------------ */
+orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off,
+                    const double *box_L, const double *x, const double *y, const double *z,
+                    const double *n_H, const double *N_H, const double *x_HI,
+                    const double *T, int n_src, const int *src_box, const double *sx,
+                    const double *sy, const double *sz, const double *ndot,
+                    const double *sigma, const double *eps);
+void orc_destroy(orc_sim *s);
+int orc_build_neighbours(orc_sim *s);
+void orc_get_neighbours(const orc_sim *s, int32_t *nbr, int64_t *h2, int32_t *src_nbr,
+                        int64_t *src_h2);
+void orc_get_quantised(const orc_sim *s, int64_t *q);
+void orc_rotate(orc_sim *s, long long step);       /* reception + emission rotations */
+void orc_get_rotations(const orc_sim *s, double *R /* [n*9] */, double *Rs /* [ns*K*9] */);
+void orc_rebin(orc_sim *s);                        /* clock reset + re-bin (Sec. 2.1) */
+void orc_emit(orc_sim *s, long long step);         /* recombination + source emission */
+int orc_transport(orc_sim *s, long long step);     /* hop loop; returns status */
+void orc_chemistry(orc_sim *s);
+int orc_step(orc_sim *s, long long step);
+/* masks of the current packets: bit k set when neighbour k of particle i lies in the
+   transmission cone of slot sl; entries of inactive slots are 0 */
+void orc_cone_masks(const orc_sim *s, uint32_t *mask /* [n*S] */);
+/* state access; slot fields are N, Mx, My, Mz, C (= N * clock), E (= N * eps) */
+void orc_get_slots(const orc_sim *s, double *f /* [6*n*S] */);
+void orc_set_slots(orc_sim *s, const double *f);
+void orc_get_state(const orc_sim *s, double *x_HI, double *T, double *N_rec,
+                   double *eps_rec);
+void orc_set_state(orc_sim *s, const double *x_HI, const double *T, const double *N_rec,
+                   const double *eps_rec);
+void orc_get_deposits(const orc_sim *s, double *abs_ /* [n*nf] */, double *absE /* [n] */,
+                      double *pass /* [n*nf] */);
+/* per box: emitted, absorbed, escaped, in flight (cumulative photon counts) */
+void orc_get_budget(const orc_sim *s, double *out /* [n_boxes*4] */);
+/* hops, virtual particles, escaped virtuals, chemistry subcycles of the last step */
+void orc_get_stats(const orc_sim *s, long long out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
