@@ -1,0 +1,441 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test would fail on a plausible mistake in the oracle: a wrong generator constant, a cone of
+the wrong opening angle, a transposed rotation, a dropped N_HI or dt in the rates, a wrong energy
+normalisation, a photon leak, or a wrong recombination coefficient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_0182_gb300 import workloads as W
+from conftest import golden, paper_values
+
+KPC, MYR, EV, K_B = W.KPC, W.MYR, W.EV, W.K_B
+
+
+# --- generator --------------------------------------------------------------------------------
+def test_philox_known_answers():
+    n = 0
+    for line in open(golden("philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t, 16) for t in line.split()]
+        assert list(oracle.philox(v[0:4], v[4:6])) == v[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_splitmix_known_answers():
+    g = 0x9E3779B97F4A7C15
+    for line in open(golden("splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, val = line.split()
+        assert oracle.mix64((int(k) - 1) * g % (1 << 64)) == int(val, 16)
+
+
+# --- cone direction sets and rotations ----------------------------------------------------------
+@pytest.mark.parametrize("n", [8, 32])
+def test_axis_sets_isotropic(n):
+    A = oracle.axis_set(n)
+    assert np.allclose(np.linalg.norm(A, axis=1), 1.0, atol=1e-15)
+    assert np.allclose(A.sum(0), 0.0, atol=1e-14)               # no preferred direction
+    assert np.allclose(A.T @ A / n, np.eye(3) / 3, atol=1e-14)  # isotropic second moment
+    # every direction's antipode is in the set
+    for a in A:
+        assert np.min(np.linalg.norm(A + a, axis=1)) < 1e-14
+    G = A @ A.T
+    np.fill_diagonal(G, -2)
+    nearest = G.max(1)
+    if n == 8:   # cube diagonals: nearest neighbours at cos = 1/3
+        assert np.allclose(nearest, 1 / 3)
+    else:        # icosahedron vertices (first 12) and dodecahedron vertices (last 20)
+        ico, dod = A[:12], A[12:]
+        Gi = ico @ ico.T
+        np.fill_diagonal(Gi, -2)
+        assert np.allclose(Gi.max(1), 1 / math.sqrt(5))
+        Gd = dod @ dod.T
+        np.fill_diagonal(Gd, -2)
+        assert np.allclose(Gd.max(1), math.sqrt(5) / 3)
+
+
+def test_rotations_are_uniform_rotations():
+    Rs = np.array([oracle.rotation(1234, 1, 7, 0, i) for i in range(4000)])
+    for R in Rs[:50]:
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(R) - 1) < 1e-14
+    # Haar measure: E[R] = 0 and the image of a fixed axis is uniform on the sphere
+    assert np.abs(Rs.mean(0)).max() < 4 / math.sqrt(4000)
+    v = Rs[:, :, 2]
+    assert np.allclose(v.T @ v / len(v), np.eye(3) / 3, atol=0.03)
+    # different counters give different rotations
+    assert not np.allclose(Rs[0], Rs[1])
+
+
+def test_transmission_cone_solid_angle():
+    """The cone holds the directions within arccos(1 - 2/N_TC) of the axis: solid angle 4pi/N_TC."""
+    rng = np.random.default_rng(3)
+    for n_tc in (2, 8, 32, 128):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        dirs = rng.normal(size=(20000, 3))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        delta = np.rint(dirs * 1e5).astype(np.int64)
+        inside = np.array([oracle.in_cone(x, d, n_tc) for x in delta])
+        frac = inside.mean()
+        sd = math.sqrt((1 / n_tc) * (1 - 1 / n_tc) / len(dirs))
+        assert abs(frac - 1 / n_tc) < 5 * sd + 1e-4
+        # agreement with the angle computed from scratch, away from the cone edge
+        ang = np.degrees(np.arccos(np.clip(delta @ d / np.linalg.norm(delta, axis=1), -1, 1)))
+        half = math.degrees(math.acos(1 - 2 / n_tc))
+        far = np.abs(ang - half) > 1e-3
+        assert np.array_equal(inside[far], (ang < half)[far])
+    assert not oracle.in_cone([0, 0, 0], [1.0, 0, 0], 8)   # coincident neighbour never inside
+
+
+def test_reception_bin_is_nearest_rotated_axis():
+    rng = np.random.default_rng(4)
+    for n in (8, 32):
+        A = oracle.axis_set(n)
+        R = oracle.rotation(99, 1, 1, 2, 3)
+        counts = np.zeros(n)
+        for _ in range(4000):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            b = oracle.recv_bin(R, A, d)
+            assert b == int(np.argmax((R @ A.T).T @ d))
+            counts[b] += 1
+        if n == 8:  # cube-diagonal cones are the 8 octants of the rotated frame
+            assert np.all(np.abs(counts / 4000 - 1 / 8) < 0.03)
+
+
+# --- neighbours ---------------------------------------------------------------------------------
+def _brute_knn(pts, q, k, self_idx=None):
+    d2 = ((pts - q) ** 2).sum(1)
+    idx = np.arange(len(pts))
+    keep = idx != self_idx if self_idx is not None else np.ones(len(pts), bool)
+    order = np.lexsort((idx[keep], d2[keep]))[:k]
+    return idx[keep][order], d2[keep][order]
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "lattice"])
+def test_knn_grid_equals_brute_force(kind):
+    rng = np.random.default_rng(5)
+    Q = 1 << 20
+    if kind == "uniform":
+        pts = rng.integers(0, Q, size=(1500, 3))
+    elif kind == "clustered":   # tight clumps, exact duplicates and empty space
+        c = rng.integers(0, Q, size=(6, 3))
+        pts = np.clip(c[rng.integers(0, 6, 1500)] + rng.normal(0, 3000, (1500, 3)), 0, Q - 1)
+        pts = pts.astype(np.int64)
+        pts[100:140] = pts[99]
+    else:                       # exact lattice: many equal distances, ties go to the lower index
+        g = np.arange(11) * (Q // 11)
+        pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pts = np.ascontiguousarray(pts, dtype=np.int64)
+    k = 32
+    i_grid, d_grid = oracle.knn(pts, pts, k, self_offset=0, use_grid=True)
+    i_br, d_br = oracle.knn(pts, pts, k, self_offset=0, use_grid=False)
+    assert np.array_equal(i_grid, i_br) and np.array_equal(d_grid, d_br)
+    for t in range(0, len(pts), 97):
+        ib, db = _brute_knn(pts, pts[t], k, self_idx=t)
+        assert np.array_equal(i_grid[t], ib) and np.array_equal(d_grid[t], db)
+    # arbitrary query points (virtual particles, sources)
+    qs = rng.integers(0, Q, size=(200, 3))
+    i_g, d_g = oracle.knn(pts, qs, k, use_grid=True)
+    for t in range(200):
+        ib, db = _brute_knn(pts, qs[t], k)
+        assert np.array_equal(i_g[t], ib) and np.array_equal(d_g[t], db)
+
+
+# --- rates and chemistry ---------------------------------------------------------------------------
+def test_recombination_coefficients_match_paper():
+    pv = paper_values()
+    r = oracle.rates(1e4)
+    t_rec = 1 / (r["alpha_B"] * 1e-3) / MYR
+    v, tol = pv["t_rec_Myr"]
+    assert abs(t_rec / v - 1) < tol
+    v, tol = pv["alphaB_over_alphaA"]
+    assert abs(r["alpha_B"] / r["alpha_A"] / v - 1) < tol
+    v, tol = pv["ionising_recomb_fraction"]
+    assert abs((r["alpha_A"] - r["alpha_B"]) / r["alpha_A"] / v - 1) < tol
+    # mean energy carried off by a recombining electron is below ~kT (Osterbrock's beta/alpha)
+    for case in ("A", "B"):
+        ratio = r[f"Lrec_{case}"] / (K_B * 1e4 * r[f"alpha_{case}"])
+        assert 0.5 < ratio < 1.0
+    # recombination slows with temperature; collisional ionisation and excitation grow
+    r2 = oracle.rates(2e4)
+    assert r2["alpha_A"] < r["alpha_A"] and r2["beta"] > r["beta"] and r2["L_cex"] > r["L_cex"]
+
+
+def test_recombination_heating_energy():
+    v, tol = paper_values()["kT_27000K_eV"]
+    assert abs(K_B * 27000 / EV / v - 1) < tol
+
+
+def _params(**kw):
+    return W.default_params(**kw)
+
+
+def test_chemistry_equilibrium_reproduces_appendix_b():
+    """Plane-parallel front of App. B: Gamma = sigma F, case B, T = 1e4 K; the converged neutral
+    fraction gives lambda_mfp and the Stromgren distance printed in the paper."""
+    pv = paper_values()
+    sigma, F, nH = 1.6e-18, 1e6, 1e-3
+    p = _params(rec_mode=W.REC_OTS_CASE_B, evolve_T=0, dt=0.1 * MYR)
+    NH = 1e60
+    x, T = 1.0, 1e4
+    for _ in range(20000):      # 2 Gyr: many recombination times
+        phot = sigma * F * (x * NH) * p["dt"]
+        x, T, nrec, nsub, _f = oracle.chem_particle(p, nH, NH, phot, 0.0, x, T)
+    r = oracle.rates(1e4)
+    aB = r["alpha_B"]
+    # the quadratic of the ion balance sigma F x = alpha_B n_H (1-x)^2 (App. B) ...
+    a, b = aB * nH, sigma * F
+    x_quad = ((2 * a + b) - math.sqrt((2 * a + b) ** 2 - 4 * a * a)) / (2 * a)
+    assert abs(x / x_quad - 1) < 2e-6
+    # ... plus collisional ionisation beta n_e x, which App. B leaves out (beta n_e/Gamma ~ 6e-7)
+    xs = x_quad
+    for _ in range(50):
+        g = b + r["beta"] * nH * (1 - xs)
+        xs = ((2 * a + g) - math.sqrt((2 * a + g) ** 2 - 4 * a * a)) / (2 * a)
+    assert abs(x / xs - 1) < 1e-9
+    lam = 1 / (sigma * nH * x) / KPC
+    v, tol = pv["lambda_mfp_kpc"]
+    assert abs(lam / v - 1) < tol
+    v, tol = pv["L_strom_kpc"]
+    assert abs(F / (aB * nH * nH) / KPC / v - 1) < tol
+    assert nrec == 0.0       # no recombination photons emitted on the spot
+
+
+def test_chemistry_photon_accounting_and_recombination_photons():
+    p = _params(rec_mode=W.REC_TRANSPORT, evolve_T=0, dt=0.01 * MYR)
+    nH, NH = 1e-3, 1e60
+    # small photon dose into neutral gas: every absorbed photon ionises one atom
+    phot = 1e-4 * NH
+    x, T, nrec, _, _ = oracle.chem_particle(p, nH, NH, phot, 0.0, 1.0, 1e4)
+    assert abs((1 - x) * NH / phot - 1) < 1e-3
+    # fully ionised gas without photons: ground-level recombinations alpha_1 n_e n_HII V dt
+    x, T, nrec, _, _ = oracle.chem_particle(p, nH, NH, 0.0, 0.0, 0.0, 1e4)
+    r = oracle.rates(1e4)
+    expect = (r["alpha_A"] - r["alpha_B"]) * nH * NH * p["dt"]
+    assert abs(nrec / expect - 1) < 2e-3
+    assert abs(x - r["alpha_A"] * nH * p["dt"]) < 2e-3 * x
+    # case A and on-the-spot modes emit nothing
+    for mode in (W.REC_OTS_CASE_B, W.REC_CASE_A):
+        q = _params(rec_mode=mode, evolve_T=0, dt=0.01 * MYR)
+        assert oracle.chem_particle(q, nH, NH, 0.0, 0.0, 0.0, 1e4)[2] == 0.0
+
+
+def test_chemistry_heating_normalisation():
+    """Absorbed energy E raises T by E / (1.5 k N_H (1 + x_HII)) when nothing else happens."""
+    p = _params(evolve_T=1, cool_flags=0, dt=0.01 * MYR, sub_cap=100000)
+    nH, NH = 1e-3, 1e60
+    E = 1e-6 * NH * EV * 13.6
+    x0 = 0.999999
+    x, T, _, nsub, _ = oracle.chem_particle(p, nH, NH, 1e-12 * NH, E, x0, 100.0)
+    dT = E / (1.5 * K_B * NH * (1 + (1 - x0)))
+    assert abs((T - 100.0) / dT - 1) < 1e-3
+    assert nsub >= 1
+
+
+def test_chemistry_cooling_reaches_floor_and_subcycles_bounded():
+    p = _params(evolve_T=1, cool_flags=15, dt=5 * MYR, sub_cap=2000)
+    x, T, _, nsub, nfloor = oracle.chem_particle(p, 1.0, 1e60, 0.0, 0.0, 0.01, 1e6)
+    assert T < 1e6 and T >= p["T_floor"]
+    assert nsub <= p["sub_cap"] + 1
+
+
+# --- transport ------------------------------------------------------------------------------------
+def test_grey_bins_of_1e5K_blackbody_match_paper():
+    pv = paper_values()
+    frac, sig, eps = W.blackbody_bins(1e5, [13.6, np.inf])
+    v, tol = pv["grey_sigma_1e5K_cm2"]
+    assert abs(sig[0] / v - 1) < tol
+    v, tol = pv["grey_eps_1e5K_eV"]
+    assert abs(eps[0] / EV / v - 1) < tol
+    v, tol = pv["sigma_13p6_cm2"]
+    assert abs(W.verner_hi(13.6) / v - 1) < tol
+    frac8, sig8, eps8 = W.blackbody_bins(1e5, W.BB_EDGES_8)
+    assert abs(frac8.sum() - 1) < 1e-6 and np.all(np.diff(sig8) < 0)
+
+
+def _run(wl, steps):
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    for st in range(steps):
+        assert s.step(st) == 0
+    return s
+
+
+def test_photon_conservation_cfg1():
+    s = _run(W.cfg1(), 12)
+    e, a, esc, fl = s.budget()[0]
+    assert e > 0 and a > 0 and esc > 0
+    assert abs(e - a - esc - fl) <= 1e-12 * e
+
+
+def test_photon_conservation_virtual_heavy():
+    wl = W.tiny(n=600, n_ngb=16, n_tc=64, n_rc=32, n_ec=32)
+    wl["x_HI"][:] = 0.05
+    s = _run(wl, 4)
+    st = s.stats()
+    assert st["virtual"] > 100
+    e, a, esc, fl = s.budget()[0]
+    assert abs(e - a - esc - fl) <= 1e-12 * e
+
+
+def test_optically_thin_box_lets_every_photon_escape():
+    wl = W.cfg1()
+    wl["x_HI"][:] = 0.0
+    s = _run(wl, 1)       # one step: afterwards the gas has recombined and is no longer thin
+    e, a, esc, fl = s.budget()[0]
+    assert a == 0.0 and fl == 0.0
+    assert abs(esc / e - 1) < 1e-12
+    assert np.all(s.deposits()[0] == 0.0)
+
+
+def test_recombination_emission_is_isotropic_and_complete():
+    wl = W.cfg1()
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    n = s.n
+    nrec = np.zeros(n)
+    nrec[[5, 77, 2000]] = [1e55, 3e54, 7e53]
+    s.set_state(N_rec=nrec, eps_rec=np.full(n, 2 * EV))
+    s.rotate(3)
+    s.rebin()
+    s.emit(3)
+    f = s.slots()
+    rec = slice(8, 16)   # recombination bin: the last 8 slots
+    N = f[0][:, rec].sum(1)
+    assert np.allclose(N[[5, 77, 2000]], nrec[[5, 77, 2000]], rtol=1e-14)
+    for i in (5, 77, 2000):
+        M = f[1:4, i, rec].sum(1)
+        assert np.linalg.norm(M) < 1e-13 * N[i]          # isotropic: net momentum cancels
+        assert np.allclose(f[5, i, rec].sum(), 2 * EV * N[i], rtol=1e-14)
+        assert np.all(f[4, i, rec] == 0.0)                # clocks start at the step start
+
+
+def _chain(n_part=40, spacing=0.1 * KPC, nH=1e-3, xHI=1e-2, steps_dt=None):
+    """Particles on a line with two neighbours each: a packet sent along the line can only reach
+    the next particle, so its photon count follows Beer-Lambert hop by hop."""
+    L = (n_part + 1) * spacing
+    x = (np.arange(n_part) + 0.5) * spacing
+    yz = np.full(n_part, 0.5 * L)
+    wl = W.tiny(n=n_part, n_ngb=2, L=L, n_tc=64)
+    wl.update(x=x, y=yz.copy(), z=yz.copy(), n_H=np.full(n_part, nH),
+              N_H=np.full(n_part, nH * spacing ** 3), x_HI=np.full(n_part, xHI),
+              T=np.full(n_part, 1e4), src_box=np.zeros(0, np.int32), src_x=np.zeros(0),
+              src_y=np.zeros(0), src_z=np.zeros(0), src_ndot=np.zeros(0))
+    if steps_dt is not None:
+        wl["params"]["dt"] = wl["params"]["dt_em"] = steps_dt
+    return wl
+
+
+def _put_packet(s, i, N, d):
+    f = np.zeros((6, s.n, s.S))
+    b = oracle.recv_bin(s.rotations()[0][i].reshape(3, 3), oracle.axis_set(s.params["n_rc"]), d)
+    f[0, i, b] = N
+    f[1:4, i, b] = N * np.asarray(d)
+    s.set_slots(f)
+
+
+def test_beer_lambert_chain():
+    wl = _chain()
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    s.rotate(0)
+    s.emit(0)
+    N0 = 1e50
+    # particle 1's two neighbours are particles 0 and 2: only 2 lies in a +x cone, and so on
+    _put_packet(s, 1, N0, [1.0, 0.0, 0.0])
+    assert s.transport(0) == 0
+    a = s.deposits()[0][:, 0]
+    sigma = wl["sigma"][0]
+    q = s.quantised()
+    u = wl["box_L"][0] / (1 << 20)
+    l = np.diff(q[1:, 0]) * u                     # projected hop lengths 1->2, 2->3, ...
+    tau = sigma * wl["x_HI"][2:] * wl["n_H"][2:] * l
+    N = N0 * np.exp(-np.concatenate([[0.0], np.cumsum(tau)]))   # photons arriving at 1, 2, ...
+    assert a[0] == 0.0 and a[1] == 0.0
+    # arrivals up to the second-to-last particle (the last one has no neighbour ahead and hands
+    # its photons to a virtual particle, which may still deposit some near the end of the chain)
+    assert np.allclose(a[2:-2], N[:-3] - N[1:-2], rtol=1e-12, atol=0)
+    e, ab, esc, fl = s.budget()[0]
+    assert abs(ab + esc - N0) <= 1e-12 * N0 and fl == 0.0
+    assert esc <= N[-1] * (1 + 1e-12)
+
+
+def test_clock_stops_packet_after_c_dt():
+    spacing = 0.1 * KPC
+    m = 7
+    dt = (m - 0.5) * spacing / 2.99792458e10     # light crosses 6.5 spacings in one step
+    wl = _chain(xHI=0.0, steps_dt=dt)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    s.rotate(0)
+    s.emit(0)
+    _put_packet(s, 1, 1e50, [1.0, 0.0, 0.0])
+    assert s.transport(0) == 0
+    f = s.slots()
+    held = np.nonzero(f[0].sum(1))[0]
+    assert list(held) == [m + 1]                  # stopped at the first particle past c dt
+    i = held[0]
+    clock = f[4, i].sum() / f[0, i].sum()
+    q = s.quantised()
+    u = wl["box_L"][0] / (1 << 20)
+    assert abs(clock - (q[m + 1, 0] - q[1, 0]) * u / 2.99792458e10) < 1e-9 * clock
+    # the next step restarts its clock and carries it further
+    s.rotate(1)
+    s.rebin()
+    assert np.all(s.slots()[4] == 0.0)
+
+
+def _front_radius(s, wl):
+    L = wl["box_L"][0]
+    pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
+    r = np.linalg.norm(pos - 0.5 * L, axis=1)
+    x = s.state()["x_HI"]
+    edges = np.linspace(0, 0.5 * L, 17)
+    prof = [x[(r >= a) & (r < b)].mean() for a, b in zip(edges[:-1], edges[1:])]
+    mid = 0.5 * (edges[:-1] + edges[1:])
+    for k in range(1, len(prof)):
+        if prof[k - 1] < 0.5 <= prof[k]:
+            t = (0.5 - prof[k - 1]) / (prof[k] - prof[k - 1])
+            return mid[k - 1] + t * (mid[k] - mid[k - 1]), np.array(prof), mid
+    return np.nan, np.array(prof), mid
+
+
+@pytest.mark.slow
+def test_stromgren_sphere_and_case_a_b_limits():
+    """Sec. 3 (Iliev Test 1 geometry): on-the-spot case B grows to the case-B Stromgren radius;
+    with transport of recombination radiation the front lies between the case-A and case-B
+    fronts and the inner neutral fraction is near the case-A value (Fig. 1 discussion)."""
+    steps = 120   # 300 Myr ~ 2.5 t_rec
+    res = {}
+    for mode in (W.REC_OTS_CASE_B, W.REC_CASE_A, W.REC_TRANSPORT):
+        wl = W.cfg1(rec_mode=mode)
+        s = _run(wl, steps)
+        rI, prof, mid = _front_radius(s, wl)
+        res[mode] = (rI, prof)
+        e, a, esc, fl = s.budget()[0]
+        assert abs(e - a - esc - fl) <= 1e-12 * e
+    aB = oracle.rates(1e4)["alpha_B"]
+    R_S = (3 * 5e48 / (4 * math.pi * aB * 1e-6)) ** (1 / 3)
+    t = steps * 2.5 * MYR
+    r_expect = R_S * (1 - math.exp(-t * aB * 1e-3)) ** (1 / 3)
+    h_mean = 13.2 * KPC / 16 * (32 * 3 / (4 * math.pi)) ** (1 / 3)
+    rB, rA, rRT = res[W.REC_OTS_CASE_B][0], res[W.REC_CASE_A][0], res[W.REC_TRANSPORT][0]
+    assert abs(rB - r_expect) < h_mean
+    assert rA < rB - 0.25 * h_mean                # case A: smaller front (Sec. 3)
+    assert abs(rRT - rB) < 0.25 * h_mean          # RT approaches case B at the front (Sec. 3)
+    # near the source (r < 0.23 R_S): RT close to case A, case B lower by alpha_B/alpha_A ~ 0.6
+    inner = slice(0, 3)
+    pB, pA, pRT = (res[m][1][inner] for m in (W.REC_OTS_CASE_B, W.REC_CASE_A, W.REC_TRANSPORT))
+    assert np.all(np.abs(pRT / pA - 1) < 0.15)
+    r = oracle.rates(1e4)
+    assert np.all(np.abs(pB / pA / (r["alpha_B"] / r["alpha_A"]) - 1) < 0.03)
