@@ -1,0 +1,280 @@
+"""Benchmark of the TRAPHIC transport sweep (transport + chemistry) on GB300.
+
+One step = one RT step of the whole hot path (rotations, re-binning, emission, the hop loop with
+virtual particles, chemistry, photon budget) over the workload.  Default workload: the 64^3
+HII region (1e5 K blackbody in 8 grey bins + the recombination bin, 32 cones, T evolving,
+FP32 transport / FP64 chemistry), started from a seeded mid-expansion state.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-sweeps/s (transport+chemistry)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n-side", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1311_0182_gb300 import workloads as W
+    return W.cfg2(n_side=args.n_side, transport_fp32=1 if args.precision == "fp32" else 0)
+
+
+def workload_config(args, wl):
+    p = wl["params"]
+    return {"workload": f"hii_region_{args.n_side}^3_bb1e5K_8bins_32cones_Tevolving",
+            "particles": int(wl["box_off"][-1]), "n_ngb": p["n_ngb"], "cones": p["n_tc"],
+            "freq_bins": p["n_freq_src"] + 1, "dt_myr": p["dt"] / 3.15576e13,
+            "start": "seeded mid-expansion HII region (front at 0.8 R_S)",
+            "transport": args.precision, "chemistry": "fp64",
+            "l2": "inputs larger than L2 (slot arrays > 1 GB)"}
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self):
+        self.rows, self.proc = [], None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def stop(self, dev=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for r in self.rows if r and r[0] == str(dev)]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_ours(args):
+    import torch
+    from paper_1311_0182_gb300 import rt
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    wl = workload(args)
+    n = int(wl["box_off"][-1])
+    stream = torch.cuda.Stream()
+    ctx = rt.Context(wl, stream=stream)
+    x0 = np.ascontiguousarray(wl["x_HI"])
+    T0 = np.ascontiguousarray(wl["T"])
+    with torch.cuda.stream(stream):
+        ctx.load_workload(wl)
+        ctx.build_neighbours()
+        step = 0
+        for _ in range(args.warmup):
+            ctx.step(step)
+            step += 1
+        ctx.profile(True)
+        stream.synchronize()
+        if dist:
+            tdist.barrier()
+        clk = Clocks()
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        launches0 = ctx.launches()
+        for _ in range(args.steps):
+            ctx.step(step)
+            step += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = ctx.launches() - launches0
+        kt = ctx.kernel_times()
+        ctx.profile(False)
+        clocks = clk.stop(local)
+        st = ctx.stats()
+        b = ctx.budget()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": "particle-sweeps/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 transport / f64 chemistry" if args.precision == "fp32" else "f64",
+           "data": "synthetic", "config": workload_config(args, wl), "gpu_launches": launches,
+           "clocks": clocks}
+    # roofline of the dominant kernel
+    out["roofline"] = roofline(ctx, kt)
+    out["stats_last_step"] = st
+    out["budget_closure"] = float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])
+    if not args.no_e2e:
+        out["e2e"] = e2e(args, ctx, wl, stream, step, x0, T0)
+    ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if dist:
+        tdist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def roofline(ctx, kt):
+    peak, kind = peaks()
+    if not kt:
+        return None
+    name = max(kt, key=lambda k: kt[k]["ms"])
+    k = kt[name]
+    ms = k["ms"] / max(k["launches"], 1)
+    B = k["bytes"] / max(k["launches"], 1)
+    ach = B / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": kind, "traffic": None,
+            "algorithmic_bytes_per_launch": B, "ms_per_launch": ms, "launches": k["launches"],
+            "share_of_step": None, "all_kernels": kt}
+
+
+def e2e(args, ctx, wl, stream, step, x0, T0):
+    """Same metric through the C ABI with host buffers: per step the state arrays go host ->
+    device, the step runs, and the state and photon budget come back."""
+    import torch
+    n = ctx.n
+    hx = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    hT = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    hx[:] = x0
+    hT[:] = T0
+    steps = max(2, args.steps)
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.set_state(x_HI=hx, T=hT)
+            ctx.step(step)
+            step += 1
+            ctx.get_state_into(x_HI=hx, T=hT)
+            ctx.budget()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": "particle-sweeps/s", "h2d_bytes_per_step": 16 * n,
+            "d2h_bytes_per_step": 16 * n + 32 * ctx.nb, "steps": steps}
+
+
+def cpu_baseline(args, budget_s=20.0):
+    """The oracle as it stands on the host cores (1 thread) on a bounded sample: whole steps
+    of the same workload at a reduced particle count, scaled per particle-sweep."""
+    import oracle
+    from paper_1311_0182_gb300 import workloads as W
+    n_side = 16
+    wl = W.cfg2(n_side=n_side)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 3 and time.perf_counter() - t0 < budget_s:
+        s.step(steps)
+        steps += 1
+    dt = time.perf_counter() - t0
+    n = n_side ** 3
+    return {"value": n * steps / dt, "unit": "particle-sweeps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} whole steps of the same HII-region workload at {n_side}^3 particles "
+                      f"(32 cones, 9 bins, same start recipe), {dt:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    wl_args = argparse.Namespace(**vars(args))
+    from paper_1311_0182_gb300 import workloads as W
+    n_side = 16
+    wl = W.cfg2(n_side=n_side)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    step = 0
+    for _ in range(args.warmup):
+        s.step(step)
+        step += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(step)
+        step += 1
+    dt = time.perf_counter() - t0
+    n = n_side ** 3
+    v = n * args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-sweeps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl_args, W.cfg2(n_side=args.n_side)),
+            "cpu_baseline": {"value": v, "unit": "particle-sweeps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step a whole RT step of the workload at {n_side}^3"},
+            "e2e": {"value": v, "unit": "particle-sweeps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * traphic_rt.h -- C ABI of the GB300 (sm_103a) TRAPHIC transport sweep with transport of
+ * ionizing recombination radiation.
+ *
+ * The method is the one of Raicevic, Pawlik, Schaye & Rahmati, "The effect of recombination
+ * radiation on the temperature and ionization state of partially ionized gas": photon
+ * packets are traced on SPH particles through transmission cones, merged per reception cone
+ * (Sec. 2.1), recombination photons are emitted into the reception cones (Sec. 2.2), and a
+ * chemistry step updates each particle's neutral fraction and temperature (Sec. 2.1).
+ *
+ * Conventions
+ *  - Units are cgs.  Particles are grouped in independent boxes (a CSR over particles);
+ *    positions are per box in [0, L_b).  Positions are quantised to 2^20 cells per box side,
+ *    so neighbour lists and cone decisions are exact integer/IEEE decisions.
+ *  - `where` says whether a pointer argument is host (RT_HOST) or device (RT_DEVICE) memory.
+ *    Host buffers are copied synchronously on `stream`; device buffers must stay valid until
+ *    the call's work on `stream` has completed.  The library never keeps a caller pointer.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
+ *    queued on it asynchronously unless noted.  A context is not thread-safe.
+ *  - The library owns every internal buffer: rt_create allocates them on the current device
+ *    and rt_destroy frees them.
+ *  - Every entry point returns an rt_status; nothing is thrown across the ABI.  After a
+ *    non-OK status rt_last_error() holds a one-line description.  Device-side limits (hop
+ *    cap, packet capacity, deposit range) set a sticky error word that rt_step/rt_transport
+ *    read when they finish; kernels never trap.
+ *  - The library needs a GPU of compute capability 10.3 (sm_103a).
+ */
+#ifndef TRAPHIC_RT_H
+#define TRAPHIC_RT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_ctx rt_ctx;
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID = 1,   /* bad argument or configuration */
+    RT_ERR_OOM = 2,       /* device allocation failed */
+    RT_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    RT_ERR_HOP_LIMIT = 4, /* hop loop reached hop_cap; unfinished free packets counted escaped */
+    RT_ERR_KNN = 5,       /* a box holds fewer than n_ngb + 1 particles */
+    RT_ERR_CAPACITY = 6,  /* more free packets (sources + virtual particles) in a hop than free_cap */
+    RT_ERR_STATE = 7,     /* call out of order, e.g. rt_transport before rt_build_neighbours */
+    RT_ERR_RANGE = 8      /* a virtual-particle deposit overflowed its fixed-point accumulator */
+} rt_status;
+
+/* Treatment of recombination radiation (Sec. 2.1, last paragraphs; Sec. 2.2) */
+typedef enum {
+    RT_REC_TRANSPORT = 0,  /* case A rates; ground-level recombinations emitted and transported */
+    RT_REC_OTS_CASE_B = 1, /* on-the-spot: case B rates, nothing emitted */
+    RT_REC_CASE_A = 2      /* case A rates, nothing emitted */
+} rt_rec_mode;
+
+enum { RT_COOL_REC = 1, RT_COOL_CEX = 2, RT_COOL_CION = 4, RT_COOL_FF = 8 };
+enum { RT_HOST = 0, RT_DEVICE = 1 };
+
+typedef struct {
+    int n_ngb;            /* SPH neighbours per particle, 1..32 */
+    int n_ec;             /* emission cones per source (8 or 32) */
+    int n_tc;             /* transmission cones: cone solid angle 4 pi / n_tc, n_tc >= 2 */
+    int n_rc;             /* reception cones per particle (8 or 32) */
+    int n_freq_src;       /* source frequency bins (>= 0); one recombination bin is added */
+    double dt;            /* RT step, s */
+    double dt_em;         /* source emission step, s (dt / dt_em rounded = emissions per step) */
+    int rec_mode;         /* rt_rec_mode */
+    int evolve_T;         /* 0: temperature held fixed */
+    int transport_fp32;   /* 1: packets in FP32 (per-box normalised); 0: all FP64 */
+    unsigned long long seed;
+    int hop_cap;          /* maximum hops per RT step */
+    int sub_cap;          /* maximum chemistry subcycles per step (subcycle floor dt/sub_cap) */
+    int cool_flags;       /* RT_COOL_* */
+    double T_floor;       /* K */
+    double eps_rr_fixed;  /* excess energy of recombination photons, erg; < 0: kT of emitter */
+    double sigma_rec;     /* grey cross-section of the recombination bin, cm^2 */
+    long long free_cap;   /* capacity of free packets per hop (0: library default) */
+} rt_config;
+
+/* rt_create -- validate cfg, allocate every device buffer for n_boxes boxes whose particle
+   ranges are box_off[0..n_boxes] (host, box_off[0] = 0) with side lengths box_L (host, cm),
+   and n_src sources.  Sizes only: particle and source data come with rt_set_particles and
+   rt_set_sources.  On success *out owns the allocations.  Errors: RT_ERR_INVALID,
+   RT_ERR_OOM, RT_ERR_CUDA (*out is NULL). */
+rt_status rt_create(const rt_config *cfg, int n_boxes, const long long *box_off,
+                    const double *box_L, int n_src, rt_ctx **out);
+
+/* rt_destroy -- free every allocation of ctx (NULL is allowed). */
+rt_status rt_destroy(rt_ctx *ctx);
+
+/* rt_set_particles -- copy the particle arrays (each [n], n = box_off[n_boxes]) into the
+   context: positions (cm, per box in [0, L_b)), hydrogen number density n_H (cm^-3),
+   hydrogen atoms per particle N_H, neutral fraction x_HI and temperature T (K).  Resets the
+   packets held by the particles, the recombination photons pending and the neighbour lists
+   (call rt_build_neighbours again).  Errors: RT_ERR_INVALID, RT_ERR_CUDA. */
+rt_status rt_set_particles(rt_ctx *ctx, const double *x, const double *y, const double *z,
+                           const double *n_H, const double *N_H, const double *x_HI,
+                           const double *T, int where, void *stream);
+
+/* rt_set_sources -- copy the sources: box index (int [n_src]), position ([n_src] each, cm),
+   photon rates ndot ([n_src * n_freq_src], row per source, s^-1), and per source frequency
+   bin the grey cross-section sigma (cm^2) and excess energy eps (erg) ([n_freq_src]) (Sec.
+   2.1: each packet carries one bin; the bin's spectrum is a grey cross-section). */
+rt_status rt_set_sources(rt_ctx *ctx, const int *box, const double *x, const double *y,
+                         const double *z, const double *ndot, const double *sigma,
+                         const double *eps, int where, void *stream);
+
+/* rt_build_neighbours -- exact n_ngb nearest neighbours of every particle and source within
+   its box, ordered by (squared quantised distance, index); smoothing length h = distance of
+   the n_ngb-th; and the receiver-sorted reverse lists (Sec. 2.1: packets search the
+   neighbours within the smoothing volume of the particle they are attached to).  Static
+   density fields: call once after rt_set_particles.  Errors: RT_ERR_KNN, RT_ERR_CUDA. */
+rt_status rt_build_neighbours(rt_ctx *ctx, void *stream);
+
+/* rt_assign_cones -- the rotations of step `step` (reception cones of every particle, once
+   per step; emission cones of every source, once per emission; Sec. 2.1) and, for the
+   packets currently held, the transmission-cone membership of every neighbour (cone of solid
+   angle 4 pi / n_tc about the packet direction, Sec. 2.1).  Read with rt_get_rotations and
+   rt_get_cone_masks. */
+rt_status rt_assign_cones(rt_ctx *ctx, long long step, void *stream);
+
+/* rt_merge -- start of an RT step: reset every packet clock to the step start and re-sort
+   the packets held by each particle into its current reception cones, merging packets that
+   share a cone and frequency (sums of photons, momentum N*d, N*clock and N*eps; Sec. 2.1,
+   Fig. 1a,b).  Uses the rotations of the last rt_assign_cones. */
+rt_status rt_merge(rt_ctx *ctx, void *stream);
+
+/* rt_emit -- emission at the start of step `step` (Sec. 2.1, Sec. 2.2, Fig. 1c,d): the
+   recombination photons of the last chemistry step go N_rec/n_rc into each reception cone of
+   the recombination bin along its rotated axis, merged with the packets there; the sources
+   emit dt/dt_em times n_ec packets per frequency bin along their rotated emission axes.
+   Also restarts the absorption counters and freezes n_HI for the transport. */
+rt_status rt_emit(rt_ctx *ctx, long long step, void *stream);
+
+/* rt_transport -- the hop loop of step `step` (Sec. 2.1): each packet whose clock is below
+   dt is split equally among the neighbours in its transmission cone (or handed to a virtual
+   particle when the cone is empty), attenuated by exp(-sigma n_HI l) photon-conservingly,
+   deposited, and merged per reception cone at the receiver, until no packet can move.
+   Synchronises `stream` once per hop to test for completion.  Errors: RT_ERR_HOP_LIMIT,
+   RT_ERR_CAPACITY, RT_ERR_RANGE, RT_ERR_CUDA. */
+rt_status rt_transport(rt_ctx *ctx, long long step, void *stream);
+
+/* rt_chemistry -- per particle: photoionisation and photoheating rates from the step's
+   absorptions, subcycled update of x_HI and T, and the ground-level recombination photons to
+   emit next step (Sec. 2.1, Sec. 2.2). */
+rt_status rt_chemistry(rt_ctx *ctx, void *stream);
+
+/* rt_step -- one RT step: rt_assign_cones, rt_merge, rt_emit, rt_transport, rt_chemistry and
+   the photon budget.  Returns the first non-OK status. */
+rt_status rt_step(rt_ctx *ctx, long long step, void *stream);
+
+/* rt_get_state / rt_set_state -- x_HI, T, pending recombination photons N_rec and their
+   excess energy eps_rec ([n] each; NULL skips a field). */
+rt_status rt_get_state(rt_ctx *ctx, double *x_HI, double *T, double *N_rec, double *eps_rec,
+                       int where, void *stream);
+rt_status rt_set_state(rt_ctx *ctx, const double *x_HI, const double *T, const double *N_rec,
+                       const double *eps_rec, int where, void *stream);
+
+/* rt_get_budget -- per box, cumulative photons emitted, absorbed, escaped and currently in
+   flight ([n_boxes * 4], host).  Synchronises `stream`.  Photon conservation (Abstract,
+   Sec. 2.1): emitted = absorbed + escaped + in flight. */
+rt_status rt_get_budget(rt_ctx *ctx, double *out, void *stream);
+
+/* --- inspection hooks (parity tests) ---------------------------------------------------- */
+/* neighbour lists [n * n_ngb] (global indices), h^2 in quantised units [n]; the same for the
+   sources ([n_src * n_ngb], [n_src]); NULL skips */
+rt_status rt_get_neighbours(rt_ctx *ctx, int *nbr, long long *h2, int *src_nbr,
+                            long long *src_h2, int where, void *stream);
+/* quantised positions [n * 3] */
+rt_status rt_get_quantised(rt_ctx *ctx, long long *q, int where, void *stream);
+/* rotation matrices (row-major): reception [n * 9], emission [n_src * K * 9], K = dt/dt_em */
+rt_status rt_get_rotations(rt_ctx *ctx, double *R, double *Rs, int where, void *stream);
+/* transmission masks of the held packets [n * S], S = n_rc * (n_freq_src + 1): bit k set
+   when neighbour k lies in the cone of slot s; 0 for slots with no packet able to move */
+rt_status rt_get_cone_masks(rt_ctx *ctx, unsigned *mask, int where, void *stream);
+/* held packets: 6 fields [6 * n * S] (N, Mx, My, Mz, C = N*clock, E = N*eps), physical units */
+rt_status rt_get_slots(rt_ctx *ctx, double *f, int where, void *stream);
+rt_status rt_set_slots(rt_ctx *ctx, const double *f, int where, void *stream);
+/* absorptions of the current step: photons [n * nf], energy [n * nf] (erg), photons passing
+   each particle [n * nf] (the intensity diagnostic of Sec. 3); nf = n_freq_src + 1 */
+rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass, int where,
+                          void *stream);
+/* statistics of the last rt_transport/rt_chemistry: hops, virtual particles, escaped virtual
+   particles, chemistry subcycles, subcycle-floor hits, peak free packets in a hop, peak
+   active slots in a hop, gas-to-gas contributions summed [8] (host) */
+rt_status rt_get_stats(rt_ctx *ctx, long long *out);
+/* the isotropic cone direction set with n directions (8 or 32), [n * 3] host */
+rt_status rt_axis_set(int n, double *out);
+
+/* rt_set_profiling -- on != 0: record a pair of CUDA events on the launching stream around
+   every kernel launch and sum their durations per kernel; 0: stop.  Both reset the sums.
+   Synchronises the device.  The launch counter runs always. */
+rt_status rt_set_profiling(rt_ctx *ctx, int on);
+
+/* rt_get_profile -- total kernel launches since rt_create, and per kernel (at most
+   max_kernels entries, host arrays, NULL skips): its name (static string), launches, summed
+   device time in ms (while profiling) and algorithmic bytes (reserved, 0).  Synchronises the
+   device. */
+rt_status rt_get_profile(rt_ctx *ctx, long long *launches_total, int max_kernels,
+                         const char **names, long long *launches, double *ms, double *bytes);
+
+const char *rt_last_error(const rt_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,786 @@
+// rt_api.cu -- the C ABI declared in include/traphic_rt.h: context life cycle, uploads, the
+// step sequence, and inspection hooks.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "rt_internal.cuh"
+
+rt_status rt_fail(rt_ctx *c, rt_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+rt_status rt_cuda_check(rt_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return RT_OK;
+    return rt_fail(c, RT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Isotropic cone direction sets (reading of Sec. 2.1): 8 = cube diagonals; 32 = the 12
+// icosahedron vertices followed by the 20 dodecahedron vertices.
+void rt_host_axis_set(int n, double *out) {
+    if (n == 8) {
+        double r = 1.0 / sqrt(3.0);
+        for (int b = 0; b < 8; ++b) {
+            out[3 * b + 0] = (b & 4) ? -r : r;
+            out[3 * b + 1] = (b & 2) ? -r : r;
+            out[3 * b + 2] = (b & 1) ? -r : r;
+        }
+        return;
+    }
+    double phi = (1.0 + sqrt(5.0)) / 2.0;
+    double a = 1.0 / sqrt(1.0 + phi * phi);
+    double pa = phi * a;
+    double r = 1.0 / sqrt(3.0);
+    double ir = (1.0 / phi) * r, pr = phi * r;
+    int v = 0;
+    // (0, +-1, +-phi) and its cyclic permutations, normalised
+    for (int g = 0; g < 3; ++g)
+        for (int s1 = 0; s1 < 2; ++s1)
+            for (int s2 = 0; s2 < 2; ++s2) {
+                double A = s1 ? -a : a, B = s2 ? -pa : pa;
+                double e[3] = {0.0, 0.0, 0.0};
+                if (g == 0) { e[1] = A; e[2] = B; }
+                else if (g == 1) { e[0] = A; e[1] = B; }
+                else { e[0] = B; e[2] = A; }
+                out[3 * v] = e[0]; out[3 * v + 1] = e[1]; out[3 * v + 2] = e[2];
+                ++v;
+            }
+    for (int b = 0; b < 8; ++b) {
+        out[3 * v + 0] = (b & 4) ? -r : r;
+        out[3 * v + 1] = (b & 2) ? -r : r;
+        out[3 * v + 2] = (b & 1) ? -r : r;
+        ++v;
+    }
+    // (0, +-1/phi, +-phi) and its cyclic permutations, normalised by 1/sqrt(3)
+    for (int g = 0; g < 3; ++g)
+        for (int s1 = 0; s1 < 2; ++s1)
+            for (int s2 = 0; s2 < 2; ++s2) {
+                double A = s1 ? -ir : ir, B = s2 ? -pr : pr;
+                double e[3] = {0.0, 0.0, 0.0};
+                if (g == 0) { e[1] = A; e[2] = B; }
+                else if (g == 1) { e[0] = A; e[1] = B; }
+                else { e[0] = B; e[2] = A; }
+                out[3 * v] = e[0]; out[3 * v + 1] = e[1]; out[3 * v + 2] = e[2];
+                ++v;
+            }
+}
+
+static cudaEvent_t ev_take(rt_ctx *c) {
+    if (c->ev_next == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_next++];
+}
+
+void kt_begin(rt_ctx *c, int id, cudaStream_t st) {
+    if (!c->prof) return;
+    cudaEvent_t e0 = ev_take(c), e1 = ev_take(c);
+    cudaEventRecord(e0, st);
+    c->ev_pending.push_back({id, {e0, e1}});
+}
+
+void kt_end(rt_ctx *c, int id, cudaStream_t st, int nlaunch) {
+    c->launches += nlaunch;
+    c->kstat[id].launches += nlaunch;
+    if (!c->prof) return;
+    cudaEventRecord(c->ev_pending.back().second.second, st);
+}
+
+void kt_resolve(rt_ctx *c) {
+    for (auto &p : c->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
+            c->kstat[p.first].ms += ms;
+    }
+    c->ev_pending.clear();
+    c->ev_next = 0;
+}
+
+static const char *KT_NAMES[KT_N] = {
+    "rotate", "rebin", "emit_rec", "emit_src", "phase_a_send", "free_a_send", "scan",
+    "expand_requests", "free_c_stage", "virtual_particles", "seg_fill", "seg_sort",
+    "phase_b_merge", "hop_counts", "hop_lens", "drop_free", "chemistry", "budget", "knn_build"};
+
+extern "C" rt_status rt_set_profiling(rt_ctx *c, int on) {
+    if (!c) return RT_ERR_INVALID;
+    cudaDeviceSynchronize();
+    kt_resolve(c);
+    c->prof = on ? 1 : 0;
+    for (int k = 0; k < KT_N; ++k) c->kstat[k] = KStat();
+    return RT_OK;
+}
+
+extern "C" rt_status rt_get_profile(rt_ctx *c, long long *launches_total, int max_kernels,
+                                    const char **names, long long *launches, double *ms,
+                                    double *bytes) {
+    if (!c) return RT_ERR_INVALID;
+    cudaDeviceSynchronize();
+    kt_resolve(c);
+    if (launches_total) *launches_total = c->launches;
+    for (int k = 0; k < KT_N && k < max_kernels; ++k) {
+        if (names) names[k] = KT_NAMES[k];
+        if (launches) launches[k] = c->kstat[k].launches;
+        if (ms) ms[k] = c->kstat[k].ms;
+        if (bytes) bytes[k] = c->kstat[k].bytes;
+    }
+    return RT_OK;
+}
+
+static void *dalloc(rt_ctx *c, size_t bytes, bool *ok) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        *ok = false;
+        return nullptr;
+    }
+    cudaMemset(p, 0, bytes);
+    c->allocs.push_back(p);
+    return p;
+}
+
+void rt_launch_quantise(rt_ctx *c, const double *x, const double *y, const double *z,
+                        cudaStream_t st);
+void rt_launch_quantise_src(rt_ctx *c, const double *x, const double *y, const double *z,
+                            cudaStream_t st);
+
+extern "C" rt_status rt_axis_set(int n, double *out) {
+    if (!out || (n != 8 && n != 32)) return RT_ERR_INVALID;
+    rt_host_axis_set(n, out);
+    return RT_OK;
+}
+
+extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long long *box_off,
+                               const double *box_L, int n_src, rt_ctx **out) {
+    if (!out) return RT_ERR_INVALID;
+    *out = nullptr;
+    if (!cfg || n_boxes < 1 || !box_off || !box_L || n_src < 0) return RT_ERR_INVALID;
+    if (cfg->n_ngb < 1 || cfg->n_ngb > RT_MAXK || cfg->n_tc < 2 || cfg->n_freq_src < 0 ||
+        (cfg->n_rc != 8 && cfg->n_rc != 32) || (cfg->n_ec != 8 && cfg->n_ec != 32) ||
+        !(cfg->dt > 0.0) || !(cfg->dt_em > 0.0) || cfg->hop_cap < 1 || cfg->sub_cap < 1 ||
+        cfg->rec_mode < 0 || cfg->rec_mode > 2)
+        return RT_ERR_INVALID;
+    if (box_off[0] != 0) return RT_ERR_INVALID;
+    for (int b = 0; b < n_boxes; ++b) {
+        if (box_off[b + 1] < box_off[b] + cfg->n_ngb + 1) return RT_ERR_KNN;
+        if (!(box_L[b] > 0.0)) return RT_ERR_INVALID;
+    }
+    long long n = box_off[n_boxes];
+    if (n >= (1ll << 27) || n * cfg->n_ngb >= (1ll << 31)) return RT_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RT_ERR_CUDA;
+
+    rt_ctx *c = new rt_ctx();
+    c->cfg = *cfg;
+    rt_ctx *x = c;
+    DevPtrs &P = c->d;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.nb = n_boxes;
+    P.ns = n_src;
+    P.nfs = cfg->n_freq_src;
+    P.nf = cfg->n_freq_src + 1;
+    P.nrc = cfg->n_rc;
+    P.nec = cfg->n_ec;
+    P.ntc = cfg->n_tc;
+    P.kn = cfg->n_ngb;
+    P.S = P.nf * P.nrc;
+    long long K = llround(cfg->dt / cfg->dt_em);
+    P.K = K < 1 ? 1 : (int)K;
+    P.fp32 = cfg->transport_fp32 ? 1 : 0;
+    P.dt = cfg->dt;
+    P.dt_em = cfg->dt_em;
+    P.sigma_rec = cfg->sigma_rec;
+    P.T_floor = cfg->T_floor;
+    P.eps_rr_fixed = cfg->eps_rr_fixed;
+    P.rec_mode = cfg->rec_mode;
+    P.evolve_T = cfg->evolve_T;
+    P.sub_cap = cfg->sub_cap;
+    P.cool_flags = cfg->cool_flags;
+    P.seed = cfg->seed;
+    long long np_src = (long long)n_src * P.K * P.nfs * P.nec;
+    long long fc = cfg->free_cap > 0 ? cfg->free_cap : std::max<long long>(65536, n * P.nrc / 2);
+    fc = std::max(fc, np_src);
+    P.F_cap = fc;
+    long long mem_per = std::max<long long>(4, 2 * ((P.kn + P.ntc - 1) / P.ntc) + 2);
+    P.ST_cap = std::max<long long>(fc * mem_per, np_src * P.kn);
+    if (P.F_cap >= (1ll << 30) || P.ST_cap >= (1ll << 31)) {
+        delete c;
+        return RT_ERR_INVALID;
+    }
+    c->box_off_h.assign(box_off, box_off + n_boxes + 1);
+    c->box_L_h.assign(box_L, box_L + n_boxes);
+    rt_host_axis_set(P.nrc, P.axes_rc);
+    rt_host_axis_set(P.nec, P.axes_ec);
+    for (int k = 0; k < 3 * P.nrc; ++k) P.axes_rcf[k] = (float)P.axes_rc[k];
+
+    bool ok = true;
+    size_t R = P.fp32 ? 4 : 8;
+    long long nkey = n * P.nf, nslot = n * P.S;
+    // per-box grids
+    std::vector<int> G(n_boxes), cs(n_boxes);
+    std::vector<long long> coff(n_boxes);
+    long long ncell = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        long long nb = box_off[b + 1] - box_off[b];
+        int g = (int)cbrt((double)nb / 6.0);
+        g = std::max(1, std::min(g, 512));
+        G[b] = g;
+        cs[b] = (int)((RT_Q + g - 1) / g);
+        coff[b] = ncell;
+        ncell += (long long)g * g * g;
+    }
+    P.grid.ncells = ncell;
+    c->gridG_h = G;
+#define A(ptr, T, cnt) ptr = (T *)dalloc(c, sizeof(T) * (size_t)(cnt), &ok)
+    A(P.box_off, long long, n_boxes + 1);
+    A(P.box_L, double, n_boxes);
+    A(P.box_u, double, n_boxes);
+    A(P.norm, double, n_boxes);
+    A(P.ref, double, n_boxes);
+    A(P.esc_fx, unsigned long long, n_boxes);
+    A(P.tally, double, 4 * n_boxes);
+    A(x->src_emit, double, n_boxes);
+    A(P.pbox, int, n);
+    A(P.qx, int, n); A(P.qy, int, n); A(P.qz, int, n);
+    A(P.nH, double, n); A(P.NH, double, n); A(P.xHI, double, n); A(P.T, double, n);
+    A(P.Nrec, double, n); A(P.epsrec, double, n); A(P.nHI, double, n); A(P.phot, double, n);
+    P.nHIr = dalloc(c, R * n, &ok);
+    P.Vr = dalloc(c, R * n, &ok);
+    P.dep_s = dalloc(c, R * n, &ok);
+    P.depE_s = dalloc(c, R * n, &ok);
+    A(P.sbox, int, n_src + 1);
+    A(P.sqx, int, n_src + 1); A(P.sqy, int, n_src + 1); A(P.sqz, int, n_src + 1);
+    A(P.ndot, double, (long long)n_src * P.nfs + 1);
+    A(P.sigma, double, P.nf);
+    A(P.eps, double, P.nf);
+    A(P.nbr, int, n * P.kn);
+    A(P.snbr, int, (long long)(n_src + 1) * P.kn);
+    A(P.h2, long long, n);
+    A(P.sh2, long long, n_src + 1);
+    A(P.fdx, float, n * P.kn); A(P.fdy, float, n * P.kn); A(P.fdz, float, n * P.kn);
+    A(P.rev_off, int, n + 1);
+    A(P.rev_ent, unsigned, n * P.kn);
+    A(P.rdx, float, n * P.kn); A(P.rdy, float, n * P.kn); A(P.rdz, float, n * P.kn);
+    A(P.grid.G, int, n_boxes);
+    A(P.grid.cs, int, n_boxes);
+    A(P.grid.coff, long long, n_boxes);
+    A(P.grid.start, int, ncell + 1);
+    A(P.grid.items, int4, n);
+    A(P.R, double, 9 * n);
+    A(P.Rf, float, 9 * n);
+    A(P.Rs, double, 9 * ((long long)n_src * P.K + 1));
+    for (int b = 0; b < 2; ++b) {
+        for (int f = 0; f < 6; ++f) P.sl[b][f] = dalloc(c, R * nslot, &ok);
+        A(P.occ[b], unsigned, nkey);
+        A(P.act[b], unsigned, nkey);
+    }
+    for (int f = 0; f < 6; ++f) P.rec[f] = dalloc(c, R * nslot, &ok);
+    A(P.bm, unsigned, n * P.kn * P.nf);
+    A(P.emp, unsigned, nkey);
+    A(P.touched, int, nkey);
+    A(P.reqcnt, int, n + fc);
+    A(P.reqoff, int, n + fc);
+    A(P.req, unsigned long long, fc);
+    for (int b = 0; b < 2; ++b) {
+        FreeBuf &F = P.fr[b];
+        A(F.box, int, fc); A(F.qx, int, fc); A(F.qy, int, fc); A(F.qz, int, fc);
+        A(F.nu, int, fc);
+        A(F.nbr, int, fc * P.kn);
+        A(F.h2, long long, fc);
+        A(F.fid, unsigned long long, fc);
+        F.N = dalloc(c, R * fc, &ok); F.dx = dalloc(c, R * fc, &ok);
+        F.dy = dalloc(c, R * fc, &ok); F.dz = dalloc(c, R * fc, &ok);
+        F.clock = dalloc(c, R * fc, &ok); F.eps = dalloc(c, R * fc, &ok);
+    }
+    A(P.st_key, int, P.ST_cap);
+    A(P.st_bin, int, P.ST_cap);
+    for (int f = 0; f < 9; ++f) P.st_v[f] = dalloc(c, R * P.ST_cap, &ok);
+    long long segn = std::max<long long>(nkey, ncell) + 1;
+    A(P.seg_cnt, int, segn);
+    A(P.seg_off, int, segn);
+    A(P.seg_fill, int, segn);
+    A(P.seg_idx, int, P.ST_cap);
+    A(P.abs, double, nkey); A(P.absE, double, nkey); A(P.pass, double, nkey);
+    A(P.fx_abs, unsigned long long, nkey);
+    A(P.fx_E, unsigned long long, nkey);
+    A(P.cnt, long long, CNT_N);
+    A(x->hop.lens, int, 8);
+    A(x->hop.fmask, unsigned, fc);
+    A(x->hop.stcnt, int, fc);
+    A(x->hop.stoff, int, fc);
+    A(x->hop.esc_r, unsigned long long, fc);
+    A(x->hop.vstat, unsigned char, fc);
+#undef A
+    // the scan scratch, sized for the largest scan (no allocation later)
+    long long maxscan = std::max(std::max(n + fc, segn), std::max(n * P.kn, ncell + 1));
+    c->scan_tmp_n = (maxscan + 1023) / 1024 + 1;
+    if (cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_n) != cudaSuccess) ok = false;
+    if (cudaMallocHost(&c->cnt_h, sizeof(long long) * CNT_N) != cudaSuccess) ok = false;
+    if (!ok) {
+        rt_destroy(c);
+        return RT_ERR_OOM;
+    }
+    std::vector<double> u(n_boxes);
+    for (int b = 0; b < n_boxes; ++b) u[b] = box_L[b] / (double)RT_Q;
+    cudaMemcpy(P.box_off, box_off, sizeof(long long) * (n_boxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(P.box_L, box_L, sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.box_u, u.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.grid.G, G.data(), sizeof(int) * n_boxes, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.grid.cs, cs.data(), sizeof(int) * n_boxes, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.grid.coff, coff.data(), sizeof(long long) * n_boxes, cudaMemcpyHostToDevice);
+    cudaMemset(P.touched, 0xff, sizeof(int) * nkey);
+    x->src_emit_h.assign(n_boxes, 0.0);
+    x->box_NH_h.assign(n_boxes, 0.0);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        rt_destroy(c);
+        return RT_ERR_CUDA;
+    }
+    *out = c;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_destroy(rt_ctx *c) {
+    if (!c) return RT_OK;
+    for (size_t k = 0; k < c->allocs.size(); ++k) cudaFree(c->allocs[k]);
+    if (c->scan_tmp) cudaFree(c->scan_tmp);
+    if (c->cnt_h) cudaFreeHost(c->cnt_h);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+    return RT_OK;
+}
+
+static rt_status copy_in(rt_ctx *c, void *dst, const void *src, size_t bytes, int where,
+                         cudaStream_t st) {
+    if (!src) return RT_OK;
+    cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, k, st);
+    if (e == cudaSuccess && where == RT_HOST) e = cudaStreamSynchronize(st);
+    return rt_cuda_check(c, e, "copy in");
+}
+
+static rt_status copy_out(rt_ctx *c, void *dst, const void *src, size_t bytes, int where,
+                          cudaStream_t st) {
+    if (!dst) return RT_OK;
+    cudaMemcpyKind k = where == RT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, k, st);
+    if (e == cudaSuccess && where == RT_HOST) e = cudaStreamSynchronize(st);
+    return rt_cuda_check(c, e, "copy out");
+}
+
+static void set_norms(rt_ctx *c) {
+    // slot unit per box: the box's source photons of one step (FP32 path), else 1 (FP64);
+    // fixed-point reference of the escaped tally: the same photon count
+    rt_ctx &x = *c;
+    int nb = c->d.nb;
+    std::vector<double> ref(nb), norm(nb);
+    for (int b = 0; b < nb; ++b) {
+        double r = x.src_emit_h[b];
+        if (!(r > 0.0)) r = 1e-3 * x.box_NH_h[b];
+        if (!(r > 0.0)) r = 1.0;
+        ref[b] = r;
+        norm[b] = c->d.fp32 ? r : 1.0;
+    }
+    cudaMemcpy(c->d.ref, ref.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d.norm, norm.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(x.src_emit, x.src_emit_h.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
+}
+
+extern "C" rt_status rt_set_particles(rt_ctx *c, const double *x, const double *y,
+                                      const double *z, const double *n_H, const double *N_H,
+                                      const double *x_HI, const double *T, int where,
+                                      void *stream) {
+    if (!c || !x || !y || !z || !n_H || !N_H || !x_HI || !T) return RT_ERR_INVALID;
+    if (where != RT_HOST && where != RT_DEVICE) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevPtrs &P = c->d;
+    size_t nb = sizeof(double) * (size_t)P.n;
+    double *tx = nullptr, *ty = nullptr, *tz = nullptr;
+    if (cudaMalloc(&tx, 3 * nb) != cudaSuccess) return rt_fail(c, RT_ERR_OOM, "position staging");
+    ty = tx + P.n;
+    tz = ty + P.n;
+    rt_status s = RT_OK;
+    if ((s = copy_in(c, tx, x, nb, where, st)) || (s = copy_in(c, ty, y, nb, where, st)) ||
+        (s = copy_in(c, tz, z, nb, where, st)) || (s = copy_in(c, P.nH, n_H, nb, where, st)) ||
+        (s = copy_in(c, P.NH, N_H, nb, where, st)) || (s = copy_in(c, P.xHI, x_HI, nb, where, st)) ||
+        (s = copy_in(c, P.T, T, nb, where, st))) {
+        cudaFree(tx);
+        return s;
+    }
+    rt_launch_quantise(c, tx, ty, tz, st);
+    cudaStreamSynchronize(st);
+    cudaFree(tx);
+    // per-box atom totals (fallback photon unit for boxes without sources)
+    std::vector<double> NHh(P.n);
+    cudaMemcpy(NHh.data(), P.NH, nb, cudaMemcpyDeviceToHost);
+    rt_ctx &xe = *c;
+    for (int b = 0; b < P.nb; ++b) {
+        double t = 0.0;
+        for (long long i = c->box_off_h[b]; i < c->box_off_h[b + 1]; ++i) t += NHh[i];
+        xe.box_NH_h[b] = t;
+    }
+    for (int b = 0; b < 2; ++b) {
+        cudaMemsetAsync(P.occ[b], 0, sizeof(unsigned) * P.n * P.nf, st);
+        cudaMemsetAsync(P.act[b], 0, sizeof(unsigned) * P.n * P.nf, st);
+    }
+    cudaMemsetAsync(P.Nrec, 0, nb, st);
+    cudaMemsetAsync(P.epsrec, 0, nb, st);
+    cudaMemsetAsync(P.tally, 0, sizeof(double) * 4 * P.nb, st);
+    cudaMemsetAsync(P.esc_fx, 0, sizeof(unsigned long long) * P.nb, st);
+    c->have_particles = true;
+    c->built = false;
+    set_norms(c);
+    return rt_cuda_check(c, cudaStreamSynchronize(st), "set particles");
+}
+
+extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, const double *y,
+                                    const double *z, const double *ndot, const double *sigma,
+                                    const double *eps, int where, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    if (where != RT_HOST && where != RT_DEVICE) return RT_ERR_INVALID;
+    DevPtrs &P = c->d;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P.nfs > 0 && (!sigma || !eps)) return RT_ERR_INVALID;
+    if (P.ns > 0 && (!box || !x || !y || !z || (P.nfs > 0 && !ndot))) return RT_ERR_INVALID;
+    size_t sb = sizeof(double) * (size_t)P.ns;
+    std::vector<int> boxh(P.ns);
+    std::vector<double> ndh((size_t)P.ns * P.nfs);
+    rt_status s;
+    if (P.ns > 0) {
+        if (where == RT_HOST) {
+            memcpy(boxh.data(), box, sizeof(int) * P.ns);
+            if (P.nfs) memcpy(ndh.data(), ndot, sizeof(double) * P.ns * P.nfs);
+        } else {
+            cudaMemcpy(boxh.data(), box, sizeof(int) * P.ns, cudaMemcpyDeviceToHost);
+            if (P.nfs) cudaMemcpy(ndh.data(), ndot, sizeof(double) * P.ns * P.nfs, cudaMemcpyDeviceToHost);
+        }
+        for (int j = 0; j < P.ns; ++j)
+            if (boxh[j] < 0 || boxh[j] >= P.nb) return rt_fail(c, RT_ERR_INVALID, "source box index");
+        double *t = nullptr;
+        if (cudaMalloc(&t, 3 * sb) != cudaSuccess) return rt_fail(c, RT_ERR_OOM, "source staging");
+        cudaMemcpy(P.sbox, boxh.data(), sizeof(int) * P.ns, cudaMemcpyHostToDevice);
+        if ((s = copy_in(c, t, x, sb, where, st)) || (s = copy_in(c, t + P.ns, y, sb, where, st)) ||
+            (s = copy_in(c, t + 2 * P.ns, z, sb, where, st))) {
+            cudaFree(t);
+            return s;
+        }
+        rt_launch_quantise_src(c, t, t + P.ns, t + 2 * P.ns, st);
+        cudaStreamSynchronize(st);
+        cudaFree(t);
+        if (P.nfs) cudaMemcpy(P.ndot, ndh.data(), sizeof(double) * P.ns * P.nfs, cudaMemcpyHostToDevice);
+    }
+    std::vector<double> sg(P.nf), ep(P.nf);
+    if (P.nfs > 0) {
+        if (where == RT_HOST) {
+            memcpy(sg.data(), sigma, sizeof(double) * P.nfs);
+            memcpy(ep.data(), eps, sizeof(double) * P.nfs);
+        } else {
+            cudaMemcpy(sg.data(), sigma, sizeof(double) * P.nfs, cudaMemcpyDeviceToHost);
+            cudaMemcpy(ep.data(), eps, sizeof(double) * P.nfs, cudaMemcpyDeviceToHost);
+        }
+    }
+    sg[P.nfs] = c->cfg.sigma_rec;
+    ep[P.nfs] = 0.0;
+    cudaMemcpy(P.sigma, sg.data(), sizeof(double) * P.nf, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.eps, ep.data(), sizeof(double) * P.nf, cudaMemcpyHostToDevice);
+    // source photons of one step per box, summed packet by packet as they are emitted
+    rt_ctx &xe = *c;
+    std::fill(xe.src_emit_h.begin(), xe.src_emit_h.end(), 0.0);
+    for (int j = 0; j < P.ns; ++j)
+        for (int k = 0; k < P.K; ++k)
+            for (int nu = 0; nu < P.nfs; ++nu) {
+                double Np = ndh[(size_t)j * P.nfs + nu] * P.dt_em / (double)P.nec;
+                for (int e = 0; e < P.nec; ++e) xe.src_emit_h[boxh[j]] += Np;
+            }
+    c->have_sources = true;
+    c->built = false;
+    set_norms(c);
+    return rt_cuda_check(c, cudaStreamSynchronize(st), "set sources");
+}
+
+extern "C" rt_status rt_build_neighbours(rt_ctx *c, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    if (!c->have_particles || !c->have_sources)
+        return rt_fail(c, RT_ERR_STATE, "rt_set_particles and rt_set_sources come first");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(&c->d.cnt[CNT_ERR], 0, sizeof(long long), st);
+    rt_status s = rt_knn_build(c, st);
+    if (s) return s;
+    long long err = 0;
+    cudaMemcpyAsync(&err, &c->d.cnt[CNT_ERR], sizeof(long long), cudaMemcpyDeviceToHost, st);
+    s = rt_cuda_check(c, cudaStreamSynchronize(st), "neighbour build");
+    if (s) return s;
+    if (err & ERRB_KNN) return rt_fail(c, RT_ERR_KNN, "a box holds too few particles");
+    c->built = true;
+    return RT_OK;
+}
+
+static rt_status need_built(rt_ctx *c) {
+    if (!c) return RT_ERR_INVALID;
+    if (!c->built) return rt_fail(c, RT_ERR_STATE, "rt_build_neighbours has not run");
+    return RT_OK;
+}
+
+extern "C" rt_status rt_assign_cones(rt_ctx *c, long long step, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = rt_run_step_parts(c, 0, step, st))) return s;
+    return rt_run_step_parts(c, 3, step, st);
+}
+
+extern "C" rt_status rt_merge(rt_ctx *c, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    return rt_run_step_parts(c, 1, 0, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_emit(rt_ctx *c, long long step, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = rt_run_step_parts(c, 2, step, st))) return s;
+    return rt_budget_launch(c, 0, st);
+}
+
+extern "C" rt_status rt_transport(rt_ctx *c, long long step, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    return rt_run_step_parts(c, 4, step, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_chemistry(rt_ctx *c, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = rt_chem_launch(c, st))) return s;
+    if ((s = rt_budget_launch(c, 1, st))) return s;
+    cudaMemcpyAsync(c->cnt_h, c->d.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+    s = rt_cuda_check(c, cudaStreamSynchronize(st), "chemistry");
+    c->stats[3] = c->cnt_h[CNT_SUB];
+    c->stats[4] = c->cnt_h[CNT_FLOOR];
+    return s;
+}
+
+extern "C" rt_status rt_step(rt_ctx *c, long long step, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = rt_run_step_parts(c, 0, step, st))) return s;
+    if ((s = rt_run_step_parts(c, 1, step, st))) return s;
+    if ((s = rt_emit(c, step, stream))) return s;
+    rt_status ts = rt_run_step_parts(c, 4, step, st);
+    if (ts != RT_OK && ts != RT_ERR_HOP_LIMIT) return ts;
+    if ((s = rt_chemistry(c, stream))) return s;
+    return ts;
+}
+
+extern "C" rt_status rt_get_state(rt_ctx *c, double *x_HI, double *T, double *N_rec,
+                                  double *eps_rec, int where, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t b = sizeof(double) * (size_t)c->d.n;
+    rt_status s;
+    if ((s = copy_out(c, x_HI, c->d.xHI, b, where, st)) || (s = copy_out(c, T, c->d.T, b, where, st)) ||
+        (s = copy_out(c, N_rec, c->d.Nrec, b, where, st)) ||
+        (s = copy_out(c, eps_rec, c->d.epsrec, b, where, st)))
+        return s;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_set_state(rt_ctx *c, const double *x_HI, const double *T,
+                                  const double *N_rec, const double *eps_rec, int where,
+                                  void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t b = sizeof(double) * (size_t)c->d.n;
+    rt_status s;
+    if ((s = copy_in(c, c->d.xHI, x_HI, b, where, st)) || (s = copy_in(c, c->d.T, T, b, where, st)) ||
+        (s = copy_in(c, c->d.Nrec, N_rec, b, where, st)) ||
+        (s = copy_in(c, c->d.epsrec, eps_rec, b, where, st)))
+        return s;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_get_budget(rt_ctx *c, double *out, void *stream) {
+    if (!c || !out) return RT_ERR_INVALID;
+    return copy_out(c, out, c->d.tally, sizeof(double) * 4 * c->d.nb, RT_HOST, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_get_neighbours(rt_ctx *c, int *nbr, long long *h2, int *src_nbr,
+                                       long long *src_h2, int where, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevPtrs &P = c->d;
+    if ((s = copy_out(c, nbr, P.nbr, sizeof(int) * P.n * P.kn, where, st)) ||
+        (s = copy_out(c, h2, P.h2, sizeof(long long) * P.n, where, st)) ||
+        (s = copy_out(c, src_nbr, P.snbr, sizeof(int) * (size_t)P.ns * P.kn, where, st)) ||
+        (s = copy_out(c, src_h2, P.sh2, sizeof(long long) * P.ns, where, st)))
+        return s;
+    return RT_OK;
+}
+
+__global__ void k_get_q(DevPtrs P, long long *q) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    q[3 * i] = P.qx[i]; q[3 * i + 1] = P.qy[i]; q[3 * i + 2] = P.qz[i];
+}
+
+template <typename T> static T *dtmp(size_t n) {
+    T *p = nullptr;
+    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) return nullptr;
+    return p;
+}
+
+extern "C" rt_status rt_get_quantised(rt_ctx *c, long long *q, int where, void *stream) {
+    if (!c || !q || !c->have_particles) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long *t = dtmp<long long>(3 * c->d.n);
+    if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
+    k_get_q<<<(unsigned)((c->d.n + 255) / 256), 256, 0, st>>>(c->d, t);
+    rt_status s = copy_out(c, q, t, sizeof(long long) * 3 * c->d.n, where, st);
+    cudaStreamSynchronize(st);
+    cudaFree(t);
+    return s;
+}
+
+extern "C" rt_status rt_get_rotations(rt_ctx *c, double *R, double *Rs, int where, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevPtrs &P = c->d;
+    rt_status s;
+    if ((s = copy_out(c, R, P.R, sizeof(double) * 9 * P.n, where, st)) ||
+        (s = copy_out(c, Rs, P.Rs, sizeof(double) * 9 * (size_t)P.ns * P.K, where, st)))
+        return s;
+    return RT_OK;
+}
+
+__global__ void k_masks(DevPtrs P, int cur, unsigned *out) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.n * P.S) return;
+    long long i = t / P.S;
+    int s = (int)(t % P.S);
+    int nu = s / P.nrc, b = s % P.nrc;
+    unsigned a = P.act[cur][i * P.nf + nu];
+    unsigned m = 0;
+    if ((a >> b) & 1u)
+        for (int k = 0; k < P.kn; ++k)
+            m |= ((P.bm[(i * P.kn + k) * P.nf + nu] >> b) & 1u) << k;
+    out[t] = m;
+}
+
+extern "C" rt_status rt_get_cone_masks(rt_ctx *c, unsigned *mask, int where, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    if (!mask) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long m = c->d.n * c->d.S;
+    unsigned *t = dtmp<unsigned>(m);
+    if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
+    k_masks<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->d, c->cur, t);
+    s = copy_out(c, mask, t, sizeof(unsigned) * m, where, st);
+    cudaStreamSynchronize(st);
+    cudaFree(t);
+    return s;
+}
+
+template <typename Real>
+__global__ void k_slots_io(DevPtrs P, int cur, double *f, int to_dev) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long m = P.n * P.S;
+    if (t >= m) return;
+    long long i = t / P.S;
+    int s = (int)(t % P.S);
+    int nu = s / P.nrc, b = s % P.nrc;
+    double nm = P.norm[P.pbox[i]];
+    Real *F[6];
+    for (int k = 0; k < 6; ++k) F[k] = (Real *)P.sl[cur][k];
+    long long key = i * P.nf + nu;
+    if (to_dev) {
+        double N = f[t];
+        for (int k = 0; k < 6; ++k) F[k][t] = (Real)(f[k * m + t] / nm);
+        bool occ = N > 0.0;
+        bool act = occ && (f[4 * m + t] / N < P.dt);
+        if (occ) atomicOr(&P.occ[cur][key], 1u << b);
+        if (act) atomicOr(&P.act[cur][key], 1u << b);
+    } else {
+        bool occ = (P.occ[cur][key] >> b) & 1u;
+        for (int k = 0; k < 6; ++k) f[k * m + t] = occ ? (double)F[k][t] * nm : 0.0;
+    }
+}
+
+extern "C" rt_status rt_get_slots(rt_ctx *c, double *f, int where, void *stream) {
+    if (!c || !f) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long m = c->d.n * c->d.S;
+    double *t = dtmp<double>(6 * m);
+    if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
+    unsigned nb = (unsigned)((m + 255) / 256);
+    if (c->d.fp32) k_slots_io<float><<<nb, 256, 0, st>>>(c->d, c->cur, t, 0);
+    else k_slots_io<double><<<nb, 256, 0, st>>>(c->d, c->cur, t, 0);
+    rt_status s = copy_out(c, f, t, sizeof(double) * 6 * m, where, st);
+    cudaStreamSynchronize(st);
+    cudaFree(t);
+    return s;
+}
+
+extern "C" rt_status rt_set_slots(rt_ctx *c, const double *f, int where, void *stream) {
+    if (!c || !f) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long m = c->d.n * c->d.S;
+    double *t = dtmp<double>(6 * m);
+    if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
+    rt_status s = copy_in(c, t, f, sizeof(double) * 6 * m, where, st);
+    if (s) { cudaFree(t); return s; }
+    cudaMemsetAsync(c->d.occ[c->cur], 0, sizeof(unsigned) * c->d.n * c->d.nf, st);
+    cudaMemsetAsync(c->d.act[c->cur], 0, sizeof(unsigned) * c->d.n * c->d.nf, st);
+    unsigned nb = (unsigned)((m + 255) / 256);
+    if (c->d.fp32) k_slots_io<float><<<nb, 256, 0, st>>>(c->d, c->cur, t, 1);
+    else k_slots_io<double><<<nb, 256, 0, st>>>(c->d, c->cur, t, 1);
+    s = rt_cuda_check(c, cudaStreamSynchronize(st), "set slots");
+    cudaFree(t);
+    return s;
+}
+
+__global__ void k_deposits(DevPtrs P, double *a, double *e) {
+    long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= P.n * P.nf) return;
+    long long i = key / P.nf;
+    double NHI = P.xHI[i] * P.NH[i];
+    a[key] = P.abs[key] + (double)P.fx_abs[key] * (NHI / FX_ABS_SCALE);
+    e[key] = P.absE[key] + (double)P.fx_E[key] * (NHI * 1.602176634e-12 / FX_E_SCALE);
+}
+
+extern "C" rt_status rt_get_deposits(rt_ctx *c, double *abs_, double *absE, double *pass,
+                                     int where, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long m = c->d.n * c->d.nf;
+    double *t = dtmp<double>(2 * m);
+    if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
+    k_deposits<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->d, t, t + m);
+    rt_status s;
+    if ((s = copy_out(c, abs_, t, sizeof(double) * m, where, st)) ||
+        (s = copy_out(c, absE, t + m, sizeof(double) * m, where, st)) ||
+        (s = copy_out(c, pass, c->d.pass, sizeof(double) * m, where, st))) {
+        cudaFree(t);
+        return s;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(t);
+    return RT_OK;
+}
+
+extern "C" rt_status rt_get_stats(rt_ctx *c, long long *out) {
+    if (!c || !out) return RT_ERR_INVALID;
+    for (int k = 0; k < 8; ++k) out[k] = c->stats[k];
+    return RT_OK;
+}
+
+extern "C" const char *rt_last_error(const rt_ctx *c) { return c ? c->err.c_str() : "null context"; }

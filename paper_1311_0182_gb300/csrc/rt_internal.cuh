@@ -1,0 +1,359 @@
+// rt_internal.cuh -- internal state and device helpers of the TRAPHIC transport library.
+//
+// The whole library is compiled with -fmad=false (and the host part with -ffp-contract=off):
+// every FP64 expression that decides an integer (neighbour order, cone membership, reception
+// cone, rotation, virtual-particle position) is evaluated with the operation order written
+// here, so that it matches a plain IEEE evaluation of the same formula.  Where a fused
+// multiply-add is wanted for speed it is written out as __fmaf_rn.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/traphic_rt.h"
+
+#define RT_Q 1048576          // 2^20 quantisation cells per box side
+#define RT_MAXK 32            // maximum neighbours per particle
+#define RT_FREE_BIT (1ull << 63)
+
+// error bits of the sticky device error word
+enum { ERRB_FREE_CAP = 1, ERRB_STAGE_CAP = 2, ERRB_RANGE = 4, ERRB_KNN = 8 };
+
+// device counters
+enum {
+    CNT_ACTIVE = 0,     // active slots after the hop
+    CNT_NREQ = 1,       // virtual-particle requests of the hop (= free packets of the next hop)
+    CNT_LIVE = 2,       // live free packets for the next hop
+    CNT_STAGE = 3,      // staged free-packet contributions of the hop
+    CNT_ERR = 4,        // sticky error bits
+    CNT_VIRT = 5,       // virtual particles this step
+    CNT_VESC = 6,       // escaped virtual particles this step
+    CNT_GAS = 7,        // gas-to-gas contributions this step
+    CNT_SUB = 8,        // chemistry subcycles
+    CNT_FLOOR = 9,      // subcycle-floor hits
+    CNT_NFREE = 10,     // free packets of the current hop
+    CNT_N = 16
+};
+
+// fixed-point scales of the virtual-particle deposits (relative to the receiver's neutral
+// atoms N_HI at the start of the step) and of the escaped tally (relative to the box's
+// photon reference)
+#define FX_ABS_SCALE 1099511627776.0   // 2^40
+#define FX_E_SCALE 68719476736.0       // 2^36 (energy in eV)
+#define FX_ESC_SCALE 1125899906842624.0 // 2^50
+
+struct FreeBuf {  // packets not held by gas particles: source packets and virtual particles
+    int *box, *qx, *qy, *qz, *nu;
+    int *nbr;                 // [cap * kn]
+    long long *h2;
+    unsigned long long *fid;
+    void *N, *dx, *dy, *dz, *clock, *eps;  // Real [cap]
+};
+
+struct Grid {                 // per-box uniform cell lists (device arrays)
+    int *G;                   // cells per side, per box
+    int *cs;                  // cell side (quantised units), per box
+    long long *coff;          // first cell of the box
+    int *start;               // [ncells + 1] offsets into items
+    int4 *items;              // (qx, qy, qz, local index) sorted by cell
+    long long ncells;
+};
+
+struct HopScratch {           // per-hop scratch: [0] free packets, [1] n + free, [2] requests, [3] staged
+    int *lens;
+    unsigned *fmask;
+    int *stcnt, *stoff;
+    unsigned long long *esc_r;
+    unsigned char *vstat;
+};
+
+struct DevPtrs {              // plain pointers handed to kernels (by value)
+    // sizes and parameters
+    long long n;
+    int nb, ns, nf, S, K, kn, nrc, nec, ntc, nfs;
+    int fp32;
+    double dt, dt_em, sigma_rec, T_floor, eps_rr_fixed;
+    int rec_mode, evolve_T, sub_cap, cool_flags;
+    unsigned long long seed;
+    long long F_cap, ST_cap;
+    // boxes
+    long long *box_off;
+    double *box_L, *box_u, *norm, *ref;
+    unsigned long long *esc_fx;
+    double *tally;            // [nb * 4]
+    // particles
+    int *pbox, *qx, *qy, *qz;
+    double *nH, *NH, *xHI, *T, *Nrec, *epsrec, *nHI, *phot;
+    void *nHIr, *Vr, *dep_s, *depE_s;   // Real [n]
+    // sources
+    int *sbox, *sqx, *sqy, *sqz;
+    double *ndot, *sigma, *eps;  // [ns*nfs], [nf], [nf]
+    // neighbours
+    int *nbr, *snbr;
+    long long *h2, *sh2;
+    float *fdx, *fdy, *fdz;   // forward offsets q_j - q_i, [n * kn]
+    int *rev_off;
+    unsigned *rev_ent;        // (i << 5) | k
+    float *rdx, *rdy, *rdz;   // offsets in reverse order
+    Grid grid;
+    // rotations
+    double *R, *Rs;
+    float *Rf;
+    // slots (double-buffered): 6 Real fields + occupancy/activity words per (i, nu)
+    void *sl[2][6];
+    unsigned *occ[2], *act[2];
+    // phase-A records (w, dx, dy, dz, clock, eps) and transposed cone bitmaps
+    void *rec[6];
+    unsigned *bm;             // [(i * kn + k) * nf + nu]
+    unsigned *emp;            // empty-cone bits [n * nf]
+    int *touched;             // hop stamp per (j, nu)
+    // requests
+    int *reqcnt, *reqoff;     // [n + F_cap]
+    unsigned long long *req;  // [F_cap]
+    FreeBuf fr[2];
+    // staged free-packet contributions
+    int *st_key;              // receiver key j*nf+nu
+    long long *st_ord;        // ordering key f*kn + k
+    int *st_bin;
+    void *st_v[9];            // T, T dx, T dy, T dz, T clock, T eps, A, A eps, w (Real)
+    int *seg_cnt, *seg_off, *seg_fill, *seg_idx;
+    // accumulators
+    double *abs, *absE, *pass;                // [n * nf]
+    unsigned long long *fx_abs, *fx_E;        // [n * nf]
+    long long *cnt;                           // CNT_N counters
+    // constant tables
+    double axes_rc[96], axes_ec[96];
+    float axes_rcf[96];
+};
+
+// kernel identities for the launch counter and the optional per-kernel timer
+enum {
+    KT_ROTATE, KT_REBIN, KT_EMIT_REC, KT_EMIT_SRC, KT_PHASE_A, KT_FREE_A, KT_SCAN, KT_EXPAND,
+    KT_FREE_C, KT_VIRTUAL, KT_SEG_FILL, KT_SEG_SORT, KT_PHASE_B, KT_HOP_COUNT, KT_HOP_LENS,
+    KT_DROP, KT_CHEM, KT_BUDGET, KT_KNN, KT_N
+};
+
+struct KStat {
+    double ms = 0.0, bytes = 0.0;
+    long long launches = 0;
+};
+
+struct rt_ctx {
+    rt_config cfg;
+    DevPtrs d;
+    std::vector<long long> box_off_h;
+    std::vector<double> box_L_h;
+    std::vector<int> gridG_h;
+    long long *cnt_h = nullptr;   // pinned
+    std::vector<void *> allocs;
+    bool have_particles = false, have_sources = false, built = false;
+    int cur = 0;                  // slot buffer holding the current packets
+    int fcur = 0;                 // free buffer of the current hop
+    long long hop_global = 0;
+    long long stats[8] = {0};
+    std::string err;
+    // scan scratch
+    int *scan_tmp = nullptr;
+    long long scan_tmp_n = 0;
+    HopScratch hop = {};
+    // launch counter and optional per-kernel timing (CUDA events on the launching stream)
+    long long launches = 0;
+    int prof = 0;
+    KStat kstat[KT_N];
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    size_t ev_next = 0;
+    double *src_emit = nullptr;   // device [nb]: source photons of one step per box
+    std::vector<double> src_emit_h, box_NH_h;
+};
+
+// ---- helpers shared by the .cu files (host side) ----
+rt_status rt_fail(rt_ctx *c, rt_status s, const std::string &msg);
+rt_status rt_cuda_check(rt_ctx *c, cudaError_t e, const char *what);
+void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
+                       int *d_total, cudaStream_t st);
+rt_status rt_knn_build(rt_ctx *c, cudaStream_t st);
+rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st);
+rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
+rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);
+void rt_host_axis_set(int n, double *out);
+// launch bookkeeping: call kt_begin before and kt_end after the launches of kernel `id`
+void kt_begin(rt_ctx *c, int id, cudaStream_t st);
+void kt_end(rt_ctx *c, int id, cudaStream_t st, int nlaunch = 1);
+void kt_resolve(rt_ctx *c);   // after a synchronisation: fold finished event pairs into kstat
+
+// ---- device helpers ----
+#define FULLMASK 0xffffffffu
+
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint2 philox_key(unsigned long long seed, unsigned purpose) {
+    return make_uint2((unsigned)seed, (unsigned)(seed >> 32) ^ purpose);
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// random rotation (row-major R) from a uniform quaternion drawn by rejection in the 4-cube
+__device__ inline void random_rotation(unsigned long long seed, unsigned purpose, unsigned c0,
+                                       unsigned c1, unsigned c2, double *R) {
+    uint2 key = philox_key(seed, purpose);
+    double q0 = 1.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+    for (unsigned a = 0; a < 16; ++a) {
+        uint4 u = philox4x32_10(make_uint4(c0, c1, c2, a), key);
+        double v0 = xsub(xmul((double)(u.x >> 8), 1.0 / 8388608.0), 1.0);
+        double v1 = xsub(xmul((double)(u.y >> 8), 1.0 / 8388608.0), 1.0);
+        double v2 = xsub(xmul((double)(u.z >> 8), 1.0 / 8388608.0), 1.0);
+        double v3 = xsub(xmul((double)(u.w >> 8), 1.0 / 8388608.0), 1.0);
+        double s = xadd(xadd(xadd(xmul(v0, v0), xmul(v1, v1)), xmul(v2, v2)), xmul(v3, v3));
+        if (s > 1e-6 && s <= 1.0) {
+            double nn = __dsqrt_rn(s);
+            q0 = __ddiv_rn(v0, nn); q1 = __ddiv_rn(v1, nn);
+            q2 = __ddiv_rn(v2, nn); q3 = __ddiv_rn(v3, nn);
+            break;
+        }
+    }
+    R[0] = xsub(1.0, xmul(2.0, xadd(xmul(q2, q2), xmul(q3, q3))));
+    R[1] = xmul(2.0, xsub(xmul(q1, q2), xmul(q0, q3)));
+    R[2] = xmul(2.0, xadd(xmul(q1, q3), xmul(q0, q2)));
+    R[3] = xmul(2.0, xadd(xmul(q1, q2), xmul(q0, q3)));
+    R[4] = xsub(1.0, xmul(2.0, xadd(xmul(q1, q1), xmul(q3, q3))));
+    R[5] = xmul(2.0, xsub(xmul(q2, q3), xmul(q0, q1)));
+    R[6] = xmul(2.0, xsub(xmul(q1, q3), xmul(q0, q2)));
+    R[7] = xmul(2.0, xadd(xmul(q2, q3), xmul(q0, q1)));
+    R[8] = xsub(1.0, xmul(2.0, xadd(xmul(q1, q1), xmul(q2, q2))));
+}
+
+// R * D (emission direction along a rotated cone axis)
+__device__ __forceinline__ void rot_apply(const double *R, const double *D, double *o) {
+    o[0] = xadd(xadd(xmul(R[0], D[0]), xmul(R[1], D[1])), xmul(R[2], D[2]));
+    o[1] = xadd(xadd(xmul(R[3], D[0]), xmul(R[4], D[1])), xmul(R[5], D[2]));
+    o[2] = xadd(xadd(xmul(R[6], D[0]), xmul(R[7], D[1])), xmul(R[8], D[2]));
+}
+
+// Transmission cone, exact form: delta . d > 0 and (delta . d)^2 >= (1 - 2/n_tc)^2 |delta|^2
+__device__ __forceinline__ bool cone_exact(int dx, int dy, int dz, double d0, double d1,
+                                           double d2, int ntc) {
+    if ((dx | dy | dz) == 0) return false;
+    double t = xadd(xadd(xmul((double)dx, d0), xmul((double)dy, d1)), xmul((double)dz, d2));
+    if (!(t > 0.0)) return false;
+    long long r2i = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+    double c = xsub(1.0, __ddiv_rn(2.0, (double)ntc));
+    return xmul(t, t) >= xmul(xmul(c, c), (double)r2i);
+}
+
+// Fast FP32 test with a guard band; falls back to the exact test inside the band.  The
+// FP32 cosine estimate is within ~1e-6 of the exact value, far inside the 2e-5 band.
+#define CONE_BAND 2e-5f
+__device__ __forceinline__ bool cone_test(int dx, int dy, int dz, float fx, float fy, float fz,
+                                          double d0, double d1, double d2, float cf, int ntc) {
+    if ((dx | dy | dz) == 0) return false;
+    float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
+    float cs = __fmaf_rn(fx, (float)d0, __fmaf_rn(fy, (float)d1, fz * (float)d2)) * rsqrtf(r2);
+    if (cs > cf + CONE_BAND) return true;
+    if (cs < cf - CONE_BAND) return false;
+    return cone_exact(dx, dy, dz, d0, d1, d2, ntc);
+}
+
+// Reception cone of direction d at a particle with rotation R: argmax_b (R^T d) . D_b,
+// first maximum on ties.  Exact (FP64) form.
+__device__ inline int bin_exact(const double *R, const double *axes, int nrc, double d0,
+                                double d1, double d2) {
+    double e0 = xadd(xadd(xmul(R[0], d0), xmul(R[3], d1)), xmul(R[6], d2));
+    double e1 = xadd(xadd(xmul(R[1], d0), xmul(R[4], d1)), xmul(R[7], d2));
+    double e2 = xadd(xadd(xmul(R[2], d0), xmul(R[5], d1)), xmul(R[8], d2));
+    int best = 0;
+    double bs = 0.0;
+    for (int b = 0; b < nrc; ++b) {
+        double sc = xadd(xadd(xmul(e0, axes[3 * b]), xmul(e1, axes[3 * b + 1])),
+                         xmul(e2, axes[3 * b + 2]));
+        if (b == 0 || sc > bs) { bs = sc; best = b; }
+    }
+    return best;
+}
+
+#define BIN_BAND 2e-5f
+// Fast FP32 reception cone with a guard band on the margin between the two best scores.
+__device__ inline int bin_fast(const float *Rf, const double *Rd, const float *axf,
+                               const double *axd, int nrc, double d0, double d1, double d2) {
+    float f0 = (float)d0, f1 = (float)d1, f2 = (float)d2;
+    float e0 = __fmaf_rn(Rf[0], f0, __fmaf_rn(Rf[3], f1, Rf[6] * f2));
+    float e1 = __fmaf_rn(Rf[1], f0, __fmaf_rn(Rf[4], f1, Rf[7] * f2));
+    float e2 = __fmaf_rn(Rf[2], f0, __fmaf_rn(Rf[5], f1, Rf[8] * f2));
+    float b1 = -3.0f, b2 = -3.0f;
+    int best = 0;
+    for (int b = 0; b < nrc; ++b) {
+        float sc = __fmaf_rn(e0, axf[3 * b], __fmaf_rn(e1, axf[3 * b + 1], e2 * axf[3 * b + 2]));
+        if (sc > b1) { b2 = b1; b1 = sc; best = b; }
+        else if (sc > b2) b2 = sc;
+    }
+    if (b1 - b2 > BIN_BAND) return best;
+    return bin_exact(Rd, axd, nrc, d0, d1, d2);
+}
+
+// M4 cubic spline of support 1 (unnormalised)
+template <typename Real>
+__device__ __forceinline__ Real kernel_w(Real q) {
+    if (q <= Real(0.5)) return Real(1) - Real(6) * q * q + Real(6) * q * q * q;
+    if (q <= Real(1)) {
+        Real a = Real(1) - q;
+        return Real(2) * a * a * a;
+    }
+    return Real(0);
+}
+
+template <typename Real> __device__ __forceinline__ Real rt_expm1(Real x);
+template <> __device__ __forceinline__ float rt_expm1<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double rt_expm1<double>(double x) { return expm1(x); }
+template <typename Real> __device__ __forceinline__ Real rt_sqrt(Real x);
+template <> __device__ __forceinline__ float rt_sqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double rt_sqrt<double>(double x) { return sqrt(x); }
+
+// Kahan-compensated accumulator (FP32 path); plain sums for FP64
+template <typename Real> struct KSum {
+    Real s, c;
+    __device__ __forceinline__ void init(Real v) { s = v; c = Real(0); }
+    __device__ __forceinline__ void add(Real v) {
+        Real y = v - c;
+        Real t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ Real get() const { return s; }
+};
+template <> struct KSum<double> {
+    double s;
+    __device__ __forceinline__ void init(double v) { s = v; }
+    __device__ __forceinline__ void add(double v) { s = s + v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+static inline int rt_blocks(long long items, int per_block, int cap = 152 * 32) {
+    long long b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}

@@ -1,0 +1,197 @@
+// rt_knn.cu -- quantisation, per-box cell lists, exact kNN of particles and sources, and the
+// receiver-sorted reverse neighbour lists (Sec. 2.1: a packet at particle i is passed to the
+// neighbours within i's smoothing volume, the n_ngb nearest particles).
+#include "rt_knn.cuh"
+
+__global__ void k_quantise(DevPtrs P, const double *x, const double *y, const double *z) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    int lo = 0, hi = P.nb - 1;          // box of particle i: box_off[b] <= i < box_off[b+1]
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.box_off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    double L = P.box_L[lo];
+    double v[3] = {x[i], y[i], z[i]};
+    int q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = __ddiv_rn(v[a], L);
+        f = __dmul_rn(f, (double)RT_Q);
+        double fl = floor(f);
+        long long qq = (long long)fl;
+        if (!(fl >= 0.0)) qq = 0;
+        if (qq > RT_Q - 1) qq = RT_Q - 1;
+        q[a] = (int)qq;
+    }
+    P.pbox[i] = lo;
+    P.qx[i] = q[0]; P.qy[i] = q[1]; P.qz[i] = q[2];
+}
+
+__global__ void k_quantise_src(DevPtrs P, const double *x, const double *y, const double *z) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.ns) return;
+    double L = P.box_L[P.sbox[i]];
+    double v[3] = {x[i], y[i], z[i]};
+    int q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = __dmul_rn(__ddiv_rn(v[a], L), (double)RT_Q);
+        double fl = floor(f);
+        long long qq = (long long)fl;
+        if (!(fl >= 0.0)) qq = 0;
+        if (qq > RT_Q - 1) qq = RT_Q - 1;
+        q[a] = (int)qq;
+    }
+    P.sqx[i] = q[0]; P.sqy[i] = q[1]; P.sqz[i] = q[2];
+}
+
+__device__ __forceinline__ long long cell_of_particle(const DevPtrs &P, long long i) {
+    int b = P.pbox[i];
+    int G = P.grid.G[b], cs = P.grid.cs[b];
+    int cx = cell_coord(P.qx[i], cs, G), cy = cell_coord(P.qy[i], cs, G),
+        cz = cell_coord(P.qz[i], cs, G);
+    return P.grid.coff[b] + ((long long)cx * G + cy) * G + cz;
+}
+
+__global__ void k_cell_count(DevPtrs P, int *cnt) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    atomicAdd(&cnt[cell_of_particle(P, i)], 1);
+}
+
+__global__ void k_cell_fill(DevPtrs P, int *fill) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    long long c = cell_of_particle(P, i);
+    int pos = P.grid.start[c] + atomicAdd(&fill[c], 1);
+    int b = P.pbox[i];
+    P.grid.items[pos] = make_int4(P.qx[i], P.qy[i], P.qz[i], (int)(i - P.box_off[b]));
+}
+
+__device__ __forceinline__ BoxGrid box_grid(const DevPtrs &P, int b) {
+    BoxGrid g;
+    g.G = P.grid.G[b];
+    g.cs = P.grid.cs[b];
+    g.coff = P.grid.coff[b];
+    g.start = P.grid.start;
+    g.items = P.grid.items;
+    return g;
+}
+
+// one warp per gas particle (exclude itself) or source
+__global__ void k_knn(DevPtrs P, int sources) {
+    int lane = threadIdx.x & 31;
+    long long nq = sources ? P.ns : P.n;
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = w0; w < nq; w += nw) {
+        int b, qx, qy, qz, ex;
+        if (sources) {
+            b = P.sbox[w]; qx = P.sqx[w]; qy = P.sqy[w]; qz = P.sqz[w]; ex = -1;
+        } else {
+            b = P.pbox[w]; qx = P.qx[w]; qy = P.qy[w]; qz = P.qz[w];
+            ex = (int)(w - P.box_off[b]);
+        }
+        long long d2;
+        int idx;
+        bool ok = warp_knn(box_grid(P, b), qx, qy, qz, ex, P.kn, d2, idx);
+        if (!ok) {
+            if (lane == 0) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_KNN);
+            continue;
+        }
+        long long g = P.box_off[b] + idx;
+        long long kd2 = __shfl_sync(FULLMASK, d2, P.kn - 1);
+        if (lane < P.kn) {
+            if (sources) {
+                P.snbr[w * P.kn + lane] = (int)g;
+            } else {
+                P.nbr[w * P.kn + lane] = (int)g;
+                P.fdx[w * P.kn + lane] = (float)(P.qx[g] - qx);
+                P.fdy[w * P.kn + lane] = (float)(P.qy[g] - qy);
+                P.fdz[w * P.kn + lane] = (float)(P.qz[g] - qz);
+            }
+        }
+        if (lane == 0) {
+            if (sources) P.sh2[w] = kd2; else P.h2[w] = kd2;
+        }
+    }
+}
+
+__global__ void k_rev_count(DevPtrs P, int *cnt) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P.n * P.kn) return;
+    atomicAdd(&cnt[P.nbr[e]], 1);
+}
+
+__global__ void k_rev_fill(DevPtrs P, int *fill) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P.n * P.kn) return;
+    long long i = e / P.kn;
+    int k = (int)(e % P.kn);
+    int j = P.nbr[e];
+    int pos = P.rev_off[j] + atomicAdd(&fill[j], 1);
+    P.rev_ent[pos] = ((unsigned)i << 5) | (unsigned)k;
+}
+
+// order each receiver's senders by index (the fill order is arbitrary) and copy the offsets
+__global__ void k_rev_sort(DevPtrs P) {
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n) return;
+    int a = P.rev_off[j], b = P.rev_off[j + 1];
+    for (int p = a + 1; p < b; ++p) {
+        unsigned v = P.rev_ent[p];
+        int q = p - 1;
+        while (q >= a && P.rev_ent[q] > v) {
+            P.rev_ent[q + 1] = P.rev_ent[q];
+            --q;
+        }
+        P.rev_ent[q + 1] = v;
+    }
+    for (int p = a; p < b; ++p) {
+        unsigned v = P.rev_ent[p];
+        long long f = (long long)(v >> 5) * P.kn + (v & 31);
+        P.rdx[p] = P.fdx[f];
+        P.rdy[p] = P.fdy[f];
+        P.rdz[p] = P.fdz[f];
+    }
+}
+
+rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
+    DevPtrs &P = c->d;
+    long long n = P.n;
+    int tb = 256;
+    unsigned nbk = (unsigned)((n + tb - 1) / tb);
+    // cell lists
+    int *cnt = P.seg_cnt, *fill = P.seg_fill;   // scratch, sized >= max(ncells, n)
+    cudaMemsetAsync(cnt, 0, sizeof(int) * (P.grid.ncells + 1), st);
+    cudaMemsetAsync(fill, 0, sizeof(int) * (P.grid.ncells + 1), st);
+    k_cell_count<<<nbk, tb, 0, st>>>(P, cnt);
+    rt_scan_exclusive(c, cnt, P.grid.start, P.grid.ncells + 1, nullptr, nullptr, st);
+    k_cell_fill<<<nbk, tb, 0, st>>>(P, fill);
+    // neighbours of particles and sources
+    k_knn<<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, 0);
+    if (P.ns > 0) k_knn<<<rt_blocks((long long)P.ns * 32, tb), tb, 0, st>>>(P, 1);
+    // reverse lists
+    cudaMemsetAsync(cnt, 0, sizeof(int) * (n + 1), st);
+    cudaMemsetAsync(fill, 0, sizeof(int) * (n + 1), st);
+    long long ne = n * P.kn;
+    unsigned nbe = (unsigned)((ne + tb - 1) / tb);
+    k_rev_count<<<nbe, tb, 0, st>>>(P, cnt);
+    rt_scan_exclusive(c, cnt, P.rev_off, n + 1, nullptr, nullptr, st);
+    k_rev_fill<<<nbe, tb, 0, st>>>(P, fill);
+    k_rev_sort<<<nbk, tb, 0, st>>>(P);
+    return rt_cuda_check(c, cudaGetLastError(), "neighbour build");
+}
+
+// launchers used by the API for particle/source upload
+void rt_launch_quantise(rt_ctx *c, const double *x, const double *y, const double *z,
+                        cudaStream_t st) {
+    long long n = c->d.n;
+    k_quantise<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->d, x, y, z);
+}
+
+void rt_launch_quantise_src(rt_ctx *c, const double *x, const double *y, const double *z,
+                            cudaStream_t st) {
+    if (c->d.ns > 0) k_quantise_src<<<(c->d.ns + 255) / 256, 256, 0, st>>>(c->d, x, y, z);
+}

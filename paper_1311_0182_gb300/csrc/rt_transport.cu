@@ -1,0 +1,903 @@
+// rt_transport.cu -- one RT step on the GPU (Sec. 2.1 and Sec. 2.2 of the paper).
+//
+// Packets live in per-particle slots (reception cone b, frequency bin nu), double-buffered
+// across hops.  One hop:
+//   A  sender side, warp per gas particle (lanes = neighbours): for every packet able to move,
+//      the transmission-cone membership of each neighbour (ballot), the equal share w = N/n,
+//      and a transposed bitmap (sender, neighbour, nu) -> bins; empty cones request a virtual
+//      particle.  Free packets (source packets in the first hop, virtual particles after) do
+//      the same with their own neighbour lists and stage their contributions.
+//   V  warp per virtual-particle request: position inside the cone (counter-based draws),
+//      escape test, exact kNN of the point, SPH-interpolated n_HI, attenuation; absorptions
+//      go to the neighbours as fixed-point integer sums (order-independent, so reproducible);
+//      the transmitted packet becomes a free packet of the next hop.
+//   B  receiver side, group of n_rc lanes per (particle, nu), lane = reception cone: walks the
+//      particle's reverse neighbour list in sender order, expands the bitmap bits into
+//      contributions, attenuates, picks the reception cone, and merges in a fixed order
+//      (sender, slot); then the staged free-packet contributions in (packet, neighbour) order.
+//      No floating-point atomics: every sum has one fixed order.
+#include "rt_knn.cuh"
+
+static const double C_LIGHT = 2.99792458e10;
+static const double EV_ERG = 1.602176634e-12;
+
+template <typename Real> struct Slots {
+    Real *N, *X, *Y, *Z, *C, *E;
+    __device__ __forceinline__ Slots(const DevPtrs &P, int b) {
+        N = (Real *)P.sl[b][0]; X = (Real *)P.sl[b][1]; Y = (Real *)P.sl[b][2];
+        Z = (Real *)P.sl[b][3]; C = (Real *)P.sl[b][4]; E = (Real *)P.sl[b][5];
+    }
+};
+
+template <typename Real>
+__device__ __forceinline__ void packet_dir(Real Mx, Real My, Real Mz, Real &d0, Real &d1, Real &d2) {
+    Real nn = rt_sqrt<Real>(Mx * Mx + My * My + Mz * Mz);
+    if (nn > Real(0)) { d0 = Mx / nn; d1 = My / nn; d2 = Mz / nn; }
+    else { d0 = Real(1); d1 = Real(0); d2 = Real(0); }
+}
+
+// ------------------------------------------------------------------------------------------
+// per-step kernels
+// ------------------------------------------------------------------------------------------
+__global__ void k_rotate(DevPtrs P, long long step) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nsrc = (long long)P.ns * P.K;
+    if (i < P.n) {
+        double R[9];
+        random_rotation(P.seed, 1u, (unsigned)step, (unsigned)(step >> 32), (unsigned)i, R);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) { P.R[i * 9 + a] = R[a]; P.Rf[i * 9 + a] = (float)R[a]; }
+    } else if (i < P.n + nsrc) {
+        long long t = i - P.n;
+        int j = (int)(t / P.K), k = (int)(t % P.K);
+        double R[9];
+        random_rotation(P.seed, 2u, (unsigned)step, (unsigned)k, (unsigned)j, R);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) P.Rs[t * 9 + a] = R[a];
+    }
+}
+
+// Start of step: clock reset and re-binning of held packets into the new reception cones.
+template <typename Real, int NRC>
+__global__ void k_rebin(DevPtrs P, int cur) {
+    long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= P.n * P.nf) return;
+    unsigned o = P.occ[cur][key];
+    if (!o) { P.act[cur][key] = 0; return; }
+    long long i = key / P.nf;
+    int nu = (int)(key % P.nf);
+    Slots<Real> S(P, cur);
+    long long s0 = i * P.S + (long long)nu * NRC;
+    Real nN[NRC], nX[NRC], nY[NRC], nZ[NRC], nE[NRC];
+    Real oN[NRC], oX[NRC], oY[NRC], oZ[NRC], oE[NRC];
+    for (int b = 0; b < NRC; ++b) {
+        nN[b] = nX[b] = nY[b] = nZ[b] = nE[b] = Real(0);
+        if ((o >> b) & 1) {
+            oN[b] = S.N[s0 + b]; oX[b] = S.X[s0 + b]; oY[b] = S.Y[s0 + b];
+            oZ[b] = S.Z[s0 + b]; oE[b] = S.E[s0 + b];
+        }
+    }
+    const double *Rd = P.R + i * 9;
+    const float *Rf = P.Rf + i * 9;
+    for (int b = 0; b < NRC; ++b) {
+        if (!((o >> b) & 1) || !(oN[b] > Real(0))) continue;
+        Real d0, d1, d2;
+        packet_dir(oX[b], oY[b], oZ[b], d0, d1, d2);
+        int nb = bin_fast(Rf, Rd, P.axes_rcf, P.axes_rc, NRC, (double)d0, (double)d1, (double)d2);
+        nN[nb] += oN[b]; nX[nb] += oX[b]; nY[nb] += oY[b]; nZ[nb] += oZ[b]; nE[nb] += oE[b];
+    }
+    unsigned no = 0;
+    for (int b = 0; b < NRC; ++b) {
+        if (nN[b] > Real(0)) {
+            no |= 1u << b;
+            S.N[s0 + b] = nN[b]; S.X[s0 + b] = nX[b]; S.Y[s0 + b] = nY[b];
+            S.Z[s0 + b] = nZ[b]; S.C[s0 + b] = Real(0); S.E[s0 + b] = nE[b];
+        }
+    }
+    P.occ[cur][key] = no;
+    P.act[cur][key] = no;   // clocks restart: every held packet can move again
+}
+
+// Recombination emission into the reception cones, counter reset, frozen n_HI.
+template <typename Real, int NRC>
+__global__ void k_emit_rec(DevPtrs P, int cur) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    int b = P.pbox[i];
+    double nm = P.norm[b];
+    for (int nu = 0; nu < P.nf; ++nu) {
+        long long key = i * P.nf + nu;
+        P.abs[key] = 0.0; P.absE[key] = 0.0; P.pass[key] = 0.0;
+        P.fx_abs[key] = 0ull; P.fx_E[key] = 0ull;
+    }
+    double x = P.xHI[i], nH = P.nH[i], NH = P.NH[i];
+    double nHI = __dmul_rn(x, nH);
+    P.nHI[i] = nHI;
+    ((Real *)P.nHIr)[i] = (Real)nHI;
+    ((Real *)P.Vr)[i] = (Real)(NH / nH);
+    double NHI = x * NH;
+    ((Real *)P.dep_s)[i] = NHI > 0.0 ? (Real)(FX_ABS_SCALE * nm / NHI) : Real(0);
+    ((Real *)P.depE_s)[i] = NHI > 0.0 ? (Real)(FX_E_SCALE * nm / (NHI * EV_ERG)) : Real(0);
+    double Nr = P.Nrec[i];
+    if (!(Nr > 0.0)) return;
+    double e_phys = Nr / (double)NRC;
+    Real e = (Real)(e_phys / nm);
+    Real epsr = (Real)P.epsrec[i];
+    int nu = P.nf - 1;
+    long long key = i * P.nf + nu;
+    unsigned o = P.occ[cur][key], a = P.act[cur][key];
+    Slots<Real> S(P, cur);
+    long long s0 = i * P.S + (long long)nu * NRC;
+    const double *R = P.R + i * 9;
+    for (int bb = 0; bb < NRC; ++bb) {
+        double A[3];
+        rot_apply(R, P.axes_rc + 3 * bb, A);
+        long long s = s0 + bb;
+        if ((o >> bb) & 1) {
+            S.N[s] += e; S.X[s] += e * (Real)A[0]; S.Y[s] += e * (Real)A[1];
+            S.Z[s] += e * (Real)A[2]; S.E[s] += e * epsr;
+        } else {
+            S.N[s] = e; S.X[s] = e * (Real)A[0]; S.Y[s] = e * (Real)A[1];
+            S.Z[s] = e * (Real)A[2]; S.C[s] = Real(0); S.E[s] = e * epsr;
+        }
+        if (e > Real(0)) { o |= 1u << bb; a |= 1u << bb; }
+    }
+    P.occ[cur][key] = o;
+    P.act[cur][key] = a;
+}
+
+// Source packets of the step: K emissions x n_freq_src bins x n_ec cones per source.
+template <typename Real>
+__global__ void k_emit_src(DevPtrs P, int fcur) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long per_src = (long long)P.K * P.nfs * P.nec;
+    if (p >= (long long)P.ns * per_src) return;
+    int j = (int)(p / per_src);
+    long long t = p % per_src;
+    int k = (int)(t / ((long long)P.nfs * P.nec));
+    int nu = (int)((t / P.nec) % P.nfs);
+    int e = (int)(t % P.nec);
+    FreeBuf F = P.fr[fcur];
+    int b = P.sbox[j];
+    double N = __ddiv_rn(__dmul_rn(P.ndot[(long long)j * P.nfs + nu], P.dt_em), (double)P.nec);
+    double d[3];
+    rot_apply(P.Rs + ((long long)j * P.K + k) * 9, P.axes_ec + 3 * e, d);
+    F.box[p] = b;
+    F.qx[p] = P.sqx[j]; F.qy[p] = P.sqy[j]; F.qz[p] = P.sqz[j];
+    for (int a = 0; a < P.kn; ++a) F.nbr[p * P.kn + a] = P.snbr[(long long)j * P.kn + a];
+    F.h2[p] = P.sh2[j];
+    ((Real *)F.N)[p] = (Real)(N / P.norm[b]);
+    ((Real *)F.dx)[p] = (Real)d[0];
+    ((Real *)F.dy)[p] = (Real)d[1];
+    ((Real *)F.dz)[p] = (Real)d[2];
+    ((Real *)F.clock)[p] = Real(0);
+    ((Real *)F.eps)[p] = (Real)P.eps[nu];
+    F.nu[p] = nu;
+    F.fid[p] = (1ull << 62) | (unsigned long long)p;
+}
+
+// ------------------------------------------------------------------------------------------
+// hop kernels
+// ------------------------------------------------------------------------------------------
+template <typename Real, int NRC>
+__global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
+    int lane = threadIdx.x & 31;
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    Slots<Real> S(P, cur);
+    Real *rw = (Real *)P.rec[0], *rx = (Real *)P.rec[1], *ry = (Real *)P.rec[2],
+         *rz = (Real *)P.rec[3], *rc = (Real *)P.rec[4], *re = (Real *)P.rec[5];
+    float cf = 1.0f - 2.0f / (float)P.ntc;
+    for (long long i = w0; i < P.n; i += nw) {
+        unsigned aw = (lane < P.nf) ? P.act[cur][i * P.nf + lane] : 0u;
+        if (__ballot_sync(FULLMASK, aw != 0u) == 0u) {
+            if (lane == 0) P.reqcnt[i] = 0;
+            continue;
+        }
+        int nb = 0, dx = 0, dy = 0, dz = 0;
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        bool valid = lane < P.kn;
+        if (valid) {
+            long long f = i * P.kn + lane;
+            nb = P.nbr[f];
+            fx = P.fdx[f]; fy = P.fdy[f]; fz = P.fdz[f];
+            dx = (int)fx; dy = (int)fy; dz = (int)fz;
+        }
+        int nreq = 0;
+        for (int nu = 0; nu < P.nf; ++nu) {
+            unsigned a = __shfl_sync(FULLMASK, aw, nu);
+            unsigned bmw = 0u, empw = 0u, rem = a;
+            while (rem) {
+                int b = __ffs(rem) - 1;
+                rem &= rem - 1u;
+                long long s = i * P.S + (long long)nu * NRC + b;
+                Real N = S.N[s];
+                Real d0, d1, d2;
+                packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
+                bool in = valid && cone_test(dx, dy, dz, fx, fy, fz, (double)d0, (double)d1,
+                                             (double)d2, cf, P.ntc);
+                unsigned m = __ballot_sync(FULLMASK, in);
+                int cm = __popc(m);
+                if (cm > 0) {
+                    if (lane == 0) {
+                        rw[s] = N / (Real)cm;
+                        rx[s] = d0; ry[s] = d1; rz[s] = d2;
+                        rc[s] = S.C[s] / N;
+                        re[s] = S.E[s] / N;
+                    }
+                    if (in) {
+                        bmw |= 1u << b;
+                        P.touched[(long long)nb * P.nf + nu] = stamp;
+                    }
+                } else {
+                    empw |= 1u << b;
+                }
+            }
+            if (a && valid) P.bm[(i * P.kn + lane) * P.nf + nu] = bmw;
+            if (lane == 0) P.emp[i * P.nf + nu] = empw;
+            nreq += __popc(empw);
+        }
+        if (lane == 0) P.reqcnt[i] = nreq;
+    }
+}
+
+// Free packets: cone membership over their own neighbour lists.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_freeA(DevPtrs P, int fcur, const int *lens,
+                                               unsigned *fmask, int *stcnt) {
+    int lane = threadIdx.x & 31;
+    long long nfree = lens[0];
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    FreeBuf F = P.fr[fcur];
+    float cf = 1.0f - 2.0f / (float)P.ntc;
+    for (long long f = w0; f < nfree; f += nw) {
+        Real N = ((Real *)F.N)[f];
+        if (!(N > Real(0))) {
+            if (lane == 0) { fmask[f] = 0u; stcnt[f] = 0; P.reqcnt[P.n + f] = 0; }
+            continue;
+        }
+        double d0 = (double)((Real *)F.dx)[f], d1 = (double)((Real *)F.dy)[f],
+               d2 = (double)((Real *)F.dz)[f];
+        bool in = false;
+        if (lane < P.kn) {
+            long long j = F.nbr[f * P.kn + lane];
+            int dx = P.qx[j] - F.qx[f], dy = P.qy[j] - F.qy[f], dz = P.qz[j] - F.qz[f];
+            in = cone_test(dx, dy, dz, (float)dx, (float)dy, (float)dz, d0, d1, d2, cf, P.ntc);
+        }
+        unsigned m = __ballot_sync(FULLMASK, in);
+        if (lane == 0) {
+            fmask[f] = m;
+            stcnt[f] = __popc(m);
+            P.reqcnt[P.n + f] = (m == 0u) ? 1 : 0;
+        }
+    }
+}
+
+// Free packets with cone members: stage one contribution per member, in (packet, neighbour)
+// order at the positions given by the scan of the member counts.
+template <typename Real, int NRC>
+__global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *lens,
+                                               const unsigned *fmask, const int *stoff) {
+    int lane = threadIdx.x & 31;
+    long long nfree = lens[0];
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    FreeBuf F = P.fr[fcur];
+    for (long long f = w0; f < nfree; f += nw) {
+        unsigned m = fmask[f];
+        if (!m) continue;
+        if (!((m >> lane) & 1u)) continue;
+        int rank = __popc(m & ((1u << lane) - 1u));
+        long long s = (long long)stoff[f] + rank;
+        if (s >= P.ST_cap) {
+            atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_STAGE_CAP);
+            continue;
+        }
+        Real N = ((Real *)F.N)[f];
+        Real w = N / (Real)__popc(m);
+        Real d0 = ((Real *)F.dx)[f], d1 = ((Real *)F.dy)[f], d2 = ((Real *)F.dz)[f];
+        Real clk = ((Real *)F.clock)[f], eps = ((Real *)F.eps)[f];
+        int nu = F.nu[f];
+        long long j = F.nbr[f * P.kn + lane];
+        int b = P.pbox[j];
+        Real t = (Real)(P.qx[j] - F.qx[f]) * d0 + (Real)(P.qy[j] - F.qy[f]) * d1 +
+                 (Real)(P.qz[j] - F.qz[f]) * d2;
+        Real l = t * (Real)P.box_u[b];
+        Real tau = ((Real)P.sigma[nu] * ((Real *)P.nHIr)[j]) * l;
+        Real A = -w * rt_expm1<Real>(-tau);
+        Real T = w - A;
+        int bt = bin_fast(P.Rf + j * 9, P.R + j * 9, P.axes_rcf, P.axes_rc, NRC, (double)d0,
+                          (double)d1, (double)d2);
+        long long key = j * P.nf + nu;
+        P.st_key[s] = (int)key;
+        P.st_bin[s] = bt;
+        Real **V = (Real **)P.st_v;
+        V[0][s] = T;
+        V[1][s] = T * d0;
+        V[2][s] = T * d1;
+        V[3][s] = T * d2;
+        V[4][s] = T * (clk + l / (Real)C_LIGHT);
+        V[5][s] = T * eps;
+        V[6][s] = A;
+        V[7][s] = A * eps;
+        V[8][s] = w;
+        atomicAdd(&P.seg_cnt[key], 1);
+    }
+}
+
+// request list: gas slots with empty cones (particle order, slot order), then free packets
+__global__ void k_expand(DevPtrs P, const int *lens) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nfree = lens[0];
+    if (t < P.n) {
+        int c = P.reqcnt[t];
+        if (!c) return;
+        long long o = P.reqoff[t];
+        for (int nu = 0; nu < P.nf; ++nu) {
+            unsigned e = P.emp[t * P.nf + nu];
+            while (e) {
+                int b = __ffs(e) - 1;
+                e &= e - 1u;
+                if (o < P.F_cap) P.req[o] = (unsigned long long)(t * P.S + (long long)nu * P.nrc + b);
+                else atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
+                ++o;
+            }
+        }
+    } else if (t < P.n + nfree) {
+        long long f = t - P.n;
+        if (!P.reqcnt[t]) return;
+        long long o = P.reqoff[t];
+        if (o < P.F_cap) P.req[o] = RT_FREE_BIT | (unsigned long long)f;
+        else atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
+    }
+}
+
+// Virtual particles (Sec. 2.1): one warp per request.
+template <typename Real, int NRC>
+__global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, const int *lens,
+                                                 long long step, int hop,
+                                                 unsigned long long *esc_r,
+                                                 unsigned char *vstat) {
+    int lane = threadIdx.x & 31;
+    long long nreq = lens[2];
+    if (nreq > P.F_cap) nreq = P.F_cap;
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    FreeBuf Fi = P.fr[fcur], Fo = P.fr[fcur ^ 1];
+    Slots<Real> S(P, cur);
+    uint2 key = philox_key(P.seed, 3u);
+    for (long long r = w0; r < nreq; r += nw) {
+        unsigned long long code = P.req[r];
+        int box, qx, qy, qz, nu;
+        long long h2;
+        Real N, d0, d1, d2, clk, eps;
+        unsigned long long fid;
+        if (!(code & RT_FREE_BIT)) {
+            long long i = (long long)(code / P.S);
+            int s = (int)(code % P.S);
+            nu = s / NRC;
+            box = P.pbox[i];
+            qx = P.qx[i]; qy = P.qy[i]; qz = P.qz[i];
+            h2 = P.h2[i];
+            N = S.N[code];
+            packet_dir(S.X[code], S.Y[code], S.Z[code], d0, d1, d2);
+            clk = S.C[code] / N;
+            eps = S.E[code] / N;
+            fid = code + 1ull;
+        } else {
+            long long f = (long long)(code & ~RT_FREE_BIT);
+            box = Fi.box[f]; qx = Fi.qx[f]; qy = Fi.qy[f]; qz = Fi.qz[f];
+            h2 = Fi.h2[f];
+            N = ((Real *)Fi.N)[f];
+            d0 = ((Real *)Fi.dx)[f]; d1 = ((Real *)Fi.dy)[f]; d2 = ((Real *)Fi.dz)[f];
+            clk = ((Real *)Fi.clock)[f];
+            eps = ((Real *)Fi.eps)[f];
+            nu = Fi.nu[f];
+            fid = Fi.fid[f];
+        }
+        double dd0 = (double)d0, dd1 = (double)d1, dd2 = (double)d2;
+        // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
+        long long H = (long long)floor(sqrt((double)h2));
+        unsigned long long span = (unsigned long long)(2 * H + 1);
+        long long Dx = 0, Dy = 0, Dz = 0;
+        bool found = false;
+        for (int a0 = 0; a0 < 64 && !found; a0 += 32) {
+            unsigned a = (unsigned)(a0 + lane);
+            uint4 u = philox4x32_10(make_uint4((unsigned)step, ((unsigned)hop << 8) | a,
+                                               (unsigned)fid, (unsigned)(fid >> 32)), key);
+            long long ex = (long long)(((unsigned long long)u.x * span) >> 32) - H;
+            long long ey = (long long)(((unsigned long long)u.y * span) >> 32) - H;
+            long long ez = (long long)(((unsigned long long)u.z * span) >> 32) - H;
+            long long r2 = ex * ex + ey * ey + ez * ez;
+            bool ok = r2 > 0 && r2 <= h2 && cone_exact((int)ex, (int)ey, (int)ez, dd0, dd1, dd2, P.ntc);
+            unsigned m = __ballot_sync(FULLMASK, ok);
+            if (m) {
+                int src = __ffs(m) - 1;
+                Dx = __shfl_sync(FULLMASK, ex, src);
+                Dy = __shfl_sync(FULLMASK, ey, src);
+                Dz = __shfl_sync(FULLMASK, ez, src);
+                found = true;
+            }
+        }
+        if (!found) {
+            double fh = 0.5 * (double)H;
+            if (fh < 1.0) fh = 1.0;
+            Dx = (long long)rint(__dmul_rn(dd0, fh));
+            Dy = (long long)rint(__dmul_rn(dd1, fh));
+            Dz = (long long)rint(__dmul_rn(dd2, fh));
+        }
+        long long vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
+        if (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) {
+            if (lane == 0) {
+                double v = (double)N * P.norm[box] / P.ref[box];
+                esc_r[r] = (unsigned long long)llrint(v * FX_ESC_SCALE);
+                vstat[r] = 1;
+                Fo.box[r] = box;
+                ((Real *)Fo.N)[r] = Real(0);
+            }
+            continue;
+        }
+        long long kd2;
+        int kidx;
+        BoxGrid g;
+        g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
+        g.start = P.grid.start; g.items = P.grid.items;
+        warp_knn(g, (int)vx, (int)vy, (int)vz, -1, P.kn, kd2, kidx);
+        long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
+        bool valid = lane < P.kn;
+        long long j = valid ? P.box_off[box] + kidx : 0;
+        Real om = Real(0), nhj = Real(0), Vj = Real(0);
+        if (valid) {
+            Real q = h2v > 0 ? rt_sqrt<Real>((Real)kd2 / (Real)h2v) : Real(0);
+            Vj = ((Real *)P.Vr)[j];
+            om = Vj * kernel_w<Real>(q);
+            nhj = ((Real *)P.nHIr)[j];
+        }
+        Real sw = om;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULLMASK, sw, o);
+        if (!(sw > Real(0))) {
+            om = Vj;
+            sw = om;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULLMASK, sw, o);
+        }
+        Real wn = om * nhj;
+        Real swn = wn;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) swn += __shfl_xor_sync(FULLMASK, swn, o);
+        Real nHIv = swn / sw;
+        Real t = (Real)Dx * d0 + (Real)Dy * d1 + (Real)Dz * d2;
+        Real l = t * (Real)P.box_u[box];
+        Real tau = ((Real)P.sigma[nu] * nHIv) * l;
+        Real A = -N * rt_expm1<Real>(-tau);
+        Real T = N - A;
+        if (valid && swn > Real(0) && wn > Real(0)) {
+            Real Ak = A * (wn / swn);
+            long long key2 = j * P.nf + nu;
+            Real fa = Ak * ((Real *)P.dep_s)[j];
+            Real fe = Ak * eps * ((Real *)P.depE_s)[j];
+            if (fa > Real(0)) {
+                unsigned long long q = (unsigned long long)llrint((double)fa);
+                unsigned long long old = atomicAdd(&P.fx_abs[key2], q);
+                if (fa > Real(4.0e18) || old > (1ull << 62))
+                    atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
+            }
+            if (fe > Real(0)) {
+                unsigned long long q = (unsigned long long)llrint((double)fe);
+                unsigned long long old = atomicAdd(&P.fx_E[key2], q);
+                if (fe > Real(4.0e18) || old > (1ull << 62))
+                    atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
+            }
+        }
+        if (valid) Fo.nbr[r * P.kn + lane] = (int)j;
+        if (lane == 0) {
+            esc_r[r] = 0ull;
+            vstat[r] = T > Real(0) ? 0 : 2;
+            Fo.box[r] = box;
+            Fo.qx[r] = (int)vx; Fo.qy[r] = (int)vy; Fo.qz[r] = (int)vz;
+            Fo.h2[r] = h2v;
+            ((Real *)Fo.N)[r] = T;
+            ((Real *)Fo.dx)[r] = d0; ((Real *)Fo.dy)[r] = d1; ((Real *)Fo.dz)[r] = d2;
+            ((Real *)Fo.clock)[r] = clk + l / (Real)C_LIGHT;
+            ((Real *)Fo.eps)[r] = eps;
+            Fo.nu[r] = nu;
+            Fo.fid[r] = mix64(fid);
+        }
+    }
+}
+
+// receiver segments of the staged contributions
+__global__ void k_seg_fill(DevPtrs P, const int *lens) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nst = lens[3];
+    if (nst > P.ST_cap) nst = P.ST_cap;
+    if (s >= nst) return;
+    int key = P.st_key[s];
+    int pos = P.seg_off[key] + atomicAdd(&P.seg_fill[key], 1);
+    P.seg_idx[pos] = (int)s;
+}
+
+__global__ void k_seg_sort(DevPtrs P) {
+    long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (key >= P.n * P.nf) return;
+    int c = P.seg_cnt[key];
+    if (c < 2) return;
+    int a = P.seg_off[key], b = a + c;
+    for (int p = a + 1; p < b; ++p) {
+        int v = P.seg_idx[p];
+        int q = p - 1;
+        while (q >= a && P.seg_idx[q] > v) {
+            P.seg_idx[q + 1] = P.seg_idx[q];
+            --q;
+        }
+        P.seg_idx[q + 1] = v;
+    }
+}
+
+// Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
+// cone.  Contributions are computed in parallel and merged in their fixed order by a
+// broadcast loop (the lane owning the target cone adds).
+template <typename Real, int G>
+__global__ void __launch_bounds__(256) k_phaseB(DevPtrs P, int cur, int stamp) {
+    long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    int gl = threadIdx.x & (G - 1);
+    unsigned base = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+    unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << base);
+    if (gid >= P.n * P.nf) return;
+    long long key = gid;
+    long long j = gid / P.nf;
+    int nu = (int)(gid % P.nf);
+    int nxt = cur ^ 1;
+    unsigned o_occ = P.occ[cur][key], o_act = P.act[cur][key];
+    unsigned park = o_occ & ~o_act;
+    bool touched = P.touched[key] == stamp;
+    int fc = P.seg_cnt[key];
+    if (!touched && park == 0u && fc == 0) {
+        if (gl == 0) { P.occ[nxt][key] = 0u; P.act[nxt][key] = 0u; }
+        return;
+    }
+    Slots<Real> So(P, cur), Sn(P, nxt);
+    long long sidx = j * P.S + (long long)nu * G + gl;
+    KSum<Real> aN, aX, aY, aZ, aC, aE, sA, sAE, sW;
+    if ((park >> gl) & 1u) {
+        aN.init(So.N[sidx]); aX.init(So.X[sidx]); aY.init(So.Y[sidx]);
+        aZ.init(So.Z[sidx]); aC.init(So.C[sidx]); aE.init(So.E[sidx]);
+    } else {
+        aN.init(Real(0)); aX.init(Real(0)); aY.init(Real(0));
+        aZ.init(Real(0)); aC.init(Real(0)); aE.init(Real(0));
+    }
+    sA.init(Real(0)); sAE.init(Real(0)); sW.init(Real(0));
+    int box = P.pbox[j];
+    if (touched) {
+        Real u = (Real)P.box_u[box];
+        Real sig_nhi = (Real)P.sigma[nu] * ((Real *)P.nHIr)[j];
+        float Rf[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) Rf[a] = P.Rf[j * 9 + a];
+        const double *Rd = P.R + j * 9;
+        const Real *rw = (const Real *)P.rec[0], *rx = (const Real *)P.rec[1],
+                   *ry = (const Real *)P.rec[2], *rz = (const Real *)P.rec[3],
+                   *rc = (const Real *)P.rec[4], *re = (const Real *)P.rec[5];
+        int e0 = P.rev_off[j], e1 = P.rev_off[j + 1];
+        for (int eb = e0; eb < e1; eb += G) {
+            int e = eb + gl;
+            unsigned word = 0u;
+            int si = 0;
+            float fx = 0.f, fy = 0.f, fz = 0.f;
+            if (e < e1) {
+                unsigned ent = P.rev_ent[e];
+                si = (int)(ent >> 5);
+                int k = (int)(ent & 31u);
+                unsigned a = P.act[cur][(long long)si * P.nf + nu];
+                if (a) word = a & P.bm[((long long)si * P.kn + k) * P.nf + nu];
+                fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
+            }
+            int cw = __popc(word);
+            int incl = cw;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                int v = __shfl_up_sync(gmask, incl, o, G);
+                if (gl >= o) incl += v;
+            }
+            int total = __shfl_sync(gmask, incl, G - 1, G);
+            int excl = incl - cw;
+            for (int cb = 0; cb < total; cb += G) {
+                int c = cb + gl;
+                int lo = 0, hi = G - 1;
+#pragma unroll
+                for (int st = G; st > 1; st >>= 1) {
+                    int mid = (lo + hi + 1) >> 1;
+                    int em = __shfl_sync(gmask, excl, mid, G);
+                    if (em <= c) lo = mid; else hi = mid - 1;
+                }
+                int o_ex = __shfl_sync(gmask, excl, lo, G);
+                unsigned o_w = __shfl_sync(gmask, word, lo, G);
+                int o_si = __shfl_sync(gmask, si, lo, G);
+                float ofx = __shfl_sync(gmask, fx, lo, G);
+                float ofy = __shfl_sync(gmask, fy, lo, G);
+                float ofz = __shfl_sync(gmask, fz, lo, G);
+                int bt = 0;
+                Real v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
+                if (c < total) {
+                    int bsrc = __fns(o_w, 0, c - o_ex + 1);
+                    long long ridx = (long long)o_si * P.S + (long long)nu * G + bsrc;
+                    Real w = rw[ridx], d0 = rx[ridx], d1 = ry[ridx], d2 = rz[ridx];
+                    Real clk = rc[ridx], eps = re[ridx];
+                    Real t = (Real)ofx * d0 + (Real)ofy * d1 + (Real)ofz * d2;
+                    Real l = t * u;
+                    Real tau = sig_nhi * l;
+                    Real A = -w * rt_expm1<Real>(-tau);
+                    Real T = w - A;
+                    sA.add(A);
+                    sAE.add(A * eps);
+                    sW.add(w);
+                    bt = bin_fast(Rf, Rd, P.axes_rcf, P.axes_rc, G, (double)d0, (double)d1,
+                                  (double)d2);
+                    v0 = T; v1 = T * d0; v2 = T * d1; v3 = T * d2;
+                    v4 = T * (clk + l / (Real)C_LIGHT);
+                    v5 = T * eps;
+                }
+                int nbt = min(G, total - cb);
+                for (int t2 = 0; t2 < nbt; ++t2) {
+                    int b_t = __shfl_sync(gmask, bt, t2, G);
+                    Real x0 = __shfl_sync(gmask, v0, t2, G), x1 = __shfl_sync(gmask, v1, t2, G),
+                         x2 = __shfl_sync(gmask, v2, t2, G), x3 = __shfl_sync(gmask, v3, t2, G),
+                         x4 = __shfl_sync(gmask, v4, t2, G), x5 = __shfl_sync(gmask, v5, t2, G);
+                    if (gl == b_t) {
+                        aN.add(x0); aX.add(x1); aY.add(x2); aZ.add(x3); aC.add(x4); aE.add(x5);
+                    }
+                }
+            }
+        }
+    }
+    if (fc > 0) {
+        int so = P.seg_off[key];
+        Real *const *V = (Real *const *)P.st_v;
+        for (int cb = 0; cb < fc; cb += G) {
+            int c = cb + gl;
+            int bt = 0;
+            Real v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
+            if (c < fc) {
+                int s = P.seg_idx[so + c];
+                bt = P.st_bin[s];
+                v0 = V[0][s]; v1 = V[1][s]; v2 = V[2][s]; v3 = V[3][s]; v4 = V[4][s]; v5 = V[5][s];
+                sA.add(V[6][s]);
+                sAE.add(V[7][s]);
+                sW.add(V[8][s]);
+            }
+            int nbt = min(G, fc - cb);
+            for (int t2 = 0; t2 < nbt; ++t2) {
+                int b_t = __shfl_sync(gmask, bt, t2, G);
+                Real x0 = __shfl_sync(gmask, v0, t2, G), x1 = __shfl_sync(gmask, v1, t2, G),
+                     x2 = __shfl_sync(gmask, v2, t2, G), x3 = __shfl_sync(gmask, v3, t2, G),
+                     x4 = __shfl_sync(gmask, v4, t2, G), x5 = __shfl_sync(gmask, v5, t2, G);
+                if (gl == b_t) {
+                    aN.add(x0); aX.add(x1); aY.add(x2); aZ.add(x3); aC.add(x4); aE.add(x5);
+                }
+            }
+        }
+    }
+    Real N = aN.get();
+    bool occ = N > Real(0);
+    bool act = occ && (aC.get() / N < (Real)P.dt);
+    unsigned lmask = (G == 32) ? FULLMASK : ((1u << G) - 1u);
+    unsigned bo = (__ballot_sync(gmask, occ) >> base) & lmask;
+    unsigned ba = (__ballot_sync(gmask, act) >> base) & lmask;
+    if (occ) {
+        Sn.N[sidx] = N; Sn.X[sidx] = aX.get(); Sn.Y[sidx] = aY.get();
+        Sn.Z[sidx] = aZ.get(); Sn.C[sidx] = aC.get(); Sn.E[sidx] = aE.get();
+    }
+    Real a = sA.get(), ae = sAE.get(), w = sW.get();
+#pragma unroll
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        a += __shfl_down_sync(gmask, a, o, G);
+        ae += __shfl_down_sync(gmask, ae, o, G);
+        w += __shfl_down_sync(gmask, w, o, G);
+    }
+    if (gl == 0) {
+        P.occ[nxt][key] = bo;
+        P.act[nxt][key] = ba;
+        if (touched || fc > 0) {
+            double nm = P.norm[box];
+            P.abs[key] += (double)a * nm;
+            P.absE[key] += (double)ae * nm;
+            P.pass[key] += (double)w * nm;
+        }
+    }
+}
+
+// After a hop: active slots, live free packets, escaped photons per box (fixed point).
+__global__ void k_hop_counts(DevPtrs P, int nxt, int fnxt, const int *lens,
+                             const unsigned long long *esc_r, const unsigned char *vstat) {
+    __shared__ long long sh[3][8];
+    long long act = 0, live = 0, nesc = 0;
+    long long nreq = lens[2];
+    if (nreq > P.F_cap) nreq = P.F_cap;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long k = t0; k < P.n * P.nf; k += stride) act += __popc(P.act[nxt][k]);
+    FreeBuf F = P.fr[fnxt];
+    for (long long r = t0; r < nreq; r += stride) {
+        unsigned char s = vstat[r];
+        live += (s == 0);
+        if (s == 1) {
+            ++nesc;
+            unsigned long long v = esc_r[r];
+            int b = F.box[r];
+            // aggregate equal boxes within the warp before the atomic
+            unsigned peers = __match_any_sync(__activemask(), b);
+            int leader = __ffs(peers) - 1;
+            unsigned long long tot = 0;
+            for (unsigned m = peers; m; m &= m - 1) {
+                int src = __ffs(m) - 1;
+                tot += __shfl_sync(peers, v, src);
+            }
+            if ((int)(threadIdx.x & 31) == leader) atomicAdd(&P.esc_fx[b], tot);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        act += __shfl_down_sync(FULLMASK, act, o);
+        live += __shfl_down_sync(FULLMASK, live, o);
+        nesc += __shfl_down_sync(FULLMASK, nesc, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sh[0][w] = act; sh[1][w] = live; sh[2][w] = nesc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0, l = 0, e = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sh[0][k]; l += sh[1][k]; e += sh[2][k]; }
+        if (a) atomicAdd((unsigned long long *)&P.cnt[CNT_ACTIVE], (unsigned long long)a);
+        if (l) atomicAdd((unsigned long long *)&P.cnt[CNT_LIVE], (unsigned long long)l);
+        if (e) atomicAdd((unsigned long long *)&P.cnt[CNT_VESC], (unsigned long long)e);
+    }
+}
+
+// bookkeeping between kernels of a hop (single thread)
+__global__ void k_hop_lens(DevPtrs P, int *lens, int phase) {
+    if (phase == 0) {            // before the hop: scan lengths
+        lens[1] = (int)(P.n + lens[0]);
+    } else if (phase == 1) {     // after the request scan: n_req
+        long long nr = lens[2];
+        if (nr > P.F_cap) {
+            atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
+        }
+        P.cnt[CNT_NREQ] = nr;
+        P.cnt[CNT_VIRT] += nr < P.F_cap ? nr : P.F_cap;
+        if (lens[3] > P.ST_cap)
+            atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_STAGE_CAP);
+    } else {                     // after the hop: the requests become the next free packets
+        long long nr = lens[2];
+        lens[0] = (int)(nr < P.F_cap ? nr : P.F_cap);
+    }
+}
+
+// Hop cap reached: the free packets still in flight leave the box (counted escaped).
+template <typename Real>
+__global__ void k_drop_free(DevPtrs P, int fcur, const int *lens) {
+    long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= lens[0]) return;
+    FreeBuf F = P.fr[fcur];
+    Real N = ((Real *)F.N)[f];
+    if (N > Real(0)) {
+        int b = F.box[f];
+        double v = (double)N * P.norm[b] / P.ref[b];
+        atomicAdd(&P.esc_fx[b], (unsigned long long)llrint(v * FX_ESC_SCALE));
+        ((Real *)F.N)[f] = Real(0);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------------
+
+#define LAUNCH(id, n, ...)          \
+    do {                            \
+        kt_begin(c, id, st);        \
+        __VA_ARGS__;                \
+        kt_end(c, id, st, n);       \
+    } while (0)
+
+template <typename Real, int NRC>
+static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st) {
+    DevPtrs &P = c->d;
+    const int tb = 256;
+    long long n = P.n;
+    long long nkey = n * P.nf;
+    HopScratch &H = c->hop;
+    if (part == 0) {  // rotations
+        long long t = n + (long long)P.ns * P.K;
+        LAUNCH(KT_ROTATE, 1, (k_rotate<<<(unsigned)((t + tb - 1) / tb), tb, 0, st>>>(P, step)));
+        return rt_cuda_check(c, cudaGetLastError(), "rotate");
+    }
+    if (part == 1) {  // re-bin held packets
+        LAUNCH(KT_REBIN, 1, (k_rebin<Real, NRC><<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P, c->cur)));
+        return rt_cuda_check(c, cudaGetLastError(), "rebin");
+    }
+    if (part == 2) {  // emission
+        LAUNCH(KT_EMIT_REC, 1, (k_emit_rec<Real, NRC><<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(P, c->cur)));
+        long long np = (long long)P.ns * P.K * P.nfs * P.nec;
+        if (np > P.F_cap) return rt_fail(c, RT_ERR_CAPACITY, "source packets exceed free_cap");
+        c->fcur = 0;
+        if (np > 0)
+            LAUNCH(KT_EMIT_SRC, 1, (k_emit_src<Real><<<(unsigned)((np + tb - 1) / tb), tb, 0, st>>>(P, c->fcur)));
+        int npi = (int)np;
+        cudaMemcpyAsync(H.lens, &npi, sizeof(int), cudaMemcpyHostToDevice, st);
+        return rt_cuda_check(c, cudaGetLastError(), "emit");
+    }
+    if (part == 3) {  // cone masks of the held packets only (inspection)
+        int stamp = (int)(++c->hop_global);
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur, stamp)));
+        return rt_cuda_check(c, cudaGetLastError(), "cone masks");
+    }
+    // part 4: the hop loop
+    cudaMemsetAsync(&P.cnt[CNT_VIRT], 0, 2 * sizeof(long long), st);
+    cudaMemsetAsync(&P.cnt[CNT_GAS], 0, sizeof(long long), st);
+    rt_status status = RT_OK;
+    long long hops = 0, peak_free = 0, peak_act = 0;
+    const int gb = 152 * 64;
+    for (int hop = 0;; ++hop) {
+        if (hop >= c->cfg.hop_cap) {
+            LAUNCH(KT_DROP, 1, (k_drop_free<Real><<<rt_blocks(P.F_cap, tb, 1 << 20), tb, 0, st>>>(P, c->fcur, H.lens)));
+            status = rt_fail(c, RT_ERR_HOP_LIMIT, "hop loop reached hop_cap");
+            break;
+        }
+        int stamp = (int)(++c->hop_global);
+        int cur = c->cur, nxt = cur ^ 1, fcur = c->fcur;
+        cudaMemsetAsync(&P.cnt[CNT_ACTIVE], 0, sizeof(long long), st);
+        cudaMemsetAsync(&P.cnt[CNT_LIVE], 0, sizeof(long long), st);
+        cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, st);
+        cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, st);
+        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 0)));
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur, stamp)));
+        LAUNCH(KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
+        LAUNCH(KT_SCAN, 6, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + P.F_cap, H.lens + 1, H.lens + 2, st),
+                            rt_scan_exclusive(c, H.stcnt, H.stoff, P.F_cap, H.lens, H.lens + 3, st)));
+        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 1)));
+        LAUNCH(KT_EXPAND, 1, (k_expand<<<(unsigned)((n + P.F_cap + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
+        LAUNCH(KT_FREE_C, 1, (k_freeC<Real, NRC><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+                                  P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
+        LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, st)));
+        LAUNCH(KT_SEG_FILL, 1, (k_seg_fill<<<(unsigned)((P.ST_cap + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
+        LAUNCH(KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P)));
+        LAUNCH(KT_PHASE_B, 1, (k_phaseB<Real, NRC><<<(unsigned)((nkey * NRC + tb - 1) / tb), tb, 0, st>>>(P, cur, stamp)));
+        LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, nxt, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
+        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 2)));
+        c->cur = nxt;
+        c->fcur = fcur ^ 1;
+        ++hops;
+        cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+        rt_status s2 = rt_cuda_check(c, cudaStreamSynchronize(st), "hop");
+        if (s2 != RT_OK) return s2;
+        kt_resolve(c);
+        if (c->cnt_h[CNT_ERR]) break;
+        if (c->cnt_h[CNT_NREQ] > peak_free) peak_free = c->cnt_h[CNT_NREQ];
+        if (c->cnt_h[CNT_ACTIVE] > peak_act) peak_act = c->cnt_h[CNT_ACTIVE];
+        if (c->cnt_h[CNT_ACTIVE] == 0 && c->cnt_h[CNT_LIVE] == 0) break;
+    }
+    cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    kt_resolve(c);
+    c->stats[0] = hops;
+    c->stats[1] = c->cnt_h[CNT_VIRT];
+    c->stats[2] = c->cnt_h[CNT_VESC];
+    c->stats[5] = peak_free;
+    c->stats[6] = peak_act;
+    c->stats[7] = c->launches;
+    long long e = c->cnt_h[CNT_ERR];
+    if (e & ERRB_FREE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "free packets exceeded free_cap");
+    if (e & ERRB_STAGE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "staged contributions exceeded capacity");
+    if (e & ERRB_RANGE) return rt_fail(c, RT_ERR_RANGE, "virtual deposit overflowed its accumulator");
+    return status;
+}
+
+rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st) {
+    int nrc = c->d.nrc;
+    if (c->d.fp32) {
+        return nrc == 8 ? run_parts<float, 8>(c, part, step, st) : run_parts<float, 32>(c, part, step, st);
+    }
+    return nrc == 8 ? run_parts<double, 8>(c, part, step, st) : run_parts<double, 32>(c, part, step, st);
+}

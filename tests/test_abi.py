@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^(?:rt_status|const char \*)\s*(rt_\w+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1311_0182_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1311_0182_gb300 import rt
+    assert sorted(rt.SYMBOLS) == names
+
+
+def test_axis_sets_bit_identical_to_oracle(lib):
+    """The direction sets are built by host code of the library: compare with the oracle's."""
+    import oracle
+    from paper_1311_0182_gb300 import rt
+    for n in (8, 32):
+        assert np.array_equal(rt.axis_set(n), oracle.axis_set(n))
+
+
+def test_invalid_configuration_is_rejected_without_touching_a_gpu(lib):
+    from paper_1311_0182_gb300 import rt, workloads as W
+    wl = W.cfg1()
+    bad = dict(wl["params"], n_rc=7)
+    with pytest.raises(rt.RTError) as e:
+        rt.Context(dict(wl, params=bad))
+    assert e.value.status == 1
+    bad = dict(wl["params"], n_ngb=33)
+    with pytest.raises(rt.RTError) as e:
+        rt.Context(dict(wl, params=bad))
+    assert e.value.status == 1
+    tiny = dict(wl, box_off=np.array([0, 20]), box_L=np.array([1.0]))
+    with pytest.raises(rt.RTError) as e:
+        rt.Context(tiny)
+    assert e.value.status == 5
