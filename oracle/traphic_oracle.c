@@ -798,6 +798,19 @@ void orc_emit(orc_sim *s, long long step) {
                 }
 }
 
+/* N_abs = N_in (1 - exp(-tau)) and the transmitted rest (Sec. 2.1), evaluated so that both
+   parts keep full relative precision: the smaller of the two is computed directly and the other
+   as the difference, which keeps N_abs + N_out = N_in. */
+static void split_absorbed(double N, double tau, double *A, double *T) {
+    if (tau < 1.0) {
+        *A = -N * expm1(-tau);
+        *T = N - *A;
+    } else {
+        *T = N * exp(-tau);
+        *A = N - *T;
+    }
+}
+
 /* Deliver w photons of a packet (direction d, clock, eps, frequency nu) from a sender
    at integer position qs to gas neighbour j (Sec. 2.1): optical depth
    tau = sigma_nu n_HI,j l with l the distance projected on the propagation direction,
@@ -813,8 +826,8 @@ static void deliver(orc_sim *s, const int64_t *qs, long long j, double w, const 
                (double)(qj[2] - qs[2]) * d[2];
     double l = t * u;
     double tau = (s->sigma[nu] * s->nHI[j]) * l;
-    double A = -w * expm1(-tau);
-    double T = w - A;
+    double A, T;
+    split_absorbed(w, tau, &A, &T);
     s->abs_[j * s->nf + nu] += A;
     s->absE[j] += A * eps;
     s->pass[j * s->nf + nu] += w;
@@ -911,8 +924,8 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
     double t = (double)del[0] * d[0] + (double)del[1] * d[1] + (double)del[2] * d[2];
     double l = t * u;
     double tau = (s->sigma[nu] * nHIv) * l;
-    double A = -N * expm1(-tau);
-    double T = N - A;
+    double A, T;
+    split_absorbed(N, tau, &A, &T);
     if (swn > 0.0) {
         for (int k = 0; k < kn; ++k) {
             long long j = v.nbr[k];
