@@ -197,6 +197,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     P.sigma_rec = cfg->sigma_rec;
     P.T_floor = cfg->T_floor;
     P.eps_rr_fixed = cfg->eps_rr_fixed;
+    P.eunit = P.fp32 ? 1.602176634e-12 : 1.0;
     P.rec_mode = cfg->rec_mode;
     P.evolve_T = cfg->evolve_T;
     P.sub_cap = cfg->sub_cap;
@@ -242,6 +243,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.box_u, double, n_boxes);
     A(P.norm, double, n_boxes);
     A(P.ref, double, n_boxes);
+    A(P.vunit, double, n_boxes);
     A(P.esc_fx, unsigned long long, n_boxes);
     A(P.tally, double, 4 * n_boxes);
     A(x->src_emit, double, n_boxes);
@@ -251,7 +253,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.Nrec, double, n); A(P.epsrec, double, n); A(P.nHI, double, n); A(P.phot, double, n);
     P.nHIr = dalloc(c, R * n, &ok);
     P.Vr = dalloc(c, R * n, &ok);
-    P.dep_s = dalloc(c, R * n, &ok);
+    A(P.dep_s, double, n);
     P.depE_s = dalloc(c, R * n, &ok);
     A(P.sbox, int, n_src + 1);
     A(P.sqx, int, n_src + 1); A(P.sqy, int, n_src + 1); A(P.sqz, int, n_src + 1);
@@ -308,6 +310,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.abs, double, nkey); A(P.absE, double, nkey); A(P.pass, double, nkey);
     A(P.fx_abs, unsigned long long, nkey);
     A(P.fx_E, unsigned long long, nkey);
+    A(P.fx_lo, unsigned long long, nkey);
     A(P.cnt, long long, CNT_N);
     A(x->hop.lens, int, 8);
     A(x->hop.fmask, unsigned, fc);
@@ -330,6 +333,13 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     cudaMemcpy(P.box_off, box_off, sizeof(long long) * (n_boxes + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_L, box_L, sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_u, u.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
+    // unit of particle volumes N_H/n_H: the mean particle volume on the FP32 path (volumes in
+    // cm^3 exceed the FP32 range), 1 on the FP64 path
+    std::vector<double> vu(n_boxes, 1.0);
+    if (P.fp32)
+        for (int b = 0; b < n_boxes; ++b)
+            vu[b] = box_L[b] * box_L[b] * box_L[b] / (double)(box_off[b + 1] - box_off[b]);
+    cudaMemcpy(P.vunit, vu.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
     cudaMemcpy(P.grid.G, G.data(), sizeof(int) * n_boxes, cudaMemcpyHostToDevice);
     cudaMemcpy(P.grid.cs, cs.data(), sizeof(int) * n_boxes, cudaMemcpyHostToDevice);
     cudaMemcpy(P.grid.coff, coff.data(), sizeof(long long) * n_boxes, cudaMemcpyHostToDevice);
@@ -704,7 +714,8 @@ __global__ void k_slots_io(DevPtrs P, int cur, double *f, int to_dev) {
     long long key = i * P.nf + nu;
     if (to_dev) {
         double N = f[t];
-        for (int k = 0; k < 6; ++k) F[k][t] = (Real)(f[k * m + t] / nm);
+        for (int k = 0; k < 5; ++k) F[k][t] = (Real)(f[k * m + t] / nm);
+        F[5][t] = (Real)(f[5 * m + t] / nm / P.eunit);
         bool occ = N > 0.0;
         bool act = occ && (f[4 * m + t] / N < P.dt);
         if (occ) atomicOr(&P.occ[cur][key], 1u << b);
@@ -712,6 +723,7 @@ __global__ void k_slots_io(DevPtrs P, int cur, double *f, int to_dev) {
     } else {
         bool occ = (P.occ[cur][key] >> b) & 1u;
         for (int k = 0; k < 6; ++k) f[k * m + t] = occ ? (double)F[k][t] * nm : 0.0;
+        f[5 * m + t] *= P.eunit;
     }
 }
 
@@ -753,7 +765,8 @@ __global__ void k_deposits(DevPtrs P, double *a, double *e) {
     if (key >= P.n * P.nf) return;
     long long i = key / P.nf;
     double NHI = P.xHI[i] * P.NH[i];
-    a[key] = P.abs[key] + (double)P.fx_abs[key] * (NHI / FX_ABS_SCALE);
+    a[key] = P.abs[key] + ((double)P.fx_abs[key] + (double)P.fx_lo[key] / FX_LO_SCALE) *
+                              (NHI / FX_ABS_SCALE);
     e[key] = P.absE[key] + (double)P.fx_E[key] * (NHI * 1.602176634e-12 / FX_E_SCALE);
 }
 

@@ -60,7 +60,8 @@ __global__ void k_chem(DevPtrs P) {
         double phot = 0.0, heat = 0.0;
         for (int nu = 0; nu < P.nf; ++nu) {
             long long key = i * P.nf + nu;
-            phot += P.abs[key] + (double)P.fx_abs[key] * (NHI / FX_ABS_SCALE);
+            phot += P.abs[key] + ((double)P.fx_abs[key] + (double)P.fx_lo[key] / FX_LO_SCALE) *
+                                     (NHI / FX_ABS_SCALE);
             heat += P.absE[key] + (double)P.fx_E[key] * (NHI * EV_ERG / FX_E_SCALE);
         }
         P.phot[i] = phot;

@@ -44,6 +44,7 @@ enum {
 #define FX_ABS_SCALE 1099511627776.0   // 2^40
 #define FX_E_SCALE 68719476736.0       // 2^36 (energy in eV)
 #define FX_ESC_SCALE 1125899906842624.0 // 2^50
+#define FX_LO_SCALE 4294967296.0        // 2^32: second word of the photon deposits
 
 struct FreeBuf {  // packets not held by gas particles: source packets and virtual particles
     int *box, *qx, *qy, *qz, *nu;
@@ -76,18 +77,20 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     int nb, ns, nf, S, K, kn, nrc, nec, ntc, nfs;
     int fp32;
     double dt, dt_em, sigma_rec, T_floor, eps_rr_fixed;
+    double eunit;             // energy unit of the slot field E: 1 erg (FP64), 1 eV (FP32)
     int rec_mode, evolve_T, sub_cap, cool_flags;
     unsigned long long seed;
     long long F_cap, ST_cap;
     // boxes
     long long *box_off;
-    double *box_L, *box_u, *norm, *ref;
+    double *box_L, *box_u, *norm, *ref, *vunit;
     unsigned long long *esc_fx;
     double *tally;            // [nb * 4]
     // particles
     int *pbox, *qx, *qy, *qz;
     double *nH, *NH, *xHI, *T, *Nrec, *epsrec, *nHI, *phot;
-    void *nHIr, *Vr, *dep_s, *depE_s;   // Real [n]
+    void *nHIr, *Vr, *depE_s;  // Real [n]
+    double *dep_s;             // [n] fixed-point scale of photon deposits
     // sources
     int *sbox, *sqx, *sqy, *sqz;
     double *ndot, *sigma, *eps;  // [ns*nfs], [nf], [nf]
@@ -122,7 +125,7 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     int *seg_cnt, *seg_off, *seg_fill, *seg_idx;
     // accumulators
     double *abs, *absE, *pass;                // [n * nf]
-    unsigned long long *fx_abs, *fx_E;        // [n * nf]
+    unsigned long long *fx_abs, *fx_lo, *fx_E;  // [n * nf]: photons (2 words), energy
     long long *cnt;                           // CNT_N counters
     // constant tables
     double axes_rc[96], axes_ec[96];
@@ -325,12 +328,28 @@ __device__ __forceinline__ Real kernel_w(Real q) {
     return Real(0);
 }
 
+template <typename Real> __device__ __forceinline__ Real rt_exp(Real x);
+template <> __device__ __forceinline__ float rt_exp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double rt_exp<double>(double x) { return exp(x); }
 template <typename Real> __device__ __forceinline__ Real rt_expm1(Real x);
 template <> __device__ __forceinline__ float rt_expm1<float>(float x) { return expm1f(x); }
 template <> __device__ __forceinline__ double rt_expm1<double>(double x) { return expm1(x); }
 template <typename Real> __device__ __forceinline__ Real rt_sqrt(Real x);
 template <> __device__ __forceinline__ float rt_sqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double rt_sqrt<double>(double x) { return sqrt(x); }
+
+// N_abs = N (1 - exp(-tau)) and the transmitted rest (Sec. 2.1), the smaller part computed
+// directly so that both keep full relative precision and A + T = N
+template <typename Real>
+__device__ __forceinline__ void split_absorbed(Real N, Real tau, Real &A, Real &T) {
+    if (tau < Real(1)) {
+        A = -N * rt_expm1<Real>(-tau);
+        T = N - A;
+    } else {
+        T = N * rt_exp<Real>(-tau);
+        A = N - T;
+    }
+}
 
 // Kahan-compensated accumulator (FP32 path); plain sums for FP64
 template <typename Real> struct KSum {

@@ -29,11 +29,26 @@ template <typename Real> struct Slots {
     }
 };
 
-template <typename Real>
-__device__ __forceinline__ void packet_dir(Real Mx, Real My, Real Mz, Real &d0, Real &d1, Real &d2) {
-    Real nn = rt_sqrt<Real>(Mx * Mx + My * My + Mz * Mz);
-    if (nn > Real(0)) { d0 = Mx / nn; d1 = My / nn; d2 = Mz / nn; }
-    else { d0 = Real(1); d1 = Real(0); d2 = Real(0); }
+// unit direction of a packet from its summed momentum M (the luminosity-weighted mean
+// direction of merged packets, Sec. 2.1, Fig. 1b)
+__device__ __forceinline__ void packet_dir(double Mx, double My, double Mz, double &d0, double &d1,
+                                           double &d2) {
+    double nn = sqrt(Mx * Mx + My * My + Mz * Mz);
+    if (nn > 0.0) { d0 = Mx / nn; d1 = My / nn; d2 = Mz / nn; }
+    else { d0 = 1.0; d1 = 0.0; d2 = 0.0; }
+}
+
+// FP32: normalised photon counts can be small enough for |M|^2 to underflow, so scale first
+__device__ __forceinline__ void packet_dir(float Mx, float My, float Mz, float &d0, float &d1,
+                                           float &d2) {
+    float s = fmaxf(fabsf(Mx), fmaxf(fabsf(My), fabsf(Mz)));
+    if (s > 0.0f) {
+        float a = Mx / s, b = My / s, c = Mz / s;
+        float nn = sqrtf(a * a + b * b + c * c);
+        d0 = a / nn; d1 = b / nn; d2 = c / nn;
+    } else {
+        d0 = 1.0f; d1 = 0.0f; d2 = 0.0f;
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -108,21 +123,21 @@ __global__ void k_emit_rec(DevPtrs P, int cur) {
     for (int nu = 0; nu < P.nf; ++nu) {
         long long key = i * P.nf + nu;
         P.abs[key] = 0.0; P.absE[key] = 0.0; P.pass[key] = 0.0;
-        P.fx_abs[key] = 0ull; P.fx_E[key] = 0ull;
+        P.fx_abs[key] = 0ull; P.fx_lo[key] = 0ull; P.fx_E[key] = 0ull;
     }
     double x = P.xHI[i], nH = P.nH[i], NH = P.NH[i];
     double nHI = __dmul_rn(x, nH);
     P.nHI[i] = nHI;
     ((Real *)P.nHIr)[i] = (Real)nHI;
-    ((Real *)P.Vr)[i] = (Real)(NH / nH);
+    ((Real *)P.Vr)[i] = (Real)(NH / nH / P.vunit[b]);   // volume in the box's volume unit
     double NHI = x * NH;
-    ((Real *)P.dep_s)[i] = NHI > 0.0 ? (Real)(FX_ABS_SCALE * nm / NHI) : Real(0);
-    ((Real *)P.depE_s)[i] = NHI > 0.0 ? (Real)(FX_E_SCALE * nm / (NHI * EV_ERG)) : Real(0);
+    P.dep_s[i] = NHI > 0.0 ? FX_ABS_SCALE * nm / NHI : 0.0;
+    ((Real *)P.depE_s)[i] = NHI > 0.0 ? (Real)(FX_E_SCALE * nm * P.eunit / (NHI * EV_ERG)) : Real(0);
     double Nr = P.Nrec[i];
     if (!(Nr > 0.0)) return;
     double e_phys = Nr / (double)NRC;
     Real e = (Real)(e_phys / nm);
-    Real epsr = (Real)P.epsrec[i];
+    Real epsr = (Real)(P.epsrec[i] / P.eunit);
     int nu = P.nf - 1;
     long long key = i * P.nf + nu;
     unsigned o = P.occ[cur][key], a = P.act[cur][key];
@@ -171,7 +186,7 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
     ((Real *)F.dy)[p] = (Real)d[1];
     ((Real *)F.dz)[p] = (Real)d[2];
     ((Real *)F.clock)[p] = Real(0);
-    ((Real *)F.eps)[p] = (Real)P.eps[nu];
+    ((Real *)F.eps)[p] = (Real)(P.eps[nu] / P.eunit);
     F.nu[p] = nu;
     F.fid[p] = (1ull << 62) | (unsigned long long)p;
 }
@@ -305,8 +320,8 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
                  (Real)(P.qz[j] - F.qz[f]) * d2;
         Real l = t * (Real)P.box_u[b];
         Real tau = ((Real)P.sigma[nu] * ((Real *)P.nHIr)[j]) * l;
-        Real A = -w * rt_expm1<Real>(-tau);
-        Real T = w - A;
+        Real A, T;
+        split_absorbed<Real>(w, tau, A, T);
         int bt = bin_fast(P.Rf + j * 9, P.R + j * 9, P.axes_rcf, P.axes_rc, NRC, (double)d0,
                           (double)d1, (double)d2);
         long long key = j * P.nf + nu;
@@ -471,17 +486,22 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
         Real t = (Real)Dx * d0 + (Real)Dy * d1 + (Real)Dz * d2;
         Real l = t * (Real)P.box_u[box];
         Real tau = ((Real)P.sigma[nu] * nHIv) * l;
-        Real A = -N * rt_expm1<Real>(-tau);
-        Real T = N - A;
+        Real A, T;
+        split_absorbed<Real>(N, tau, A, T);
         if (valid && swn > Real(0) && wn > Real(0)) {
             Real Ak = A * (wn / swn);
             long long key2 = j * P.nf + nu;
-            Real fa = Ak * ((Real *)P.dep_s)[j];
+            // two fixed-point words: units of 2^-40 N_HI and 2^-72 N_HI (integer sums do not
+            // depend on their order)
+            double fa = (double)Ak * P.dep_s[j];
             Real fe = Ak * eps * ((Real *)P.depE_s)[j];
-            if (fa > Real(0)) {
-                unsigned long long q = (unsigned long long)llrint((double)fa);
-                unsigned long long old = atomicAdd(&P.fx_abs[key2], q);
-                if (fa > Real(4.0e18) || old > (1ull << 62))
+            if (fa > 0.0) {
+                double hi = floor(fa);
+                unsigned long long qh = (unsigned long long)hi;
+                unsigned long long ql = (unsigned long long)llrint((fa - hi) * FX_LO_SCALE);
+                unsigned long long old = qh ? atomicAdd(&P.fx_abs[key2], qh) : 0ull;
+                if (ql) atomicAdd(&P.fx_lo[key2], ql);
+                if (fa > 4.0e18 || old > (1ull << 62))
                     atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
             }
             if (fe > Real(0)) {
@@ -628,8 +648,8 @@ __global__ void __launch_bounds__(256) k_phaseB(DevPtrs P, int cur, int stamp) {
                     Real t = (Real)ofx * d0 + (Real)ofy * d1 + (Real)ofz * d2;
                     Real l = t * u;
                     Real tau = sig_nhi * l;
-                    Real A = -w * rt_expm1<Real>(-tau);
-                    Real T = w - A;
+                    Real A, T;
+                    split_absorbed<Real>(w, tau, A, T);
                     sA.add(A);
                     sAE.add(A * eps);
                     sW.add(w);
@@ -702,7 +722,7 @@ __global__ void __launch_bounds__(256) k_phaseB(DevPtrs P, int cur, int stamp) {
         if (touched || fc > 0) {
             double nm = P.norm[box];
             P.abs[key] += (double)a * nm;
-            P.absE[key] += (double)ae * nm;
+            P.absE[key] += (double)ae * nm * P.eunit;
             P.pass[key] += (double)w * nm;
         }
     }
