@@ -104,7 +104,8 @@ void kt_resolve(rt_ctx *c) {
 static const char *KT_NAMES[KT_N] = {
     "rotate", "rebin", "emit_rec", "emit_src", "phase_a_send", "free_a_send", "scan",
     "expand_requests", "free_c_stage", "virtual_particles", "seg_fill", "seg_sort",
-    "phase_b_merge", "hop_counts", "hop_lens", "drop_free", "chemistry", "budget", "knn_build"};
+    "phase_b_merge", "hop_counts", "hop_lens", "drop_free", "chemistry", "budget", "knn_build",
+    "worklist"};
 
 extern "C" rt_status rt_set_profiling(rt_ctx *c, int on) {
     if (!c) return RT_ERR_INVALID;
@@ -215,9 +216,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     }
     c->box_off_h.assign(box_off, box_off + n_boxes + 1);
     c->box_L_h.assign(box_L, box_L + n_boxes);
-    rt_host_axis_set(P.nrc, P.axes_rc);
-    rt_host_axis_set(P.nec, P.axes_ec);
-    for (int k = 0; k < 3 * P.nrc; ++k) P.axes_rcf[k] = (float)P.axes_rc[k];
+    P.ax_rc = P.nrc == 8 ? 0 : 1;
+    P.ax_ec = P.nec == 8 ? 0 : 1;
+    rt_upload_axes();
 
     bool ok = true;
     size_t R = P.fp32 ? 4 : 8;
@@ -283,6 +284,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     }
     for (int f = 0; f < 6; ++f) P.rec[f] = dalloc(c, R * nslot, &ok);
     A(P.bm, unsigned, n * P.kn * P.nf);
+    A(P.revpos, int, n * P.kn);
+    A(P.worklist, int, nkey);
     A(P.emp, unsigned, nkey);
     A(P.touched, int, nkey);
     A(P.reqcnt, int, n + fc);
@@ -679,9 +682,10 @@ __global__ void k_masks(DevPtrs P, int cur, unsigned *out) {
     int nu = s / P.nrc, b = s % P.nrc;
     unsigned a = P.act[cur][i * P.nf + nu];
     unsigned m = 0;
+    const unsigned *bmr = P.bm + (long long)nu * P.n * P.kn;
     if ((a >> b) & 1u)
         for (int k = 0; k < P.kn; ++k)
-            m |= ((P.bm[(i * P.kn + k) * P.nf + nu] >> b) & 1u) << k;
+            m |= ((bmr[P.revpos[i * P.kn + k]] >> b) & 1u) << k;
     out[t] = m;
 }
 

@@ -110,7 +110,8 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     unsigned *occ[2], *act[2];
     // phase-A records (w, dx, dy, dz, clock, eps) and transposed cone bitmaps
     void *rec[6];
-    unsigned *bm;             // [(i * kn + k) * nf + nu]
+    unsigned *bm;             // receiver-ordered cone bitmaps [nu * n * kn + p], p = reverse position
+    int *revpos;              // position of forward entry (i, k) in the reverse lists
     unsigned *emp;            // empty-cone bits [n * nf]
     int *touched;             // hop stamp per (j, nu)
     // requests
@@ -127,16 +128,15 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     double *abs, *absE, *pass;                // [n * nf]
     unsigned long long *fx_abs, *fx_lo, *fx_E;  // [n * nf]: photons (2 words), energy
     long long *cnt;                           // CNT_N counters
-    // constant tables
-    double axes_rc[96], axes_ec[96];
-    float axes_rcf[96];
+    int ax_rc, ax_ec;         // index of the reception / emission direction set in c_axes*
+    int *worklist;            // (particle, nu) keys a hop's receiver side has to visit
 };
 
 // kernel identities for the launch counter and the optional per-kernel timer
 enum {
     KT_ROTATE, KT_REBIN, KT_EMIT_REC, KT_EMIT_SRC, KT_PHASE_A, KT_FREE_A, KT_SCAN, KT_EXPAND,
     KT_FREE_C, KT_VIRTUAL, KT_SEG_FILL, KT_SEG_SORT, KT_PHASE_B, KT_HOP_COUNT, KT_HOP_LENS,
-    KT_DROP, KT_CHEM, KT_BUDGET, KT_KNN, KT_N
+    KT_DROP, KT_CHEM, KT_BUDGET, KT_KNN, KT_WORKLIST, KT_N
 };
 
 struct KStat {
@@ -153,6 +153,7 @@ struct rt_ctx {
     long long *cnt_h = nullptr;   // pinned
     std::vector<void *> allocs;
     bool have_particles = false, have_sources = false, built = false;
+    bool bm_dirty = false;        // cone bitmaps left by rt_assign_cones (cleared before a hop loop)
     int cur = 0;                  // slot buffer holding the current packets
     int fcur = 0;                 // free buffer of the current hop
     long long hop_global = 0;
@@ -183,6 +184,7 @@ rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);
 void rt_host_axis_set(int n, double *out);
+void rt_upload_axes();
 // launch bookkeeping: call kt_begin before and kt_end after the launches of kernel `id`
 void kt_begin(rt_ctx *c, int id, cudaStream_t st);
 void kt_end(rt_ctx *c, int id, cudaStream_t st, int nlaunch = 1);
@@ -258,8 +260,8 @@ __device__ __forceinline__ void rot_apply(const double *R, const double *D, doub
 }
 
 // Transmission cone, exact form: delta . d > 0 and (delta . d)^2 >= (1 - 2/n_tc)^2 |delta|^2
-__device__ __forceinline__ bool cone_exact(int dx, int dy, int dz, double d0, double d1,
-                                           double d2, int ntc) {
+static __device__ __noinline__ bool cone_exact(int dx, int dy, int dz, double d0, double d1,
+                                        double d2, int ntc) {
     if ((dx | dy | dz) == 0) return false;
     double t = xadd(xadd(xmul((double)dx, d0), xmul((double)dy, d1)), xmul((double)dz, d2));
     if (!(t > 0.0)) return false;
@@ -283,13 +285,14 @@ __device__ __forceinline__ bool cone_test(int dx, int dy, int dz, float fx, floa
 
 // Reception cone of direction d at a particle with rotation R: argmax_b (R^T d) . D_b,
 // first maximum on ties.  Exact (FP64) form.
-__device__ inline int bin_exact(const double *R, const double *axes, int nrc, double d0,
-                                double d1, double d2) {
+static __device__ __noinline__ int bin_exact(const double *R, const double *axes, int nrc, double d0,
+                                      double d1, double d2) {
     double e0 = xadd(xadd(xmul(R[0], d0), xmul(R[3], d1)), xmul(R[6], d2));
     double e1 = xadd(xadd(xmul(R[1], d0), xmul(R[4], d1)), xmul(R[7], d2));
     double e2 = xadd(xadd(xmul(R[2], d0), xmul(R[5], d1)), xmul(R[8], d2));
     int best = 0;
     double bs = 0.0;
+#pragma unroll 1
     for (int b = 0; b < nrc; ++b) {
         double sc = xadd(xadd(xmul(e0, axes[3 * b]), xmul(e1, axes[3 * b + 1])),
                          xmul(e2, axes[3 * b + 2]));
@@ -308,6 +311,7 @@ __device__ inline int bin_fast(const float *Rf, const double *Rd, const float *a
     float e2 = __fmaf_rn(Rf[2], f0, __fmaf_rn(Rf[5], f1, Rf[8] * f2));
     float b1 = -3.0f, b2 = -3.0f;
     int best = 0;
+#pragma unroll 1
     for (int b = 0; b < nrc; ++b) {
         float sc = __fmaf_rn(e0, axf[3 * b], __fmaf_rn(e1, axf[3 * b + 1], e2 * axf[3 * b + 2]));
         if (sc > b1) { b2 = b1; b1 = sc; best = b; }

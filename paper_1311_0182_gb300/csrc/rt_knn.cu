@@ -151,6 +151,7 @@ __global__ void k_rev_sort(DevPtrs P) {
     for (int p = a; p < b; ++p) {
         unsigned v = P.rev_ent[p];
         long long f = (long long)(v >> 5) * P.kn + (v & 31);
+        P.revpos[f] = p;
         P.rdx[p] = P.fdx[f];
         P.rdy[p] = P.fdy[f];
         P.rdz[p] = P.fdz[f];

@@ -21,6 +21,21 @@
 static const double C_LIGHT = 2.99792458e10;
 static const double EV_ERG = 1.602176634e-12;
 
+// the two isotropic direction sets (index 0: 8 directions, 1: 32), FP64 and FP32 copies
+__constant__ double c_axd[2][96];
+__constant__ float c_axf[2][96];
+
+void rt_upload_axes() {
+    double d[2][96] = {{0}};
+    float f[2][96];
+    rt_host_axis_set(8, d[0]);
+    rt_host_axis_set(32, d[1]);
+    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < 96; ++k) f[a][k] = (float)d[a][k];
+    cudaMemcpyToSymbol(c_axd, d, sizeof(d));
+    cudaMemcpyToSymbol(c_axf, f, sizeof(f));
+}
+
 template <typename Real> struct Slots {
     Real *N, *X, *Y, *Z, *C, *E;
     __device__ __forceinline__ Slots(const DevPtrs &P, int b) {
@@ -98,7 +113,7 @@ __global__ void k_rebin(DevPtrs P, int cur) {
         if (!((o >> b) & 1) || !(oN[b] > Real(0))) continue;
         Real d0, d1, d2;
         packet_dir(oX[b], oY[b], oZ[b], d0, d1, d2);
-        int nb = bin_fast(Rf, Rd, P.axes_rcf, P.axes_rc, NRC, (double)d0, (double)d1, (double)d2);
+        int nb = bin_fast(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC, (double)d0, (double)d1, (double)d2);
         nN[nb] += oN[b]; nX[nb] += oX[b]; nY[nb] += oY[b]; nZ[nb] += oZ[b]; nE[nb] += oE[b];
     }
     unsigned no = 0;
@@ -146,7 +161,7 @@ __global__ void k_emit_rec(DevPtrs P, int cur) {
     const double *R = P.R + i * 9;
     for (int bb = 0; bb < NRC; ++bb) {
         double A[3];
-        rot_apply(R, P.axes_rc + 3 * bb, A);
+        rot_apply(R, c_axd[P.ax_rc] + 3 * bb, A);
         long long s = s0 + bb;
         if ((o >> bb) & 1) {
             S.N[s] += e; S.X[s] += e * (Real)A[0]; S.Y[s] += e * (Real)A[1];
@@ -176,7 +191,7 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
     int b = P.sbox[j];
     double N = __ddiv_rn(__dmul_rn(P.ndot[(long long)j * P.nfs + nu], P.dt_em), (double)P.nec);
     double d[3];
-    rot_apply(P.Rs + ((long long)j * P.K + k) * 9, P.axes_ec + 3 * e, d);
+    rot_apply(P.Rs + ((long long)j * P.K + k) * 9, c_axd[P.ax_ec] + 3 * e, d);
     F.box[p] = b;
     F.qx[p] = P.sqx[j]; F.qy[p] = P.sqy[j]; F.qz[p] = P.sqz[j];
     for (int a = 0; a < P.kn; ++a) F.nbr[p * P.kn + a] = P.snbr[(long long)j * P.kn + a];
@@ -209,12 +224,14 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
             if (lane == 0) P.reqcnt[i] = 0;
             continue;
         }
-        int nb = 0, dx = 0, dy = 0, dz = 0;
+        int nb = 0, dx = 0, dy = 0, dz = 0, rp = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f;
         bool valid = lane < P.kn;
+        long long nrev = P.n * P.kn;
         if (valid) {
             long long f = i * P.kn + lane;
             nb = P.nbr[f];
+            rp = P.revpos[f];
             fx = P.fdx[f]; fy = P.fdy[f]; fz = P.fdz[f];
             dx = (int)fx; dy = (int)fy; dz = (int)fz;
         }
@@ -248,7 +265,7 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
                     empw |= 1u << b;
                 }
             }
-            if (a && valid) P.bm[(i * P.kn + lane) * P.nf + nu] = bmw;
+            if (bmw) P.bm[(long long)nu * nrev + rp] = bmw;   // the receiver clears it
             if (lane == 0) P.emp[i * P.nf + nu] = empw;
             nreq += __popc(empw);
         }
@@ -322,8 +339,8 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         Real tau = ((Real)P.sigma[nu] * ((Real *)P.nHIr)[j]) * l;
         Real A, T;
         split_absorbed<Real>(w, tau, A, T);
-        int bt = bin_fast(P.Rf + j * 9, P.R + j * 9, P.axes_rcf, P.axes_rc, NRC, (double)d0,
-                          (double)d1, (double)d2);
+        int bt = bin_fast(P.Rf + j * 9, P.R + j * 9, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC,
+                          (double)d0, (double)d1, (double)d2);
         long long key = j * P.nf + nu;
         P.st_key[s] = (int)key;
         P.st_bin[s] = bt;
@@ -413,8 +430,11 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
         }
         double dd0 = (double)d0, dd1 = (double)d1, dd2 = (double)d2;
         // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
-        long long H = (long long)floor(sqrt((double)h2));
+        long long H = 0;
+        if (lane == 0) H = (long long)floor(sqrt((double)h2));
+        H = __shfl_sync(FULLMASK, H, 0);
         unsigned long long span = (unsigned long long)(2 * H + 1);
+        float cf = 1.0f - 2.0f / (float)P.ntc;
         long long Dx = 0, Dy = 0, Dz = 0;
         bool found = false;
         for (int a0 = 0; a0 < 64 && !found; a0 += 32) {
@@ -425,7 +445,9 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             long long ey = (long long)(((unsigned long long)u.y * span) >> 32) - H;
             long long ez = (long long)(((unsigned long long)u.z * span) >> 32) - H;
             long long r2 = ex * ex + ey * ey + ez * ez;
-            bool ok = r2 > 0 && r2 <= h2 && cone_exact((int)ex, (int)ey, (int)ez, dd0, dd1, dd2, P.ntc);
+            bool ok = r2 > 0 && r2 <= h2 &&
+                      cone_test((int)ex, (int)ey, (int)ez, (float)ex, (float)ey, (float)ez, dd0,
+                                dd1, dd2, cf, P.ntc);
             unsigned m = __ballot_sync(FULLMASK, ok);
             if (m) {
                 int src = __ffs(m) - 1;
@@ -556,174 +578,205 @@ __global__ void k_seg_sort(DevPtrs P) {
     }
 }
 
+#ifndef PHASEB_MINB
+#define PHASEB_MINB 3
+#endif
 // Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
 // cone.  Contributions are computed in parallel and merged in their fixed order by a
 // broadcast loop (the lane owning the target cone adds).
+// The receiver groups with work this hop: receivers touched by a gas sender, receivers of
+// staged free-packet contributions, and particles holding waiting packets.  Block-level
+// compaction with one atomic per block; the order of the list does not matter.
+__global__ void __launch_bounds__(256) k_worklist(DevPtrs P, int cur, int stamp, int *wl_n) {
+    __shared__ int wcount[8], wbase[8], bbase;
+    long long nkey = P.n * P.nf;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x; k0 < nkey;
+         k0 += (long long)gridDim.x * blockDim.x) {
+        long long key = k0 + threadIdx.x;
+        bool f = false;
+        if (key < nkey)
+            f = P.touched[key] == stamp || P.seg_cnt[key] > 0 ||
+                (P.occ[cur][key] & ~P.act[cur][key]) != 0u;
+        unsigned m = __ballot_sync(FULLMASK, f);
+        if (lane == 0) wcount[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int k = 0; k < 8; ++k) { wbase[k] = t; t += wcount[k]; }
+            bbase = t ? atomicAdd(wl_n, t) : 0;
+        }
+        __syncthreads();
+        if (f) P.worklist[bbase + wbase[w] + __popc(m & ((1u << lane) - 1u))] = (int)key;
+        __syncthreads();
+    }
+}
+
+#ifndef PHASEB_MINB
+#define PHASEB_MINB 3
+#endif
+// Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
+// cone.  Contributions are computed in parallel and merged in their fixed order by a
+// broadcast loop (the lane owning the target cone adds).  Groups come from the work list;
+// the next buffer's occupancy words were cleared before the launch.
 template <typename Real, int G>
-__global__ void __launch_bounds__(256) k_phaseB(DevPtrs P, int cur, int stamp) {
-    long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+__global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur, int stamp, const int *wl_n) {
+    // contributions of the current chunk, one per lane: bin and 6 values (T, T d, T clock, T eps)
+    __shared__ Real sv[6][256];
+    __shared__ int sb[256];
     int gl = threadIdx.x & (G - 1);
+    int gbase = threadIdx.x - gl;               // first thread of this group in the block
     unsigned base = (threadIdx.x & 31) & ~(unsigned)(G - 1);
     unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << base);
-    if (gid >= P.n * P.nf) return;
-    long long key = gid;
-    long long j = gid / P.nf;
-    int nu = (int)(gid % P.nf);
+    long long ng = *wl_n;
+    long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    long long gstride = ((long long)gridDim.x * blockDim.x) / G;
     int nxt = cur ^ 1;
-    unsigned o_occ = P.occ[cur][key], o_act = P.act[cur][key];
-    unsigned park = o_occ & ~o_act;
-    bool touched = P.touched[key] == stamp;
-    int fc = P.seg_cnt[key];
-    if (!touched && park == 0u && fc == 0) {
-        if (gl == 0) { P.occ[nxt][key] = 0u; P.act[nxt][key] = 0u; }
-        return;
-    }
-    Slots<Real> So(P, cur), Sn(P, nxt);
-    long long sidx = j * P.S + (long long)nu * G + gl;
-    KSum<Real> aN, aX, aY, aZ, aC, aE, sA, sAE, sW;
-    if ((park >> gl) & 1u) {
-        aN.init(So.N[sidx]); aX.init(So.X[sidx]); aY.init(So.Y[sidx]);
-        aZ.init(So.Z[sidx]); aC.init(So.C[sidx]); aE.init(So.E[sidx]);
-    } else {
-        aN.init(Real(0)); aX.init(Real(0)); aY.init(Real(0));
-        aZ.init(Real(0)); aC.init(Real(0)); aE.init(Real(0));
-    }
-    sA.init(Real(0)); sAE.init(Real(0)); sW.init(Real(0));
-    int box = P.pbox[j];
-    if (touched) {
-        Real u = (Real)P.box_u[box];
-        Real sig_nhi = (Real)P.sigma[nu] * ((Real *)P.nHIr)[j];
-        float Rf[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) Rf[a] = P.Rf[j * 9 + a];
-        const double *Rd = P.R + j * 9;
-        const Real *rw = (const Real *)P.rec[0], *rx = (const Real *)P.rec[1],
-                   *ry = (const Real *)P.rec[2], *rz = (const Real *)P.rec[3],
-                   *rc = (const Real *)P.rec[4], *re = (const Real *)P.rec[5];
-        int e0 = P.rev_off[j], e1 = P.rev_off[j + 1];
-        for (int eb = e0; eb < e1; eb += G) {
-            int e = eb + gl;
-            unsigned word = 0u;
-            int si = 0;
-            float fx = 0.f, fy = 0.f, fz = 0.f;
-            if (e < e1) {
-                unsigned ent = P.rev_ent[e];
-                si = (int)(ent >> 5);
-                int k = (int)(ent & 31u);
-                unsigned a = P.act[cur][(long long)si * P.nf + nu];
-                if (a) word = a & P.bm[((long long)si * P.kn + k) * P.nf + nu];
-                fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
-            }
-            int cw = __popc(word);
-            int incl = cw;
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                int v = __shfl_up_sync(gmask, incl, o, G);
-                if (gl >= o) incl += v;
-            }
-            int total = __shfl_sync(gmask, incl, G - 1, G);
-            int excl = incl - cw;
-            for (int cb = 0; cb < total; cb += G) {
-                int c = cb + gl;
-                int lo = 0, hi = G - 1;
-#pragma unroll
-                for (int st = G; st > 1; st >>= 1) {
-                    int mid = (lo + hi + 1) >> 1;
-                    int em = __shfl_sync(gmask, excl, mid, G);
-                    if (em <= c) lo = mid; else hi = mid - 1;
+    for (long long gi = g0; gi < ng; gi += gstride) {
+        long long key = P.worklist[gi];
+        long long j = key / P.nf;
+        int nu = (int)(key % P.nf);
+        unsigned park = P.occ[cur][key] & ~P.act[cur][key];
+        bool touched = P.touched[key] == stamp;
+        int fc = P.seg_cnt[key];
+        Slots<Real> So(P, cur), Sn(P, nxt);
+        long long sidx = j * P.S + (long long)nu * G + gl;
+        KSum<Real> aN, aX, aY, aZ, aC, aE, sA, sAE, sW;
+        if ((park >> gl) & 1u) {
+            aN.init(So.N[sidx]); aX.init(So.X[sidx]); aY.init(So.Y[sidx]);
+            aZ.init(So.Z[sidx]); aC.init(So.C[sidx]); aE.init(So.E[sidx]);
+        } else {
+            aN.init(Real(0)); aX.init(Real(0)); aY.init(Real(0));
+            aZ.init(Real(0)); aC.init(Real(0)); aE.init(Real(0));
+        }
+        sA.init(Real(0)); sAE.init(Real(0)); sW.init(Real(0));
+        int box = P.pbox[j];
+        // merge this chunk's staged contributions (lanes gbase .. gbase + nbt - 1) in order
+        auto merge_chunk = [&](int nbt) {
+            __syncwarp(gmask);
+            for (int t2 = 0; t2 < nbt; ++t2) {
+                if (sb[gbase + t2] == gl) {
+                    aN.add(sv[0][gbase + t2]); aX.add(sv[1][gbase + t2]);
+                    aY.add(sv[2][gbase + t2]); aZ.add(sv[3][gbase + t2]);
+                    aC.add(sv[4][gbase + t2]); aE.add(sv[5][gbase + t2]);
                 }
-                int o_ex = __shfl_sync(gmask, excl, lo, G);
-                unsigned o_w = __shfl_sync(gmask, word, lo, G);
-                int o_si = __shfl_sync(gmask, si, lo, G);
-                float ofx = __shfl_sync(gmask, fx, lo, G);
-                float ofy = __shfl_sync(gmask, fy, lo, G);
-                float ofz = __shfl_sync(gmask, fz, lo, G);
-                int bt = 0;
-                Real v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
-                if (c < total) {
-                    int bsrc = __fns(o_w, 0, c - o_ex + 1);
-                    long long ridx = (long long)o_si * P.S + (long long)nu * G + bsrc;
-                    Real w = rw[ridx], d0 = rx[ridx], d1 = ry[ridx], d2 = rz[ridx];
-                    Real clk = rc[ridx], eps = re[ridx];
-                    Real t = (Real)ofx * d0 + (Real)ofy * d1 + (Real)ofz * d2;
-                    Real l = t * u;
-                    Real tau = sig_nhi * l;
-                    Real A, T;
-                    split_absorbed<Real>(w, tau, A, T);
-                    sA.add(A);
-                    sAE.add(A * eps);
-                    sW.add(w);
-                    bt = bin_fast(Rf, Rd, P.axes_rcf, P.axes_rc, G, (double)d0, (double)d1,
-                                  (double)d2);
-                    v0 = T; v1 = T * d0; v2 = T * d1; v3 = T * d2;
-                    v4 = T * (clk + l / (Real)C_LIGHT);
-                    v5 = T * eps;
-                }
-                int nbt = min(G, total - cb);
-                for (int t2 = 0; t2 < nbt; ++t2) {
-                    int b_t = __shfl_sync(gmask, bt, t2, G);
-                    Real x0 = __shfl_sync(gmask, v0, t2, G), x1 = __shfl_sync(gmask, v1, t2, G),
-                         x2 = __shfl_sync(gmask, v2, t2, G), x3 = __shfl_sync(gmask, v3, t2, G),
-                         x4 = __shfl_sync(gmask, v4, t2, G), x5 = __shfl_sync(gmask, v5, t2, G);
-                    if (gl == b_t) {
-                        aN.add(x0); aX.add(x1); aY.add(x2); aZ.add(x3); aC.add(x4); aE.add(x5);
+            }
+            __syncwarp(gmask);
+        };
+        if (touched) {
+            Real u = (Real)P.box_u[box];
+            Real sig_nhi = (Real)P.sigma[nu] * ((Real *)P.nHIr)[j];
+            const float *Rf = P.Rf + j * 9;
+            const double *Rd = P.R + j * 9;
+            const Real *rw = (const Real *)P.rec[0], *rx = (const Real *)P.rec[1],
+                       *ry = (const Real *)P.rec[2], *rz = (const Real *)P.rec[3],
+                       *rc = (const Real *)P.rec[4], *re = (const Real *)P.rec[5];
+            int e0 = P.rev_off[j], e1 = P.rev_off[j + 1];
+            unsigned *bmr = P.bm + (long long)nu * P.n * P.kn;
+            for (int eb = e0; eb < e1; eb += G) {
+                int e = eb + gl;
+                unsigned word = 0u;
+                int si = 0;
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                if (e < e1) {
+                    word = bmr[e];
+                    if (word) {
+                        bmr[e] = 0u;
+                        si = (int)(P.rev_ent[e] >> 5);
+                        fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
                     }
                 }
-            }
-        }
-    }
-    if (fc > 0) {
-        int so = P.seg_off[key];
-        Real *const *V = (Real *const *)P.st_v;
-        for (int cb = 0; cb < fc; cb += G) {
-            int c = cb + gl;
-            int bt = 0;
-            Real v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
-            if (c < fc) {
-                int s = P.seg_idx[so + c];
-                bt = P.st_bin[s];
-                v0 = V[0][s]; v1 = V[1][s]; v2 = V[2][s]; v3 = V[3][s]; v4 = V[4][s]; v5 = V[5][s];
-                sA.add(V[6][s]);
-                sAE.add(V[7][s]);
-                sW.add(V[8][s]);
-            }
-            int nbt = min(G, fc - cb);
-            for (int t2 = 0; t2 < nbt; ++t2) {
-                int b_t = __shfl_sync(gmask, bt, t2, G);
-                Real x0 = __shfl_sync(gmask, v0, t2, G), x1 = __shfl_sync(gmask, v1, t2, G),
-                     x2 = __shfl_sync(gmask, v2, t2, G), x3 = __shfl_sync(gmask, v3, t2, G),
-                     x4 = __shfl_sync(gmask, v4, t2, G), x5 = __shfl_sync(gmask, v5, t2, G);
-                if (gl == b_t) {
-                    aN.add(x0); aX.add(x1); aY.add(x2); aZ.add(x3); aC.add(x4); aE.add(x5);
+                int cw = __popc(word);
+                int incl = cw;
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    int v = __shfl_up_sync(gmask, incl, o, G);
+                    if (gl >= o) incl += v;
+                }
+                int total = __shfl_sync(gmask, incl, G - 1, G);
+                int excl = incl - cw;
+                for (int cb = 0; cb < total; cb += G) {
+                    int c = cb + gl;
+                    int lo = 0, hi = G - 1;
+#pragma unroll
+                    for (int st = G; st > 1; st >>= 1) {
+                        int mid = (lo + hi + 1) >> 1;
+                        int em = __shfl_sync(gmask, excl, mid, G);
+                        if (em <= c) lo = mid; else hi = mid - 1;
+                    }
+                    int o_ex = __shfl_sync(gmask, excl, lo, G);
+                    unsigned o_w = __shfl_sync(gmask, word, lo, G);
+                    int o_si = __shfl_sync(gmask, si, lo, G);
+                    float ofx = __shfl_sync(gmask, fx, lo, G);
+                    float ofy = __shfl_sync(gmask, fy, lo, G);
+                    float ofz = __shfl_sync(gmask, fz, lo, G);
+                    if (c < total) {
+                        int bsrc = __fns(o_w, 0, c - o_ex + 1);
+                        long long ridx = (long long)o_si * P.S + (long long)nu * G + bsrc;
+                        Real w = rw[ridx], d0 = rx[ridx], d1 = ry[ridx], d2 = rz[ridx];
+                        Real clk = rc[ridx], eps = re[ridx];
+                        Real t = (Real)ofx * d0 + (Real)ofy * d1 + (Real)ofz * d2;
+                        Real l = t * u;
+                        Real A, T;
+                        split_absorbed<Real>(w, sig_nhi * l, A, T);
+                        sA.add(A);
+                        sAE.add(A * eps);
+                        sW.add(w);
+                        sb[threadIdx.x] = bin_fast(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], G,
+                                                   (double)d0, (double)d1, (double)d2);
+                        sv[0][threadIdx.x] = T;
+                        sv[1][threadIdx.x] = T * d0;
+                        sv[2][threadIdx.x] = T * d1;
+                        sv[3][threadIdx.x] = T * d2;
+                        sv[4][threadIdx.x] = T * (clk + l / (Real)C_LIGHT);
+                        sv[5][threadIdx.x] = T * eps;
+                    }
+                    merge_chunk(min(G, total - cb));
                 }
             }
         }
-    }
-    Real N = aN.get();
-    bool occ = N > Real(0);
-    bool act = occ && (aC.get() / N < (Real)P.dt);
-    unsigned lmask = (G == 32) ? FULLMASK : ((1u << G) - 1u);
-    unsigned bo = (__ballot_sync(gmask, occ) >> base) & lmask;
-    unsigned ba = (__ballot_sync(gmask, act) >> base) & lmask;
-    if (occ) {
-        Sn.N[sidx] = N; Sn.X[sidx] = aX.get(); Sn.Y[sidx] = aY.get();
-        Sn.Z[sidx] = aZ.get(); Sn.C[sidx] = aC.get(); Sn.E[sidx] = aE.get();
-    }
-    Real a = sA.get(), ae = sAE.get(), w = sW.get();
+        if (fc > 0) {
+            int so = P.seg_off[key];
+            Real *const *V = (Real *const *)P.st_v;
+            for (int cb = 0; cb < fc; cb += G) {
+                int c = cb + gl;
+                if (c < fc) {
+                    int s = P.seg_idx[so + c];
+                    sb[threadIdx.x] = P.st_bin[s];
+                    for (int f = 0; f < 6; ++f) sv[f][threadIdx.x] = V[f][s];
+                    sA.add(V[6][s]);
+                    sAE.add(V[7][s]);
+                    sW.add(V[8][s]);
+                }
+                merge_chunk(min(G, fc - cb));
+            }
+        }
+        Real N = aN.get();
+        bool occ = N > Real(0);
+        bool act = occ && (aC.get() / N < (Real)P.dt);
+        unsigned lmask = (G == 32) ? FULLMASK : ((1u << G) - 1u);
+        unsigned bo = (__ballot_sync(gmask, occ) >> base) & lmask;
+        unsigned ba = (__ballot_sync(gmask, act) >> base) & lmask;
+        if (occ) {
+            Sn.N[sidx] = N; Sn.X[sidx] = aX.get(); Sn.Y[sidx] = aY.get();
+            Sn.Z[sidx] = aZ.get(); Sn.C[sidx] = aC.get(); Sn.E[sidx] = aE.get();
+        }
+        Real a = sA.get(), ae = sAE.get(), w = sW.get();
 #pragma unroll
-    for (int o = G >> 1; o > 0; o >>= 1) {
-        a += __shfl_down_sync(gmask, a, o, G);
-        ae += __shfl_down_sync(gmask, ae, o, G);
-        w += __shfl_down_sync(gmask, w, o, G);
-    }
-    if (gl == 0) {
-        P.occ[nxt][key] = bo;
-        P.act[nxt][key] = ba;
-        if (touched || fc > 0) {
-            double nm = P.norm[box];
-            P.abs[key] += (double)a * nm;
-            P.absE[key] += (double)ae * nm * P.eunit;
-            P.pass[key] += (double)w * nm;
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            a += __shfl_down_sync(gmask, a, o, G);
+            ae += __shfl_down_sync(gmask, ae, o, G);
+            w += __shfl_down_sync(gmask, w, o, G);
+        }
+        if (gl == 0) {
+            P.occ[nxt][key] = bo;
+            P.act[nxt][key] = ba;
+            if (touched || fc > 0) {
+                double nm = P.norm[box];
+                P.abs[key] += (double)a * nm;
+                P.absE[key] += (double)ae * nm * P.eunit;
+                P.pass[key] += (double)w * nm;
+            }
         }
     }
 }
@@ -848,11 +901,17 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         return rt_cuda_check(c, cudaGetLastError(), "emit");
     }
     if (part == 3) {  // cone masks of the held packets only (inspection)
+        cudaMemsetAsync(P.bm, 0, sizeof(unsigned) * n * P.kn * P.nf, st);
+        c->bm_dirty = true;
         int stamp = (int)(++c->hop_global);
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur, stamp)));
         return rt_cuda_check(c, cudaGetLastError(), "cone masks");
     }
     // part 4: the hop loop
+    if (c->bm_dirty) {
+        cudaMemsetAsync(P.bm, 0, sizeof(unsigned) * n * P.kn * P.nf, st);
+        c->bm_dirty = false;
+    }
     cudaMemsetAsync(&P.cnt[CNT_VIRT], 0, 2 * sizeof(long long), st);
     cudaMemsetAsync(&P.cnt[CNT_GAS], 0, sizeof(long long), st);
     rt_status status = RT_OK;
@@ -883,7 +942,11 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, st)));
         LAUNCH(KT_SEG_FILL, 1, (k_seg_fill<<<(unsigned)((P.ST_cap + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
         LAUNCH(KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P)));
-        LAUNCH(KT_PHASE_B, 1, (k_phaseB<Real, NRC><<<(unsigned)((nkey * NRC + tb - 1) / tb), tb, 0, st>>>(P, cur, stamp)));
+        cudaMemsetAsync(H.lens + 4, 0, sizeof(int), st);
+        LAUNCH(KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, st>>>(P, cur, stamp, H.lens + 4)));
+        cudaMemsetAsync(P.occ[nxt], 0, sizeof(unsigned) * nkey, st);
+        cudaMemsetAsync(P.act[nxt], 0, sizeof(unsigned) * nkey, st);
+        LAUNCH(KT_PHASE_B, 1, (k_phaseB<Real, NRC><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, st>>>(P, cur, stamp, H.lens + 4)));
         LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, nxt, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 2)));
         c->cur = nxt;
