@@ -162,7 +162,7 @@ def run_ours(args):
            "data": "synthetic", "config": workload_config(args, wl), "gpu_launches": launches,
            "clocks": clocks}
     # roofline of the dominant kernel
-    out["roofline"] = roofline(ctx, kt)
+    out["roofline"] = roofline(ctx, kt, ms, args)
     out["stats_last_step"] = st
     out["budget_closure"] = float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])
     if not args.no_e2e:
@@ -175,19 +175,61 @@ def run_ours(args):
     return out if rank == 0 else None
 
 
-def roofline(ctx, kt):
+MODELLED = ("phase_b_merge", "virtual_particles", "phase_a_send")
+
+
+def source_hash() -> str:
+    """Hash of the CUDA sources: a committed ncu traffic figure is valid only for this source."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1311_0182_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, n_side: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to this workload
+    by particle count, or None when the summary belongs to other source code."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for line in lines:
+        parts = line.strip().strip("|").split("|")
+        parts = [p.strip() for p in parts]
+        if len(parts) >= 4 and parts[0] == kernel:
+            try:
+                nbytes, n_cap, src = float(parts[1]), int(parts[2]), parts[3]
+            except ValueError:
+                continue
+            if src != source_hash():
+                return None
+            return nbytes * (n_side ** 3) / n_cap
+    return None
+
+
+def roofline(ctx, kt, ms_step_total, args):
     peak, kind = peaks()
     if not kt:
         return None
     name = max(kt, key=lambda k: kt[k]["ms"])
+    if name not in MODELLED:
+        name = max(MODELLED, key=lambda k: kt.get(k, {"ms": 0})["ms"])
     k = kt[name]
     ms = k["ms"] / max(k["launches"], 1)
     B = k["bytes"] / max(k["launches"], 1)
     ach = B / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "peak_kind": kind, "traffic": None,
+            "frac": ach / peak, "peak_kind": f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else kind,
+            "traffic": committed_traffic(name, args.n_side),
             "algorithmic_bytes_per_launch": B, "ms_per_launch": ms, "launches": k["launches"],
-            "share_of_step": None, "all_kernels": kt}
+            "share_of_step": k["ms"] / ms_step_total if ms_step_total else None,
+            "all_kernels": {n: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                                "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] and v["bytes"] else None}
+                            for n, v in kt.items()}}
 
 
 def e2e(args, ctx, wl, stream, step, x0, T0):

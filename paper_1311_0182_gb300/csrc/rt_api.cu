@@ -254,7 +254,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.Nrec, double, n); A(P.epsrec, double, n); A(P.nHI, double, n); A(P.phot, double, n);
     P.nHIr = dalloc(c, R * n, &ok);
     P.Vr = dalloc(c, R * n, &ok);
-    A(P.dep_s, double, n);
+    P.dep_s = dalloc(c, R * n, &ok);
     P.depE_s = dalloc(c, R * n, &ok);
     A(P.sbox, int, n_src + 1);
     A(P.sqx, int, n_src + 1); A(P.sqy, int, n_src + 1); A(P.sqz, int, n_src + 1);

@@ -35,7 +35,13 @@ enum {
     CNT_SUB = 8,        // chemistry subcycles
     CNT_FLOOR = 9,      // subcycle-floor hits
     CNT_NFREE = 10,     // free packets of the current hop
-    CNT_N = 16
+    CNT_ACTP = 11,      // particles with a packet able to move, summed over hops
+    CNT_ACTS = 12,      // packets able to move (slots), summed over hops
+    CNT_GCON = 13,      // gas-to-gas contributions, summed over hops
+    CNT_STG = 14,       // staged free-packet contributions, summed over hops
+    CNT_WLS = 15,       // receiver work-list entries, summed over hops
+    CNT_OUT = 16,       // occupied slots written by the receiver side, summed over hops
+    CNT_N = 24
 };
 
 // fixed-point scales of the virtual-particle deposits (relative to the receiver's neutral
@@ -90,7 +96,7 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     int *pbox, *qx, *qy, *qz;
     double *nH, *NH, *xHI, *T, *Nrec, *epsrec, *nHI, *phot;
     void *nHIr, *Vr, *depE_s;  // Real [n]
-    double *dep_s;             // [n] fixed-point scale of photon deposits
+    void *dep_s;               // Real [n]: fixed-point scale of photon deposits
     // sources
     int *sbox, *sqx, *sqy, *sqz;
     double *ndot, *sigma, *eps;  // [ns*nfs], [nf], [nf]
@@ -156,6 +162,7 @@ struct rt_ctx {
     bool bm_dirty = false;        // cone bitmaps left by rt_assign_cones (cleared before a hop loop)
     int cur = 0;                  // slot buffer holding the current packets
     int fcur = 0;                 // free buffer of the current hop
+    long long nfree_h = 0;        // free packets of the current hop (host copy)
     long long hop_global = 0;
     long long stats[8] = {0};
     std::string err;
@@ -273,14 +280,17 @@ static __device__ __noinline__ bool cone_exact(int dx, int dy, int dz, double d0
 // Fast FP32 test with a guard band; falls back to the exact test inside the band.  The
 // FP32 cosine estimate is within ~1e-6 of the exact value, far inside the 2e-5 band.
 #define CONE_BAND 2e-5f
+// (the direction comes in the packet's own precision; conversions to FP64 run on the FP64
+// pipe, so they happen only inside the band)
+template <typename Real>
 __device__ __forceinline__ bool cone_test(int dx, int dy, int dz, float fx, float fy, float fz,
-                                          double d0, double d1, double d2, float cf, int ntc) {
+                                          Real d0, Real d1, Real d2, float cf, int ntc) {
     if ((dx | dy | dz) == 0) return false;
     float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
     float cs = __fmaf_rn(fx, (float)d0, __fmaf_rn(fy, (float)d1, fz * (float)d2)) * rsqrtf(r2);
     if (cs > cf + CONE_BAND) return true;
     if (cs < cf - CONE_BAND) return false;
-    return cone_exact(dx, dy, dz, d0, d1, d2, ntc);
+    return cone_exact(dx, dy, dz, (double)d0, (double)d1, (double)d2, ntc);
 }
 
 // Reception cone of direction d at a particle with rotation R: argmax_b (R^T d) . D_b,
@@ -303,8 +313,9 @@ static __device__ __noinline__ int bin_exact(const double *R, const double *axes
 
 #define BIN_BAND 2e-5f
 // Fast FP32 reception cone with a guard band on the margin between the two best scores.
+template <typename Real>
 __device__ inline int bin_fast(const float *Rf, const double *Rd, const float *axf,
-                               const double *axd, int nrc, double d0, double d1, double d2) {
+                               const double *axd, int nrc, Real d0, Real d1, Real d2) {
     float f0 = (float)d0, f1 = (float)d1, f2 = (float)d2;
     float e0 = __fmaf_rn(Rf[0], f0, __fmaf_rn(Rf[3], f1, Rf[6] * f2));
     float e1 = __fmaf_rn(Rf[1], f0, __fmaf_rn(Rf[4], f1, Rf[7] * f2));
@@ -318,7 +329,7 @@ __device__ inline int bin_fast(const float *Rf, const double *Rd, const float *a
         else if (sc > b2) b2 = sc;
     }
     if (b1 - b2 > BIN_BAND) return best;
-    return bin_exact(Rd, axd, nrc, d0, d1, d2);
+    return bin_exact(Rd, axd, nrc, (double)d0, (double)d1, (double)d2);
 }
 
 // M4 cubic spline of support 1 (unnormalised)
@@ -353,6 +364,23 @@ __device__ __forceinline__ void split_absorbed(Real N, Real tau, Real &A, Real &
         T = N * rt_exp<Real>(-tau);
         A = N - T;
     }
+}
+
+// Split a photon deposit, already scaled to units of 2^-40 N_HI, into the two fixed-point
+// words (units 1 and 2^-32).  Returns false when the value is outside the accumulator range.
+__device__ __forceinline__ bool fx_split(double fa, unsigned long long &qh, unsigned long long &ql) {
+    if (!(fa < 4.0e18)) return false;
+    double hi = floor(fa);
+    qh = (unsigned long long)hi;
+    ql = (unsigned long long)llrint((fa - hi) * 4294967296.0);
+    return true;
+}
+__device__ __forceinline__ bool fx_split(float fa, unsigned long long &qh, unsigned long long &ql) {
+    if (!(fa < 4.0e18f)) return false;
+    float hi = floorf(fa);
+    qh = __float2ull_rz(hi);
+    ql = __float2ull_rn((fa - hi) * 4294967296.0f);
+    return true;
 }
 
 // Kahan-compensated accumulator (FP32 path); plain sums for FP64

@@ -16,6 +16,8 @@
 //      contributions, attenuates, picks the reception cone, and merges in a fixed order
 //      (sender, slot); then the staged free-packet contributions in (packet, neighbour) order.
 //      No floating-point atomics: every sum has one fixed order.
+#include <algorithm>
+
 #include "rt_knn.cuh"
 
 static const double C_LIGHT = 2.99792458e10;
@@ -113,7 +115,7 @@ __global__ void k_rebin(DevPtrs P, int cur) {
         if (!((o >> b) & 1) || !(oN[b] > Real(0))) continue;
         Real d0, d1, d2;
         packet_dir(oX[b], oY[b], oZ[b], d0, d1, d2);
-        int nb = bin_fast(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC, (double)d0, (double)d1, (double)d2);
+        int nb = bin_fast<Real>(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC, d0, d1, d2);
         nN[nb] += oN[b]; nX[nb] += oX[b]; nY[nb] += oY[b]; nZ[nb] += oZ[b]; nE[nb] += oE[b];
     }
     unsigned no = 0;
@@ -146,7 +148,7 @@ __global__ void k_emit_rec(DevPtrs P, int cur) {
     ((Real *)P.nHIr)[i] = (Real)nHI;
     ((Real *)P.Vr)[i] = (Real)(NH / nH / P.vunit[b]);   // volume in the box's volume unit
     double NHI = x * NH;
-    P.dep_s[i] = NHI > 0.0 ? FX_ABS_SCALE * nm / NHI : 0.0;
+    ((Real *)P.dep_s)[i] = NHI > 0.0 ? (Real)(FX_ABS_SCALE * nm / NHI) : Real(0);
     ((Real *)P.depE_s)[i] = NHI > 0.0 ? (Real)(FX_E_SCALE * nm * P.eunit / (NHI * EV_ERG)) : Real(0);
     double Nr = P.Nrec[i];
     if (!(Nr > 0.0)) return;
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
     Real *rw = (Real *)P.rec[0], *rx = (Real *)P.rec[1], *ry = (Real *)P.rec[2],
          *rz = (Real *)P.rec[3], *rc = (Real *)P.rec[4], *re = (Real *)P.rec[5];
     float cf = 1.0f - 2.0f / (float)P.ntc;
+    long long ncon = 0;
     for (long long i = w0; i < P.n; i += nw) {
         unsigned aw = (lane < P.nf) ? P.act[cur][i * P.nf + lane] : 0u;
         if (__ballot_sync(FULLMASK, aw != 0u) == 0u) {
@@ -246,10 +249,10 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
                 Real N = S.N[s];
                 Real d0, d1, d2;
                 packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
-                bool in = valid && cone_test(dx, dy, dz, fx, fy, fz, (double)d0, (double)d1,
-                                             (double)d2, cf, P.ntc);
+                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, d0, d1, d2, cf, P.ntc);
                 unsigned m = __ballot_sync(FULLMASK, in);
                 int cm = __popc(m);
+                ncon += cm;
                 if (cm > 0) {
                     if (lane == 0) {
                         rw[s] = N / (Real)cm;
@@ -271,6 +274,7 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
         }
         if (lane == 0) P.reqcnt[i] = nreq;
     }
+    if (lane == 0 && ncon) atomicAdd((unsigned long long *)&P.cnt[CNT_GCON], (unsigned long long)ncon);
 }
 
 // Free packets: cone membership over their own neighbour lists.
@@ -289,13 +293,12 @@ __global__ void __launch_bounds__(256) k_freeA(DevPtrs P, int fcur, const int *l
             if (lane == 0) { fmask[f] = 0u; stcnt[f] = 0; P.reqcnt[P.n + f] = 0; }
             continue;
         }
-        double d0 = (double)((Real *)F.dx)[f], d1 = (double)((Real *)F.dy)[f],
-               d2 = (double)((Real *)F.dz)[f];
+        Real d0 = ((Real *)F.dx)[f], d1 = ((Real *)F.dy)[f], d2 = ((Real *)F.dz)[f];
         bool in = false;
         if (lane < P.kn) {
             long long j = F.nbr[f * P.kn + lane];
             int dx = P.qx[j] - F.qx[f], dy = P.qy[j] - F.qy[f], dz = P.qz[j] - F.qz[f];
-            in = cone_test(dx, dy, dz, (float)dx, (float)dy, (float)dz, d0, d1, d2, cf, P.ntc);
+            in = cone_test<Real>(dx, dy, dz, (float)dx, (float)dy, (float)dz, d0, d1, d2, cf, P.ntc);
         }
         unsigned m = __ballot_sync(FULLMASK, in);
         if (lane == 0) {
@@ -339,8 +342,8 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         Real tau = ((Real)P.sigma[nu] * ((Real *)P.nHIr)[j]) * l;
         Real A, T;
         split_absorbed<Real>(w, tau, A, T);
-        int bt = bin_fast(P.Rf + j * 9, P.R + j * 9, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC,
-                          (double)d0, (double)d1, (double)d2);
+        int bt = bin_fast<Real>(P.Rf + j * 9, P.R + j * 9, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC,
+                                d0, d1, d2);
         long long key = j * P.nf + nu;
         P.st_key[s] = (int)key;
         P.st_bin[s] = bt;
@@ -428,7 +431,6 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             nu = Fi.nu[f];
             fid = Fi.fid[f];
         }
-        double dd0 = (double)d0, dd1 = (double)d1, dd2 = (double)d2;
         // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
         long long H = 0;
         if (lane == 0) H = (long long)floor(sqrt((double)h2));
@@ -446,8 +448,8 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             long long ez = (long long)(((unsigned long long)u.z * span) >> 32) - H;
             long long r2 = ex * ex + ey * ey + ez * ez;
             bool ok = r2 > 0 && r2 <= h2 &&
-                      cone_test((int)ex, (int)ey, (int)ez, (float)ex, (float)ey, (float)ez, dd0,
-                                dd1, dd2, cf, P.ntc);
+                      cone_test<Real>((int)ex, (int)ey, (int)ez, (float)ex, (float)ey, (float)ez,
+                                      d0, d1, d2, cf, P.ntc);
             unsigned m = __ballot_sync(FULLMASK, ok);
             if (m) {
                 int src = __ffs(m) - 1;
@@ -460,9 +462,9 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
         if (!found) {
             double fh = 0.5 * (double)H;
             if (fh < 1.0) fh = 1.0;
-            Dx = (long long)rint(__dmul_rn(dd0, fh));
-            Dy = (long long)rint(__dmul_rn(dd1, fh));
-            Dz = (long long)rint(__dmul_rn(dd2, fh));
+            Dx = (long long)rint(__dmul_rn((double)d0, fh));
+            Dy = (long long)rint(__dmul_rn((double)d1, fh));
+            Dz = (long long)rint(__dmul_rn((double)d2, fh));
         }
         long long vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
         if (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) {
@@ -515,15 +517,14 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             long long key2 = j * P.nf + nu;
             // two fixed-point words: units of 2^-40 N_HI and 2^-72 N_HI (integer sums do not
             // depend on their order)
-            double fa = (double)Ak * P.dep_s[j];
+            Real fa = Ak * ((Real *)P.dep_s)[j];
             Real fe = Ak * eps * ((Real *)P.depE_s)[j];
-            if (fa > 0.0) {
-                double hi = floor(fa);
-                unsigned long long qh = (unsigned long long)hi;
-                unsigned long long ql = (unsigned long long)llrint((fa - hi) * FX_LO_SCALE);
-                unsigned long long old = qh ? atomicAdd(&P.fx_abs[key2], qh) : 0ull;
+            if (fa > Real(0)) {
+                unsigned long long qh = 0, ql = 0, old = 0;
+                bool inr = fx_split(fa, qh, ql);
+                if (qh) old = atomicAdd(&P.fx_abs[key2], qh);
                 if (ql) atomicAdd(&P.fx_lo[key2], ql);
-                if (fa > 4.0e18 || old > (1ull << 62))
+                if (!inr || old > (1ull << 62))
                     atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
             }
             if (fe > Real(0)) {
@@ -552,13 +553,14 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
 
 // receiver segments of the staged contributions
 __global__ void k_seg_fill(DevPtrs P, const int *lens) {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nst = lens[3];
     if (nst > P.ST_cap) nst = P.ST_cap;
-    if (s >= nst) return;
-    int key = P.st_key[s];
-    int pos = P.seg_off[key] + atomicAdd(&P.seg_fill[key], 1);
-    P.seg_idx[pos] = (int)s;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < nst;
+         s += (long long)gridDim.x * blockDim.x) {
+        int key = P.st_key[s];
+        int pos = P.seg_off[key] + atomicAdd(&P.seg_fill[key], 1);
+        P.seg_idx[pos] = (int)s;
+    }
 }
 
 __global__ void k_seg_sort(DevPtrs P) {
@@ -722,8 +724,8 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
                         sA.add(A);
                         sAE.add(A * eps);
                         sW.add(w);
-                        sb[threadIdx.x] = bin_fast(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], G,
-                                                   (double)d0, (double)d1, (double)d2);
+                        sb[threadIdx.x] = bin_fast<Real>(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], G,
+                                                         d0, d1, d2);
                         sv[0][threadIdx.x] = T;
                         sv[1][threadIdx.x] = T * d0;
                         sv[2][threadIdx.x] = T * d1;
@@ -784,13 +786,22 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
 // After a hop: active slots, live free packets, escaped photons per box (fixed point).
 __global__ void k_hop_counts(DevPtrs P, int nxt, int fnxt, const int *lens,
                              const unsigned long long *esc_r, const unsigned char *vstat) {
-    __shared__ long long sh[3][8];
-    long long act = 0, live = 0, nesc = 0;
+    __shared__ long long sh[5][8];
+    long long act = 0, live = 0, nesc = 0, actp = 0, occs = 0;
     long long nreq = lens[2];
     if (nreq > P.F_cap) nreq = P.F_cap;
     long long stride = (long long)gridDim.x * blockDim.x;
     long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (long long k = t0; k < P.n * P.nf; k += stride) act += __popc(P.act[nxt][k]);
+    for (long long i = t0; i < P.n; i += stride) {
+        unsigned any = 0u;
+        for (int nu = 0; nu < P.nf; ++nu) {
+            unsigned a = P.act[nxt][i * P.nf + nu];
+            any |= a;
+            act += __popc(a);
+            occs += __popc(P.occ[nxt][i * P.nf + nu]);
+        }
+        actp += (any != 0u);
+    }
     FreeBuf F = P.fr[fnxt];
     for (long long r = t0; r < nreq; r += stride) {
         unsigned char s = vstat[r];
@@ -815,16 +826,25 @@ __global__ void k_hop_counts(DevPtrs P, int nxt, int fnxt, const int *lens,
         act += __shfl_down_sync(FULLMASK, act, o);
         live += __shfl_down_sync(FULLMASK, live, o);
         nesc += __shfl_down_sync(FULLMASK, nesc, o);
+        actp += __shfl_down_sync(FULLMASK, actp, o);
+        occs += __shfl_down_sync(FULLMASK, occs, o);
     }
     int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { sh[0][w] = act; sh[1][w] = live; sh[2][w] = nesc; }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][w] = act; sh[1][w] = live; sh[2][w] = nesc; sh[3][w] = actp; sh[4][w] = occs;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long a = 0, l = 0, e = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += sh[0][k]; l += sh[1][k]; e += sh[2][k]; }
+        long long a = 0, l = 0, e = 0, ap = 0, oc = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            a += sh[0][k]; l += sh[1][k]; e += sh[2][k]; ap += sh[3][k]; oc += sh[4][k];
+        }
         if (a) atomicAdd((unsigned long long *)&P.cnt[CNT_ACTIVE], (unsigned long long)a);
+        if (a) atomicAdd((unsigned long long *)&P.cnt[CNT_ACTS], (unsigned long long)a);
         if (l) atomicAdd((unsigned long long *)&P.cnt[CNT_LIVE], (unsigned long long)l);
         if (e) atomicAdd((unsigned long long *)&P.cnt[CNT_VESC], (unsigned long long)e);
+        if (ap) atomicAdd((unsigned long long *)&P.cnt[CNT_ACTP], (unsigned long long)ap);
+        if (oc) atomicAdd((unsigned long long *)&P.cnt[CNT_OUT], (unsigned long long)oc);
     }
 }
 
@@ -844,6 +864,8 @@ __global__ void k_hop_lens(DevPtrs P, int *lens, int phase) {
     } else {                     // after the hop: the requests become the next free packets
         long long nr = lens[2];
         lens[0] = (int)(nr < P.F_cap ? nr : P.F_cap);
+        P.cnt[CNT_STG] += lens[3];
+        P.cnt[CNT_WLS] += lens[4];
     }
 }
 
@@ -898,6 +920,7 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
             LAUNCH(KT_EMIT_SRC, 1, (k_emit_src<Real><<<(unsigned)((np + tb - 1) / tb), tb, 0, st>>>(P, c->fcur)));
         int npi = (int)np;
         cudaMemcpyAsync(H.lens, &npi, sizeof(int), cudaMemcpyHostToDevice, st);
+        c->nfree_h = np;
         return rt_cuda_check(c, cudaGetLastError(), "emit");
     }
     if (part == 3) {  // cone masks of the held packets only (inspection)
@@ -914,6 +937,7 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     }
     cudaMemsetAsync(&P.cnt[CNT_VIRT], 0, 2 * sizeof(long long), st);
     cudaMemsetAsync(&P.cnt[CNT_GAS], 0, sizeof(long long), st);
+    cudaMemsetAsync(&P.cnt[CNT_ACTP], 0, 6 * sizeof(long long), st);
     rt_status status = RT_OK;
     long long hops = 0, peak_free = 0, peak_act = 0;
     const int gb = 152 * 64;
@@ -929,18 +953,20 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         cudaMemsetAsync(&P.cnt[CNT_LIVE], 0, sizeof(long long), st);
         cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, st);
         cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, st);
+        // free packets of this hop: known on the host from the last hop's counters
+        long long nfr = std::max<long long>(c->nfree_h, 1);
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 0)));
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur, stamp)));
-        LAUNCH(KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
-        LAUNCH(KT_SCAN, 6, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + P.F_cap, H.lens + 1, H.lens + 2, st),
-                            rt_scan_exclusive(c, H.stcnt, H.stoff, P.F_cap, H.lens, H.lens + 3, st)));
+        LAUNCH(KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
+        LAUNCH(KT_SCAN, 6, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st),
+                            rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, st)));
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 1)));
-        LAUNCH(KT_EXPAND, 1, (k_expand<<<(unsigned)((n + P.F_cap + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
-        LAUNCH(KT_FREE_C, 1, (k_freeC<Real, NRC><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+        LAUNCH(KT_EXPAND, 1, (k_expand<<<(unsigned)((n + nfr + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
+        LAUNCH(KT_FREE_C, 1, (k_freeC<Real, NRC><<<rt_blocks(nfr * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stoff)));
         LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
         LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, st)));
-        LAUNCH(KT_SEG_FILL, 1, (k_seg_fill<<<(unsigned)((P.ST_cap + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
+        LAUNCH(KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, st>>>(P, H.lens)));
         LAUNCH(KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P)));
         cudaMemsetAsync(H.lens + 4, 0, sizeof(int), st);
         LAUNCH(KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, st>>>(P, cur, stamp, H.lens + 4)));
@@ -957,6 +983,7 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         if (s2 != RT_OK) return s2;
         kt_resolve(c);
         if (c->cnt_h[CNT_ERR]) break;
+        c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], P.F_cap);
         if (c->cnt_h[CNT_NREQ] > peak_free) peak_free = c->cnt_h[CNT_NREQ];
         if (c->cnt_h[CNT_ACTIVE] > peak_act) peak_act = c->cnt_h[CNT_ACTIVE];
         if (c->cnt_h[CNT_ACTIVE] == 0 && c->cnt_h[CNT_LIVE] == 0) break;
@@ -964,6 +991,22 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     kt_resolve(c);
+    // the active packets of the first hop were made by the emission: add them to the model
+    // counts below (CNT_ACTS/ACTP count those produced by each hop's receiver side)
+    {
+        const double R = sizeof(Real), kn = P.kn;
+        double actp = (double)c->cnt_h[CNT_ACTP], acts = (double)c->cnt_h[CNT_ACTS];
+        double gcon = (double)c->cnt_h[CNT_GCON], stg = (double)c->cnt_h[CNT_STG];
+        double wls = (double)c->cnt_h[CNT_WLS], outs = (double)c->cnt_h[CNT_OUT];
+        double vreq = (double)c->cnt_h[CNT_VIRT];
+        // algorithmic bytes: each input read once and each output written once
+        c->kstat[KT_PHASE_A].bytes += actp * (kn * (4 + 4 + 12) + P.nf * 4) + acts * 12 * R +
+                                      gcon * 8 + (double)hops * (double)n * 4;
+        c->kstat[KT_PHASE_B].bytes += wls * (16 + 8 + 48 + kn * 4) + gcon * (16 + 6 * R + 4) +
+                                      stg * (8 + 9 * R) + outs * 6 * R;
+        c->kstat[KT_VIRTUAL].bytes += vreq * (8 + 6 * R + 40 + kn * (16 + 4 * R + 16 + 4) +
+                                              6 * R + 40);
+    }
     c->stats[0] = hops;
     c->stats[1] = c->cnt_h[CNT_VIRT];
     c->stats[2] = c->cnt_h[CNT_VESC];
