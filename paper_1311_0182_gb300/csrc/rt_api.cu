@@ -171,7 +171,11 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         if (!(box_L[b] > 0.0)) return RT_ERR_INVALID;
     }
     long long n = box_off[n_boxes];
-    if (n >= (1ll << 27) || n * cfg->n_ngb >= (1ll << 31)) return RT_ERR_INVALID;
+    // particle indices < 2^27 (packed with the neighbour rank), and slot codes and (particle,
+    // frequency) keys < 2^31 (32-bit index arithmetic in the kernels)
+    long long n_slots = n * (long long)(cfg->n_freq_src + 1) * cfg->n_rc;
+    if (n >= (1ll << 27) || n * cfg->n_ngb >= (1ll << 31) || n_slots >= (1ll << 31))
+        return RT_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RT_ERR_CUDA;
 
@@ -261,6 +265,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.ndot, double, (long long)n_src * P.nfs + 1);
     A(P.sigma, double, P.nf);
     A(P.eps, double, P.nf);
+    A(P.sigmaf, float, P.nf);
+    A(P.box_uf, float, n_boxes);
+    A(P.escf, float, n_boxes);
     A(P.nbr, int, n * P.kn);
     A(P.snbr, int, (long long)(n_src + 1) * P.kn);
     A(P.h2, long long, n);
@@ -311,6 +318,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.seg_fill, int, segn);
     A(P.seg_idx, int, P.ST_cap);
     A(P.abs, double, nkey); A(P.absE, double, nkey); A(P.pass, double, nkey);
+    A(P.passf, float, nkey);
     A(P.fx_abs, unsigned long long, nkey);
     A(P.fx_E, unsigned long long, nkey);
     A(P.fx_lo, unsigned long long, nkey);
@@ -336,6 +344,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     cudaMemcpy(P.box_off, box_off, sizeof(long long) * (n_boxes + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_L, box_L, sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_u, u.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
+    std::vector<float> uf(u.begin(), u.end());
+    cudaMemcpy(P.box_uf, uf.data(), sizeof(float) * n_boxes, cudaMemcpyHostToDevice);
     // unit of particle volumes N_H/n_H: the mean particle volume on the FP32 path (volumes in
     // cm^3 exceed the FP32 range), 1 on the FP64 path
     std::vector<double> vu(n_boxes, 1.0);
@@ -400,6 +410,9 @@ static void set_norms(rt_ctx *c) {
         norm[b] = c->d.fp32 ? r : 1.0;
     }
     cudaMemcpy(c->d.ref, ref.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
+    std::vector<float> escf(nb);
+    for (int b = 0; b < nb; ++b) escf[b] = (float)(FX_ESC_SCALE * norm[b] / ref[b]);
+    cudaMemcpy(c->d.escf, escf.data(), sizeof(float) * nb, cudaMemcpyHostToDevice);
     cudaMemcpy(c->d.norm, norm.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
     cudaMemcpy(x.src_emit, x.src_emit_h.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
 }
@@ -500,6 +513,8 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
     sg[P.nfs] = c->cfg.sigma_rec;
     ep[P.nfs] = 0.0;
     cudaMemcpy(P.sigma, sg.data(), sizeof(double) * P.nf, cudaMemcpyHostToDevice);
+    std::vector<float> sgf(sg.begin(), sg.end());
+    cudaMemcpy(P.sigmaf, sgf.data(), sizeof(float) * P.nf, cudaMemcpyHostToDevice);
     cudaMemcpy(P.eps, ep.data(), sizeof(double) * P.nf, cudaMemcpyHostToDevice);
     // source photons of one step per box, summed packet by packet as they are emitted
     rt_ctx &xe = *c;
@@ -764,10 +779,11 @@ extern "C" rt_status rt_set_slots(rt_ctx *c, const double *f, int where, void *s
     return s;
 }
 
-__global__ void k_deposits(DevPtrs P, double *a, double *e) {
+__global__ void k_deposits(DevPtrs P, double *a, double *e, double *ps) {
     long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (key >= P.n * P.nf) return;
     long long i = key / P.nf;
+    ps[key] = P.pass[key] + (double)P.passf[key] * P.norm[P.pbox[i]];
     double NHI = P.xHI[i] * P.NH[i];
     a[key] = P.abs[key] + ((double)P.fx_abs[key] + (double)P.fx_lo[key] / FX_LO_SCALE) *
                               (NHI / FX_ABS_SCALE);
@@ -779,13 +795,13 @@ extern "C" rt_status rt_get_deposits(rt_ctx *c, double *abs_, double *absE, doub
     if (!c) return RT_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     long long m = c->d.n * c->d.nf;
-    double *t = dtmp<double>(2 * m);
+    double *t = dtmp<double>(3 * m);
     if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
-    k_deposits<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->d, t, t + m);
+    k_deposits<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->d, t, t + m, t + 2 * m);
     rt_status s;
     if ((s = copy_out(c, abs_, t, sizeof(double) * m, where, st)) ||
         (s = copy_out(c, absE, t + m, sizeof(double) * m, where, st)) ||
-        (s = copy_out(c, pass, c->d.pass, sizeof(double) * m, where, st))) {
+        (s = copy_out(c, pass, t + 2 * m, sizeof(double) * m, where, st))) {
         cudaFree(t);
         return s;
     }

@@ -100,6 +100,8 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     // sources
     int *sbox, *sqx, *sqy, *sqz;
     double *ndot, *sigma, *eps;  // [ns*nfs], [nf], [nf]
+    float *sigmaf, *box_uf, *escf;  // FP32 copies: sigma [nf], box unit [nb], escape scale [nb]
+    float *passf;                // [n * nf] photons passing (FP32 path, slot units)
     // neighbours
     int *nbr, *snbr;
     long long *h2, *sh2;
@@ -375,11 +377,29 @@ __device__ __forceinline__ bool fx_split(double fa, unsigned long long &qh, unsi
     ql = (unsigned long long)llrint((fa - hi) * 4294967296.0);
     return true;
 }
+// Conversions built from 32-bit pieces: on GB300 conversions between 64-bit integers and
+// floating point issue to the (narrow) FP64 pipe.
+__device__ __forceinline__ unsigned long long f2u64_rz(float v) {   // 0 <= v < 2^64
+    float hi = floorf(v * 2.3283064365386963e-10f);                 // v / 2^32
+    float lo = v - hi * 4294967296.0f;
+    return ((unsigned long long)__float2uint_rz(hi) << 32) + __float2uint_rz(lo);
+}
+__device__ __forceinline__ float i64_to_f(long long v) {            // |v| < 2^52
+    long long hi = v >> 21;
+    return (float)(int)hi * 2097152.0f + (float)(int)(v - (hi << 21));
+}
+// floor(sqrt(v)) for 0 <= v < 2^52, exact, without FP64
+__device__ __forceinline__ long long isqrt64(long long v) {
+    long long s = (long long)__float2uint_rz(sqrtf(i64_to_f(v)));
+    while (s * s > v) --s;
+    while ((s + 1) * (s + 1) <= v) ++s;
+    return s;
+}
 __device__ __forceinline__ bool fx_split(float fa, unsigned long long &qh, unsigned long long &ql) {
     if (!(fa < 4.0e18f)) return false;
     float hi = floorf(fa);
-    qh = __float2ull_rz(hi);
-    ql = __float2ull_rn((fa - hi) * 4294967296.0f);
+    qh = f2u64_rz(hi);
+    ql = __float2uint_rn((fa - hi) * 4294967296.0f);   // < 2^32
     return true;
 }
 

@@ -88,7 +88,7 @@ __device__ __forceinline__ long long box_d2(int qx, int qy, int qz, int lx, int 
 // Visit a list of contiguous item ranges, one per lane (lane l owns [rs, rs + rc)); merge the
 // candidates into the running top-k.
 __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
-                                 int rs, int rc, long long &td2, int &tidx) {
+                                 int rs, int rc, long long bound, long long &td2, int &tidx) {
     int lane = threadIdx.x & 31;
     // inclusive scan of range counts
     int incl = rc;
@@ -123,7 +123,7 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
         }
         long long kd2 = __shfl_sync(FULLMASK, td2, kn - 1);
         int kidx = __shfl_sync(FULLMASK, tidx, kn - 1);
-        bool better = kless(cd2, cidx, kd2, kidx);
+        bool better = cd2 <= bound && kless(cd2, cidx, kd2, kidx);
         if (__any_sync(FULLMASK, better)) {
             if (!better) { cd2 = KNN_INF; cidx = 0x7fffffff; }
             warp_merge(td2, tidx, cd2, cidx);
@@ -133,9 +133,11 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
 
 // Exact kNN of point q (quantised, inside [0, RT_Q)^3) among the box's points, excluding the
 // point with local index `exclude` (-1: none).  Lane l < kn returns the l-th nearest.
+// `bound` is an upper bound on the squared distance of the kn-th neighbour (KNN_INF when none
+// is known): points and cells beyond it are skipped, which leaves the result unchanged.
 // Returns false when the box holds fewer than kn candidates.
 __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
-                                long long &out_d2, int &out_idx) {
+                                long long &out_d2, int &out_idx, long long bound = KNN_INF) {
     int lane = threadIdx.x & 31;
     long long td2 = KNN_INF;
     int tidx = 0x7fffffff;
@@ -146,6 +148,7 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
         int side = 2 * r + 1;
         int ncol = side * side;
         long long prune = __shfl_sync(FULLMASK, td2, kn - 1);   // cells farther cannot help
+        if (bound < prune) prune = bound;
         for (int cb = 0; cb < ncol; cb += 32) {
             int col = cb + lane;
             // up to two z-ranges per column
@@ -176,8 +179,9 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
                     }
                 }
             }
-            knn_visit(g, qx, qy, qz, exclude, kn, rs0, rc0, td2, tidx);
-            if (__any_sync(FULLMASK, rc1 > 0)) knn_visit(g, qx, qy, qz, exclude, kn, rs1, rc1, td2, tidx);
+            knn_visit(g, qx, qy, qz, exclude, kn, rs0, rc0, bound, td2, tidx);
+            if (__any_sync(FULLMASK, rc1 > 0))
+                knn_visit(g, qx, qy, qz, exclude, kn, rs1, rc1, bound, td2, tidx);
         }
         // distance from q to the outside of the visited block [c - r, c + r]^3
         long long b = -1;

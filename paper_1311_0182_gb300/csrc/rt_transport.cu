@@ -68,6 +68,28 @@ __device__ __forceinline__ void packet_dir(float Mx, float My, float Mz, float &
     }
 }
 
+// precision-matched constants: FP64 values on the FP64 path, FP32 copies on the FP32 path
+template <typename Real> __device__ __forceinline__ Real box_unit(const DevPtrs &P, int b);
+template <> __device__ __forceinline__ double box_unit<double>(const DevPtrs &P, int b) { return P.box_u[b]; }
+template <> __device__ __forceinline__ float box_unit<float>(const DevPtrs &P, int b) { return P.box_uf[b]; }
+template <typename Real> __device__ __forceinline__ Real sigma_of(const DevPtrs &P, int nu);
+template <> __device__ __forceinline__ double sigma_of<double>(const DevPtrs &P, int nu) { return P.sigma[nu]; }
+template <> __device__ __forceinline__ float sigma_of<float>(const DevPtrs &P, int nu) { return P.sigmaf[nu]; }
+template <typename Real> __device__ __forceinline__ Real to_real(long long v);
+template <> __device__ __forceinline__ double to_real<double>(long long v) { return (double)v; }
+template <> __device__ __forceinline__ float to_real<float>(long long v) { return i64_to_f(v); }
+
+__device__ __forceinline__ unsigned long long to_fixed(double v) { return (unsigned long long)llrint(v); }
+__device__ __forceinline__ unsigned long long to_fixed(float v) { return f2u64_rz(v + 0.5f); }
+
+// escaped photons in the fixed-point unit of the box's escape tally
+__device__ __forceinline__ unsigned long long esc_fixed(double N, const DevPtrs &P, int box) {
+    return (unsigned long long)llrint(N * P.norm[box] / P.ref[box] * FX_ESC_SCALE);
+}
+__device__ __forceinline__ unsigned long long esc_fixed(float N, const DevPtrs &P, int box) {
+    return f2u64_rz(N * P.escf[box] + 0.5f);
+}
+
 // ------------------------------------------------------------------------------------------
 // per-step kernels
 // ------------------------------------------------------------------------------------------
@@ -81,7 +103,7 @@ __global__ void k_rotate(DevPtrs P, long long step) {
         for (int a = 0; a < 9; ++a) { P.R[i * 9 + a] = R[a]; P.Rf[i * 9 + a] = (float)R[a]; }
     } else if (i < P.n + nsrc) {
         long long t = i - P.n;
-        int j = (int)(t / P.K), k = (int)(t % P.K);
+        int j = (int)((unsigned)t / (unsigned)P.K), k = (int)((unsigned)t % (unsigned)P.K);
         double R[9];
         random_rotation(P.seed, 2u, (unsigned)step, (unsigned)k, (unsigned)j, R);
 #pragma unroll
@@ -96,8 +118,8 @@ __global__ void k_rebin(DevPtrs P, int cur) {
     if (key >= P.n * P.nf) return;
     unsigned o = P.occ[cur][key];
     if (!o) { P.act[cur][key] = 0; return; }
-    long long i = key / P.nf;
-    int nu = (int)(key % P.nf);
+    long long i = (unsigned)key / (unsigned)P.nf;   // keys < 2^31: 32-bit division
+    int nu = (int)((unsigned)key % (unsigned)P.nf);
     Slots<Real> S(P, cur);
     long long s0 = i * P.S + (long long)nu * NRC;
     Real nN[NRC], nX[NRC], nY[NRC], nZ[NRC], nE[NRC];
@@ -140,7 +162,7 @@ __global__ void k_emit_rec(DevPtrs P, int cur) {
     for (int nu = 0; nu < P.nf; ++nu) {
         long long key = i * P.nf + nu;
         P.abs[key] = 0.0; P.absE[key] = 0.0; P.pass[key] = 0.0;
-        P.fx_abs[key] = 0ull; P.fx_lo[key] = 0ull; P.fx_E[key] = 0ull;
+        P.fx_abs[key] = 0ull; P.fx_lo[key] = 0ull; P.fx_E[key] = 0ull; P.passf[key] = 0.0f;
     }
     double x = P.xHI[i], nH = P.nH[i], NH = P.NH[i];
     double nHI = __dmul_rn(x, nH);
@@ -184,11 +206,11 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long per_src = (long long)P.K * P.nfs * P.nec;
     if (p >= (long long)P.ns * per_src) return;
-    int j = (int)(p / per_src);
-    long long t = p % per_src;
-    int k = (int)(t / ((long long)P.nfs * P.nec));
-    int nu = (int)((t / P.nec) % P.nfs);
-    int e = (int)(t % P.nec);
+    unsigned ps = (unsigned)per_src, tt = (unsigned)(p % ps);
+    int j = (int)((unsigned)p / ps);
+    int k = (int)(tt / (unsigned)(P.nfs * P.nec));
+    int nu = (int)((tt / (unsigned)P.nec) % (unsigned)P.nfs);
+    int e = (int)(tt % (unsigned)P.nec);
     FreeBuf F = P.fr[fcur];
     int b = P.sbox[j];
     double N = __ddiv_rn(__dmul_rn(P.ndot[(long long)j * P.nfs + nu], P.dt_em), (double)P.nec);
@@ -211,6 +233,11 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
 // ------------------------------------------------------------------------------------------
 // hop kernels
 // ------------------------------------------------------------------------------------------
+// Sender side.  Warp per particle.  The particle's packets able to move are taken 32 at a
+// time (lane = packet: load, direction, clock), then tested one after the other against the
+// neighbours (lane = neighbour k: cone membership, ballot).  For each (frequency, neighbour)
+// the bits of the packets whose cone holds the neighbour go to the neighbour's receiver-ordered
+// bitmap word; empty cones become virtual-particle requests.
 template <typename Real, int NRC>
 __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
     int lane = threadIdx.x & 31;
@@ -220,6 +247,7 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
     Real *rw = (Real *)P.rec[0], *rx = (Real *)P.rec[1], *ry = (Real *)P.rec[2],
          *rz = (Real *)P.rec[3], *rc = (Real *)P.rec[4], *re = (Real *)P.rec[5];
     float cf = 1.0f - 2.0f / (float)P.ntc;
+    long long nrev = P.n * P.kn;
     long long ncon = 0;
     for (long long i = w0; i < P.n; i += nw) {
         unsigned aw = (lane < P.nf) ? P.act[cur][i * P.nf + lane] : 0u;
@@ -227,10 +255,10 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
             if (lane == 0) P.reqcnt[i] = 0;
             continue;
         }
+        // neighbour k = lane
         int nb = 0, dx = 0, dy = 0, dz = 0, rp = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f;
         bool valid = lane < P.kn;
-        long long nrev = P.n * P.kn;
         if (valid) {
             long long f = i * P.kn + lane;
             nb = P.nbr[f];
@@ -238,42 +266,91 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
             fx = P.fdx[f]; fy = P.fdy[f]; fz = P.fdz[f];
             dx = (int)fx; dy = (int)fy; dz = (int)fz;
         }
-        int nreq = 0;
-        for (int nu = 0; nu < P.nf; ++nu) {
-            unsigned a = __shfl_sync(FULLMASK, aw, nu);
-            unsigned bmw = 0u, empw = 0u, rem = a;
-            while (rem) {
-                int b = __ffs(rem) - 1;
-                rem &= rem - 1u;
-                long long s = i * P.S + (long long)nu * NRC + b;
-                Real N = S.N[s];
-                Real d0, d1, d2;
-                packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
-                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, d0, d1, d2, cf, P.ntc);
-                unsigned m = __ballot_sync(FULLMASK, in);
-                int cm = __popc(m);
-                ncon += cm;
-                if (cm > 0) {
-                    if (lane == 0) {
-                        rw[s] = N / (Real)cm;
-                        rx[s] = d0; ry[s] = d1; rz[s] = d2;
-                        rc[s] = S.C[s] / N;
-                        re[s] = S.E[s] / N;
-                    }
-                    if (in) {
-                        bmw |= 1u << b;
-                        P.touched[(long long)nb * P.nf + nu] = stamp;
-                    }
-                } else {
-                    empw |= 1u << b;
-                }
-            }
-            if (bmw) P.bm[(long long)nu * nrev + rp] = bmw;   // the receiver clears it
-            if (lane == 0) P.emp[i * P.nf + nu] = empw;
-            nreq += __popc(empw);
+        // active packets in (nu, b) order: prefix of the per-frequency counts
+        int cnt = __popc(aw);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(FULLMASK, incl, o);
+            if (lane >= o) incl += v;
         }
+        int total = __shfl_sync(FULLMASK, incl, 31);
+        int excl = incl - cnt;
+        int nreq = 0;
+        unsigned emp_acc = 0u;        // lane nu: empty-cone bits of frequency nu
+        for (int cb = 0; cb < total; cb += 32) {
+            // lane t takes packet cb + t: its frequency (owner lane) and bin
+            int t = cb + lane;
+            int onu = 0;
+            for (int q = 1; q < P.nf; ++q) {
+                int eq = __shfl_sync(FULLMASK, excl, q);
+                if (eq <= t) onu = q;
+            }
+            unsigned ow = __shfl_sync(FULLMASK, aw, onu);
+            int oex = __shfl_sync(FULLMASK, excl, onu);
+            bool has = t < total;
+            int ob = has ? __fns(ow, 0, t - oex + 1) : 0;
+            long long s = i * P.S + (long long)onu * NRC + ob;
+            Real N = Real(0), d0 = Real(1), d1 = Real(0), d2 = Real(0), C = Real(0), E = Real(0);
+            if (has) {
+                N = S.N[s];
+                packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
+                C = S.C[s];
+                E = S.E[s];
+            }
+            int nb_chunk = min(32, total - cb);
+            int my_cm = 0;
+            unsigned my_mask = 0u;
+            for (int u = 0; u < nb_chunk; ++u) {
+                Real e0 = __shfl_sync(FULLMASK, d0, u), e1 = __shfl_sync(FULLMASK, d1, u),
+                     e2 = __shfl_sync(FULLMASK, d2, u);
+                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, e0, e1, e2, cf, P.ntc);
+                unsigned m = __ballot_sync(FULLMASK, in);
+                if (lane == u) { my_mask = m; my_cm = __popc(m); }
+            }
+            ncon += (lane < nb_chunk) ? my_cm : 0;
+            if (has && my_cm > 0) {
+                rw[s] = N / (Real)my_cm;
+                rx[s] = d0; ry[s] = d1; rz[s] = d2;
+                rc[s] = C / N;
+                re[s] = E / N;
+            }
+            // empty cones of this chunk, folded into the per-frequency words
+            bool empty = has && my_cm == 0;
+            unsigned emb = __ballot_sync(FULLMASK, empty);
+            nreq += __popc(emb);
+            // bitmap words: lane k collects, frequency by frequency, the bins whose cone holds k
+            unsigned word = 0u;
+            int cur_nu = __shfl_sync(FULLMASK, onu, 0);
+            for (int u = 0; u < nb_chunk; ++u) {
+                int unu = __shfl_sync(FULLMASK, onu, u);
+                int ub = __shfl_sync(FULLMASK, ob, u);
+                unsigned um = __shfl_sync(FULLMASK, my_mask, u);
+                if (unu != cur_nu) {
+                    if (valid && word) {
+                        P.bm[(long long)cur_nu * nrev + rp] |= word;
+                        P.touched[(long long)nb * P.nf + cur_nu] = stamp;
+                    }
+                    word = 0u;
+                    cur_nu = unu;
+                }
+                if ((um >> lane) & 1u) word |= 1u << ub;
+            }
+            if (valid && word) {
+                P.bm[(long long)cur_nu * nrev + rp] |= word;
+                P.touched[(long long)nb * P.nf + cur_nu] = stamp;
+            }
+            // empty-cone bins per frequency, gathered on lane nu
+            for (int q = 0; q < P.nf; ++q) {
+                unsigned red = __reduce_or_sync(FULLMASK, (empty && onu == q) ? (1u << ob) : 0u);
+                if (lane == q) emp_acc |= red;
+            }
+        }
+        if (lane < P.nf) P.emp[i * P.nf + lane] = emp_acc;
         if (lane == 0) P.reqcnt[i] = nreq;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ncon += __shfl_down_sync(FULLMASK, ncon, o);
     if (lane == 0 && ncon) atomicAdd((unsigned long long *)&P.cnt[CNT_GCON], (unsigned long long)ncon);
 }
 
@@ -338,8 +415,8 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         int b = P.pbox[j];
         Real t = (Real)(P.qx[j] - F.qx[f]) * d0 + (Real)(P.qy[j] - F.qy[f]) * d1 +
                  (Real)(P.qz[j] - F.qz[f]) * d2;
-        Real l = t * (Real)P.box_u[b];
-        Real tau = ((Real)P.sigma[nu] * ((Real *)P.nHIr)[j]) * l;
+        Real l = t * box_unit<Real>(P, b);
+        Real tau = (sigma_of<Real>(P, nu) * ((Real *)P.nHIr)[j]) * l;
         Real A, T;
         split_absorbed<Real>(w, tau, A, T);
         int bt = bin_fast<Real>(P.Rf + j * 9, P.R + j * 9, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC,
@@ -408,9 +485,10 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
         long long h2;
         Real N, d0, d1, d2, clk, eps;
         unsigned long long fid;
+        const int *snb;             // the sender's neighbour list (bounds the kNN search)
         if (!(code & RT_FREE_BIT)) {
-            long long i = (long long)(code / P.S);
-            int s = (int)(code % P.S);
+            long long i = (unsigned)code / (unsigned)P.S;   // slot codes < 2^31
+            int s = (int)((unsigned)code % (unsigned)P.S);
             nu = s / NRC;
             box = P.pbox[i];
             qx = P.qx[i]; qy = P.qy[i]; qz = P.qz[i];
@@ -420,6 +498,7 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             clk = S.C[code] / N;
             eps = S.E[code] / N;
             fid = code + 1ull;
+            snb = P.nbr + i * P.kn;
         } else {
             long long f = (long long)(code & ~RT_FREE_BIT);
             box = Fi.box[f]; qx = Fi.qx[f]; qy = Fi.qy[f]; qz = Fi.qz[f];
@@ -430,11 +509,10 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             eps = ((Real *)Fi.eps)[f];
             nu = Fi.nu[f];
             fid = Fi.fid[f];
+            snb = Fi.nbr + f * P.kn;
         }
         // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
-        long long H = 0;
-        if (lane == 0) H = (long long)floor(sqrt((double)h2));
-        H = __shfl_sync(FULLMASK, H, 0);
+        long long H = isqrt64(h2);   // = floor(sqrt(h2)) exactly (h2 < 2^62)
         unsigned long long span = (unsigned long long)(2 * H + 1);
         float cf = 1.0f - 2.0f / (float)P.ntc;
         long long Dx = 0, Dy = 0, Dz = 0;
@@ -469,26 +547,38 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
         long long vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
         if (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) {
             if (lane == 0) {
-                double v = (double)N * P.norm[box] / P.ref[box];
-                esc_r[r] = (unsigned long long)llrint(v * FX_ESC_SCALE);
+                esc_r[r] = esc_fixed(N, P, box);
                 vstat[r] = 1;
                 Fo.box[r] = box;
                 ((Real *)Fo.N)[r] = Real(0);
             }
             continue;
         }
+        // the sender's kn neighbours are kn points of the box: the farthest of them from the
+        // virtual particle bounds its kn-th neighbour distance
+        long long sb2 = 0;
+        if (lane < P.kn) {
+            int q = snb[lane];
+            long long ex = P.qx[q] - vx, ey = P.qy[q] - vy, ez = P.qz[q] - vz;
+            sb2 = ex * ex + ey * ey + ez * ez;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            long long t = __shfl_xor_sync(FULLMASK, sb2, o);
+            sb2 = t > sb2 ? t : sb2;
+        }
         long long kd2;
         int kidx;
         BoxGrid g;
         g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
         g.start = P.grid.start; g.items = P.grid.items;
-        warp_knn(g, (int)vx, (int)vy, (int)vz, -1, P.kn, kd2, kidx);
+        warp_knn(g, (int)vx, (int)vy, (int)vz, -1, P.kn, kd2, kidx, sb2);
         long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
         bool valid = lane < P.kn;
         long long j = valid ? P.box_off[box] + kidx : 0;
         Real om = Real(0), nhj = Real(0), Vj = Real(0);
         if (valid) {
-            Real q = h2v > 0 ? rt_sqrt<Real>((Real)kd2 / (Real)h2v) : Real(0);
+            Real q = h2v > 0 ? rt_sqrt<Real>(to_real<Real>(kd2) / to_real<Real>(h2v)) : Real(0);
             Vj = ((Real *)P.Vr)[j];
             om = Vj * kernel_w<Real>(q);
             nhj = ((Real *)P.nHIr)[j];
@@ -507,9 +597,9 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) swn += __shfl_xor_sync(FULLMASK, swn, o);
         Real nHIv = swn / sw;
-        Real t = (Real)Dx * d0 + (Real)Dy * d1 + (Real)Dz * d2;
-        Real l = t * (Real)P.box_u[box];
-        Real tau = ((Real)P.sigma[nu] * nHIv) * l;
+        Real t = (Real)(int)Dx * d0 + (Real)(int)Dy * d1 + (Real)(int)Dz * d2;
+        Real l = t * box_unit<Real>(P, box);
+        Real tau = (sigma_of<Real>(P, nu) * nHIv) * l;
         Real A, T;
         split_absorbed<Real>(N, tau, A, T);
         if (valid && swn > Real(0) && wn > Real(0)) {
@@ -528,7 +618,7 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
                     atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
             }
             if (fe > Real(0)) {
-                unsigned long long q = (unsigned long long)llrint((double)fe);
+                unsigned long long q = to_fixed(fe);
                 unsigned long long old = atomicAdd(&P.fx_E[key2], q);
                 if (fe > Real(4.0e18) || old > (1ull << 62))
                     atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
@@ -580,12 +670,6 @@ __global__ void k_seg_sort(DevPtrs P) {
     }
 }
 
-#ifndef PHASEB_MINB
-#define PHASEB_MINB 3
-#endif
-// Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
-// cone.  Contributions are computed in parallel and merged in their fixed order by a
-// broadcast loop (the lane owning the target cone adds).
 // The receiver groups with work this hop: receivers touched by a gas sender, receivers of
 // staged free-packet contributions, and particles holding waiting packets.  Block-level
 // compaction with one atomic per block; the order of the list does not matter.
@@ -614,6 +698,41 @@ __global__ void __launch_bounds__(256) k_worklist(DevPtrs P, int cur, int stamp,
     }
 }
 
+// absorptions of one receiver group in one hop.  FP64 path: FP64 sums.  FP32 path: the
+// group's (fixed-order) sums go into the particle's fixed-point words, like the virtual-particle
+// deposits, so no FP64 instruction runs in the hop loop; pass counts stay in FP32.
+template <typename Real>
+__device__ __forceinline__ void deposit_group(const DevPtrs &P, long long key, long long j, int box,
+                                              Real a, Real ae, Real w);
+template <>
+__device__ __forceinline__ void deposit_group<double>(const DevPtrs &P, long long key, long long j,
+                                                      int box, double a, double ae, double w) {
+    double nm = P.norm[box];
+    P.abs[key] += a * nm;
+    P.absE[key] += ae * nm * P.eunit;
+    P.pass[key] += w * nm;
+}
+template <>
+__device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long key, long long j,
+                                                     int box, float a, float ae, float w) {
+    float fa = a * ((float *)P.dep_s)[j];
+    if (fa > 0.0f) {
+        unsigned long long qh, ql;
+        if (fx_split(fa, qh, ql)) {
+            unsigned long long old = P.fx_abs[key];
+            P.fx_abs[key] = old + qh;
+            P.fx_lo[key] += ql;
+            if (old > (1ull << 62))
+                atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
+        } else {
+            atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
+        }
+    }
+    float fe = ae * ((float *)P.depE_s)[j];
+    if (fe > 0.0f) P.fx_E[key] += f2u64_rz(fe + 0.5f);
+    P.passf[key] += w;
+}
+
 #ifndef PHASEB_MINB
 #define PHASEB_MINB 3
 #endif
@@ -636,8 +755,8 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
     int nxt = cur ^ 1;
     for (long long gi = g0; gi < ng; gi += gstride) {
         long long key = P.worklist[gi];
-        long long j = key / P.nf;
-        int nu = (int)(key % P.nf);
+        long long j = (unsigned)key / (unsigned)P.nf;
+        int nu = (int)((unsigned)key % (unsigned)P.nf);
         unsigned park = P.occ[cur][key] & ~P.act[cur][key];
         bool touched = P.touched[key] == stamp;
         int fc = P.seg_cnt[key];
@@ -666,8 +785,8 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
             __syncwarp(gmask);
         };
         if (touched) {
-            Real u = (Real)P.box_u[box];
-            Real sig_nhi = (Real)P.sigma[nu] * ((Real *)P.nHIr)[j];
+            Real u = box_unit<Real>(P, box);
+            Real sig_nhi = sigma_of<Real>(P, nu) * ((Real *)P.nHIr)[j];
             const float *Rf = P.Rf + j * 9;
             const double *Rd = P.R + j * 9;
             const Real *rw = (const Real *)P.rec[0], *rx = (const Real *)P.rec[1],
@@ -773,12 +892,7 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
         if (gl == 0) {
             P.occ[nxt][key] = bo;
             P.act[nxt][key] = ba;
-            if (touched || fc > 0) {
-                double nm = P.norm[box];
-                P.abs[key] += (double)a * nm;
-                P.absE[key] += (double)ae * nm * P.eunit;
-                P.pass[key] += (double)w * nm;
-            }
+            if (touched || fc > 0) deposit_group<Real>(P, key, j, box, a, ae, w);
         }
     }
 }
@@ -878,8 +992,7 @@ __global__ void k_drop_free(DevPtrs P, int fcur, const int *lens) {
     Real N = ((Real *)F.N)[f];
     if (N > Real(0)) {
         int b = F.box[f];
-        double v = (double)N * P.norm[b] / P.ref[b];
-        atomicAdd(&P.esc_fx[b], (unsigned long long)llrint(v * FX_ESC_SCALE));
+        atomicAdd(&P.esc_fx[b], esc_fixed(N, P, b));
         ((Real *)F.N)[f] = Real(0);
     }
 }
