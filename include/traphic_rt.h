@@ -175,6 +175,18 @@ rt_status rt_get_rotations(rt_ctx *ctx, double *R, double *Rs, int where, void *
 /* transmission masks of the held packets [n * S], S = n_rc * (n_freq_src + 1): bit k set
    when neighbour k lies in the cone of slot s; 0 for slots with no packet able to move */
 rt_status rt_get_cone_masks(rt_ctx *ctx, unsigned *mask, int where, void *stream);
+/* rt_get_cone_masks_noalloc -- the same masks as rt_get_cone_masks, for callers that must not
+   allocate device memory: code running under a caller-owned memory budget or pool, or a host
+   thread that may not call cudaMalloc/cudaFree while other work is in flight.  The paper has
+   no counterpart (it is an interface convenience).  No allocation: the masks are assembled in
+   a file-scope device array of 4,194,304 entries (16 MiB) that every GPU loading the library
+   holds until the process exits; n * S beyond that is rejected with RT_ERR_INVALID.  The first
+   call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+   device current); make that first call before any stream capture.  All calls share the
+   array: calls whose work overlaps on the GPU race, so serialise them (one stream, or wait for
+   the previous call's copy).  With where == RT_HOST the call synchronises `stream`; with
+   RT_DEVICE the copy is queued on `stream`. */
+rt_status rt_get_cone_masks_noalloc(rt_ctx *ctx, unsigned *mask, int where, void *stream);
 /* held packets: 6 fields [6 * n * S] (N, Mx, My, Mz, C = N*clock, E = N*eps), physical units */
 rt_status rt_get_slots(rt_ctx *ctx, double *f, int where, void *stream);
 rt_status rt_set_slots(rt_ctx *ctx, const double *f, int where, void *stream);

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "rt_internal.cuh"
 
@@ -105,7 +107,7 @@ static const char *KT_NAMES[KT_N] = {
     "rotate", "rebin", "emit_rec", "emit_src", "phase_a_send", "free_a_send", "scan",
     "expand_requests", "free_c_stage", "virtual_particles", "seg_fill", "seg_sort",
     "phase_b_merge", "hop_counts", "hop_lens", "drop_free", "chemistry", "budget", "knn_build",
-    "worklist"};
+    "worklist", "cone_masks"};
 
 extern "C" rt_status rt_set_profiling(rt_ctx *c, int on) {
     if (!c) return RT_ERR_INVALID;
@@ -717,6 +719,55 @@ extern "C" rt_status rt_get_cone_masks(rt_ctx *c, unsigned *mask, int where, voi
     cudaStreamSynchronize(st);
     cudaFree(t);
     return s;
+}
+
+// ---- cone masks without allocation -----------------------------------------------------------
+// The same masks as rt_get_cone_masks, assembled in a file-scope device array instead of a
+// buffer obtained from cudaMalloc, for callers that must not allocate device memory.
+#define RT_STATIC_MASKS (1 << 22)   // 4,194,304 masks (16 MiB), held by every device that loads the library
+static __device__ __align__(256) unsigned g_mask_scratch[RT_STATIC_MASKS];
+
+// device address of g_mask_scratch, looked up once per device (with that device current)
+static unsigned *mask_scratch(int dev, cudaError_t *err) {
+    static std::mutex mu;
+    static unsigned *addr[128] = {nullptr};
+    *err = cudaSuccess;
+    if (dev < 0 || dev >= 128) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_mask_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        addr[dev] = (unsigned *)p;
+    }
+    return addr[dev];
+}
+
+extern "C" rt_status rt_get_cone_masks_noalloc(rt_ctx *c, unsigned *mask, int where,
+                                               void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    if (!mask || (where != RT_HOST && where != RT_DEVICE)) return RT_ERR_INVALID;
+    long long m = c->d.n * c->d.S;
+    if (m > RT_STATIC_MASKS)
+        return rt_fail(c, RT_ERR_INVALID,
+                       "rt_get_cone_masks_noalloc: n * S = " + std::to_string(m) +
+                           " masks exceed the static scratch of 4194304");
+    int dev = 0;
+    if ((s = rt_cuda_check(c, cudaGetDevice(&dev), "cudaGetDevice"))) return s;
+    cudaError_t e;
+    unsigned *t = mask_scratch(dev, &e);
+    if (!t) return rt_cuda_check(c, e, "cudaGetSymbolAddress(g_mask_scratch)");
+    cudaStream_t st = (cudaStream_t)stream;
+    // every entry of [0, m) is written, so the previous call's contents need no clearing
+    kt_begin(c, KT_MASKS, st);
+    k_masks<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->d, c->cur, t);
+    kt_end(c, KT_MASKS, st);
+    if ((s = rt_cuda_check(c, cudaGetLastError(), "mask kernel"))) return s;
+    return copy_out(c, mask, t, sizeof(unsigned) * m, where, st);
 }
 
 template <typename Real>

@@ -144,7 +144,7 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
 enum {
     KT_ROTATE, KT_REBIN, KT_EMIT_REC, KT_EMIT_SRC, KT_PHASE_A, KT_FREE_A, KT_SCAN, KT_EXPAND,
     KT_FREE_C, KT_VIRTUAL, KT_SEG_FILL, KT_SEG_SORT, KT_PHASE_B, KT_HOP_COUNT, KT_HOP_LENS,
-    KT_DROP, KT_CHEM, KT_BUDGET, KT_KNN, KT_WORKLIST, KT_N
+    KT_DROP, KT_CHEM, KT_BUDGET, KT_KNN, KT_WORKLIST, KT_MASKS, KT_N
 };
 
 struct KStat {

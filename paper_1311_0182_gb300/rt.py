@@ -19,7 +19,8 @@ STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
 SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_build_neighbours",
            "rt_assign_cones", "rt_merge", "rt_emit", "rt_transport", "rt_chemistry", "rt_step",
            "rt_get_state", "rt_set_state", "rt_get_budget", "rt_get_neighbours", "rt_get_quantised",
-           "rt_get_rotations", "rt_get_cone_masks", "rt_get_slots", "rt_set_slots",
+           "rt_get_rotations", "rt_get_cone_masks", "rt_get_cone_masks_noalloc", "rt_get_slots",
+           "rt_set_slots",
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
            "rt_get_profile", "rt_last_error"]
 
@@ -77,6 +78,7 @@ def load(build_if_missing: bool = False):
     L.rt_get_quantised.argtypes = [vp, vp, i, vp]
     L.rt_get_rotations.argtypes = [vp, vp, vp, i, vp]
     L.rt_get_cone_masks.argtypes = [vp, vp, i, vp]
+    L.rt_get_cone_masks_noalloc.argtypes = [vp, vp, i, vp]
     L.rt_get_slots.argtypes = [vp, vp, i, vp]
     L.rt_set_slots.argtypes = [vp, vp, i, vp]
     L.rt_get_deposits.argtypes = [vp, vp, vp, vp, i, vp]
@@ -267,6 +269,14 @@ class Context:
         m = np.zeros((self.n, self.S), np.uint32)
         self._check(self.L.rt_get_cone_masks(self.h, m.ctypes.data, RT_HOST, self._s()),
                     "rt_get_cone_masks")
+        return m
+
+    def cone_masks_noalloc(self, out=None):
+        """Cone masks through the entry point that allocates nothing (static device scratch)."""
+        m = np.zeros((self.n, self.S), np.uint32) if out is None else out
+        p, where = _ptr(m)
+        self._check(self.L.rt_get_cone_masks_noalloc(self.h, p, where, self._s()),
+                    "rt_get_cone_masks_noalloc")
         return m
 
     def slots(self):
