@@ -35,6 +35,7 @@ def parse():
     ap.add_argument("--n-side", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     return ap.parse_args()
 
 
@@ -151,9 +152,8 @@ def run_ours(args):
         st = ctx.stats()
         b = ctx.budget()
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_1311_0182_gb300.distributed import max_over_ranks
+        ms = max_over_ranks(ms, device="cuda")      # one replica per rank: the slowest decides
     value = world * n * args.steps / (ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": "particle-sweeps/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -168,6 +168,8 @@ def run_ours(args):
     if not args.no_e2e:
         out["e2e"] = e2e(args, ctx, wl, stream, step, x0, T0)
     ctx.close()
+    if not args.no_fp64 and args.precision == "fp32":
+        out["fp64_path"] = fp64_path(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
@@ -183,7 +185,7 @@ def source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1311_0182_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in ("rt_transport.cu", "rt_internal.cuh", "rt_knn.cuh"):   # where the hop kernels live
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
@@ -232,6 +234,32 @@ def roofline(ctx, kt, ms_step_total, args):
                             for n, v in kt.items()}}
 
 
+def fp64_path(args, stream):
+    """The all-FP64 GPU path on the same workload and start state (the comparison path)."""
+    import torch
+    from paper_1311_0182_gb300 import rt, workloads as W
+    wl = W.cfg2(n_side=args.n_side, transport_fp32=0)
+    ctx = rt.Context(wl, stream=stream)
+    steps = max(1, min(args.steps, 2))
+    with torch.cuda.stream(stream):
+        ctx.load_workload(wl)
+        ctx.build_neighbours()
+        for s in range(args.warmup):
+            ctx.step(s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(steps):
+            ctx.step(args.warmup + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    n = int(wl["box_off"][-1])
+    ctx.close()
+    return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
+            "ms_per_step": ms / steps, "steps": steps, "dtype": "f64"}
+
+
 def e2e(args, ctx, wl, stream, step, x0, T0):
     """Same metric through the C ABI with host buffers: per step the state arrays go host ->
     device, the step runs, and the state and photon budget come back."""
@@ -262,20 +290,22 @@ def cpu_baseline(args, budget_s=20.0):
     of the same workload at a reduced particle count, scaled per particle-sweep."""
     import oracle
     from paper_1311_0182_gb300 import workloads as W
-    n_side = 16
+    n_side = 24
     wl = W.cfg2(n_side=n_side)
     s = oracle.Sim(wl)
     s.build_neighbours()
+    s.step(0)            # the first step carries no recombination photons yet: not timed
     t0 = time.perf_counter()
     steps = 0
-    while steps < 3 and time.perf_counter() - t0 < budget_s:
-        s.step(steps)
+    while steps < 4 and time.perf_counter() - t0 < budget_s:
+        s.step(1 + steps)
         steps += 1
     dt = time.perf_counter() - t0
     n = n_side ** 3
     return {"value": n * steps / dt, "unit": "particle-sweeps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} whole steps of the same HII-region workload at {n_side}^3 particles "
-                      f"(32 cones, 9 bins, same start recipe), {dt:.1f} s single-threaded"}
+            "sample": f"{steps} whole RT steps (after one untimed) of the same HII-region recipe "
+                      f"at {n_side}^3 particles instead of 64^3 (32 cones, 9 bins, T evolving), "
+                      f"{dt:.1f} s single-threaded; per-particle cost grows with the box (more hops)"}
 
 
 def run_reference(args):
@@ -285,7 +315,7 @@ def run_reference(args):
     import oracle
     wl_args = argparse.Namespace(**vars(args))
     from paper_1311_0182_gb300 import workloads as W
-    n_side = 16
+    n_side = 24
     wl = W.cfg2(n_side=n_side)
     s = oracle.Sim(wl)
     s.build_neighbours()

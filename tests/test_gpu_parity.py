@@ -249,3 +249,126 @@ def test_no_sources_and_minimal_box():
     assert _xhi_ok(g.state()["x_HI"], o.state()["x_HI"]).all()
     b = g.budget()[0]
     assert abs(b[0] - b[1] - b[2] - b[3]) <= 1e-9 * max(b[0], 1.0)
+
+
+# --- regimes and options ------------------------------------------------------------------------
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_clock_limited_steps_park_and_rebin(fp32):
+    """c dt (3 kpc) shorter than the box: packets wait at particles, restart next step and are
+    re-sorted into the new reception cones (rt_merge)."""
+    wl = W.cfg1(dt=0.01 * W.MYR, dt_em=0.01 * W.MYR)
+    wl["x_HI"][:] = 0.2
+    g, o = _pair(wl, transport_fp32=fp32)
+    for step in range(6):
+        g.step(step)
+        assert o.step(step) == 0
+    fg, fo = g.slots(), o.slots()
+    assert (fo[0] > 0).sum() > 100                 # packets are waiting
+    ok = _xhi_ok(g.state()["x_HI"], o.state()["x_HI"])
+    bg, bo = g.budget()[0], o.budget()[0]
+    if fp32 == 0:
+        assert ok.all()
+        assert np.array_equal(fg[0] > 0, fo[0] > 0)
+        assert np.allclose(fg[0], fo[0], rtol=1e-9, atol=1e-12 * fo[0].max())
+    else:
+        assert ok.mean() > 0.99
+    assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
+    assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
+
+
+@pytest.mark.parametrize("mode", [W.REC_OTS_CASE_B, W.REC_CASE_A])
+def test_on_the_spot_and_case_a_modes(mode):
+    wl = W.cfg1(rec_mode=mode)
+    g, o = _pair(wl, transport_fp32=0)
+    for step in range(8):
+        g.step(step)
+        assert o.step(step) == 0
+    assert _xhi_ok(g.state()["x_HI"], o.state()["x_HI"]).all()
+    assert np.all(g.state()["N_rec"] == 0.0)
+
+
+@pytest.mark.parametrize("n_ngb,n_tc,n_rc,n_ec", [(16, 2, 8, 32), (24, 64, 32, 8), (12, 3, 8, 8)])
+def test_other_neighbour_and_cone_counts(n_ngb, n_tc, n_rc, n_ec):
+    wl = W.cfg1(n_side=12, n_ngb=n_ngb, n_tc=n_tc, n_rc=n_rc, n_ec=n_ec)
+    wl["x_HI"][:] = 0.05
+    g, o = _pair(wl, transport_fp32=0)
+    for a, b in zip(g.neighbours(), o.neighbours()):
+        assert np.array_equal(a, b)
+    for step in range(3):
+        g.step(step)
+        assert o.step(step) == 0
+    assert _xhi_ok(g.state()["x_HI"], o.state()["x_HI"]).all()
+    bg, bo = g.budget()[0], o.budget()[0]
+    assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
+
+
+def test_fixed_recombination_energy_and_evolving_temperature():
+    wl = W.cfg2(n_side=14, eps_rr_fixed=2.3 * W.EV)
+    g, o = _pair(wl, transport_fp32=0)
+    for step in range(3):
+        g.step(step)
+        o.step(step)
+    sg, so = g.state(), o.state()
+    assert np.all(sg["eps_rec"] == 2.3 * W.EV)
+    assert _xhi_ok(sg["x_HI"], so["x_HI"]).all()
+    assert (np.abs(sg["T"] / so["T"] - 1) < 1e-3).all()
+
+
+def test_parts_equal_the_whole_step():
+    """rt_assign_cones + rt_merge + rt_emit + rt_transport + rt_chemistry == rt_step."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg1()
+    a = rt.context_for(wl)
+    b = rt.context_for(wl)
+    for step in range(4):
+        a.step(step)
+        b.assign_cones(step)
+        b.merge()
+        b.emit(step)
+        b.transport(step)
+        b.chemistry()
+    assert np.array_equal(a.state()["x_HI"], b.state()["x_HI"])
+    assert np.array_equal(a.budget(), b.budget())
+
+
+def test_hop_cap_reports_and_conserves():
+    wl = W.cfg1(hop_cap=5)
+    wl["x_HI"][:] = 1e-3
+    g, o = _pair(wl, transport_fp32=0)
+    from paper_1311_0182_gb300 import rt
+    g.assign_cones(0); g.merge(); g.emit(0)
+    st = g.transport(0, allow_hop_limit=True)
+    assert st == 4                                  # RT_ERR_HOP_LIMIT
+    g.chemistry()
+    o.rotate(0); o.rebin(); o.emit(0)
+    assert o.transport(0) == 4
+    o.chemistry()
+    bg, bo = g.budget()[0], o.budget()[0]
+    assert np.allclose(bg, bo, rtol=1e-9, atol=1e-9 * bo[0])
+    assert abs(bg[0] - bg[1:].sum()) <= 1e-9 * bg[0]
+
+
+def test_free_packet_capacity_is_an_error_not_a_fault():
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg1(free_cap=300)
+    wl["x_HI"][:] = 1e-3
+    g = rt.context_for(wl)
+    with pytest.raises(rt.RTError) as e:
+        for step in range(3):
+            g.step(step)
+    assert e.value.status == 6                      # RT_ERR_CAPACITY
+    # the context still works for inspection after the error
+    assert g.state()["x_HI"].shape == (g.n,)
+
+
+def test_state_round_trip_host_and_device():
+    import torch
+    from paper_1311_0182_gb300 import rt
+    g = rt.context_for(W.cfg1())
+    g.step(0)
+    s = g.state()
+    x = torch.tensor(s["x_HI"] * 0.5, device="cuda")
+    g.set_state(x_HI=x)
+    assert np.allclose(g.state()["x_HI"], s["x_HI"] * 0.5, rtol=0, atol=0)
+    g.set_state(x_HI=s["x_HI"])
+    assert np.array_equal(g.state()["x_HI"], s["x_HI"])
