@@ -129,7 +129,9 @@ def run_ours(args):
         for _ in range(args.warmup):
             ctx.step(step)
             step += 1
-        ctx.profile(True)
+        # CUDA events around the modelled hop kernels only: the timed region stays close to an
+        # unprofiled run
+        ctx.profile(MODELLED)
         stream.synchronize()
         if dist:
             tdist.barrier()
@@ -147,10 +149,15 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         launches = ctx.launches() - launches0
         kt = ctx.kernel_times()
-        ctx.profile(False)
         clocks = clk.stop(local)
         st = ctx.stats()
         b = ctx.budget()
+        # one more (untimed) step with every kernel timed: the per-kernel shares of a step
+        ctx.profile(True)
+        ctx.step(step)
+        step += 1
+        shares = kernel_shares(ctx.kernel_times())
+        ctx.profile(False)
     if dist:
         from paper_1311_0182_gb300.distributed import max_over_ranks
         ms = max_over_ranks(ms, device="cuda")      # one replica per rank: the slowest decides
@@ -163,6 +170,7 @@ def run_ours(args):
            "clocks": clocks}
     # roofline of the dominant kernel
     out["roofline"] = roofline(ctx, kt, ms, args)
+    out["kernel_shares"] = shares
     out["stats_last_step"] = st
     out["budget_closure"] = float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])
     if not args.no_e2e:
@@ -178,6 +186,14 @@ def run_ours(args):
 
 
 MODELLED = ("phase_b_merge", "virtual_particles", "phase_a_send")
+
+
+def kernel_shares(kt: dict) -> dict:
+    """Per kernel of one profiled step: launches, ms and share of the summed kernel time."""
+    tot = sum(v["ms"] for v in kt.values()) or 1.0
+    return {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                "share": round(v["ms"] / tot, 4)}
+            for k, v in sorted(kt.items(), key=lambda kv: -kv[1]["ms"]) if v["ms"] > 0}
 
 
 def source_hash() -> str:
@@ -231,7 +247,7 @@ def roofline(ctx, kt, ms_step_total, args):
             "share_of_step": k["ms"] / ms_step_total if ms_step_total else None,
             "all_kernels": {n: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                 "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] and v["bytes"] else None}
-                            for n, v in kt.items()}}
+                            for n, v in kt.items() if v["ms"] > 0}}
 
 
 def fp64_path(args, stream):

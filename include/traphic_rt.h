@@ -82,8 +82,9 @@ typedef struct {
 /* rt_create -- validate cfg, allocate every device buffer for n_boxes boxes whose particle
    ranges are box_off[0..n_boxes] (host, box_off[0] = 0) with side lengths box_L (host, cm),
    and n_src sources.  Sizes only: particle and source data come with rt_set_particles and
-   rt_set_sources.  On success *out owns the allocations.  Errors: RT_ERR_INVALID,
-   RT_ERR_OOM, RT_ERR_CUDA (*out is NULL). */
+   rt_set_sources.  On success *out owns the allocations.  Limits: a box holds at most
+   2^22 - 1 particles, all boxes together fewer than 2^27.  Errors: RT_ERR_INVALID (also
+   beyond those limits), RT_ERR_KNN, RT_ERR_OOM, RT_ERR_CUDA (*out is NULL). */
 rt_status rt_create(const rt_config *cfg, int n_boxes, const long long *box_off,
                     const double *box_L, int n_src, rt_ctx **out);
 
@@ -194,17 +195,22 @@ rt_status rt_set_slots(rt_ctx *ctx, const double *f, int where, void *stream);
    each particle [n * nf] (the intensity diagnostic of Sec. 3); nf = n_freq_src + 1 */
 rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass, int where,
                           void *stream);
-/* statistics of the last rt_transport/rt_chemistry: hops, virtual particles, escaped virtual
-   particles, chemistry subcycles, subcycle-floor hits, peak free packets in a hop, peak
-   active slots in a hop, gas-to-gas contributions summed [8] (host) */
+/* statistics of the last rt_transport/rt_chemistry, out[RT_NSTATS] (host): hops, virtual
+   particles, escaped virtual particles, chemistry subcycles, subcycle-floor hits, peak free
+   packets in a hop, peak active slots in a hop; then summed over the hops of the last
+   transport: gas-to-gas contributions, particles with a packet able to move, packets able to
+   move, staged free-packet contributions, receiver work-list entries, occupied slots written
+   by the receiver side; out[13..15] are 0 */
+#define RT_NSTATS 16
 rt_status rt_get_stats(rt_ctx *ctx, long long *out);
 /* the isotropic cone direction set with n directions (8 or 32), [n * 3] host */
 rt_status rt_axis_set(int n, double *out);
 
-/* rt_set_profiling -- on != 0: record a pair of CUDA events on the launching stream around
-   every kernel launch and sum their durations per kernel; 0: stop.  Both reset the sums.
-   Synchronises the device.  The launch counter runs always. */
-rt_status rt_set_profiling(rt_ctx *ctx, int on);
+/* rt_set_profiling -- mask: bit k (k = the kernel's position in rt_get_profile's list)
+   records a pair of CUDA events on the launching stream around every launch of kernel k and
+   sums their durations; -1 profiles every kernel, 0 stops.  Resets the sums.  Synchronises
+   the device.  The launch counters run always. */
+rt_status rt_set_profiling(rt_ctx *ctx, int mask);
 
 /* rt_get_profile -- total kernel launches since rt_create, and per kernel (at most
    max_kernels entries, host arrays, NULL skips): its name (static string), launches, summed

@@ -80,7 +80,7 @@ static cudaEvent_t ev_take(rt_ctx *c) {
 }
 
 void kt_begin(rt_ctx *c, int id, cudaStream_t st) {
-    if (!c->prof) return;
+    if (!((c->prof >> id) & 1)) return;
     cudaEvent_t e0 = ev_take(c), e1 = ev_take(c);
     cudaEventRecord(e0, st);
     c->ev_pending.push_back({id, {e0, e1}});
@@ -89,7 +89,7 @@ void kt_begin(rt_ctx *c, int id, cudaStream_t st) {
 void kt_end(rt_ctx *c, int id, cudaStream_t st, int nlaunch) {
     c->launches += nlaunch;
     c->kstat[id].launches += nlaunch;
-    if (!c->prof) return;
+    if (!((c->prof >> id) & 1)) return;
     cudaEventRecord(c->ev_pending.back().second.second, st);
 }
 
@@ -113,7 +113,7 @@ extern "C" rt_status rt_set_profiling(rt_ctx *c, int on) {
     if (!c) return RT_ERR_INVALID;
     cudaDeviceSynchronize();
     kt_resolve(c);
-    c->prof = on ? 1 : 0;
+    c->prof = (unsigned)on & ((1u << KT_N) - 1u);
     for (int k = 0; k < KT_N; ++k) c->kstat[k] = KStat();
     return RT_OK;
 }
@@ -170,6 +170,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     if (box_off[0] != 0) return RT_ERR_INVALID;
     for (int b = 0; b < n_boxes; ++b) {
         if (box_off[b + 1] < box_off[b] + cfg->n_ngb + 1) return RT_ERR_KNN;
+        // the kNN search packs a box-local index into 22 bits
+        if (box_off[b + 1] - box_off[b] >= (1ll << 22)) return RT_ERR_INVALID;
         if (!(box_L[b] > 0.0)) return RT_ERR_INVALID;
     }
     long long n = box_off[n_boxes];
@@ -253,6 +255,19 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.vunit, double, n_boxes);
     A(P.esc_fx, unsigned long long, n_boxes);
     A(P.tally, double, 4 * n_boxes);
+    // budget chunks: each box cut into ranges of at most RT_BUDGET_CHUNK particles
+    std::vector<int> box_bch(n_boxes + 1, 0);
+    std::vector<long long> bch_lo;
+    for (int b = 0; b < n_boxes; ++b) {
+        box_bch[b] = (int)bch_lo.size();
+        for (long long i = box_off[b]; i < box_off[b + 1]; i += RT_BUDGET_CHUNK) bch_lo.push_back(i);
+    }
+    box_bch[n_boxes] = (int)bch_lo.size();
+    P.nbch = (int)bch_lo.size();
+    bch_lo.push_back(n);
+    A(P.box_bch, int, n_boxes + 1);
+    A(P.bch_lo, long long, P.nbch + 1);
+    A(P.bpart, double, 2 * (long long)P.nbch);
     A(x->src_emit, double, n_boxes);
     A(P.pbox, int, n);
     A(P.qx, int, n); A(P.qy, int, n); A(P.qz, int, n);
@@ -291,7 +306,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         A(P.occ[b], unsigned, nkey);
         A(P.act[b], unsigned, nkey);
     }
-    for (int f = 0; f < 6; ++f) P.rec[f] = dalloc(c, R * nslot, &ok);
+    P.rec = dalloc(c, 8 * R * nslot, &ok);
     A(P.bm, unsigned, n * P.kn * P.nf);
     A(P.revpos, int, n * P.kn);
     A(P.worklist, int, nkey);
@@ -344,6 +359,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     std::vector<double> u(n_boxes);
     for (int b = 0; b < n_boxes; ++b) u[b] = box_L[b] / (double)RT_Q;
     cudaMemcpy(P.box_off, box_off, sizeof(long long) * (n_boxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(P.box_bch, box_bch.data(), sizeof(int) * (n_boxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(P.bch_lo, bch_lo.data(), sizeof(long long) * (P.nbch + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_L, box_L, sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_u, u.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
     std::vector<float> uf(u.begin(), u.end());
@@ -863,7 +880,7 @@ extern "C" rt_status rt_get_deposits(rt_ctx *c, double *abs_, double *absE, doub
 
 extern "C" rt_status rt_get_stats(rt_ctx *c, long long *out) {
     if (!c || !out) return RT_ERR_INVALID;
-    for (int k = 0; k < 8; ++k) out[k] = c->stats[k];
+    for (int k = 0; k < RT_NSTATS; ++k) out[k] = c->stats[k];
     return RT_OK;
 }
 

@@ -148,7 +148,7 @@ rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st) {
     return rt_cuda_check(c, cudaGetLastError(), "chemistry");
 }
 
-// ---- photon budget: one block per box, fixed reduction order -----------------------------
+// ---- photon budget: fixed chunks of particles, fixed reduction order --------------------
 __device__ double block_sum(double v, double *sh) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -162,14 +162,14 @@ __device__ double block_sum(double v, double *sh) {
     return t;
 }
 
-// phase 0 (at emission): emitted += recombination photons of the last chemistry step +
-// the box's source photons of one step.  phase 1 (end of step): absorbed += sum of
-// absorptions; escaped += fixed-point escapes; in flight = photons held in slots.
+// One block per chunk (a fixed particle range inside one box): partial sums of
+// phase 0: the recombination photons of the last chemistry step;
+// phase 1: the absorptions, and the photons held in slots.
 template <typename Real>
-__global__ void k_budget(DevPtrs P, int phase, int cur, const double *src_emit) {
+__global__ void k_budget_part(DevPtrs P, int phase, int cur) {
     __shared__ double sh[32];
-    int b = blockIdx.x;
-    long long i0 = P.box_off[b], i1 = P.box_off[b + 1];
+    int ch = blockIdx.x;
+    long long i0 = P.bch_lo[ch], i1 = P.bch_lo[ch + 1];
     if (phase == 0) {
         double s = 0.0;
         for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
@@ -177,7 +177,7 @@ __global__ void k_budget(DevPtrs P, int phase, int cur, const double *src_emit) 
             if (Nr > 0.0) s += (Nr / (double)P.nrc) * (double)P.nrc;
         }
         double t = block_sum(s, sh);
-        if (threadIdx.x == 0) P.tally[4 * b + 0] += t + src_emit[b];
+        if (threadIdx.x == 0) P.bpart[2 * ch] = t;
         return;
     }
     double a = 0.0, fl = 0.0;
@@ -196,18 +196,39 @@ __global__ void k_budget(DevPtrs P, int phase, int cur, const double *src_emit) 
     double ta = block_sum(a, sh);
     double tf = block_sum(fl, sh);
     if (threadIdx.x == 0) {
-        P.tally[4 * b + 1] += ta;
-        P.tally[4 * b + 2] += (double)P.esc_fx[b] * (P.ref[b] / FX_ESC_SCALE);
-        P.esc_fx[b] = 0ull;
-        P.tally[4 * b + 3] = tf * P.norm[b];
+        P.bpart[2 * ch] = ta;
+        P.bpart[2 * ch + 1] = tf;
     }
+}
+
+// One thread per box: the box's chunk sums in chunk order.
+// phase 0 (at emission): emitted += recombination photons + the box's source photons of one
+// step.  phase 1 (end of step): absorbed += absorptions; escaped += fixed-point escapes;
+// in flight = photons held in slots.
+__global__ void k_budget_fin(DevPtrs P, int phase, const double *src_emit) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= P.nb) return;
+    double s0 = 0.0, s1 = 0.0;
+    for (int ch = P.box_bch[b]; ch < P.box_bch[b + 1]; ++ch) {
+        s0 += P.bpart[2 * ch];
+        s1 += P.bpart[2 * ch + 1];
+    }
+    if (phase == 0) {
+        P.tally[4 * b + 0] += s0 + src_emit[b];
+        return;
+    }
+    P.tally[4 * b + 1] += s0;
+    P.tally[4 * b + 2] += (double)P.esc_fx[b] * (P.ref[b] / FX_ESC_SCALE);
+    P.esc_fx[b] = 0ull;
+    P.tally[4 * b + 3] = s1 * P.norm[b];
 }
 
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st) {
     DevPtrs &P = c->d;
     kt_begin(c, KT_BUDGET, st);
-    if (P.fp32) k_budget<float><<<P.nb, 256, 0, st>>>(P, phase, c->cur, c->src_emit);
-    else k_budget<double><<<P.nb, 256, 0, st>>>(P, phase, c->cur, c->src_emit);
+    if (P.fp32) k_budget_part<float><<<P.nbch, 256, 0, st>>>(P, phase, c->cur);
+    else k_budget_part<double><<<P.nbch, 256, 0, st>>>(P, phase, c->cur);
+    k_budget_fin<<<(P.nb + 127) / 128, 128, 0, st>>>(P, phase, c->src_emit);
     kt_end(c, KT_BUDGET, st);
     return rt_cuda_check(c, cudaGetLastError(), "budget");
 }

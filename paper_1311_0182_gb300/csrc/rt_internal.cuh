@@ -16,6 +16,7 @@
 #include "../../include/traphic_rt.h"
 
 #define RT_Q 1048576          // 2^20 quantisation cells per box side
+#define RT_BUDGET_CHUNK 4096
 #define RT_MAXK 32            // maximum neighbours per particle
 #define RT_FREE_BIT (1ull << 63)
 
@@ -92,6 +93,11 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     double *box_L, *box_u, *norm, *ref, *vunit;
     unsigned long long *esc_fx;
     double *tally;            // [nb * 4]
+    // budget reduction: fixed chunks of RT_BUDGET_CHUNK particles (CSR over boxes)
+    int nbch;
+    int *box_bch;             // [nb + 1] first chunk of each box
+    long long *bch_lo;        // [nbch + 1] particle ranges
+    double *bpart;            // [nbch * 2]
     // particles
     int *pbox, *qx, *qy, *qz;
     double *nH, *NH, *xHI, *T, *Nrec, *epsrec, *nHI, *phot;
@@ -116,8 +122,10 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     // slots (double-buffered): 6 Real fields + occupancy/activity words per (i, nu)
     void *sl[2][6];
     unsigned *occ[2], *act[2];
-    // phase-A records (w, dx, dy, dz, clock, eps) and transposed cone bitmaps
-    void *rec[6];
+    // phase-A records, one per slot, 8 Real each (w, dx, dy, dz, clock, eps, unused, unused):
+    // the receiver side reads a record as one aligned 32-byte (FP32) or 64-byte (FP64) piece;
+    // and transposed cone bitmaps
+    void *rec;
     unsigned *bm;             // receiver-ordered cone bitmaps [nu * n * kn + p], p = reverse position
     int *revpos;              // position of forward entry (i, k) in the reverse lists
     unsigned *emp;            // empty-cone bits [n * nf]
@@ -166,7 +174,7 @@ struct rt_ctx {
     int fcur = 0;                 // free buffer of the current hop
     long long nfree_h = 0;        // free packets of the current hop (host copy)
     long long hop_global = 0;
-    long long stats[8] = {0};
+    long long stats[RT_NSTATS] = {0};
     std::string err;
     // scan scratch
     int *scan_tmp = nullptr;
@@ -174,7 +182,7 @@ struct rt_ctx {
     HopScratch hop = {};
     // launch counter and optional per-kernel timing (CUDA events on the launching stream)
     long long launches = 0;
-    int prof = 0;
+    unsigned prof = 0;         // bit mask of the kernels timed with events
     KStat kstat[KT_N];
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
@@ -313,26 +321,9 @@ static __device__ __noinline__ int bin_exact(const double *R, const double *axes
     return best;
 }
 
-#define BIN_BAND 2e-5f
-// Fast FP32 reception cone with a guard band on the margin between the two best scores.
-template <typename Real>
-__device__ inline int bin_fast(const float *Rf, const double *Rd, const float *axf,
-                               const double *axd, int nrc, Real d0, Real d1, Real d2) {
-    float f0 = (float)d0, f1 = (float)d1, f2 = (float)d2;
-    float e0 = __fmaf_rn(Rf[0], f0, __fmaf_rn(Rf[3], f1, Rf[6] * f2));
-    float e1 = __fmaf_rn(Rf[1], f0, __fmaf_rn(Rf[4], f1, Rf[7] * f2));
-    float e2 = __fmaf_rn(Rf[2], f0, __fmaf_rn(Rf[5], f1, Rf[8] * f2));
-    float b1 = -3.0f, b2 = -3.0f;
-    int best = 0;
-#pragma unroll 1
-    for (int b = 0; b < nrc; ++b) {
-        float sc = __fmaf_rn(e0, axf[3 * b], __fmaf_rn(e1, axf[3 * b + 1], e2 * axf[3 * b + 2]));
-        if (sc > b1) { b2 = b1; b1 = sc; best = b; }
-        else if (sc > b2) b2 = sc;
-    }
-    if (b1 - b2 > BIN_BAND) return best;
-    return bin_exact(Rd, axd, nrc, (double)d0, (double)d1, (double)d2);
-}
+// octahedral-map candidate table of the reception cones (bin_fast, rt_transport.cu)
+#define BIN_TAB_M 32
+#define BIN_TAB_ALL 0xfefefefeu   // table entry: scan every direction
 
 // M4 cubic spline of support 1 (unnormalised)
 template <typename Real>

@@ -80,7 +80,8 @@ __device__ __forceinline__ BoxGrid box_grid(const DevPtrs &P, int b) {
 }
 
 // one warp per gas particle (exclude itself) or source
-__global__ void k_knn(DevPtrs P, int sources) {
+__global__ void __launch_bounds__(256) k_knn(DevPtrs P, int sources) {
+    __shared__ int sdelta[8][32];
     int lane = threadIdx.x & 31;
     long long nq = sources ? P.ns : P.n;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -95,7 +96,7 @@ __global__ void k_knn(DevPtrs P, int sources) {
         }
         long long d2;
         int idx;
-        bool ok = warp_knn(box_grid(P, b), qx, qy, qz, ex, P.kn, d2, idx);
+        bool ok = warp_knn(box_grid(P, b), qx, qy, qz, ex, P.kn, d2, idx, sdelta[threadIdx.x >> 5]);
         if (!ok) {
             if (lane == 0) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_KNN);
             continue;

@@ -5,63 +5,60 @@
 // of cells around the query, then growing shells of cells (skipping cells that cannot hold a
 // point at or below the current k-th distance) until the k-th distance is below the distance
 // to the outside of the visited block.
+//
+// A pair is one 64-bit key, d2 * 2^22 + index: quantised offsets are below 2^20 per axis, so
+// d2 < 3 * 2^40 < 2^42, and a box holds fewer than 2^22 particles (checked when the context
+// is created).  Key order is the (d2, index) order, and one compare or shuffle pair moves it.
 #pragma once
 #include "rt_internal.cuh"
 
 #define KNN_INF 0x7fffffffffffffffll
+#define KNN_IDX_BITS 22
+#define KNN_IDX_MASK ((1ull << KNN_IDX_BITS) - 1ull)
+#define KNN_KEY_NONE 0xffffffffffffffffull
+// merge by insertion when at most this many candidates of a batch pass the k-th key
+#define KNN_INSERT_MAX 12
 
-struct KKey {
-    long long d2;
-    int idx;
-};
-
-__device__ __forceinline__ bool kless(long long da, int ia, long long db, int ib) {
-    return da < db || (da == db && ia < ib);
-}
-
-__device__ __forceinline__ void kshfl(long long &d2, int &idx, int src_lane, long long &od2,
-                                      int &oidx) {
-    od2 = __shfl_sync(FULLMASK, d2, src_lane);
-    oidx = __shfl_sync(FULLMASK, idx, src_lane);
+__device__ __forceinline__ unsigned long long knn_key(long long d2, int idx) {
+    return ((unsigned long long)d2 << KNN_IDX_BITS) | (unsigned long long)idx;
 }
 
 // bitonic sort (ascending) of one key per lane across the warp
-__device__ __forceinline__ void warp_sort(long long &d2, int &idx) {
+__device__ __forceinline__ void warp_sort(unsigned long long &k) {
     int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
+    for (int s = 2; s <= 32; s <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            long long od2;
-            int oidx;
-            kshfl(d2, idx, lane ^ j, od2, oidx);
-            bool up = ((lane & k) == 0);
+        for (int j = s >> 1; j > 0; j >>= 1) {
+            unsigned long long o = __shfl_xor_sync(FULLMASK, k, j);
+            bool up = ((lane & s) == 0);
             bool lower = (lane & j) == 0;
             bool take_min = (lower == up);
-            bool o_less = kless(od2, oidx, d2, idx);
-            if (take_min ? o_less : !o_less) { d2 = od2; idx = oidx; }
+            if (take_min ? o < k : o > k) k = o;
         }
     }
 }
 
 // top (sorted ascending across lanes) <- the 32 smallest of top U batch (batch unsorted)
-__device__ __forceinline__ void warp_merge(long long &td2, int &tidx, long long bd2, int bidx) {
+__device__ __forceinline__ void warp_merge(unsigned long long &t, unsigned long long b) {
     int lane = threadIdx.x & 31;
-    warp_sort(bd2, bidx);
-    long long rd2;
-    int ridx;
-    kshfl(bd2, bidx, 31 - lane, rd2, ridx);
-    if (kless(rd2, ridx, td2, tidx)) { td2 = rd2; tidx = ridx; }
-    // td2 is now bitonic: merge down
+    warp_sort(b);
+    unsigned long long r = __shfl_sync(FULLMASK, b, 31 - lane);
+    if (r < t) t = r;
+    // t is now bitonic: merge down
 #pragma unroll
     for (int j = 16; j > 0; j >>= 1) {
-        long long od2;
-        int oidx;
-        kshfl(td2, tidx, lane ^ j, od2, oidx);
+        unsigned long long o = __shfl_xor_sync(FULLMASK, t, j);
         bool lower = (lane & j) == 0;
-        bool o_less = kless(od2, oidx, td2, tidx);
-        if (lower ? o_less : !o_less) { td2 = od2; tidx = oidx; }
+        if (lower ? o < t : o > t) t = o;
     }
+}
+
+// insert key c (unique) into the sorted top list; a key above every entry changes nothing
+__device__ __forceinline__ void warp_insert(unsigned long long &t, unsigned long long c) {
+    int lane = threadIdx.x & 31;
+    unsigned long long p = __shfl_up_sync(FULLMASK, t, 1);
+    if (t > c) t = (lane == 0 || p < c) ? c : p;
 }
 
 struct BoxGrid {
@@ -85,10 +82,35 @@ __device__ __forceinline__ long long box_d2(int qx, int qy, int qz, int lx, int 
     return dx * dx + dy * dy + dz * dz;
 }
 
-// Visit a list of contiguous item ranges, one per lane (lane l owns [rs, rs + rc)); merge the
-// candidates into the running top-k.
+// Item base + lane of the concatenated ranges (lane l owns [rs, rs + rc), starting at position
+// excl of the concatenation); out-of-range lanes get index -2.  The lanes whose range starts
+// inside this batch publish (item start - position) at that batch position in sdelta (one
+// 32-entry array per warp); a lane takes the value of the last start at or before it, else
+// `carry`, the value in force at the end of the previous batch (updated here).
+__device__ __forceinline__ int4 knn_fetch(const BoxGrid &g, int base, int total, int rs, int rc,
+                                          int excl, int *sdelta, int &carry) {
+    int lane = threadIdx.x & 31;
+    bool st = rc > 0 && excl >= base && excl < base + 32;
+    if (st) sdelta[excl - base] = rs - excl;
+    unsigned sm = __reduce_or_sync(FULLMASK, st ? 1u << (excl - base) : 0u);
+    __syncwarp();
+    unsigned below = sm & (0xffffffffu >> (31 - lane));
+    int delta = below ? sdelta[31 - __clz(below)] : carry;
+    carry = __shfl_sync(FULLMASK, delta, 31);
+    __syncwarp();
+    int c = base + lane;
+    int4 it = make_int4(0, 0, 0, -2);
+    if (c < total) it = g.items[c + delta];
+    return it;
+}
+
+// Merge the candidates of a list of contiguous item ranges, one per lane, into the running
+// top list t; kth is the key held by lane kn - 1 (uniform), bkey the largest key allowed.
+// The items of the next batch of 32 are loaded before the current batch is merged, so the
+// load latency overlaps the merge.
 __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
-                                 int rs, int rc, long long bound, long long &td2, int &tidx) {
+                                 int rs, int rc, unsigned long long bkey, unsigned long long &t,
+                                 unsigned long long &kth, int *sdelta) {
     int lane = threadIdx.x & 31;
     // inclusive scan of range counts
     int incl = rc;
@@ -99,35 +121,36 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
     }
     int total = __shfl_sync(FULLMASK, incl, 31);
     int excl = incl - rc;
+    if (total == 0) return;
+    int carry = 0;
+    int4 nxt = knn_fetch(g, 0, total, rs, rc, excl, sdelta, carry);
     for (int base = 0; base < total; base += 32) {
-        int c = base + lane;
-        // owner lane: the last lane whose exclusive start is <= c
-        int lo = 0, hi = 31;
-#pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            int mid = (lo + hi + 1) >> 1;
-            int em = __shfl_sync(FULLMASK, excl, mid);
-            if (em <= c) lo = mid; else hi = mid - 1;
+        int4 it = nxt;
+        if (base + 32 < total) nxt = knn_fetch(g, base + 32, total, rs, rc, excl, sdelta, carry);
+        unsigned long long ck = KNN_KEY_NONE;
+        if (it.w >= 0 && it.w != exclude) {
+            long long dx = it.x - qx, dy = it.y - qy, dz = it.z - qz;
+            ck = knn_key(dx * dx + dy * dy + dz * dz, it.w);
         }
-        int o_rs = __shfl_sync(FULLMASK, rs, lo);
-        int o_ex = __shfl_sync(FULLMASK, excl, lo);
-        long long cd2 = KNN_INF;
-        int cidx = 0x7fffffff;
-        if (c < total) {
-            int4 it = g.items[o_rs + (c - o_ex)];
-            if (it.w != exclude) {
-                long long dx = it.x - qx, dy = it.y - qy, dz = it.z - qz;
-                cd2 = dx * dx + dy * dy + dz * dz;
-                cidx = it.w;
+        bool pass = ck < kth && ck <= bkey;
+        unsigned m = __ballot_sync(FULLMASK, pass);
+        if (!m) continue;
+        if (__popc(m) <= KNN_INSERT_MAX) {
+            // few candidates: insert them one by one (one that no longer beats the list's last
+            // entry falls off its end)
+            while (m) {
+                int src = __ffs(m) - 1;
+                m &= m - 1u;
+                warp_insert(t, __shfl_sync(FULLMASK, ck, src));
             }
+        } else if (__shfl_sync(FULLMASK, t, 0) == KNN_KEY_NONE) {
+            // first candidates: the sorted batch is the list
+            t = pass ? ck : KNN_KEY_NONE;
+            warp_sort(t);
+        } else {
+            warp_merge(t, pass ? ck : KNN_KEY_NONE);
         }
-        long long kd2 = __shfl_sync(FULLMASK, td2, kn - 1);
-        int kidx = __shfl_sync(FULLMASK, tidx, kn - 1);
-        bool better = cd2 <= bound && kless(cd2, cidx, kd2, kidx);
-        if (__any_sync(FULLMASK, better)) {
-            if (!better) { cd2 = KNN_INF; cidx = 0x7fffffff; }
-            warp_merge(td2, tidx, cd2, cidx);
-        }
+        kth = __shfl_sync(FULLMASK, t, kn - 1);
     }
 }
 
@@ -135,26 +158,39 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
 // point with local index `exclude` (-1: none).  Lane l < kn returns the l-th nearest.
 // `bound` is an upper bound on the squared distance of the kn-th neighbour (KNN_INF when none
 // is known): points and cells beyond it are skipped, which leaves the result unchanged.
+// sdelta: 32 ints of shared memory owned by the calling warp.
 // Returns false when the box holds fewer than kn candidates.
 __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
-                                long long &out_d2, int &out_idx, long long bound = KNN_INF) {
-    int lane = threadIdx.x & 31;
-    long long td2 = KNN_INF;
-    int tidx = 0x7fffffff;
+                                long long &out_d2, int &out_idx, int *sdelta,
+                                long long bound = KNN_INF) {
+    unsigned long long t = KNN_KEY_NONE, kth = KNN_KEY_NONE;
+    unsigned long long bkey = bound >= (1ll << 42) ? KNN_KEY_NONE - 1ull
+                                                   : knn_key(bound, (int)KNN_IDX_MASK);
     int G = g.G, cs = g.cs;
     int cx = cell_coord(qx, cs, G), cy = cell_coord(qy, cs, G), cz = cell_coord(qz, cs, G);
     for (int r = 1; r <= G; ++r) {
         // the columns (x, y) of the shell at Chebyshev radius r (r = 1: the whole 3x3x3 block)
         int side = 2 * r + 1;
         int ncol = side * side;
-        long long prune = __shfl_sync(FULLMASK, td2, kn - 1);   // cells farther cannot help
+        // cells farther than the current k-th distance (or the bound) cannot help
+        long long prune = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> KNN_IDX_BITS);
         if (bound < prune) prune = bound;
         for (int cb = 0; cb < ncol; cb += 32) {
-            int col = cb + lane;
+            int col = cb + (threadIdx.x & 31);
             // up to two z-ranges per column
             int rs0 = 0, rc0 = 0, rs1 = 0, rc1 = 0;
             if (col < ncol) {
-                int ix = cx - r + col / side, iy = cy - r + col % side;
+                int ix, iy;
+                if (r == 1) {
+                    // the 3x3 block: the query's column first, then the four sharing a face
+                    // with it, then the corners (near points first make the k-th distance tight
+                    // sooner); offsets + 1 packed two bits per column
+                    ix = cx - 1 + (int)((0x28251u >> (2 * col)) & 3u);
+                    iy = cy - 1 + (int)((0x22185u >> (2 * col)) & 3u);
+                } else {
+                    ix = cx - r + col / side;
+                    iy = cy - r + col % side;
+                }
                 if (ix >= 0 && iy >= 0 && ix < G && iy < G) {
                     bool edge = (r == 1) || ix == cx - r || ix == cx + r || iy == cy - r ||
                                 iy == cy + r;
@@ -179,9 +215,9 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
                     }
                 }
             }
-            knn_visit(g, qx, qy, qz, exclude, kn, rs0, rc0, bound, td2, tidx);
+            knn_visit(g, qx, qy, qz, exclude, kn, rs0, rc0, bkey, t, kth, sdelta);
             if (__any_sync(FULLMASK, rc1 > 0))
-                knn_visit(g, qx, qy, qz, exclude, kn, rs1, rc1, bound, td2, tidx);
+                knn_visit(g, qx, qy, qz, exclude, kn, rs1, rc1, bkey, t, kth, sdelta);
         }
         // distance from q to the outside of the visited block [c - r, c + r]^3
         long long b = -1;
@@ -197,12 +233,15 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
                 if (b < 0 || hi < b) b = hi;
             }
         }
-        long long kd2 = __shfl_sync(FULLMASK, td2, kn - 1);
         if (b < 0) break;
-        if (kd2 != KNN_INF && kd2 < b * b) break;
+        if (kth != KNN_KEY_NONE && (long long)(kth >> KNN_IDX_BITS) < b * b) break;
     }
-    out_d2 = td2;
-    out_idx = tidx;
-    long long kd2 = __shfl_sync(FULLMASK, td2, kn - 1);
-    return kd2 != KNN_INF;
+    if (t == KNN_KEY_NONE) {
+        out_d2 = KNN_INF;
+        out_idx = 0x7fffffff;
+    } else {
+        out_d2 = (long long)(t >> KNN_IDX_BITS);
+        out_idx = (int)(t & KNN_IDX_MASK);
+    }
+    return kth != KNN_KEY_NONE;
 }

@@ -26,6 +26,98 @@ static const double EV_ERG = 1.602176634e-12;
 // the two isotropic direction sets (index 0: 8 directions, 1: 32), FP64 and FP32 copies
 __constant__ double c_axd[2][96];
 __constant__ float c_axf[2][96];
+// FP32 copy in global memory for lane-divergent reads, and the candidate table of each set
+__device__ float g_axf[2][96];
+__device__ unsigned g_bin_tab[2][BIN_TAB_M * BIN_TAB_M];
+
+// Candidate table of a direction set.  Cell (i, j) of the octahedral map covers
+// u in [-1 + 2i/M, -1 + 2(i+1)/M], v likewise; its entry lists (one byte each, 0xff unused) the
+// directions D_b that can be the nearest for some direction p of the cell, i.e. whose gap
+// f_b(p) = p.D_b - max_a p.D_a comes near zero there.  f_b is 2-Lipschitz in p, and the
+// inverse map (u, v) -> p is 3-Lipschitz (the point on the octahedron moves by at most
+// sqrt(3) |d(u, v)| and has norm >= 1/sqrt(3)), so sampling the cell on a grid of spacing sp
+// bounds f_b everywhere in it to within 2 * 3 * sp / sqrt(2) of the sampled maximum.
+static void build_bin_table(const double *D, int nax, unsigned *tab) {
+    const int M = BIN_TAB_M, S = 17;
+    const double sp = 2.0 / (M * (S - 1.0));
+    const double thr = -(6.0 * sp / sqrt(2.0) + 1e-3);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double fmax[32];
+            for (int k = 0; k < nax; ++k) fmax[k] = -1e30;
+            for (int a = 0; a < S; ++a)
+                for (int b = 0; b < S; ++b) {
+                    double u = -1.0 + 2.0 * (i + a / (S - 1.0)) / M;
+                    double v = -1.0 + 2.0 * (j + b / (S - 1.0)) / M;
+                    double x = u, y = v, z = 1.0 - fabs(u) - fabs(v);
+                    if (z < 0.0) {
+                        x = (u < 0.0 ? -1.0 : 1.0) * (1.0 - fabs(v));
+                        y = (v < 0.0 ? -1.0 : 1.0) * (1.0 - fabs(u));
+                    }
+                    double nn = sqrt(x * x + y * y + z * z);
+                    x /= nn; y /= nn; z /= nn;
+                    double sc[32], best = -2.0;
+                    for (int k = 0; k < nax; ++k) {
+                        sc[k] = x * D[3 * k] + y * D[3 * k + 1] + z * D[3 * k + 2];
+                        best = std::max(best, sc[k]);
+                    }
+                    for (int k = 0; k < nax; ++k) fmax[k] = std::max(fmax[k], sc[k] - best);
+                }
+            unsigned w = 0xffffffffu;
+            int cnt = 0;
+            for (int k = 0; k < nax; ++k) {
+                if (!(fmax[k] > thr)) continue;
+                if (cnt < 4) w = (w & ~(0xffu << (8 * cnt))) | ((unsigned)k << (8 * cnt));
+                ++cnt;
+            }
+            tab[i * M + j] = cnt <= 4 ? w : BIN_TAB_ALL;
+        }
+}
+
+#define BIN_BAND 2e-5f
+// Reception cone of direction d at a particle with rotation R: argmax_b (R^T d) . D_b, first
+// maximum on ties.  FP32 scores of the cell's candidates with a guard band on the margin
+// between the two best; inside the band (or for a tie) the exact FP64 scan decides.  Every
+// direction left out of a cell is more than 1e-3 below the best everywhere in the cell, far
+// beyond the FP32 error (~1e-6), so the fast answer is the exact argmax.
+template <typename Real>
+__device__ inline int bin_fast(const float *Rf, const double *Rd, int ax, int nrc, Real d0,
+                               Real d1, Real d2) {
+    float f0 = (float)d0, f1 = (float)d1, f2 = (float)d2;
+    float e0 = __fmaf_rn(Rf[0], f0, __fmaf_rn(Rf[3], f1, Rf[6] * f2));
+    float e1 = __fmaf_rn(Rf[1], f0, __fmaf_rn(Rf[4], f1, Rf[7] * f2));
+    float e2 = __fmaf_rn(Rf[2], f0, __fmaf_rn(Rf[5], f1, Rf[8] * f2));
+    // octahedral map of e onto [-1, 1]^2
+    float is = __fdividef(1.0f, fabsf(e0) + fabsf(e1) + fabsf(e2));
+    float u = e0 * is, v = e1 * is;
+    if (e2 < 0.0f) {
+        float uu = copysignf(1.0f - fabsf(v), u), vv = copysignf(1.0f - fabsf(u), v);
+        u = uu;
+        v = vv;
+    }
+    int cu = min(max(__float2int_rd((u + 1.0f) * (0.5f * BIN_TAB_M)), 0), BIN_TAB_M - 1);
+    int cv = min(max(__float2int_rd((v + 1.0f) * (0.5f * BIN_TAB_M)), 0), BIN_TAB_M - 1);
+    unsigned c = __ldg(&g_bin_tab[ax][cu * BIN_TAB_M + cv]);
+    const float *axf = g_axf[ax];
+    float b1 = -3.0f, b2 = -3.0f;
+    int best = 0;
+    int nk = c == BIN_TAB_ALL ? nrc : 4;
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {
+        int b = c == BIN_TAB_ALL ? k : (int)((c >> (8 * k)) & 0xffu);
+        if (b == 0xff) break;
+        float sc = __fmaf_rn(e0, __ldg(&axf[3 * b]),
+                             __fmaf_rn(e1, __ldg(&axf[3 * b + 1]), e2 * __ldg(&axf[3 * b + 2])));
+        if (sc > b1) { b2 = b1; b1 = sc; best = b; }
+        else if (sc > b2) b2 = sc;
+    }
+    if (b1 - b2 > BIN_BAND) return best;
+    return bin_exact(Rd, c_axd[ax], nrc, (double)d0, (double)d1, (double)d2);
+}
+
+struct BinTables {
+    unsigned t[2][BIN_TAB_M * BIN_TAB_M];
+};
 
 void rt_upload_axes() {
     double d[2][96] = {{0}};
@@ -34,9 +126,21 @@ void rt_upload_axes() {
     rt_host_axis_set(32, d[1]);
     for (int a = 0; a < 2; ++a)
         for (int k = 0; k < 96; ++k) f[a][k] = (float)d[a][k];
+    static const BinTables *tab = [&d] {   // built once (thread-safe static initialisation)
+        BinTables *t = new BinTables;
+        build_bin_table(d[0], 8, t->t[0]);
+        build_bin_table(d[1], 32, t->t[1]);
+        return t;
+    }();
     cudaMemcpyToSymbol(c_axd, d, sizeof(d));
     cudaMemcpyToSymbol(c_axf, f, sizeof(f));
+    cudaMemcpyToSymbol(g_axf, f, sizeof(f));
+    cudaMemcpyToSymbol(g_bin_tab, tab->t, sizeof(tab->t));
 }
+
+// Resident 256-thread blocks per SM asked of the hop kernels: four (64 registers a thread)
+// for FP32 packets; three for FP64, whose wider values would otherwise spill.
+#define HOP_MINB(Real) (sizeof(Real) == 4 ? 4 : 3)
 
 template <typename Real> struct Slots {
     Real *N, *X, *Y, *Z, *C, *E;
@@ -45,6 +149,34 @@ template <typename Real> struct Slots {
         Z = (Real *)P.sl[b][3]; C = (Real *)P.sl[b][4]; E = (Real *)P.sl[b][5];
     }
 };
+
+// phase-A record of a slot: (w, d, clock, eps) in one aligned piece of 8 Real
+__device__ __forceinline__ void rec_store(void *rec, long long s, float w, float d0, float d1,
+                                          float d2, float c, float e) {
+    float4 *p = (float4 *)rec + 2 * s;
+    p[0] = make_float4(w, d0, d1, d2);
+    *(float2 *)(p + 1) = make_float2(c, e);
+}
+__device__ __forceinline__ void rec_store(void *rec, long long s, double w, double d0, double d1,
+                                          double d2, double c, double e) {
+    double2 *p = (double2 *)rec + 4 * s;
+    p[0] = make_double2(w, d0);
+    p[1] = make_double2(d1, d2);
+    p[2] = make_double2(c, e);
+}
+__device__ __forceinline__ void rec_load(const void *rec, long long s, float &w, float &d0,
+                                         float &d1, float &d2, float &c, float &e) {
+    const float4 *p = (const float4 *)rec + 2 * s;
+    float4 a = p[0];
+    float2 b = *(const float2 *)(p + 1);
+    w = a.x; d0 = a.y; d1 = a.z; d2 = a.w; c = b.x; e = b.y;
+}
+__device__ __forceinline__ void rec_load(const void *rec, long long s, double &w, double &d0,
+                                         double &d1, double &d2, double &c, double &e) {
+    const double2 *p = (const double2 *)rec + 4 * s;
+    double2 a = p[0], b = p[1], d = p[2];
+    w = a.x; d0 = a.y; d1 = b.x; d2 = b.y; c = d.x; e = d.y;
+}
 
 // unit direction of a packet from its summed momentum M (the luminosity-weighted mean
 // direction of merged packets, Sec. 2.1, Fig. 1b)
@@ -137,7 +269,7 @@ __global__ void k_rebin(DevPtrs P, int cur) {
         if (!((o >> b) & 1) || !(oN[b] > Real(0))) continue;
         Real d0, d1, d2;
         packet_dir(oX[b], oY[b], oZ[b], d0, d1, d2);
-        int nb = bin_fast<Real>(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC, d0, d1, d2);
+        int nb = bin_fast<Real>(Rf, Rd, P.ax_rc, NRC, d0, d1, d2);
         nN[nb] += oN[b]; nX[nb] += oX[b]; nY[nb] += oY[b]; nZ[nb] += oZ[b]; nE[nb] += oE[b];
     }
     unsigned no = 0;
@@ -234,21 +366,23 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
 // hop kernels
 // ------------------------------------------------------------------------------------------
 // Sender side.  Warp per particle.  The particle's packets able to move are taken 32 at a
-// time (lane = packet: load, direction, clock), then tested one after the other against the
-// neighbours (lane = neighbour k: cone membership, ballot).  For each (frequency, neighbour)
-// the bits of the packets whose cone holds the neighbour go to the neighbour's receiver-ordered
-// bitmap word; empty cones become virtual-particle requests.
+// time (lane = packet: load, direction, clock); each lane tests its packet against every
+// neighbour (unit offsets staged in shared memory) and gets the packet's membership mask.
+// A warp transpose of the 32 x 32 bit matrix gives each neighbour lane the packets whose cone
+// holds it; for each (frequency, neighbour) their bins go to the neighbour's receiver-ordered
+// bitmap word.  Empty cones become virtual-particle requests.
 template <typename Real, int NRC>
-__global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
-    int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int cur, int stamp) {
+    __shared__ float4 snh[8][32];          // per warp: unit offset to neighbour k (0: none)
+    __shared__ unsigned short spk[8][32];  // per warp: frequency * 256 + bin of chunk packet t
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     Slots<Real> S(P, cur);
-    Real *rw = (Real *)P.rec[0], *rx = (Real *)P.rec[1], *ry = (Real *)P.rec[2],
-         *rz = (Real *)P.rec[3], *rc = (Real *)P.rec[4], *re = (Real *)P.rec[5];
     float cf = 1.0f - 2.0f / (float)P.ntc;
     long long nrev = P.n * P.kn;
     long long ncon = 0;
+    int kn = P.kn;
     for (long long i = w0; i < P.n; i += nw) {
         unsigned aw = (lane < P.nf) ? P.act[cur][i * P.nf + lane] : 0u;
         if (__ballot_sync(FULLMASK, aw != 0u) == 0u) {
@@ -256,16 +390,23 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
             continue;
         }
         // neighbour k = lane
-        int nb = 0, dx = 0, dy = 0, dz = 0, rp = 0;
+        int nb = 0, rp = 0;
+        bool valid = lane < kn;
+        float4 nh = make_float4(0.f, 0.f, 0.f, 0.f);
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        bool valid = lane < P.kn;
         if (valid) {
-            long long f = i * P.kn + lane;
+            long long f = i * kn + lane;
             nb = P.nbr[f];
             rp = P.revpos[f];
             fx = P.fdx[f]; fy = P.fdy[f]; fz = P.fdz[f];
-            dx = (int)fx; dy = (int)fy; dz = (int)fz;
+            float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
+            if (r2 > 0.0f) {
+                float inv = rsqrtf(r2);
+                nh = make_float4(fx * inv, fy * inv, fz * inv, 0.f);
+            }
         }
+        __syncwarp();
+        snh[wib][lane] = nh;
         // active packets in (nu, b) order: prefix of the per-frequency counts
         int cnt = __popc(aw);
         int incl = cnt;
@@ -291,52 +432,81 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
             bool has = t < total;
             int ob = has ? __fns(ow, 0, t - oex + 1) : 0;
             long long s = i * P.S + (long long)onu * NRC + ob;
-            Real N = Real(0), d0 = Real(1), d1 = Real(0), d2 = Real(0), C = Real(0), E = Real(0);
+            spk[wib][lane] = (unsigned short)(onu * 256 + ob);
+            __syncwarp();
+            Real N = Real(0), d0 = Real(1), d1 = Real(0), d2 = Real(0);
             if (has) {
                 N = S.N[s];
                 packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
-                C = S.C[s];
-                E = S.E[s];
             }
+            // cone membership of each packet over the neighbours: with many packets, lane =
+            // packet looping over the neighbours; with few, lane = neighbour and one ballot per
+            // packet (the cost follows the packet count)
             int nb_chunk = min(32, total - cb);
-            int my_cm = 0;
             unsigned my_mask = 0u;
-            for (int u = 0; u < nb_chunk; ++u) {
-                Real e0 = __shfl_sync(FULLMASK, d0, u), e1 = __shfl_sync(FULLMASK, d1, u),
-                     e2 = __shfl_sync(FULLMASK, d2, u);
-                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, e0, e1, e2, cf, P.ntc);
-                unsigned m = __ballot_sync(FULLMASK, in);
-                if (lane == u) { my_mask = m; my_cm = __popc(m); }
+            if (nb_chunk >= 16) {
+                if (has) {
+                    float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
+                    for (int k = 0; k < kn; ++k) {
+                        float4 h = snh[wib][k];
+                        float cs = __fmaf_rn(h.x, e0, __fmaf_rn(h.y, e1, h.z * e2));
+                        bool in = cs > cf + CONE_BAND;
+                        if (!in && !(cs < cf - CONE_BAND)) {   // inside the guard band: exact
+                            long long f = i * kn + k;
+                            in = cone_exact((int)P.fdx[f], (int)P.fdy[f], (int)P.fdz[f],
+                                            (double)d0, (double)d1, (double)d2, P.ntc);
+                        }
+                        my_mask |= (unsigned)in << k;
+                    }
+                }
+            } else {
+                for (int u = 0; u < nb_chunk; ++u) {
+                    Real e0 = __shfl_sync(FULLMASK, d0, u), e1 = __shfl_sync(FULLMASK, d1, u),
+                         e2 = __shfl_sync(FULLMASK, d2, u);
+                    bool in = valid && cone_test<Real>((int)fx, (int)fy, (int)fz, fx, fy, fz, e0,
+                                                       e1, e2, cf, P.ntc);
+                    unsigned m = __ballot_sync(FULLMASK, in);
+                    if (lane == u) my_mask = m;
+                }
             }
-            ncon += (lane < nb_chunk) ? my_cm : 0;
-            if (has && my_cm > 0) {
-                rw[s] = N / (Real)my_cm;
-                rx[s] = d0; ry[s] = d1; rz[s] = d2;
-                rc[s] = C / N;
-                re[s] = E / N;
+            if (has) {
+                int my_cm = __popc(my_mask);
+                ncon += my_cm;
+                if (my_cm > 0)
+                    rec_store(P.rec, s, N / (Real)my_cm, d0, d1, d2, S.C[s] / N, S.E[s] / N);
             }
             // empty cones of this chunk, folded into the per-frequency words
-            bool empty = has && my_cm == 0;
+            bool empty = has && my_mask == 0u;
             unsigned emb = __ballot_sync(FULLMASK, empty);
             nreq += __popc(emb);
-            // bitmap words: lane k collects, frequency by frequency, the bins whose cone holds k
-            unsigned word = 0u;
-            int cur_nu = __shfl_sync(FULLMASK, onu, 0);
-            for (int u = 0; u < nb_chunk; ++u) {
-                int unu = __shfl_sync(FULLMASK, onu, u);
-                int ub = __shfl_sync(FULLMASK, ob, u);
-                unsigned um = __shfl_sync(FULLMASK, my_mask, u);
-                if (unu != cur_nu) {
-                    if (valid && word) {
-                        P.bm[(long long)cur_nu * nrev + rp] |= word;
-                        P.touched[(long long)nb * P.nf + cur_nu] = stamp;
-                    }
-                    word = 0u;
-                    cur_nu = unu;
-                }
-                if ((um >> lane) & 1u) word |= 1u << ub;
+            // transpose the (packet, neighbour) bit matrix: lane k gets the packets holding k
+            unsigned x = my_mask;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+                const unsigned m = j == 16 ? 0x0000ffffu : j == 8 ? 0x00ff00ffu : j == 4 ? 0x0f0f0f0fu
+                                 : j == 2 ? 0x33333333u : 0x55555555u;
+                unsigned y = __shfl_xor_sync(FULLMASK, x, j);
+                x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
             }
-            if (valid && word) {
+            // bitmap words: lane k collects, frequency by frequency, the bins whose cone holds k
+            if (valid && x) {
+                unsigned word = 0u;
+                int cur_nu = -1;
+                while (x) {
+                    int tt = __ffs(x) - 1;
+                    x &= x - 1u;
+                    int pk = spk[wib][tt];
+                    int unu = pk >> 8;
+                    if (unu != cur_nu) {
+                        if (word) {
+                            P.bm[(long long)cur_nu * nrev + rp] |= word;
+                            P.touched[(long long)nb * P.nf + cur_nu] = stamp;
+                        }
+                        word = 0u;
+                        cur_nu = unu;
+                    }
+                    word |= 1u << (pk & 255);
+                }
                 P.bm[(long long)cur_nu * nrev + rp] |= word;
                 P.touched[(long long)nb * P.nf + cur_nu] = stamp;
             }
@@ -345,6 +515,7 @@ __global__ void __launch_bounds__(256) k_phaseA(DevPtrs P, int cur, int stamp) {
                 unsigned red = __reduce_or_sync(FULLMASK, (empty && onu == q) ? (1u << ob) : 0u);
                 if (lane == q) emp_acc |= red;
             }
+            __syncwarp();
         }
         if (lane < P.nf) P.emp[i * P.nf + lane] = emp_acc;
         if (lane == 0) P.reqcnt[i] = nreq;
@@ -419,8 +590,7 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         Real tau = (sigma_of<Real>(P, nu) * ((Real *)P.nHIr)[j]) * l;
         Real A, T;
         split_absorbed<Real>(w, tau, A, T);
-        int bt = bin_fast<Real>(P.Rf + j * 9, P.R + j * 9, c_axf[P.ax_rc], c_axd[P.ax_rc], NRC,
-                                d0, d1, d2);
+        int bt = bin_fast<Real>(P.Rf + j * 9, P.R + j * 9, P.ax_rc, NRC, d0, d1, d2);
         long long key = j * P.nf + nu;
         P.st_key[s] = (int)key;
         P.st_bin[s] = bt;
@@ -465,12 +635,32 @@ __global__ void k_expand(DevPtrs P, const int *lens) {
     }
 }
 
+// No accepted draw: the point on the packet's axis at h/2 (at least one quantum), rounded to
+// the nearest integer offset.  FP64 path: in FP64.  FP32 path: in FP32 (fh = H/2 is exact,
+// the product is rounded once), so no FP64 instruction runs in the hop loop.
+__device__ __forceinline__ void axis_offset(double d0, double d1, double d2, long long H,
+                                            long long &Dx, long long &Dy, long long &Dz) {
+    double fh = 0.5 * (double)H;
+    if (fh < 1.0) fh = 1.0;
+    Dx = (long long)rint(__dmul_rn(d0, fh));
+    Dy = (long long)rint(__dmul_rn(d1, fh));
+    Dz = (long long)rint(__dmul_rn(d2, fh));
+}
+__device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long long H,
+                                            long long &Dx, long long &Dy, long long &Dz) {
+    float fh = fmaxf(0.5f * (float)(int)H, 1.0f);   // H < 2^21
+    Dx = __float2int_rn(__fmul_rn(d0, fh));
+    Dy = __float2int_rn(__fmul_rn(d1, fh));
+    Dz = __float2int_rn(__fmul_rn(d2, fh));
+}
+
 // Virtual particles (Sec. 2.1): one warp per request.
 template <typename Real, int NRC>
-__global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, const int *lens,
+__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur, const int *lens,
                                                  long long step, int hop,
                                                  unsigned long long *esc_r,
                                                  unsigned char *vstat) {
+    __shared__ int sdelta[8][32];   // kNN batch bookkeeping, one row per warp
     int lane = threadIdx.x & 31;
     long long nreq = lens[2];
     if (nreq > P.F_cap) nreq = P.F_cap;
@@ -512,8 +702,8 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             snb = Fi.nbr + f * P.kn;
         }
         // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
-        long long H = isqrt64(h2);   // = floor(sqrt(h2)) exactly (h2 < 2^62)
-        unsigned long long span = (unsigned long long)(2 * H + 1);
+        long long H = isqrt64(h2);   // = floor(sqrt(h2)) exactly (h2 < 3 * 2^40)
+        unsigned span = (unsigned)(2 * H + 1);   // < 2^22
         float cf = 1.0f - 2.0f / (float)P.ntc;
         long long Dx = 0, Dy = 0, Dz = 0;
         bool found = false;
@@ -521,29 +711,26 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
             unsigned a = (unsigned)(a0 + lane);
             uint4 u = philox4x32_10(make_uint4((unsigned)step, ((unsigned)hop << 8) | a,
                                                (unsigned)fid, (unsigned)(fid >> 32)), key);
-            long long ex = (long long)(((unsigned long long)u.x * span) >> 32) - H;
-            long long ey = (long long)(((unsigned long long)u.y * span) >> 32) - H;
-            long long ez = (long long)(((unsigned long long)u.z * span) >> 32) - H;
+            // floor(u * span / 2^32) - H, |e| <= H < 2^21: 32-bit integers (a 64-bit integer to
+            // float conversion would run on the FP64 pipe)
+            int ix = (int)__umulhi(u.x, span) - (int)H;
+            int iy = (int)__umulhi(u.y, span) - (int)H;
+            int iz = (int)__umulhi(u.z, span) - (int)H;
+            long long ex = ix, ey = iy, ez = iz;
             long long r2 = ex * ex + ey * ey + ez * ez;
             bool ok = r2 > 0 && r2 <= h2 &&
-                      cone_test<Real>((int)ex, (int)ey, (int)ez, (float)ex, (float)ey, (float)ez,
-                                      d0, d1, d2, cf, P.ntc);
+                      cone_test<Real>(ix, iy, iz, (float)ix, (float)iy, (float)iz, d0, d1, d2, cf,
+                                      P.ntc);
             unsigned m = __ballot_sync(FULLMASK, ok);
             if (m) {
                 int src = __ffs(m) - 1;
-                Dx = __shfl_sync(FULLMASK, ex, src);
-                Dy = __shfl_sync(FULLMASK, ey, src);
-                Dz = __shfl_sync(FULLMASK, ez, src);
+                Dx = __shfl_sync(FULLMASK, ix, src);
+                Dy = __shfl_sync(FULLMASK, iy, src);
+                Dz = __shfl_sync(FULLMASK, iz, src);
                 found = true;
             }
         }
-        if (!found) {
-            double fh = 0.5 * (double)H;
-            if (fh < 1.0) fh = 1.0;
-            Dx = (long long)rint(__dmul_rn((double)d0, fh));
-            Dy = (long long)rint(__dmul_rn((double)d1, fh));
-            Dz = (long long)rint(__dmul_rn((double)d2, fh));
-        }
+        if (!found) axis_offset(d0, d1, d2, H, Dx, Dy, Dz);
         long long vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
         if (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) {
             if (lane == 0) {
@@ -572,7 +759,7 @@ __global__ void __launch_bounds__(256) k_virtual(DevPtrs P, int cur, int fcur, c
         BoxGrid g;
         g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
         g.start = P.grid.start; g.items = P.grid.items;
-        warp_knn(g, (int)vx, (int)vy, (int)vz, -1, P.kn, kd2, kidx, sb2);
+        warp_knn(g, (int)vx, (int)vy, (int)vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2);
         long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
         bool valid = lane < P.kn;
         long long j = valid ? P.box_off[box] + kidx : 0;
@@ -733,18 +920,16 @@ __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long
     P.passf[key] += w;
 }
 
-#ifndef PHASEB_MINB
-#define PHASEB_MINB 3
-#endif
 // Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
 // cone.  Contributions are computed in parallel and merged in their fixed order by a
 // broadcast loop (the lane owning the target cone adds).  Groups come from the work list;
 // the next buffer's occupancy words were cleared before the launch.
 template <typename Real, int G>
-__global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur, int stamp, const int *wl_n) {
-    // contributions of the current chunk, one per lane: bin and 6 values (T, T d, T clock, T eps)
+__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int cur, int stamp, const int *wl_n) {
+    // contributions of the current chunk, one per lane: 6 values (T, T d, T clock, T eps); and
+    // per reception cone of each group, the mask of the chunk's lanes that feed it
     __shared__ Real sv[6][256];
-    __shared__ int sb[256];
+    __shared__ unsigned sm[256];
     int gl = threadIdx.x & (G - 1);
     int gbase = threadIdx.x - gl;               // first thread of this group in the block
     unsigned base = (threadIdx.x & 31) & ~(unsigned)(G - 1);
@@ -772,15 +957,22 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
         }
         sA.init(Real(0)); sAE.init(Real(0)); sW.init(Real(0));
         int box = P.pbox[j];
-        // merge this chunk's staged contributions (lanes gbase .. gbase + nbt - 1) in order
-        auto merge_chunk = [&](int nbt) {
+        // merge this chunk's contributions: lane gl of the group holds one for reception cone
+        // mybin (-1: none).  Lanes of equal cone find each other (match), the lowest of them
+        // publishes the set, and lane b adds the contributions to cone b in lane order.
+        auto merge_chunk = [&](int mybin) {
+            unsigned peers = __match_any_sync(gmask, mybin >= 0 ? mybin : G + gl);
+            sm[threadIdx.x] = 0u;
             __syncwarp(gmask);
-            for (int t2 = 0; t2 < nbt; ++t2) {
-                if (sb[gbase + t2] == gl) {
-                    aN.add(sv[0][gbase + t2]); aX.add(sv[1][gbase + t2]);
-                    aY.add(sv[2][gbase + t2]); aZ.add(sv[3][gbase + t2]);
-                    aC.add(sv[4][gbase + t2]); aE.add(sv[5][gbase + t2]);
-                }
+            if (mybin >= 0 && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0u)
+                sm[gbase + mybin] = peers >> base;
+            __syncwarp(gmask);
+            unsigned m = sm[threadIdx.x];
+            while (m) {
+                int t2 = gbase + __ffs(m) - 1;
+                m &= m - 1u;
+                aN.add(sv[0][t2]); aX.add(sv[1][t2]); aY.add(sv[2][t2]);
+                aZ.add(sv[3][t2]); aC.add(sv[4][t2]); aE.add(sv[5][t2]);
             }
             __syncwarp(gmask);
         };
@@ -789,9 +981,6 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
             Real sig_nhi = sigma_of<Real>(P, nu) * ((Real *)P.nHIr)[j];
             const float *Rf = P.Rf + j * 9;
             const double *Rd = P.R + j * 9;
-            const Real *rw = (const Real *)P.rec[0], *rx = (const Real *)P.rec[1],
-                       *ry = (const Real *)P.rec[2], *rz = (const Real *)P.rec[3],
-                       *rc = (const Real *)P.rec[4], *re = (const Real *)P.rec[5];
             int e0 = P.rev_off[j], e1 = P.rev_off[j + 1];
             unsigned *bmr = P.bm + (long long)nu * P.n * P.kn;
             for (int eb = e0; eb < e1; eb += G) {
@@ -831,11 +1020,12 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
                     float ofx = __shfl_sync(gmask, fx, lo, G);
                     float ofy = __shfl_sync(gmask, fy, lo, G);
                     float ofz = __shfl_sync(gmask, fz, lo, G);
+                    int mybin = -1;
                     if (c < total) {
                         int bsrc = __fns(o_w, 0, c - o_ex + 1);
                         long long ridx = (long long)o_si * P.S + (long long)nu * G + bsrc;
-                        Real w = rw[ridx], d0 = rx[ridx], d1 = ry[ridx], d2 = rz[ridx];
-                        Real clk = rc[ridx], eps = re[ridx];
+                        Real w, d0, d1, d2, clk, eps;
+                        rec_load(P.rec, ridx, w, d0, d1, d2, clk, eps);
                         Real t = (Real)ofx * d0 + (Real)ofy * d1 + (Real)ofz * d2;
                         Real l = t * u;
                         Real A, T;
@@ -843,8 +1033,7 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
                         sA.add(A);
                         sAE.add(A * eps);
                         sW.add(w);
-                        sb[threadIdx.x] = bin_fast<Real>(Rf, Rd, c_axf[P.ax_rc], c_axd[P.ax_rc], G,
-                                                         d0, d1, d2);
+                        mybin = bin_fast<Real>(Rf, Rd, P.ax_rc, G, d0, d1, d2);
                         sv[0][threadIdx.x] = T;
                         sv[1][threadIdx.x] = T * d0;
                         sv[2][threadIdx.x] = T * d1;
@@ -852,7 +1041,7 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
                         sv[4][threadIdx.x] = T * (clk + l / (Real)C_LIGHT);
                         sv[5][threadIdx.x] = T * eps;
                     }
-                    merge_chunk(min(G, total - cb));
+                    merge_chunk(mybin);
                 }
             }
         }
@@ -861,15 +1050,16 @@ __global__ void __launch_bounds__(256, PHASEB_MINB) k_phaseB(DevPtrs P, int cur,
             Real *const *V = (Real *const *)P.st_v;
             for (int cb = 0; cb < fc; cb += G) {
                 int c = cb + gl;
+                int mybin = -1;
                 if (c < fc) {
                     int s = P.seg_idx[so + c];
-                    sb[threadIdx.x] = P.st_bin[s];
+                    mybin = P.st_bin[s];
                     for (int f = 0; f < 6; ++f) sv[f][threadIdx.x] = V[f][s];
                     sA.add(V[6][s]);
                     sAE.add(V[7][s]);
                     sW.add(V[8][s]);
                 }
-                merge_chunk(min(G, fc - cb));
+                merge_chunk(mybin);
             }
         }
         Real N = aN.get();
@@ -1125,7 +1315,12 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     c->stats[2] = c->cnt_h[CNT_VESC];
     c->stats[5] = peak_free;
     c->stats[6] = peak_act;
-    c->stats[7] = c->launches;
+    c->stats[7] = c->cnt_h[CNT_GCON];
+    c->stats[8] = c->cnt_h[CNT_ACTP];
+    c->stats[9] = c->cnt_h[CNT_ACTS];
+    c->stats[10] = c->cnt_h[CNT_STG];
+    c->stats[11] = c->cnt_h[CNT_WLS];
+    c->stats[12] = c->cnt_h[CNT_OUT];
     long long e = c->cnt_h[CNT_ERR];
     if (e & ERRB_FREE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "free packets exceeded free_cap");
     if (e & ERRB_STAGE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "staged contributions exceeded capacity");

@@ -298,8 +298,21 @@ class Context:
                                            RT_HOST, self._s()), "rt_get_deposits")
         return a, e, ps
 
-    def profile(self, on: bool):
-        self._check(self.L.rt_set_profiling(self.h, int(on)), "rt_set_profiling")
+    def profile(self, on=True):
+        """Time kernels with CUDA events: True every kernel, False none, or an iterable of
+        kernel names (as kernel_times() reports them)."""
+        if on is True or on is False:
+            mask = -1 if on else 0
+        else:
+            names = self.kernel_names()
+            mask = 0
+            for nm in on:
+                mask |= 1 << names.index(nm)
+        self._check(self.L.rt_set_profiling(self.h, mask), "rt_set_profiling")
+
+    def kernel_names(self) -> list:
+        names = self._profile()[1]
+        return [names[k].decode() if names[k] else "" for k in range(32)]
 
     def _profile(self):
         nk = 32
@@ -321,10 +334,11 @@ class Context:
                 for k in range(32) if names[k] and la[k] > 0}
 
     def stats(self):
-        out = (C.c_longlong * 8)()
+        out = (C.c_longlong * 16)()
         self._check(self.L.rt_get_stats(self.h, out), "rt_get_stats")
         keys = ["hops", "virtual", "escaped_virtual", "subcycles", "floor_hits", "peak_free",
-                "peak_active", "gas_contrib"]
+                "peak_active", "gas_contrib", "senders", "moving_packets", "staged_contrib",
+                "receiver_groups", "receiver_outputs"]
         return dict(zip(keys, list(out)))
 
 

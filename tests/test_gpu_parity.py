@@ -372,3 +372,20 @@ def test_state_round_trip_host_and_device():
     assert np.allclose(g.state()["x_HI"], s["x_HI"] * 0.5, rtol=0, atol=0)
     g.set_state(x_HI=s["x_HI"])
     assert np.array_equal(g.state()["x_HI"], s["x_HI"])
+
+
+def test_profiling_mask_times_only_the_chosen_kernels():
+    """Kernels outside the mask are counted but not timed; the mask leaves results unchanged."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg1()
+    a = rt.context_for(wl)
+    b = rt.context_for(wl)
+    a.profile(["virtual_particles", "phase_a_send"])
+    for step in range(2):
+        a.step(step)
+        b.step(step)
+    kt = a.kernel_times()
+    assert kt["virtual_particles"]["ms"] > 0 and kt["phase_a_send"]["ms"] > 0
+    assert kt["phase_b_merge"]["launches"] > 0 and kt["phase_b_merge"]["ms"] == 0
+    a.profile(False)
+    assert np.array_equal(a.state()["x_HI"], b.state()["x_HI"])
