@@ -237,7 +237,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     long long ncell = 0;
     for (int b = 0; b < n_boxes; ++b) {
         long long nb = box_off[b + 1] - box_off[b];
-        int g = (int)cbrt((double)nb / 6.0);
+        int g = (int)cbrt((double)nb / 9.0);
         g = std::max(1, std::min(g, 512));
         G[b] = g;
         cs[b] = (int)((RT_Q + g - 1) / g);

@@ -366,23 +366,19 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
 // hop kernels
 // ------------------------------------------------------------------------------------------
 // Sender side.  Warp per particle.  The particle's packets able to move are taken 32 at a
-// time (lane = packet: load, direction, clock); each lane tests its packet against every
-// neighbour (unit offsets staged in shared memory) and gets the packet's membership mask.
-// A warp transpose of the 32 x 32 bit matrix gives each neighbour lane the packets whose cone
-// holds it; for each (frequency, neighbour) their bins go to the neighbour's receiver-ordered
-// bitmap word.  Empty cones become virtual-particle requests.
+// time (lane = packet: load, direction, clock), then tested one after the other against the
+// neighbours (lane = neighbour k: cone membership, ballot).  For each (frequency, neighbour)
+// the bits of the packets whose cone holds the neighbour go to the neighbour's receiver-ordered
+// bitmap word; empty cones become virtual-particle requests.
 template <typename Real, int NRC>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int cur, int stamp) {
-    __shared__ float4 snh[8][32];          // per warp: unit offset to neighbour k (0: none)
-    __shared__ unsigned short spk[8][32];  // per warp: frequency * 256 + bin of chunk packet t
-    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     Slots<Real> S(P, cur);
     float cf = 1.0f - 2.0f / (float)P.ntc;
     long long nrev = P.n * P.kn;
     long long ncon = 0;
-    int kn = P.kn;
     for (long long i = w0; i < P.n; i += nw) {
         unsigned aw = (lane < P.nf) ? P.act[cur][i * P.nf + lane] : 0u;
         if (__ballot_sync(FULLMASK, aw != 0u) == 0u) {
@@ -390,23 +386,16 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
             continue;
         }
         // neighbour k = lane
-        int nb = 0, rp = 0;
-        bool valid = lane < kn;
-        float4 nh = make_float4(0.f, 0.f, 0.f, 0.f);
+        int nb = 0, dx = 0, dy = 0, dz = 0, rp = 0;
         float fx = 0.f, fy = 0.f, fz = 0.f;
+        bool valid = lane < P.kn;
         if (valid) {
-            long long f = i * kn + lane;
+            long long f = i * P.kn + lane;
             nb = P.nbr[f];
             rp = P.revpos[f];
             fx = P.fdx[f]; fy = P.fdy[f]; fz = P.fdz[f];
-            float r2 = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, fz * fz));
-            if (r2 > 0.0f) {
-                float inv = rsqrtf(r2);
-                nh = make_float4(fx * inv, fy * inv, fz * inv, 0.f);
-            }
+            dx = (int)fx; dy = (int)fy; dz = (int)fz;
         }
-        __syncwarp();
-        snh[wib][lane] = nh;
         // active packets in (nu, b) order: prefix of the per-frequency counts
         int cnt = __popc(aw);
         int incl = cnt;
@@ -419,6 +408,8 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
         int excl = incl - cnt;
         int nreq = 0;
         unsigned emp_acc = 0u;        // lane nu: empty-cone bits of frequency nu
+        unsigned word = 0u;           // lane k: the current bitmap word and its frequency
+        int cur_nu = -1;
         for (int cb = 0; cb < total; cb += 32) {
             // lane t takes packet cb + t: its frequency (owner lane) and bin
             int t = cb + lane;
@@ -432,90 +423,56 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
             bool has = t < total;
             int ob = has ? __fns(ow, 0, t - oex + 1) : 0;
             long long s = i * P.S + (long long)onu * NRC + ob;
-            spk[wib][lane] = (unsigned short)(onu * 256 + ob);
-            __syncwarp();
-            Real N = Real(0), d0 = Real(1), d1 = Real(0), d2 = Real(0);
+            Real N = Real(0), d0 = Real(1), d1 = Real(0), d2 = Real(0), C = Real(0), E = Real(0);
             if (has) {
                 N = S.N[s];
                 packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
+                C = S.C[s];
+                E = S.E[s];
             }
-            // cone membership of each packet over the neighbours: with many packets, lane =
-            // packet looping over the neighbours; with few, lane = neighbour and one ballot per
-            // packet (the cost follows the packet count)
             int nb_chunk = min(32, total - cb);
+            int my_cm = 0;
             unsigned my_mask = 0u;
-            if (nb_chunk >= 16) {
-                if (has) {
-                    float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
-                    for (int k = 0; k < kn; ++k) {
-                        float4 h = snh[wib][k];
-                        float cs = __fmaf_rn(h.x, e0, __fmaf_rn(h.y, e1, h.z * e2));
-                        bool in = cs > cf + CONE_BAND;
-                        if (!in && !(cs < cf - CONE_BAND)) {   // inside the guard band: exact
-                            long long f = i * kn + k;
-                            in = cone_exact((int)P.fdx[f], (int)P.fdy[f], (int)P.fdz[f],
-                                            (double)d0, (double)d1, (double)d2, P.ntc);
-                        }
-                        my_mask |= (unsigned)in << k;
-                    }
-                }
-            } else {
-                for (int u = 0; u < nb_chunk; ++u) {
-                    Real e0 = __shfl_sync(FULLMASK, d0, u), e1 = __shfl_sync(FULLMASK, d1, u),
-                         e2 = __shfl_sync(FULLMASK, d2, u);
-                    bool in = valid && cone_test<Real>((int)fx, (int)fy, (int)fz, fx, fy, fz, e0,
-                                                       e1, e2, cf, P.ntc);
-                    unsigned m = __ballot_sync(FULLMASK, in);
-                    if (lane == u) my_mask = m;
-                }
+            for (int u = 0; u < nb_chunk; ++u) {
+                Real e0 = __shfl_sync(FULLMASK, d0, u), e1 = __shfl_sync(FULLMASK, d1, u),
+                     e2 = __shfl_sync(FULLMASK, d2, u);
+                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, e0, e1, e2, cf, P.ntc);
+                unsigned m = __ballot_sync(FULLMASK, in);
+                if (lane == u) { my_mask = m; my_cm = __popc(m); }
             }
-            if (has) {
-                int my_cm = __popc(my_mask);
-                ncon += my_cm;
-                if (my_cm > 0)
-                    rec_store(P.rec, s, N / (Real)my_cm, d0, d1, d2, S.C[s] / N, S.E[s] / N);
-            }
+            ncon += (lane < nb_chunk) ? my_cm : 0;
+            if (has && my_cm > 0) rec_store(P.rec, s, N / (Real)my_cm, d0, d1, d2, C / N, E / N);
             // empty cones of this chunk, folded into the per-frequency words
-            bool empty = has && my_mask == 0u;
+            bool empty = has && my_cm == 0;
             unsigned emb = __ballot_sync(FULLMASK, empty);
             nreq += __popc(emb);
-            // transpose the (packet, neighbour) bit matrix: lane k gets the packets holding k
-            unsigned x = my_mask;
-#pragma unroll
-            for (int j = 16; j > 0; j >>= 1) {
-                const unsigned m = j == 16 ? 0x0000ffffu : j == 8 ? 0x00ff00ffu : j == 4 ? 0x0f0f0f0fu
-                                 : j == 2 ? 0x33333333u : 0x55555555u;
-                unsigned y = __shfl_xor_sync(FULLMASK, x, j);
-                x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
-            }
             // bitmap words: lane k collects, frequency by frequency, the bins whose cone holds k
-            if (valid && x) {
-                unsigned word = 0u;
-                int cur_nu = -1;
-                while (x) {
-                    int tt = __ffs(x) - 1;
-                    x &= x - 1u;
-                    int pk = spk[wib][tt];
-                    int unu = pk >> 8;
-                    if (unu != cur_nu) {
-                        if (word) {
-                            P.bm[(long long)cur_nu * nrev + rp] |= word;
-                            P.touched[(long long)nb * P.nf + cur_nu] = stamp;
-                        }
-                        word = 0u;
-                        cur_nu = unu;
+            // (a word continues across chunks while the frequency does)
+            for (int u = 0; u < nb_chunk; ++u) {
+                int unu = __shfl_sync(FULLMASK, onu, u);
+                int ub = __shfl_sync(FULLMASK, ob, u);
+                unsigned um = __shfl_sync(FULLMASK, my_mask, u);
+                if (unu != cur_nu) {
+                    if (valid && word) {
+                        P.bm[(long long)cur_nu * nrev + rp] = word;
+                        P.touched[(long long)nb * P.nf + cur_nu] = stamp;
                     }
-                    word |= 1u << (pk & 255);
+                    word = 0u;
+                    cur_nu = unu;
                 }
-                P.bm[(long long)cur_nu * nrev + rp] |= word;
-                P.touched[(long long)nb * P.nf + cur_nu] = stamp;
+                if ((um >> lane) & 1u) word |= 1u << ub;
             }
             // empty-cone bins per frequency, gathered on lane nu
             for (int q = 0; q < P.nf; ++q) {
                 unsigned red = __reduce_or_sync(FULLMASK, (empty && onu == q) ? (1u << ob) : 0u);
                 if (lane == q) emp_acc |= red;
             }
-            __syncwarp();
+        }
+        // every word starts the hop at zero (the receiver side clears the words it reads), and
+        // each (frequency, neighbour) word is written once: a plain store
+        if (valid && word) {
+            P.bm[(long long)cur_nu * nrev + rp] = word;
+            P.touched[(long long)nb * P.nf + cur_nu] = stamp;
         }
         if (lane < P.nf) P.emp[i * P.nf + lane] = emp_acc;
         if (lane == 0) P.reqcnt[i] = nreq;
@@ -639,15 +596,15 @@ __global__ void k_expand(DevPtrs P, const int *lens) {
 // the nearest integer offset.  FP64 path: in FP64.  FP32 path: in FP32 (fh = H/2 is exact,
 // the product is rounded once), so no FP64 instruction runs in the hop loop.
 __device__ __forceinline__ void axis_offset(double d0, double d1, double d2, long long H,
-                                            long long &Dx, long long &Dy, long long &Dz) {
+                                            int &Dx, int &Dy, int &Dz) {
     double fh = 0.5 * (double)H;
     if (fh < 1.0) fh = 1.0;
-    Dx = (long long)rint(__dmul_rn(d0, fh));
-    Dy = (long long)rint(__dmul_rn(d1, fh));
-    Dz = (long long)rint(__dmul_rn(d2, fh));
+    Dx = (int)rint(__dmul_rn(d0, fh));
+    Dy = (int)rint(__dmul_rn(d1, fh));
+    Dz = (int)rint(__dmul_rn(d2, fh));
 }
 __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long long H,
-                                            long long &Dx, long long &Dy, long long &Dz) {
+                                            int &Dx, int &Dy, int &Dz) {
     float fh = fmaxf(0.5f * (float)(int)H, 1.0f);   // H < 2^21
     Dx = __float2int_rn(__fmul_rn(d0, fh));
     Dy = __float2int_rn(__fmul_rn(d1, fh));
@@ -669,8 +626,16 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     FreeBuf Fi = P.fr[fcur], Fo = P.fr[fcur ^ 1];
     Slots<Real> S(P, cur);
     uint2 key = philox_key(P.seed, 3u);
+    // Latency: the next request's code is loaded one request ahead; per-box and per-frequency
+    // values and the sender's neighbour positions are loaded before the position draws; the
+    // four per-neighbour inputs of the interpolation and deposit are gathered together; the
+    // values returned by the deposit atomics are checked one request later.
+    unsigned long long code_next = w0 < nreq ? P.req[w0] : 0ull;
+    unsigned long long pend_a = 0ull, pend_e = 0ull;   // words before this lane's last adds
+    bool bad = false;
     for (long long r = w0; r < nreq; r += nw) {
-        unsigned long long code = P.req[r];
+        unsigned long long code = code_next;
+        if (r + nw < nreq) code_next = P.req[r + nw];
         int box, qx, qy, qz, nu;
         long long h2;
         Real N, d0, d1, d2, clk, eps;
@@ -701,11 +666,18 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             fid = Fi.fid[f];
             snb = Fi.nbr + f * P.kn;
         }
+        long long boff = P.box_off[box];
+        Real sig = sigma_of<Real>(P, nu), bu = box_unit<Real>(P, box);
+        int sqx = 0, sqy = 0, sqz = 0;
+        if (lane < P.kn) {
+            int q = snb[lane];
+            sqx = P.qx[q]; sqy = P.qy[q]; sqz = P.qz[q];
+        }
         // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
         long long H = isqrt64(h2);   // = floor(sqrt(h2)) exactly (h2 < 3 * 2^40)
         unsigned span = (unsigned)(2 * H + 1);   // < 2^22
         float cf = 1.0f - 2.0f / (float)P.ntc;
-        long long Dx = 0, Dy = 0, Dz = 0;
+        int Dx = 0, Dy = 0, Dz = 0;   // |D| <= H < 2^21
         bool found = false;
         for (int a0 = 0; a0 < 64 && !found; a0 += 32) {
             unsigned a = (unsigned)(a0 + lane);
@@ -731,7 +703,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             }
         }
         if (!found) axis_offset(d0, d1, d2, H, Dx, Dy, Dz);
-        long long vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
+        int vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
         if (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) {
             if (lane == 0) {
                 esc_r[r] = esc_fixed(N, P, box);
@@ -743,10 +715,10 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         }
         // the sender's kn neighbours are kn points of the box: the farthest of them from the
         // virtual particle bounds its kn-th neighbour distance
+        bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
         long long sb2 = 0;
         if (lane < P.kn) {
-            int q = snb[lane];
-            long long ex = P.qx[q] - vx, ey = P.qy[q] - vy, ez = P.qz[q] - vz;
+            long long ex = sqx - vx, ey = sqy - vy, ez = sqz - vz;
             sb2 = ex * ex + ey * ey + ez * ez;
         }
 #pragma unroll
@@ -759,16 +731,18 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         BoxGrid g;
         g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
         g.start = P.grid.start; g.items = P.grid.items;
-        warp_knn(g, (int)vx, (int)vy, (int)vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2);
+        warp_knn(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2);
         long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
         bool valid = lane < P.kn;
-        long long j = valid ? P.box_off[box] + kidx : 0;
-        Real om = Real(0), nhj = Real(0), Vj = Real(0);
+        long long j = valid ? boff + kidx : 0;
+        Real om = Real(0), nhj = Real(0), Vj = Real(0), dsj = Real(0), dej = Real(0);
         if (valid) {
-            Real q = h2v > 0 ? rt_sqrt<Real>(to_real<Real>(kd2) / to_real<Real>(h2v)) : Real(0);
             Vj = ((Real *)P.Vr)[j];
-            om = Vj * kernel_w<Real>(q);
             nhj = ((Real *)P.nHIr)[j];
+            dsj = ((Real *)P.dep_s)[j];
+            dej = ((Real *)P.depE_s)[j];
+            Real q = h2v > 0 ? rt_sqrt<Real>(to_real<Real>(kd2) / to_real<Real>(h2v)) : Real(0);
+            om = Vj * kernel_w<Real>(q);
         }
         Real sw = om;
 #pragma unroll
@@ -784,9 +758,9 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) swn += __shfl_xor_sync(FULLMASK, swn, o);
         Real nHIv = swn / sw;
-        Real t = (Real)(int)Dx * d0 + (Real)(int)Dy * d1 + (Real)(int)Dz * d2;
-        Real l = t * box_unit<Real>(P, box);
-        Real tau = (sigma_of<Real>(P, nu) * nHIv) * l;
+        Real t = (Real)Dx * d0 + (Real)Dy * d1 + (Real)Dz * d2;
+        Real l = t * bu;
+        Real tau = (sig * nHIv) * l;
         Real A, T;
         split_absorbed<Real>(N, tau, A, T);
         if (valid && swn > Real(0) && wn > Real(0)) {
@@ -794,21 +768,19 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             long long key2 = j * P.nf + nu;
             // two fixed-point words: units of 2^-40 N_HI and 2^-72 N_HI (integer sums do not
             // depend on their order)
-            Real fa = Ak * ((Real *)P.dep_s)[j];
-            Real fe = Ak * eps * ((Real *)P.depE_s)[j];
+            Real fa = Ak * dsj;
+            Real fe = Ak * eps * dej;
+            pend_a = 0ull;
+            pend_e = 0ull;
             if (fa > Real(0)) {
-                unsigned long long qh = 0, ql = 0, old = 0;
-                bool inr = fx_split(fa, qh, ql);
-                if (qh) old = atomicAdd(&P.fx_abs[key2], qh);
+                unsigned long long qh = 0, ql = 0;
+                bad |= !fx_split(fa, qh, ql);
+                if (qh) pend_a = atomicAdd(&P.fx_abs[key2], qh);
                 if (ql) atomicAdd(&P.fx_lo[key2], ql);
-                if (!inr || old > (1ull << 62))
-                    atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
             }
             if (fe > Real(0)) {
-                unsigned long long q = to_fixed(fe);
-                unsigned long long old = atomicAdd(&P.fx_E[key2], q);
-                if (fe > Real(4.0e18) || old > (1ull << 62))
-                    atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
+                bad |= fe > Real(4.0e18);
+                pend_e = atomicAdd(&P.fx_E[key2], to_fixed(fe));
             }
         }
         if (valid) Fo.nbr[r * P.kn + lane] = (int)j;
@@ -816,7 +788,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             esc_r[r] = 0ull;
             vstat[r] = T > Real(0) ? 0 : 2;
             Fo.box[r] = box;
-            Fo.qx[r] = (int)vx; Fo.qy[r] = (int)vy; Fo.qz[r] = (int)vz;
+            Fo.qx[r] = vx; Fo.qy[r] = vy; Fo.qz[r] = vz;
             Fo.h2[r] = h2v;
             ((Real *)Fo.N)[r] = T;
             ((Real *)Fo.dx)[r] = d0; ((Real *)Fo.dy)[r] = d1; ((Real *)Fo.dz)[r] = d2;
@@ -826,6 +798,8 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             Fo.fid[r] = mix64(fid);
         }
     }
+    bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
+    if (bad) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
 }
 
 // receiver segments of the staged contributions
@@ -930,6 +904,11 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
     // per reception cone of each group, the mask of the chunk's lanes that feed it
     __shared__ Real sv[6][256];
     __shared__ unsigned sm[256];
+    // the current chunk of reverse edges: offset and sender; bitmap word and first
+    // contribution; and per contribution chunk, the edge lane where each range starts
+    __shared__ float4 se[256];
+    __shared__ uint2 sw2[256];
+    __shared__ int sown[256];
     int gl = threadIdx.x & (G - 1);
     int gbase = threadIdx.x - gl;               // first thread of this group in the block
     unsigned base = (threadIdx.x & 31) & ~(unsigned)(G - 1);
@@ -988,13 +967,11 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                 unsigned word = 0u;
                 int si = 0;
                 float fx = 0.f, fy = 0.f, fz = 0.f;
-                if (e < e1) {
+                if (e < e1) {   // the edge's data is loaded with its word (one memory round)
                     word = bmr[e];
-                    if (word) {
-                        bmr[e] = 0u;
-                        si = (int)(P.rev_ent[e] >> 5);
-                        fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
-                    }
+                    si = (int)(P.rev_ent[e] >> 5);
+                    fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
+                    if (word) bmr[e] = 0u;
                 }
                 int cw = __popc(word);
                 int incl = cw;
@@ -1005,28 +982,29 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                 }
                 int total = __shfl_sync(gmask, incl, G - 1, G);
                 int excl = incl - cw;
+                // the chunk's edges in shared memory; contribution c belongs to the edge whose
+                // range [excl, excl + cw) holds it
+                se[threadIdx.x] = make_float4(fx, fy, fz, __int_as_float(si));
+                sw2[threadIdx.x] = make_uint2(word, (unsigned)excl);
+                int carry = 0;   // owner of the last contribution of the previous chunk
                 for (int cb = 0; cb < total; cb += G) {
+                    bool st = cw > 0 && excl >= cb && excl < cb + G;
+                    if (st) sown[gbase + excl - cb] = gl;
+                    unsigned smk = __reduce_or_sync(gmask, st ? 1u << (excl - cb) : 0u);
+                    __syncwarp(gmask);
+                    unsigned below = smk & (0xffffffffu >> (31 - gl));
+                    int own = below ? sown[gbase + 31 - __clz(below)] : carry;
+                    carry = __shfl_sync(gmask, own, G - 1, G);
                     int c = cb + gl;
-                    int lo = 0, hi = G - 1;
-#pragma unroll
-                    for (int st = G; st > 1; st >>= 1) {
-                        int mid = (lo + hi + 1) >> 1;
-                        int em = __shfl_sync(gmask, excl, mid, G);
-                        if (em <= c) lo = mid; else hi = mid - 1;
-                    }
-                    int o_ex = __shfl_sync(gmask, excl, lo, G);
-                    unsigned o_w = __shfl_sync(gmask, word, lo, G);
-                    int o_si = __shfl_sync(gmask, si, lo, G);
-                    float ofx = __shfl_sync(gmask, fx, lo, G);
-                    float ofy = __shfl_sync(gmask, fy, lo, G);
-                    float ofz = __shfl_sync(gmask, fz, lo, G);
                     int mybin = -1;
                     if (c < total) {
-                        int bsrc = __fns(o_w, 0, c - o_ex + 1);
-                        long long ridx = (long long)o_si * P.S + (long long)nu * G + bsrc;
+                        float4 ed = se[gbase + own];
+                        uint2 ow = sw2[gbase + own];
+                        int bsrc = __fns(ow.x, 0, c - (int)ow.y + 1);
+                        long long ridx = (long long)__float_as_int(ed.w) * P.S + (long long)nu * G + bsrc;
                         Real w, d0, d1, d2, clk, eps;
                         rec_load(P.rec, ridx, w, d0, d1, d2, clk, eps);
-                        Real t = (Real)ofx * d0 + (Real)ofy * d1 + (Real)ofz * d2;
+                        Real t = (Real)ed.x * d0 + (Real)ed.y * d1 + (Real)ed.z * d2;
                         Real l = t * u;
                         Real A, T;
                         split_absorbed<Real>(w, sig_nhi * l, A, T);
