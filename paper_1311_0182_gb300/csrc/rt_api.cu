@@ -351,7 +351,16 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     long long maxscan = std::max(std::max(n + fc, segn), std::max(n * P.kn, ncell + 1));
     c->scan_tmp_n = (maxscan + 1023) / 1024 + 1;
     if (cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_n) != cudaSuccess) ok = false;
+    if (cudaMalloc(&c->scan_tmp2, sizeof(int) * c->scan_tmp_n) != cudaSuccess) ok = false;
     if (cudaMallocHost(&c->cnt_h, sizeof(long long) * CNT_N) != cudaSuccess) ok = false;
+    // the hop loop's second stream, at the highest priority: its receiver-side kernels take
+    // SM slots ahead of the virtual-particle kernel that runs beside them
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, prio_hi) != cudaSuccess)
+        ok = false;
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventCreateWithFlags(&c->hev[k], cudaEventDisableTiming) != cudaSuccess) ok = false;
     if (!ok) {
         rt_destroy(c);
         return RT_ERR_OOM;
@@ -391,7 +400,14 @@ extern "C" rt_status rt_destroy(rt_ctx *c) {
     if (!c) return RT_OK;
     for (size_t k = 0; k < c->allocs.size(); ++k) cudaFree(c->allocs[k]);
     if (c->scan_tmp) cudaFree(c->scan_tmp);
+    if (c->scan_tmp2) cudaFree(c->scan_tmp2);
     if (c->cnt_h) cudaFreeHost(c->cnt_h);
+    if (c->st2) {
+        cudaStreamSynchronize(c->st2);
+        cudaStreamDestroy(c->st2);
+    }
+    for (int k = 0; k < 4; ++k)
+        if (c->hev[k]) cudaEventDestroy(c->hev[k]);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return RT_OK;

@@ -179,6 +179,11 @@ struct rt_ctx {
     // scan scratch
     int *scan_tmp = nullptr;
     long long scan_tmp_n = 0;
+    int *scan_tmp2 = nullptr;     // scratch of the scans on the second stream
+    // second stream of the hop loop (work independent of the caller's stream's kernels) and
+    // the events that order the two
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t hev[4] = {nullptr, nullptr, nullptr, nullptr};
     HopScratch hop = {};
     // launch counter and optional per-kernel timing (CUDA events on the launching stream)
     long long launches = 0;
@@ -195,7 +200,7 @@ struct rt_ctx {
 rt_status rt_fail(rt_ctx *c, rt_status s, const std::string &msg);
 rt_status rt_cuda_check(rt_ctx *c, cudaError_t e, const char *what);
 void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
-                       int *d_total, cudaStream_t st);
+                       int *d_total, cudaStream_t st, int *tmp = nullptr);
 rt_status rt_knn_build(rt_ctx *c, cudaStream_t st);
 rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st);
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);

@@ -67,16 +67,14 @@ __global__ void k_scan_add(int *out, long long n, const int *btot) {
     if (i < n) out[i] += btot[blockIdx.x];
 }
 
+// tmp: block-total scratch of at least scan_tmp_n ints (default: the context's); two scans in
+// flight at once need two.  n never exceeds what rt_create sized scan_tmp_n for.
 void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
-                       int *d_total, cudaStream_t st) {
+                       int *d_total, cudaStream_t st, int *tmp) {
     long long nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
     if (nb < 1) nb = 1;
-    if (c->scan_tmp_n < nb) {
-        if (c->scan_tmp) cudaFree(c->scan_tmp);
-        cudaMalloc(&c->scan_tmp, sizeof(int) * nb);
-        c->scan_tmp_n = nb;
-    }
-    k_scan_blocks<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, out, n, d_len, c->scan_tmp);
-    k_scan_totals<<<1, SCAN_BLOCK, 0, st>>>(c->scan_tmp, nb, d_total);
-    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, c->scan_tmp);
+    if (!tmp) tmp = c->scan_tmp;
+    k_scan_blocks<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, out, n, d_len, tmp);
+    k_scan_totals<<<1, SCAN_BLOCK, 0, st>>>(tmp, nb, d_total);
+    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, tmp);
 }

@@ -876,13 +876,13 @@ __device__ __forceinline__ void deposit_group<double>(const DevPtrs &P, long lon
 template <>
 __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long key, long long j,
                                                      int box, float a, float ae, float w) {
+    // atomics: virtual-particle deposits into the same words may run at the same time
     float fa = a * ((float *)P.dep_s)[j];
     if (fa > 0.0f) {
         unsigned long long qh, ql;
         if (fx_split(fa, qh, ql)) {
-            unsigned long long old = P.fx_abs[key];
-            P.fx_abs[key] = old + qh;
-            P.fx_lo[key] += ql;
+            unsigned long long old = atomicAdd(&P.fx_abs[key], qh);
+            atomicAdd(&P.fx_lo[key], ql);
             if (old > (1ull << 62))
                 atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
         } else {
@@ -890,7 +890,7 @@ __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long
         }
     }
     float fe = ae * ((float *)P.depE_s)[j];
-    if (fe > 0.0f) P.fx_E[key] += f2u64_rz(fe + 0.5f);
+    if (fe > 0.0f) atomicAdd(&P.fx_E[key], f2u64_rz(fe + 0.5f));
     P.passf[key] += w;
 }
 
@@ -1169,12 +1169,13 @@ __global__ void k_drop_free(DevPtrs P, int fcur, const int *lens) {
 // host orchestration
 // ------------------------------------------------------------------------------------------
 
-#define LAUNCH(id, n, ...)          \
+#define LAUNCH_ON(sx, id, n, ...)   \
     do {                            \
-        kt_begin(c, id, st);        \
+        kt_begin(c, id, sx);        \
         __VA_ARGS__;                \
-        kt_end(c, id, st, n);       \
+        kt_end(c, id, sx, n);       \
     } while (0)
+#define LAUNCH(id, n, ...) LAUNCH_ON(st, id, n, __VA_ARGS__)
 
 template <typename Real, int NRC>
 static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st) {
@@ -1230,38 +1231,53 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         }
         int stamp = (int)(++c->hop_global);
         int cur = c->cur, nxt = cur ^ 1, fcur = c->fcur;
+        // Two streams.  st: gas senders, the request list, virtual particles, the hop counts.
+        // s2: free-packet senders and staging, receiver segments, work list, receiver side.
+        // s2 starts after everything before this hop on st; the work list waits for the gas
+        // senders (touched stamps, bitmaps, records); the request scan and its length check
+        // wait for the free-packet cone tests; the hop counts wait for the receiver side.
+        cudaStream_t s2 = c->st2;
+        cudaEvent_t evFork = c->hev[0], evA = c->hev[1], evFree = c->hev[2], evB = c->hev[3];
         cudaMemsetAsync(&P.cnt[CNT_ACTIVE], 0, sizeof(long long), st);
         cudaMemsetAsync(&P.cnt[CNT_LIVE], 0, sizeof(long long), st);
-        cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, st);
-        cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, st);
         // free packets of this hop: known on the host from the last hop's counters
         long long nfr = std::max<long long>(c->nfree_h, 1);
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 0)));
+        cudaEventRecord(evFork, st);
+        cudaStreamWaitEvent(s2, evFork, 0);
+        cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, s2);
+        cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, s2);
+        LAUNCH_ON(s2, KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
+        LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
+        cudaEventRecord(evFree, s2);
+        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur, stamp)));
-        LAUNCH(KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
-        LAUNCH(KT_SCAN, 6, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st),
-                            rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, st)));
+        cudaEventRecord(evA, st);
+        cudaStreamWaitEvent(st, evFree, 0);
+        LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 1)));
         LAUNCH(KT_EXPAND, 1, (k_expand<<<(unsigned)((n + nfr + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
-        LAUNCH(KT_FREE_C, 1, (k_freeC<Real, NRC><<<rt_blocks(nfr * 32, tb, gb), tb, 0, st>>>(P, fcur, H.lens, H.fmask, H.stoff)));
         LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
-        LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, st)));
-        LAUNCH(KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, st>>>(P, H.lens)));
-        LAUNCH(KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P)));
-        cudaMemsetAsync(H.lens + 4, 0, sizeof(int), st);
-        LAUNCH(KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, st>>>(P, cur, stamp, H.lens + 4)));
-        cudaMemsetAsync(P.occ[nxt], 0, sizeof(unsigned) * nkey, st);
-        cudaMemsetAsync(P.act[nxt], 0, sizeof(unsigned) * nkey, st);
-        LAUNCH(KT_PHASE_B, 1, (k_phaseB<Real, NRC><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, st>>>(P, cur, stamp, H.lens + 4)));
+        LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
+        LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
+        LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));
+        cudaMemsetAsync(H.lens + 4, 0, sizeof(int), s2);
+        cudaStreamWaitEvent(s2, evA, 0);
+        LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
+        cudaMemsetAsync(P.occ[nxt], 0, sizeof(unsigned) * nkey, s2);
+        cudaMemsetAsync(P.act[nxt], 0, sizeof(unsigned) * nkey, s2);
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
+        cudaEventRecord(evB, s2);
+        cudaStreamWaitEvent(st, evB, 0);
         LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, nxt, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 2)));
         c->cur = nxt;
         c->fcur = fcur ^ 1;
         ++hops;
         cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
-        rt_status s2 = rt_cuda_check(c, cudaStreamSynchronize(st), "hop");
-        if (s2 != RT_OK) return s2;
+        rt_status hs = rt_cuda_check(c, cudaStreamSynchronize(st), "hop");
+        if (hs != RT_OK) return hs;
         kt_resolve(c);
         if (c->cnt_h[CNT_ERR]) break;
         c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], P.F_cap);
