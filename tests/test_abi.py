@@ -57,3 +57,22 @@ def test_invalid_configuration_is_rejected_without_touching_a_gpu(lib):
     with pytest.raises(rt.RTError) as e:
         rt.Context(tiny)
     assert e.value.status == 5
+
+
+def test_box_too_large_for_the_knn_keys_is_rejected(lib):
+    """The kNN search packs a box-local index into 22 bits: a box of 2^22 particles is refused
+    before any device work."""
+    from paper_1311_0182_gb300 import rt, workloads as W
+    wl = W.cfg1()
+    big = dict(wl, box_off=np.array([0, 1 << 22]), box_L=np.array([1.0]))
+    with pytest.raises(rt.RTError) as e:
+        rt.Context(big)
+    assert e.value.status == 1
+    # one particle fewer passes the validation and then needs a device (checked where none is
+    # present: with a GPU it would allocate a 4M-particle context)
+    import torch
+    if not torch.cuda.is_available():
+        ok = dict(wl, box_off=np.array([0, (1 << 22) - 1]), box_L=np.array([1.0]))
+        with pytest.raises(rt.RTError) as e:
+            rt.Context(ok)
+        assert e.value.status == 3
