@@ -389,3 +389,21 @@ def test_profiling_mask_times_only_the_chosen_kernels():
     assert kt["phase_b_merge"]["launches"] > 0 and kt["phase_b_merge"]["ms"] == 0
     a.profile(False)
     assert np.array_equal(a.state()["x_HI"], b.state()["x_HI"])
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_runs_are_bitwise_reproducible(fp32):
+    """The hop loop runs on two streams with integer atomics; every floating-point sum has one
+    fixed order, so two runs of the same input agree bit for bit (the HII region at 24^3)."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg2(n_side=24, transport_fp32=fp32)
+    a = rt.context_for(wl)
+    b = rt.context_for(wl)
+    for step in range(3):
+        a.step(step)
+        b.step(step)
+    sa, sb = a.state(), b.state()
+    assert np.array_equal(sa["x_HI"], sb["x_HI"])
+    assert np.array_equal(sa["T"], sb["T"])
+    assert np.array_equal(a.budget(), b.budget())
+    assert np.array_equal(a.deposits()[0], b.deposits()[0])
