@@ -407,3 +407,47 @@ def test_runs_are_bitwise_reproducible(fp32):
     assert np.array_equal(sa["T"], sb["T"])
     assert np.array_equal(a.budget(), b.budget())
     assert np.array_equal(a.deposits()[0], b.deposits()[0])
+
+
+def test_workload1_all_200_steps_against_the_oracle():
+    """Workload 1 (16^3 Stromgren sphere, 8 cones) for all of its 200 steps of 2.5 Myr: both GPU
+    paths against the oracle at steps 50, 100 and 200 (x_HI bar and budget within 1e-6)."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg1()
+    o = oracle.Sim(wl)
+    o.build_neighbours()
+    gs = {fp: rt.context_for(dict(wl, params=dict(wl["params"], transport_fp32=fp))) for fp in (0, 1)}
+    for st in range(200):
+        assert o.step(st) == 0
+        for g in gs.values():
+            g.step(st)
+        if st in (49, 99, 199):
+            xo, bo = o.state()["x_HI"], o.budget()[0]
+            for fp, g in gs.items():
+                assert _xhi_ok(g.state()["x_HI"], xo).all(), (st, fp)
+                bg = g.budget()[0]
+                assert np.allclose(bg[:3], bo[:3], rtol=1e-6, atol=1e-6 * bo[0]), (st, fp)
+                assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
+    # the FP64 path follows the oracle to rounding
+    xg = gs[0].state()["x_HI"]
+    assert np.max(np.abs(xg / o.state()["x_HI"] - 1)) < 1e-10
+
+
+def test_full_size_batched_and_clump_workloads_conserve_photons():
+    """Workload 4 (512 boxes, 7.1M particles) and workload 3 (2.1M particles with a 200x clump,
+    the three recombination modes) at full size: every box closes its photon budget to 1e-6."""
+    from paper_1311_0182_gb300 import rt
+    g = rt.context_for(W.cfg4())
+    for st in range(2):
+        g.step(st)
+    b = g.budget()
+    assert (np.abs(b[:, 0] - b[:, 1:].sum(1)) <= 1e-6 * b[:, 0]).all()
+    assert g.stats()["virtual"] > 0
+    g.close()
+    wl3 = W.cfg3()
+    for mode in (W.REC_TRANSPORT, W.REC_OTS_CASE_B, W.REC_CASE_A):
+        g = rt.context_for(dict(wl3, params=dict(wl3["params"], rec_mode=mode)))
+        g.step(0)
+        b = g.budget()[0]
+        assert abs(b[0] - b[1:].sum()) <= 1e-6 * b[0]
+        g.close()
