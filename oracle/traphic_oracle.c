@@ -30,7 +30,7 @@ static const double EV = 1.602176634e-12;  /* erg */
 static const double C_LIGHT = 2.99792458e10; /* cm/s */
 static const double T_HI = 157807.0;       /* K, hydrogen ionisation temperature */
 
-enum { PURPOSE_RECEPTION = 1, PURPOSE_EMISSION = 2, PURPOSE_VIRTUAL = 3 };
+enum { PURPOSE_RECEPTION = 1, PURPOSE_EMISSION = 2, PURPOSE_VIRTUAL = 3, PURPOSE_REC_EMISSION = 4 };
 
 /* ------------------------------------------------------------------------------ */
 /* Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).    */
@@ -278,7 +278,8 @@ void orc_chem_particle(const orc_config *cfg, double nH, double NH, double phot,
             xn = x;
             intII = (1.0 - x) * h;
         }
-        if (cfg->rec_mode == ORC_REC_TRANSPORT) Nrec += (r[0] - r[1]) * ne * NH * intII;
+        if (cfg->rec_mode == ORC_REC_TRANSPORT || cfg->rec_mode == ORC_REC_EMISSION_CONES)
+            Nrec += (r[0] - r[1]) * ne * NH * intII;
         if (cfg->evolve_T) {
             double un = u + h * dudt;
             T = un / (1.5 * K_B * nH * (1.0 + (1.0 - xn)));
@@ -749,16 +750,16 @@ void orc_rebin(orc_sim *s) {
        emission axes; their clocks start at the beginning of the step. They leave the
        source in the first hop.
    Absorption and pass counters restart, and the neutral density seen by the transport
-   is frozen at its value at the start of the step (operator split, Sec. 2.1). */
+   is frozen at its value at the start of the step (operator split, Sec. 2.1).
+   With rec_mode ORC_REC_EMISSION_CONES, (1) is replaced by (3) below. */
 void orc_emit(orc_sim *s, long long step) {
-    (void)step;
     int S = s->S, nrc = s->cfg.n_rc, nfs = s->cfg.n_freq_src;
     for (long long i = 0; i < s->n * s->nf; ++i) { s->abs_[i] = 0.0; s->pass[i] = 0.0; }
     for (long long i = 0; i < s->n; ++i) {
         s->absE[i] = 0.0;
         s->nHI[i] = s->xHI[i] * s->nH[i];
     }
-    for (long long i = 0; i < s->n; ++i) {
+    for (long long i = 0; i < s->n && s->cfg.rec_mode != ORC_REC_EMISSION_CONES; ++i) {
         double Nr = s->Nrec[i];
         if (!(Nr > 0.0)) continue;
         double e = Nr / (double)nrc;
@@ -796,6 +797,40 @@ void orc_emit(orc_sim *s, long long step) {
                     tally_add(s, p.box, 0, p.N);
                     fl_push(&s->cur, &p);
                 }
+    /* (3) The original implementation of recombination radiation (Sec. 2.2): every particle
+       with recombination photons is a source with its own N_EC emission cones, rotated at
+       random before each of the K emissions of the step, like a star; its packets carry
+       N_rec / (K N_EC) photons each, stay separate from the packets the particle holds, and
+       leave it in the first hop through its own neighbours.  Packet identities follow
+       (particle, emission, cone) whether or not a particle emits. */
+    if (s->cfg.rec_mode == ORC_REC_EMISSION_CONES) {
+        int nrb = s->nf - 1;                       /* the recombination frequency bin */
+        for (long long i = 0; i < s->n; ++i) {
+            double Nr = s->Nrec[i];
+            if (!(Nr > 0.0)) continue;
+            for (int k = 0; k < s->K; ++k) {
+                double R[9];
+                orc_rotation(s->cfg.seed, PURPOSE_REC_EMISSION, (uint32_t)step, (uint32_t)k,
+                             (uint32_t)i, R);
+                for (int e = 0; e < nec; ++e) {
+                    freep_t p;
+                    memset(&p, 0, sizeof(p));
+                    p.box = s->box[i];
+                    p.q[0] = s->q[3 * i]; p.q[1] = s->q[3 * i + 1]; p.q[2] = s->q[3 * i + 2];
+                    memcpy(p.nbr, s->nbr + i * kn, sizeof(int32_t) * (size_t)kn);
+                    p.h2 = s->h2[i];
+                    p.N = Nr / (double)(s->K * nec);
+                    rotate_axis(R, s->axes_ec + 3 * e, p.d);
+                    p.clock = 0.0;
+                    p.eps = s->epsrec[i];
+                    p.nu = nrb;
+                    p.fid = (2ull << 62) | (uint64_t)((i * s->K + k) * nec + e);
+                    tally_add(s, p.box, 0, p.N);
+                    fl_push(&s->cur, &p);
+                }
+            }
+        }
+    }
 }
 
 /* N_abs = N_in (1 - exp(-tau)) and the transmitted rest (Sec. 2.1), evaluated so that both

@@ -23,7 +23,11 @@ extern "C" {
 #endif
 
 enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_HOP_LIMIT = 4 };
-enum { ORC_REC_TRANSPORT = 0, ORC_REC_OTS_CASE_B = 1, ORC_REC_CASE_A = 2 };
+/* recombination radiation: transported through the reception cones (Sec. 2.2, the new
+   implementation); on-the-spot case B; case A; transported through N_EC per-particle emission
+   cones whose packets stay separate (Sec. 2.2, the original implementation) */
+enum { ORC_REC_TRANSPORT = 0, ORC_REC_OTS_CASE_B = 1, ORC_REC_CASE_A = 2,
+       ORC_REC_EMISSION_CONES = 3 };
 /* cooling terms (bit flags): recombination, collisional excitation,
    collisional ionisation, free-free */
 enum { ORC_COOL_REC = 1, ORC_COOL_CEX = 2, ORC_COOL_CION = 4, ORC_COOL_FF = 8 };

@@ -27,7 +27,7 @@ EV = 1.602176634e-12
 K_B = 1.380649e-16
 T_HI = 157807.0
 
-REC_TRANSPORT, REC_OTS_CASE_B, REC_CASE_A = 0, 1, 2
+REC_TRANSPORT, REC_OTS_CASE_B, REC_CASE_A, REC_EMISSION_CONES = 0, 1, 2, 3
 COOL_REC, COOL_CEX, COOL_CION, COOL_FF = 1, 2, 4, 8
 
 
