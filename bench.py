@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--original", action="store_true",
+                    help="also time the original (emission-cone) recombination implementation")
     return ap.parse_args()
 
 
@@ -178,6 +180,11 @@ def run_ours(args):
     ctx.close()
     if not args.no_fp64 and args.precision == "fp32":
         out["fp64_path"] = fp64_path(args, stream)
+    if args.original:
+        # the original implementation of recombination radiation (Sec. 2.2): per-particle
+        # emission cones, on the same workload and precision
+        out["original_recombination"] = fp64_path(
+            args, stream, transport_fp32=int(args.precision == "fp32"), rec_mode=3)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
@@ -250,11 +257,12 @@ def roofline(ctx, kt, ms_step_total, args):
                             for n, v in kt.items() if v["ms"] > 0}}
 
 
-def fp64_path(args, stream):
-    """The all-FP64 GPU path on the same workload and start state (the comparison path)."""
+def fp64_path(args, stream, **over):
+    """The all-FP64 GPU path on the same workload and start state (the comparison path); with
+    `over`, the same timing for other parameters."""
     import torch
     from paper_1311_0182_gb300 import rt, workloads as W
-    wl = W.cfg2(n_side=args.n_side, transport_fp32=0)
+    wl = W.cfg2(n_side=args.n_side, **dict(dict(transport_fp32=0), **over))
     ctx = rt.Context(wl, stream=stream)
     steps = max(1, min(args.steps, 2))
     with torch.cuda.stream(stream):
@@ -273,7 +281,8 @@ def fp64_path(args, stream):
     n = int(wl["box_off"][-1])
     ctx.close()
     return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
-            "ms_per_step": ms / steps, "steps": steps, "dtype": "f64"}
+            "ms_per_step": ms / steps, "steps": steps,
+            "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
 
 
 def e2e(args, ctx, wl, stream, step, x0, T0):

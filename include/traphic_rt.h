@@ -52,7 +52,11 @@ typedef enum {
 typedef enum {
     RT_REC_TRANSPORT = 0,  /* case A rates; ground-level recombinations emitted and transported */
     RT_REC_OTS_CASE_B = 1, /* on-the-spot: case B rates, nothing emitted */
-    RT_REC_CASE_A = 2      /* case A rates, nothing emitted */
+    RT_REC_CASE_A = 2,     /* case A rates, nothing emitted */
+    RT_REC_EMISSION_CONES = 3 /* case A rates; the original implementation (Sec. 2.2): each
+                                 recombining particle emits n_ec separate packets in its own
+                                 randomly rotated emission cones, K times a step, sent in the
+                                 first hop like source packets */
 } rt_rec_mode;
 
 enum { RT_COOL_REC = 1, RT_COOL_CEX = 2, RT_COOL_CION = 4, RT_COOL_FF = 8 };

@@ -165,7 +165,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     if (cfg->n_ngb < 1 || cfg->n_ngb > RT_MAXK || cfg->n_tc < 2 || cfg->n_freq_src < 0 ||
         (cfg->n_rc != 8 && cfg->n_rc != 32) || (cfg->n_ec != 8 && cfg->n_ec != 32) ||
         !(cfg->dt > 0.0) || !(cfg->dt_em > 0.0) || cfg->hop_cap < 1 || cfg->sub_cap < 1 ||
-        cfg->rec_mode < 0 || cfg->rec_mode > 2)
+        cfg->rec_mode < 0 || cfg->rec_mode > 3)
         return RT_ERR_INVALID;
     if (box_off[0] != 0) return RT_ERR_INVALID;
     for (int b = 0; b < n_boxes; ++b) {
@@ -213,6 +213,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     P.cool_flags = cfg->cool_flags;
     P.seed = cfg->seed;
     long long np_src = (long long)n_src * P.K * P.nfs * P.nec;
+    // the original recombination implementation adds K * n_ec packets per particle
+    if (cfg->rec_mode == RT_REC_EMISSION_CONES) np_src += n * P.K * P.nec;
     long long fc = cfg->free_cap > 0 ? cfg->free_cap : std::max<long long>(65536, n * P.nrc / 2);
     fc = std::max(fc, np_src);
     P.F_cap = fc;

@@ -110,7 +110,8 @@ __global__ void k_chem(DevPtrs P) {
                 xn = x;
                 intII = (1.0 - x) * h;
             }
-            if (P.rec_mode == RT_REC_TRANSPORT) Nrec += (r.aA - r.aB) * ne * NH * intII;
+            if (P.rec_mode == RT_REC_TRANSPORT || P.rec_mode == RT_REC_EMISSION_CONES)
+                Nrec += (r.aA - r.aB) * ne * NH * intII;
             if (P.evolve_T) {
                 double un = u + h * dudt;
                 T = un / (1.5 * K_B * nH * (1.0 + (1.0 - xn)));
@@ -172,9 +173,12 @@ __global__ void k_budget_part(DevPtrs P, int phase, int cur) {
     long long i0 = P.bch_lo[ch], i1 = P.bch_lo[ch + 1];
     if (phase == 0) {
         double s = 0.0;
+        // the packets' photon counts as emitted: N_rec split over the reception cones, or over
+        // K emissions of n_ec emission cones in the original implementation
+        double parts = P.rec_mode == RT_REC_EMISSION_CONES ? (double)P.K * P.nec : (double)P.nrc;
         for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             double Nr = P.Nrec[i];
-            if (Nr > 0.0) s += (Nr / (double)P.nrc) * (double)P.nrc;
+            if (Nr > 0.0) s += (Nr / parts) * parts;
         }
         double t = block_sum(s, sh);
         if (threadIdx.x == 0) P.bpart[2 * ch] = t;

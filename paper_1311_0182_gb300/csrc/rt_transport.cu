@@ -305,7 +305,7 @@ __global__ void k_emit_rec(DevPtrs P, int cur) {
     ((Real *)P.dep_s)[i] = NHI > 0.0 ? (Real)(FX_ABS_SCALE * nm / NHI) : Real(0);
     ((Real *)P.depE_s)[i] = NHI > 0.0 ? (Real)(FX_E_SCALE * nm * P.eunit / (NHI * EV_ERG)) : Real(0);
     double Nr = P.Nrec[i];
-    if (!(Nr > 0.0)) return;
+    if (!(Nr > 0.0) || P.rec_mode == RT_REC_EMISSION_CONES) return;
     double e_phys = Nr / (double)NRC;
     Real e = (Real)(e_phys / nm);
     Real epsr = (Real)(P.epsrec[i] / P.eunit);
@@ -360,6 +360,40 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
     ((Real *)F.eps)[p] = (Real)(P.eps[nu] / P.eunit);
     F.nu[p] = nu;
     F.fid[p] = (1ull << 62) | (unsigned long long)p;
+}
+
+// The original implementation of recombination radiation (Sec. 2.2): particle i emits, K
+// times a step, n_ec packets of N_rec / (K n_ec) photons along its emission axes, rotated at
+// random before each emission; they are free packets at the particle's position with its
+// neighbour list, written after the source packets (index base + (i K + k) n_ec + e).
+// Particles without recombination photons leave packets of N = 0, which never move.
+template <typename Real>
+__global__ void k_emit_rec_cones(DevPtrs P, int fcur, long long base, long long step) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long per = (long long)P.K * P.nec;
+    if (p >= P.n * per) return;
+    long long i = p / per;
+    int k = (int)((p % per) / P.nec), e = (int)(p % P.nec);
+    FreeBuf F = P.fr[fcur];
+    long long f = base + p;
+    int b = P.pbox[i];
+    double Nr = P.Nrec[i];
+    double N = Nr > 0.0 ? __ddiv_rn(Nr, (double)per) : 0.0;
+    double R[9], d[3];
+    random_rotation(P.seed, 4u, (unsigned)step, (unsigned)k, (unsigned)i, R);
+    rot_apply(R, c_axd[P.ax_ec] + 3 * e, d);
+    F.box[f] = b;
+    F.qx[f] = P.qx[i]; F.qy[f] = P.qy[i]; F.qz[f] = P.qz[i];
+    for (int a = 0; a < P.kn; ++a) F.nbr[f * P.kn + a] = P.nbr[i * P.kn + a];
+    F.h2[f] = P.h2[i];
+    ((Real *)F.N)[f] = (Real)(N / P.norm[b]);
+    ((Real *)F.dx)[f] = (Real)d[0];
+    ((Real *)F.dy)[f] = (Real)d[1];
+    ((Real *)F.dz)[f] = (Real)d[2];
+    ((Real *)F.clock)[f] = Real(0);
+    ((Real *)F.eps)[f] = (Real)(P.epsrec[i] / P.eunit);
+    F.nu[f] = P.nf - 1;
+    F.fid[f] = (2ull << 62) | (unsigned long long)p;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1195,11 +1229,15 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     }
     if (part == 2) {  // emission
         LAUNCH(KT_EMIT_REC, 1, (k_emit_rec<Real, NRC><<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(P, c->cur)));
-        long long np = (long long)P.ns * P.K * P.nfs * P.nec;
+        long long np_s = (long long)P.ns * P.K * P.nfs * P.nec;
+        long long np_r = P.rec_mode == RT_REC_EMISSION_CONES ? n * P.K * P.nec : 0;
+        long long np = np_s + np_r;
         if (np > P.F_cap) return rt_fail(c, RT_ERR_CAPACITY, "source packets exceed free_cap");
         c->fcur = 0;
-        if (np > 0)
-            LAUNCH(KT_EMIT_SRC, 1, (k_emit_src<Real><<<(unsigned)((np + tb - 1) / tb), tb, 0, st>>>(P, c->fcur)));
+        if (np_s > 0)
+            LAUNCH(KT_EMIT_SRC, 1, (k_emit_src<Real><<<(unsigned)((np_s + tb - 1) / tb), tb, 0, st>>>(P, c->fcur)));
+        if (np_r > 0)
+            LAUNCH(KT_EMIT_SRC, 1, (k_emit_rec_cones<Real><<<(unsigned)((np_r + tb - 1) / tb), tb, 0, st>>>(P, c->fcur, np_s, step)));
         int npi = (int)np;
         cudaMemcpyAsync(H.lens, &npi, sizeof(int), cudaMemcpyHostToDevice, st);
         c->nfree_h = np;

@@ -287,6 +287,27 @@ def test_on_the_spot_and_case_a_modes(mode):
     assert np.all(g.state()["N_rec"] == 0.0)
 
 
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_original_emission_cone_recombination_mode(fp32):
+    """Recombination radiation through per-particle emission cones (Sec. 2.2, the original
+    implementation): free packets from every recombining particle in the first hop.  FP64: the
+    same numbers as the oracle to rounding; FP32: within the x_HI bar; budgets within 1e-6."""
+    wl = W.cfg1(rec_mode=W.REC_EMISSION_CONES, n_ec=8)
+    wl["x_HI"][:] = 0.05
+    g, o = _pair(wl, transport_fp32=fp32)
+    for step in range(6):
+        g.step(step)
+        assert o.step(step) == 0
+    xg, xo = g.state()["x_HI"], o.state()["x_HI"]
+    assert _xhi_ok(xg, xo).all()
+    if not fp32:
+        assert np.max(np.abs(xg / xo - 1)) < 1e-10
+    assert g.state()["N_rec"].max() > 0
+    bg, bo = g.budget()[0], o.budget()[0]
+    assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
+    assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
+
+
 @pytest.mark.parametrize("n_ngb,n_tc,n_rc,n_ec", [(16, 2, 8, 32), (24, 64, 32, 8), (12, 3, 8, 8)])
 def test_other_neighbour_and_cone_counts(n_ngb, n_tc, n_rc, n_ec):
     wl = W.cfg1(n_side=12, n_ngb=n_ngb, n_tc=n_tc, n_rc=n_rc, n_ec=n_ec)
