@@ -180,6 +180,7 @@ def run_ours(args):
     ctx.close()
     if not args.no_fp64 and args.precision == "fp32":
         out["fp64_path"] = fp64_path(args, stream)
+        out["fp32_vs_fp64_per_shell"] = precision_errors(args, stream)
     if args.original:
         # the original implementation of recombination radiation (Sec. 2.2): per-particle
         # emission cones, on the same workload and precision
@@ -283,6 +284,43 @@ def fp64_path(args, stream, **over):
     return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
             "ms_per_step": ms / steps, "steps": steps,
             "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
+
+
+def precision_errors(args, stream, steps=10):
+    """FP32-transport path against the all-FP64 path (which follows the oracle to rounding in
+    the parity tests), same workload and start, after `steps` steps: the relative error of x_HI
+    and T per radial shell around the source (shells of 1/16 of the box side)."""
+    import torch
+    import numpy as np
+    from paper_1311_0182_gb300 import rt, workloads as W
+    st = {}
+    for fp in (1, 0):
+        wl = W.cfg2(n_side=args.n_side, transport_fp32=fp)
+        ctx = rt.Context(wl, stream=stream)
+        with torch.cuda.stream(stream):
+            ctx.load_workload(wl)
+            ctx.build_neighbours()
+            for s in range(steps):
+                ctx.step(s)
+        st[fp] = ctx.state()
+        ctx.close()
+    pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
+    src = np.array([wl["src_x"][0], wl["src_y"][0], wl["src_z"][0]])
+    L = float(wl["box_L"][0])
+    r = np.linalg.norm(pos - src, axis=1) / L
+    out = {"steps": steps, "shell_width_of_box": 1 / 16, "shells": []}
+    for k in range(8):
+        m = (r >= k / 16) & (r < (k + 1) / 16)
+        if not m.any():
+            continue
+        sh = {"r_over_L": [k / 16, (k + 1) / 16], "particles": int(m.sum())}
+        for f in ("x_HI", "T"):
+            a, b = st[1][f][m], st[0][f][m]
+            rel = np.abs(a / b - 1)
+            sh[f] = {"median_rel": float(np.median(rel)), "max_rel": float(rel.max()),
+                     "median_value": float(np.median(b))}
+        out["shells"].append(sh)
+    return out
 
 
 def e2e(args, ctx, wl, stream, step, x0, T0):

@@ -81,6 +81,8 @@ typedef struct {
     double eps_rr_fixed;  /* excess energy of recombination photons, erg; < 0: kT of emitter */
     double sigma_rec;     /* grey cross-section of the recombination bin, cm^2 */
     long long free_cap;   /* capacity of free packets per hop (0: library default) */
+    int cell_occupancy;   /* particles per cell of the kNN grids; 0: chosen by timing the
+                             neighbour search over 5, 7, 9, 12 and 16 in rt_build_neighbours */
 } rt_config;
 
 /* rt_create -- validate cfg, allocate every device buffer for n_boxes boxes whose particle
@@ -204,7 +206,7 @@ rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass,
    packets in a hop, peak active slots in a hop; then summed over the hops of the last
    transport: gas-to-gas contributions, particles with a packet able to move, packets able to
    move, staged free-packet contributions, receiver work-list entries, occupied slots written
-   by the receiver side; out[13..15] are 0 */
+   by the receiver side; then the cell occupancy of the kNN grids in use; out[14..15] are 0 */
 #define RT_NSTATS 16
 rt_status rt_get_stats(rt_ctx *ctx, long long *out);
 /* the isotropic cone direction set with n directions (8 or 32), [n * 3] host */

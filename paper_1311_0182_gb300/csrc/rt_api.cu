@@ -157,6 +157,33 @@ extern "C" rt_status rt_axis_set(int n, double *out) {
     return RT_OK;
 }
 
+// cells per box side for a target occupancy
+static int grid_side(long long nb, int occupancy) {
+    int g = (int)cbrt((double)nb / (double)occupancy);
+    return std::max(1, std::min(g, 512));
+}
+
+void rt_set_grid(rt_ctx *c, int occupancy) {
+    DevPtrs &P = c->d;
+    int nb = P.nb;
+    std::vector<int> G(nb), cs(nb);
+    std::vector<long long> coff(nb);
+    long long ncell = 0;
+    for (int b = 0; b < nb; ++b) {
+        int g = grid_side(c->box_off_h[b + 1] - c->box_off_h[b], occupancy);
+        G[b] = g;
+        cs[b] = (int)((RT_Q + g - 1) / g);
+        coff[b] = ncell;
+        ncell += (long long)g * g * g;
+    }
+    P.grid.ncells = ncell;   // <= grid_cap: occupancy >= the smallest one allocated for
+    c->gridG_h = G;
+    c->cell_occ = occupancy;
+    cudaMemcpy(P.grid.G, G.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.grid.cs, cs.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.grid.coff, coff.data(), sizeof(long long) * nb, cudaMemcpyHostToDevice);
+}
+
 extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long long *box_off,
                                const double *box_L, int n_src, rt_ctx **out) {
     if (!out) return RT_ERR_INVALID;
@@ -233,21 +260,19 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     bool ok = true;
     size_t R = P.fp32 ? 4 : 8;
     long long nkey = n * P.nf, nslot = n * P.S;
-    // per-box grids
-    std::vector<int> G(n_boxes), cs(n_boxes);
-    std::vector<long long> coff(n_boxes);
+    // per-box grids: storage for the finest grid that can be chosen
+    if (cfg->cell_occupancy < 0) {
+        delete c;
+        return RT_ERR_INVALID;
+    }
+    c->cell_occ = cfg->cell_occupancy > 0 ? cfg->cell_occupancy : 9;
+    c->grid_tuned = cfg->cell_occupancy > 0;
     long long ncell = 0;
     for (int b = 0; b < n_boxes; ++b) {
         long long nb = box_off[b + 1] - box_off[b];
-        int g = (int)cbrt((double)nb / 9.0);
-        g = std::max(1, std::min(g, 512));
-        G[b] = g;
-        cs[b] = (int)((RT_Q + g - 1) / g);
-        coff[b] = ncell;
-        ncell += (long long)g * g * g;
+        int gmax = grid_side(nb, cfg->cell_occupancy > 0 ? cfg->cell_occupancy : RT_OCC_MIN);
+        ncell += (long long)gmax * gmax * gmax;
     }
-    P.grid.ncells = ncell;
-    c->gridG_h = G;
 #define A(ptr, T, cnt) ptr = (T *)dalloc(c, sizeof(T) * (size_t)(cnt), &ok)
     A(P.box_off, long long, n_boxes + 1);
     A(P.box_L, double, n_boxes);
@@ -299,6 +324,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.grid.cs, int, n_boxes);
     A(P.grid.coff, long long, n_boxes);
     A(P.grid.start, int, ncell + 1);
+    c->grid_cap = ncell;
     A(P.grid.items, int4, n);
     A(P.R, double, 9 * n);
     A(P.Rf, float, 9 * n);
@@ -383,9 +409,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         for (int b = 0; b < n_boxes; ++b)
             vu[b] = box_L[b] * box_L[b] * box_L[b] / (double)(box_off[b + 1] - box_off[b]);
     cudaMemcpy(P.vunit, vu.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
-    cudaMemcpy(P.grid.G, G.data(), sizeof(int) * n_boxes, cudaMemcpyHostToDevice);
-    cudaMemcpy(P.grid.cs, cs.data(), sizeof(int) * n_boxes, cudaMemcpyHostToDevice);
-    cudaMemcpy(P.grid.coff, coff.data(), sizeof(long long) * n_boxes, cudaMemcpyHostToDevice);
+    rt_set_grid(c, c->cell_occ);
     cudaMemset(P.touched, 0xff, sizeof(int) * nkey);
     x->src_emit_h.assign(n_boxes, 0.0);
     x->box_NH_h.assign(n_boxes, 0.0);
@@ -899,6 +923,7 @@ extern "C" rt_status rt_get_deposits(rt_ctx *c, double *abs_, double *absE, doub
 extern "C" rt_status rt_get_stats(rt_ctx *c, long long *out) {
     if (!c || !out) return RT_ERR_INVALID;
     for (int k = 0; k < RT_NSTATS; ++k) out[k] = c->stats[k];
+    out[13] = c->cell_occ;
     return RT_OK;
 }
 

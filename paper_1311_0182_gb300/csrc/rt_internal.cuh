@@ -17,6 +17,7 @@
 
 #define RT_Q 1048576          // 2^20 quantisation cells per box side
 #define RT_BUDGET_CHUNK 4096
+#define RT_OCC_MIN 5           // finest kNN grid the occupancy search tries
 #define RT_MAXK 32            // maximum neighbours per particle
 #define RT_FREE_BIT (1ull << 63)
 
@@ -166,6 +167,9 @@ struct rt_ctx {
     std::vector<long long> box_off_h;
     std::vector<double> box_L_h;
     std::vector<int> gridG_h;
+    int cell_occ = 9;              // particles per cell of the kNN grids in use
+    long long grid_cap = 0;        // cells allocated (the finest grid that can be chosen)
+    bool grid_tuned = false;       // occupancy chosen (or fixed by the configuration)
     long long *cnt_h = nullptr;   // pinned
     std::vector<void *> allocs;
     bool have_particles = false, have_sources = false, built = false;
@@ -202,6 +206,7 @@ rt_status rt_cuda_check(rt_ctx *c, cudaError_t e, const char *what);
 void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
                        int *d_total, cudaStream_t st, int *tmp = nullptr);
 rt_status rt_knn_build(rt_ctx *c, cudaStream_t st);
+void rt_set_grid(rt_ctx *c, int occupancy);   // per-box cell grids for a target occupancy
 rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st);
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);

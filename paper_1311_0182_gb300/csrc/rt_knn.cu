@@ -159,18 +159,58 @@ __global__ void k_rev_sort(DevPtrs P) {
     }
 }
 
-rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
+static void cell_lists(rt_ctx *c, cudaStream_t st) {
     DevPtrs &P = c->d;
-    long long n = P.n;
     int tb = 256;
-    unsigned nbk = (unsigned)((n + tb - 1) / tb);
-    // cell lists
+    unsigned nbk = (unsigned)((P.n + tb - 1) / tb);
     int *cnt = P.seg_cnt, *fill = P.seg_fill;   // scratch, sized >= max(ncells, n)
     cudaMemsetAsync(cnt, 0, sizeof(int) * (P.grid.ncells + 1), st);
     cudaMemsetAsync(fill, 0, sizeof(int) * (P.grid.ncells + 1), st);
     k_cell_count<<<nbk, tb, 0, st>>>(P, cnt);
     rt_scan_exclusive(c, cnt, P.grid.start, P.grid.ncells + 1, nullptr, nullptr, st);
     k_cell_fill<<<nbk, tb, 0, st>>>(P, fill);
+}
+
+// The occupancy of the kNN cell grids (the tile of candidates each search walks) is picked
+// on the particle set itself: the gas-particle kNN pass, the same warp search the virtual
+// particles run, is timed on each candidate grid and the fastest wins.  Done once per
+// context, at its first neighbour build; the result is the same search on another grid, so
+// only the time depends on the choice.
+static void tune_grid(rt_ctx *c, cudaStream_t st) {
+    static const int cand[] = {5, 7, 9, 12, 16};
+    DevPtrs &P = c->d;
+    int tb = 256;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 0.f;
+    int best = c->cell_occ;
+    for (int occ : cand) {
+        rt_set_grid(c, occ);
+        cell_lists(c, st);
+        cudaEventRecord(e0, st);
+        k_knn<<<rt_blocks(P.n * 32, tb, 152 * 64), tb, 0, st>>>(P, 0);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (occ == cand[0] || ms < best_ms) { best_ms = ms; best = occ; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rt_set_grid(c, best);
+    c->grid_tuned = true;
+}
+
+rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
+    DevPtrs &P = c->d;
+    long long n = P.n;
+    int tb = 256;
+    unsigned nbk = (unsigned)((n + tb - 1) / tb);
+    int *cnt = P.seg_cnt, *fill = P.seg_fill;
+    if (!c->grid_tuned) tune_grid(c, st);
+    // cell lists
+    cell_lists(c, st);
     // neighbours of particles and sources
     k_knn<<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, 0);
     if (P.ns > 0) k_knn<<<rt_blocks((long long)P.ns * 32, tb), tb, 0, st>>>(P, 1);

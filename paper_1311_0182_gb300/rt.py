@@ -38,7 +38,7 @@ class Config(C.Structure):
         ("rec_mode", C.c_int), ("evolve_T", C.c_int), ("transport_fp32", C.c_int),
         ("seed", C.c_ulonglong), ("hop_cap", C.c_int), ("sub_cap", C.c_int),
         ("cool_flags", C.c_int), ("T_floor", C.c_double), ("eps_rr_fixed", C.c_double),
-        ("sigma_rec", C.c_double), ("free_cap", C.c_longlong),
+        ("sigma_rec", C.c_double), ("free_cap", C.c_longlong), ("cell_occupancy", C.c_int),
     ]
 
 
@@ -102,7 +102,7 @@ def make_config(p: dict) -> Config:
         evolve_T=p["evolve_T"], transport_fp32=p.get("transport_fp32", 0), seed=p["seed"],
         hop_cap=p["hop_cap"], sub_cap=p["sub_cap"], cool_flags=p["cool_flags"],
         T_floor=p["T_floor"], eps_rr_fixed=p["eps_rr_fixed"], sigma_rec=p["sigma_rec"],
-        free_cap=p.get("free_cap", 0))
+        free_cap=p.get("free_cap", 0), cell_occupancy=p.get("cell_occupancy", 0))
 
 
 def _ptr(a):
@@ -338,7 +338,7 @@ class Context:
         self._check(self.L.rt_get_stats(self.h, out), "rt_get_stats")
         keys = ["hops", "virtual", "escaped_virtual", "subcycles", "floor_hits", "peak_free",
                 "peak_active", "gas_contrib", "senders", "moving_packets", "staged_contrib",
-                "receiver_groups", "receiver_outputs"]
+                "receiver_groups", "receiver_outputs", "cell_occupancy"]
         return dict(zip(keys, list(out)))
 
 

@@ -472,3 +472,23 @@ def test_full_size_batched_and_clump_workloads_conserve_photons():
         b = g.budget()[0]
         assert abs(b[0] - b[1:].sum()) <= 1e-6 * b[0]
         g.close()
+
+
+def test_grid_occupancy_search_changes_nothing_but_time():
+    """The kNN grid occupancy is picked by timing the neighbour search (cell_occupancy 0); any
+    grid gives the same exact neighbours, and the steps agree bit for bit."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg2(n_side=20)
+    ctxs = {occ: rt.context_for(dict(wl, params=dict(wl["params"], cell_occupancy=occ)))
+            for occ in (0, 5, 16)}
+    assert ctxs[0].stats()["cell_occupancy"] in (5, 7, 9, 12, 16)
+    assert ctxs[5].stats()["cell_occupancy"] == 5
+    ref = ctxs[5].neighbours()
+    for occ in (0, 16):
+        for a, b in zip(ctxs[occ].neighbours(), ref):
+            assert np.array_equal(a, b)
+    for g in ctxs.values():
+        for step in range(2):
+            g.step(step)
+    x = ctxs[5].state()["x_HI"]
+    assert all(np.array_equal(g.state()["x_HI"], x) for g in ctxs.values())
