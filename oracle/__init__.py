@@ -94,6 +94,9 @@ def lib():
             L.orc_get_deposits.argtypes = [vp, P(d), P(d), P(d)]
             L.orc_get_budget.argtypes = [vp, P(d)]
             L.orc_get_stats.argtypes = [vp, P(C.c_longlong)]
+            L.orc_set_source_options.argtypes = [vp, P(d), P(C.c_int)]
+            L.orc_set_barrier.argtypes = [vp, C.c_int, C.c_int, P(d), d]
+            L.orc_barrier_test.argtypes = [P(i64), P(i64), C.c_int, i64, i64, i64, i64]
             _lib = L
     return _lib
 
@@ -178,6 +181,12 @@ def knn(pts, qpts, k, self_offset=-1, use_grid=True):
     return idx, d2
 
 
+def barrier_test(a, b, axis, p2, c1, c2, r2) -> bool:
+    aa = np.ascontiguousarray(a, dtype=np.int64)
+    bb = np.ascontiguousarray(b, dtype=np.int64)
+    return bool(lib().orc_barrier_test(_p(aa, C.c_int64), _p(bb, C.c_int64), axis, p2, c1, c2, r2))
+
+
 # --- the simulation --------------------------------------------------------------------------
 class Sim:
     """One oracle simulation over the particles and sources of a workload dictionary."""
@@ -217,6 +226,14 @@ class Sim:
             _p(eps, d))
         if not self.h:
             raise ValueError("orc_create rejected the configuration")
+        # optional: directed / gated sources and photon barriers (Sec. 4 set-up)
+        if "src_dir" in wl or "src_gate" in wl:
+            sd = arr(wl.get("src_dir", np.zeros((self.ns, 3))), np.float64)
+            sg = arr(wl.get("src_gate", np.zeros(self.ns)), np.int32)
+            self.L.orc_set_source_options(self.h, _p(sd, d), _p(sg, C.c_int))
+        for (b, axis, centre, radius) in wl.get("barriers", []):
+            c = arr(centre, np.float64)
+            self.L.orc_set_barrier(self.h, int(b), int(axis), _p(c, d), float(radius))
 
     def __del__(self):
         h = getattr(self, "h", None)

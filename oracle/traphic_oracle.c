@@ -467,6 +467,15 @@ static void fl_push(freelist_t *l, const freep_t *p) {
     l->p[l->n++] = *p;
 }
 
+/* An artificial photon barrier (Sec. 4): a disk perpendicular to a coordinate axis that
+   removes every packet whose path crosses it.  In doubled quantised units: the plane sits at
+   the odd coordinate p2 along `axis` (no particle lies on it), the centre at (c1, c2) in the
+   other two axes (cyclic order), the radius is r2. */
+typedef struct {
+    int axis;
+    int64_t p2, c1, c2, r2;
+} barrier_t;
+
 struct orc_sim {
     orc_config cfg;
     int nb;
@@ -481,6 +490,9 @@ struct orc_sim {
     int *sbox;
     int64_t *sq;
     double *ndot, *sigma, *eps;
+    double *sdir;  /* [ns*3] fixed emission direction of a directed source, 0: isotropic */
+    int *sgate;    /* [ns] 1: emits only while its nearest gas particle has x_HI < 0.5 */
+    barrier_t *bar; /* [nb] photon barrier of each box (axis < 0: none) */
     int32_t *nbr, *snbr;
     int64_t *h2, *sh2;
     grid_t *grids;
@@ -571,6 +583,10 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
         s->sq[3 * i + 2] = quantise(sz[i], L);
         for (int f = 0; f < nfs; ++f) s->ndot[i * nfs + f] = ndot[i * nfs + f];
     }
+    s->sdir = (double *)calloc((size_t)(3 * n_src + 3), sizeof(double));
+    s->sgate = (int *)calloc((size_t)(n_src + 1), sizeof(int));
+    s->bar = (barrier_t *)calloc((size_t)n_boxes, sizeof(barrier_t));
+    for (int b = 0; b < n_boxes; ++b) s->bar[b].axis = -1;
     s->sigma = (double *)malloc(sizeof(double) * (size_t)s->nf);
     s->eps = (double *)malloc(sizeof(double) * (size_t)s->nf);
     for (int f = 0; f < nfs; ++f) {
@@ -610,6 +626,7 @@ void orc_destroy(orc_sim *s) {
     if (!s) return;
     free(s->box_off); free(s->box_L); free(s->q); free(s->box); free(s->nH); free(s->NH);
     free(s->xHI); free(s->T); free(s->sbox); free(s->sq); free(s->ndot); free(s->sigma);
+    free(s->sdir); free(s->sgate); free(s->bar);
     free(s->eps); free(s->nbr); free(s->h2); free(s->snbr); free(s->sh2);
     for (int b = 0; b < s->nb; ++b) grid_free(&s->grids[b]);
     free(s->grids); free(s->R); free(s->Rs);
@@ -617,6 +634,49 @@ void orc_destroy(orc_sim *s) {
     free(s->abs_); free(s->pass); free(s->absE); free(s->nHI); free(s->Nrec);
     free(s->epsrec); free(s->tally); free(s->tallc); free(s->cur.p); free(s->nxt.p);
     free(s);
+}
+
+void orc_set_source_options(orc_sim *s, const double *dir, const int *gate) {
+    for (int j = 0; j < s->ns; ++j) {
+        for (int a = 0; a < 3; ++a) s->sdir[3 * j + a] = dir ? dir[3 * j + a] : 0.0;
+        s->sgate[j] = gate ? gate[j] : 0;
+    }
+}
+
+void orc_set_barrier(orc_sim *s, int box, int axis, const double centre[3], double radius) {
+    barrier_t *B = &s->bar[box];
+    if (!(radius > 0.0) || axis < 0 || axis > 2) {
+        B->axis = -1;
+        return;
+    }
+    double L = s->box_L[box];
+    B->axis = axis;
+    B->p2 = 2 * quantise(centre[axis], L) + 1;
+    B->c1 = 2 * quantise(centre[(axis + 1) % 3], L);
+    B->c2 = 2 * quantise(centre[(axis + 2) % 3], L);
+    B->r2 = (int64_t)llround(2.0 * radius / L * (double)ORC_Q);
+}
+
+/* Does the straight path from a to b (quantised) cross the box's barrier disk?  Exact
+   integer test: the plane separates a and b, and the crossing point (a rational point) lies
+   within the radius; 128-bit products keep every term exact. */
+static int barrier_crosses(const barrier_t *B, const int64_t *a, const int64_t *b) {
+    if (B->axis < 0) return 0;
+    int ax = B->axis, i1 = (ax + 1) % 3, i2 = (ax + 2) % 3;
+    int64_t sa = 2 * a[ax] - B->p2, sb = 2 * b[ax] - B->p2;   /* odd: never 0 */
+    if ((sa < 0) == (sb < 0)) return 0;
+    int64_t D = sa - sb;
+    __int128 y = (__int128)(2 * a[i1] - B->c1) * D + (__int128)sa * (2 * (b[i1] - a[i1]));
+    __int128 z = (__int128)(2 * a[i2] - B->c2) * D + (__int128)sa * (2 * (b[i2] - a[i2]));
+    __int128 rD = (__int128)B->r2 * D;
+    return (unsigned __int128)(y * y) + (unsigned __int128)(z * z) <=
+           (unsigned __int128)(rD * rD);
+}
+
+int orc_barrier_test(const int64_t a[3], const int64_t b[3], int axis, int64_t p2, int64_t c1,
+                     int64_t c2, int64_t r2) {
+    barrier_t B = {axis, p2, c1, c2, r2};
+    return barrier_crosses(&B, a, b);
 }
 
 /* k nearest gas particles of point q in box b; returns global indices */
@@ -777,19 +837,33 @@ void orc_emit(orc_sim *s, long long step) {
     }
     s->cur.n = 0;
     int kn = s->cfg.n_ngb, nec = s->cfg.n_ec;
-    uint64_t idx = 0;
-    for (int j = 0; j < s->ns; ++j)
+    for (int j = 0; j < s->ns; ++j) {
+        /* a gated source (the boundary emitters of Sec. 4 and App. B) emits only once the
+           I-front has passed it: its nearest gas particle is more than half ionised */
+        if (s->sgate[j] && !(s->xHI[s->snbr[(long long)j * kn]] < 0.5)) continue;
+        const double *dir = s->sdir + 3 * j;
+        int directed = dir[0] != 0.0 || dir[1] != 0.0 || dir[2] != 0.0;
         for (int k = 0; k < s->K; ++k)
             for (int nu = 0; nu < nfs; ++nu)
-                for (int e = 0; e < nec; ++e, ++idx) {
+                for (int e = 0; e < nec; ++e) {
+                    /* a directed source (a packet of the plane-parallel front of Sec. 4) sends
+                       one packet per emission and frequency along its direction */
+                    if (directed && e > 0) continue;
+                    uint64_t idx = (((uint64_t)j * s->K + k) * nfs + nu) * nec + e;
                     freep_t p;
                     memset(&p, 0, sizeof(p));
                     p.box = s->sbox[j];
                     p.q[0] = s->sq[3 * j]; p.q[1] = s->sq[3 * j + 1]; p.q[2] = s->sq[3 * j + 2];
                     memcpy(p.nbr, s->snbr + (long long)j * kn, sizeof(int32_t) * (size_t)kn);
                     p.h2 = s->sh2[j];
-                    p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em / (double)nec;
-                    rotate_axis(s->Rs + 9 * ((long long)j * s->K + k), s->axes_ec + 3 * e, p.d);
+                    if (directed) {
+                        p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em;
+                        p.d[0] = dir[0]; p.d[1] = dir[1]; p.d[2] = dir[2];
+                    } else {
+                        p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em / (double)nec;
+                        rotate_axis(s->Rs + 9 * ((long long)j * s->K + k), s->axes_ec + 3 * e,
+                                    p.d);
+                    }
                     p.clock = 0.0;
                     p.eps = s->eps[nu];
                     p.nu = nu;
@@ -797,6 +871,7 @@ void orc_emit(orc_sim *s, long long step) {
                     tally_add(s, p.box, 0, p.N);
                     fl_push(&s->cur, &p);
                 }
+    }
     /* (3) The original implementation of recombination radiation (Sec. 2.2): every particle
        with recombination photons is a source with its own N_EC emission cones, rotated at
        random before each of the K emissions of the step, like a star; its packets carry
@@ -855,6 +930,10 @@ static void deliver(orc_sim *s, const int64_t *qs, long long j, double w, const 
                     double clock, double eps, int nu) {
     int nrc = s->cfg.n_rc, S = s->S;
     int b = s->box[j];
+    if (barrier_crosses(&s->bar[b], qs, s->q + 3 * j)) {   /* removed (Sec. 4): leaves the box */
+        tally_add(s, b, 2, w);
+        return;
+    }
     double u = s->box_L[b] / (double)ORC_Q;
     const int64_t *qj = s->q + 3 * j;
     double t = (double)(qj[0] - qs[0]) * d[0] + (double)(qj[1] - qs[1]) * d[1] +
@@ -928,6 +1007,10 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
         qv[2] >= ORC_Q) {
         tally_add(s, box, 2, N);
         s->st_escaped_v++;
+        return;
+    }
+    if (barrier_crosses(&s->bar[box], qs, qv)) {   /* removed on the way to the point */
+        tally_add(s, box, 2, N);
         return;
     }
     freep_t v;

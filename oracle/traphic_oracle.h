@@ -80,6 +80,19 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
                     const double *sy, const double *sz, const double *ndot,
                     const double *sigma, const double *eps);
 void orc_destroy(orc_sim *s);
+/* per source: a fixed unit emission direction (dir [ns*3], zero vector: isotropic emission
+   cones) and a gate (1: emits only while its nearest gas particle has x_HI < 0.5); NULL
+   resets to isotropic / ungated (Sec. 4 and App. B: the plane-parallel front and the
+   boundary emitters) */
+void orc_set_source_options(orc_sim *s, const double *dir, const int *gate);
+/* an artificial barrier in box `box` (Sec. 4): the disk of the given radius (cm) centred at
+   `centre` (box coordinates, cm), perpendicular to coordinate axis `axis`, removes every
+   packet whose straight path crosses it (counted as escaped); radius <= 0 removes it */
+void orc_set_barrier(orc_sim *s, int box, int axis, const double centre[3], double radius);
+/* the barrier test on its own (doubled quantised units, see orc_set_barrier): does the path
+   from a to b cross the disk? */
+int orc_barrier_test(const int64_t a[3], const int64_t b[3], int axis, int64_t p2, int64_t c1,
+                     int64_t c2, int64_t r2);
 int orc_build_neighbours(orc_sim *s);
 void orc_get_neighbours(const orc_sim *s, int32_t *nbr, int64_t *h2, int32_t *src_nbr,
                         int64_t *src_h2);

@@ -12,6 +12,8 @@ Workloads (seed = 1000 + number):
      3e51 s^-1 source; grey 1e5 K bin (Sec. 4 values); 0.1 Myr steps.
   4  512 independent boxes of 8^3..40^3 particles (log-uniform count), lognormal density fields.
   5  256^3 equal-mass particles sampled from a lognormal field in a 20 Mpc box, 256 sources.
+  6  the shadow test of Sec. 4: a plane-parallel front, a disk barrier and boundary emitters
+     of recombination radiation (App. B) in a 32^3 box.
 
 All quantities are cgs.  Positions are per box in [0, L).
 """
@@ -280,6 +282,62 @@ def cfg5(n_side=256, seed=1005, n_src=256, **kw):
     params.update(kw)
     return _pack(params, [L], [0, n], pos, nH, N_H, np.ones(n), np.full(n, 100.0),
                  np.zeros(n_src, np.int32), src, ndot[:, None], [1.6e-18], [6.3 * EV])
+
+
+def shadow(n_side=32, seed=1006, n_front=100, n_bnd=50, barrier=True, boundary=True,
+           rec_mode=REC_TRANSPORT, **kw):
+    """Workload 6, the shadow test of Sec. 4 (App. B).
+
+    A 13.2 kpc box of n_H = 1e-3 hydrogen on an n_side^3 jittered grid, neutral at 100 K,
+    T evolving.  A plane-parallel front of flux F = 1e6 s^-1 cm^-2 enters through x = 0: n_front^2
+    directed emitters on that face send their packets along +x (grey 1e5 K bin: sigma = 1.6e-18,
+    eps = 6.3 eV).  A disk barrier of radius 0.2 L at (0.27, 0.5, 0.5) L, perpendicular to x,
+    removes the packets that cross it.  The recombination radiation of the ionised gas outside
+    the box enters from the four sides parallel to x: n_bnd^2 isotropic emitters per side, each
+    switched on once the front has passed it, in their own bin (sigma = 6.3e-18, eps = 2.3 eV),
+    with the App. B intensity I = 0.63 lambda_mfp E_RR, E_RR = alpha_1 n_H^2 x_HII^2 and
+    lambda_mfp = 1251.37 kpc (App. B); alpha_1 = (2/3) alpha_B with alpha_B from t_rec = 122.4
+    Myr (Sec. 3) and alpha_1 / alpha_A ~ 0.4 (Sec. 1).  N_TC = 128, N_RC = N_EC = 8,
+    dt = dt_em = 0.1 Myr (Sec. 4)."""
+    rng = np.random.default_rng(seed)
+    L = 13.2 * KPC
+    n = n_side ** 3
+    pos = jittered_grid(n_side, L, rng)
+    nH = np.full(n, 1e-3)
+    NH = np.full(n, 1e-3 * L ** 3 / n)
+    F = 1e6
+    # front emitters on the x = 0 face
+    g = (np.arange(n_front) + 0.5) / n_front * L
+    fy, fz = np.meshgrid(g, g, indexing="ij")
+    front = np.stack([np.zeros(n_front ** 2), fy.ravel(), fz.ravel()], 1)
+    # boundary emitters on the y = 0, y = L, z = 0, z = L faces
+    gb = (np.arange(n_bnd) + 0.5) / n_bnd * L
+    bx, bo = np.meshgrid(gb, gb, indexing="ij")
+    bx, bo = bx.ravel(), bo.ravel()
+    top = np.nextafter(L, 0.0)
+    sides = [np.stack([bx, np.zeros_like(bx), bo], 1), np.stack([bx, np.full_like(bx, top), bo], 1),
+             np.stack([bx, bo, np.zeros_like(bx)], 1), np.stack([bx, bo, np.full_like(bx, top)], 1)]
+    bnd = np.concatenate(sides) if boundary else np.zeros((0, 3))
+    alpha_B = 1.0 / (122.4 * MYR * 1e-3)
+    alpha_1 = (2.0 / 3.0) * alpha_B
+    I = 0.63 * 1251.37 * KPC * alpha_1 * 1e-3 ** 2          # x_HII ~ 1 in front of the barrier
+    src = np.concatenate([front, bnd])
+    ndot = np.zeros((len(src), 2))
+    ndot[: len(front), 0] = F * (L / n_front) ** 2
+    ndot[len(front):, 1] = I * L ** 2 / n_bnd ** 2
+    params = default_params(seed=seed, n_ngb=32, n_ec=8, n_tc=128, n_rc=8, n_freq_src=2,
+                            dt=0.1 * MYR, dt_em=0.1 * MYR, evolve_T=1, rec_mode=rec_mode,
+                            cool_flags=COOL_REC | COOL_CEX)
+    params.update(kw)
+    wl = _pack(params, [L], [0, n], pos, nH, NH, np.ones(n), np.full(n, 100.0),
+               np.zeros(len(src), int), src, ndot, [1.6e-18, 6.3e-18],
+               [6.3 * EV, 2.3 * EV])
+    wl["src_dir"] = np.zeros((len(src), 3))
+    wl["src_dir"][: len(front), 0] = 1.0
+    wl["src_gate"] = np.zeros(len(src), np.int32)
+    wl["src_gate"][len(front):] = 1
+    wl["barriers"] = [(0, 0, np.array([0.27 * L, 0.5 * L, 0.5 * L]), 0.2 * L)] if barrier else []
+    return wl
 
 
 def tiny(n=200, seed=7, n_ngb=16, L=1.0 * KPC, **kw):

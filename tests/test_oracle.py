@@ -471,3 +471,89 @@ def test_original_and_new_recombination_implementations_agree():
     med = {m: np.array([np.median(x[(r >= a) & (r < b)]) for a, b in shells]) for m, x in res.items()}
     assert np.all(np.abs(med[W.REC_EMISSION_CONES] / med[W.REC_TRANSPORT] - 1) < 0.03)
     assert np.max(np.abs(med[W.REC_CASE_A] / med[W.REC_TRANSPORT] - 1)) > 0.10
+
+
+def test_barrier_test_is_exact_against_rational_arithmetic():
+    """The barrier disk test (Sec. 4) against exact rational arithmetic on random segments,
+    including long ones and ones that graze the rim."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    Q = 1 << 20
+    n_hit = 0
+    for trial in range(3000):
+        axis = int(rng.integers(3))
+        p2 = 2 * int(rng.integers(Q)) + 1
+        c1, c2 = 2 * int(rng.integers(Q)), 2 * int(rng.integers(Q))
+        r2 = int(rng.integers(1, 1 << 21))
+        a = rng.integers(0, Q, 3)
+        b = rng.integers(0, Q, 3) if trial % 3 else a + rng.integers(-40, 41, 3)
+        if trial % 5 == 0:           # put the ends on both sides of the plane, near the rim
+            a[axis], b[axis] = (p2 - 1) // 2, (p2 + 1) // 2
+            a[(axis + 1) % 3] = (c1 + r2) // 2
+        i1, i2 = (axis + 1) % 3, (axis + 2) % 3
+        sa, sb = 2 * int(a[axis]) - p2, 2 * int(b[axis]) - p2
+        want = False
+        if (sa < 0) != (sb < 0):
+            t = Fraction(sa, sa - sb)
+            y = 2 * int(a[i1]) + t * 2 * (int(b[i1]) - int(a[i1])) - c1
+            z = 2 * int(a[i2]) + t * 2 * (int(b[i2]) - int(a[i2])) - c2
+            want = y * y + z * z <= r2 * r2
+        n_hit += want
+        assert oracle.barrier_test(a, b, axis, p2, c1, c2, r2) == want, (a, b, axis)
+    assert n_hit > 30
+
+
+def test_plane_parallel_front_advances_at_F_over_nH():
+    """The directed emitters of the plane-parallel front (Sec. 4): before recombinations
+    matter (t << t_rec) every photon ionises one atom, so the front of an initially neutral
+    slab of density n_H stands at x = F t / n_H.  With steps short enough for the front to
+    cross less than a particle spacing per step, the front lies within one spacing of it."""
+    wl = W.shadow(n_side=16, n_front=20, n_bnd=10, barrier=False, boundary=False,
+                  rec_mode=W.REC_OTS_CASE_B, dt=0.01 * MYR, dt_em=0.01 * MYR)
+    s = _run(wl, 40)
+    e, a, esc, fl = s.budget()[0]
+    assert abs(e - a - esc - fl) <= 1e-12 * e
+    L = wl["box_L"][0]
+    x = s.state()["x_HI"]
+    px = wl["x"] / L
+    edges = np.linspace(0, 1, 17)
+    prof = np.array([x[(px >= lo) & (px < hi)].mean() for lo, hi in zip(edges[:-1], edges[1:])])
+    k = int(np.argmax((prof[:-1] < 0.5) & (prof[1:] >= 0.5)))
+    mid = 0.5 * (edges[:-1] + edges[1:]) * L
+    xf = mid[k] + (0.5 - prof[k]) / (prof[k + 1] - prof[k]) * (mid[k + 1] - mid[k])
+    expect = 1e6 * 40 * 0.01 * MYR / 1e-3
+    assert abs(xf - expect) < L / 16
+
+
+def _shadow_regions(wl):
+    L = wl["box_L"][0]
+    p = np.stack([wl["x"], wl["y"], wl["z"]], 1) / L
+    r = np.hypot(p[:, 1] - 0.5, p[:, 2] - 0.5)
+    behind = (p[:, 0] > 0.40) & (p[:, 0] < 0.9)
+    return behind & (r < 0.12), behind & (r > 0.30)
+
+
+@pytest.mark.slow
+def test_barrier_shadow_is_ionised_and_heated_by_recombination_radiation():
+    """Sec. 4: a disk barrier in a plane-parallel front casts a shadow.  On the spot (case B,
+    no diffuse radiation) the shadow stays neutral and cold while the gas beside it is ionised
+    and hot.  With recombination radiation transported, including the boundary emitters of
+    App. B, the shadow becomes highly ionised, and is heated less than the directly lit gas
+    (recombination photons carry less excess energy).  Photons are conserved with the barrier
+    removing packets."""
+    res = {}
+    for name, kw in (("B", dict(rec_mode=W.REC_OTS_CASE_B, boundary=False)),
+                     ("RT", dict(rec_mode=W.REC_TRANSPORT, boundary=True))):
+        wl = W.shadow(n_side=16, n_front=20, n_bnd=10, **kw)
+        s = _run(wl, 30)
+        e, a, esc, fl = s.budget()[0]
+        assert abs(e - a - esc - fl) <= 1e-12 * e
+        st = s.state()
+        sh, op = _shadow_regions(wl)
+        res[name] = (np.median(st["x_HI"][sh]), np.median(st["x_HI"][op]),
+                     np.median(st["T"][sh]), np.median(st["T"][op]))
+    xs, xo, Ts, To = res["B"]
+    assert xs > 0.9 and xo < 1e-3 and Ts < 1000 and To > 1.5e4
+    xs, xo, Ts, To = res["RT"]
+    assert xs < 1e-2 and xo < 1e-3
+    assert 5e3 < Ts < 0.7 * To
