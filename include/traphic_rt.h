@@ -114,6 +114,26 @@ rt_status rt_set_sources(rt_ctx *ctx, const int *box, const double *x, const dou
                          const double *z, const double *ndot, const double *sigma,
                          const double *eps, int where, void *stream);
 
+/* rt_set_source_options -- per source, a fixed unit emission direction (dir [n_src * 3]; a zero
+   vector keeps the n_ec randomly rotated emission cones) and a gate (gate [n_src]: 1 = the
+   source emits only while its nearest gas particle has x_HI < 0.5 at the start of the step,
+   0 = always).  A directed source sends, per emission and frequency, one packet of
+   ndot * dt_em photons along its direction: the packets of the plane-parallel front of the
+   shadow test; the gate switches on its boundary emitters once the front has passed them
+   (Sec. 4, App. B).  NULL resets the option for every source.  Host or device arrays
+   (`where`); synchronises `stream`.  Errors: RT_ERR_INVALID. */
+rt_status rt_set_source_options(rt_ctx *ctx, const double *dir, const int *gate, int where,
+                                void *stream);
+
+/* rt_set_barrier -- an artificial photon barrier in box `box` (Sec. 4): the disk of radius
+   `radius` (cm) centred at centre[3] (box coordinates, cm), perpendicular to coordinate axis
+   `axis` (0, 1, 2), removes every packet whose straight path from sender to receiver (or to
+   its virtual particle) crosses it.  Removed photons are counted as escaped.  The plane is
+   placed half a quantisation cell above the centre's cell, so no particle lies on it; the
+   test is exact integer arithmetic.  radius <= 0 removes the barrier.  Errors:
+   RT_ERR_INVALID. */
+rt_status rt_set_barrier(rt_ctx *ctx, int box, int axis, const double *centre, double radius);
+
 /* rt_build_neighbours -- exact n_ngb nearest neighbours of every particle and source within
    its box, ordered by (squared quantised distance, index); smoothing length h = distance of
    the n_ngb-th; and the receiver-sorted reverse lists (Sec. 2.1: packets search the

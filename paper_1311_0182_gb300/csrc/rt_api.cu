@@ -316,6 +316,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.snbr, int, (long long)(n_src + 1) * P.kn);
     A(P.h2, long long, n);
     A(P.sh2, long long, n_src + 1);
+    A(P.sdir, double, 3 * (long long)n_src + 3);
+    A(P.sgate, int, n_src + 1);
+    A(P.bar, Barrier, n_boxes);
     A(P.fdx, float, n * P.kn); A(P.fdy, float, n * P.kn); A(P.fdz, float, n * P.kn);
     A(P.rev_off, int, n + 1);
     A(P.rev_ent, unsigned, n * P.kn);
@@ -410,6 +413,11 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
             vu[b] = box_L[b] * box_L[b] * box_L[b] / (double)(box_off[b + 1] - box_off[b]);
     cudaMemcpy(P.vunit, vu.data(), sizeof(double) * n_boxes, cudaMemcpyHostToDevice);
     rt_set_grid(c, c->cell_occ);
+    {
+        std::vector<Barrier> nob(n_boxes, Barrier{-1, 0, 0, 0, 0});
+        cudaMemcpy(P.bar, nob.data(), sizeof(Barrier) * n_boxes, cudaMemcpyHostToDevice);
+        c->bar_h = nob;
+    }
     cudaMemset(P.touched, 0xff, sizeof(int) * nkey);
     x->src_emit_h.assign(n_boxes, 0.0);
     x->box_NH_h.assign(n_boxes, 0.0);
@@ -590,6 +598,66 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
     c->built = false;
     set_norms(c);
     return rt_cuda_check(c, cudaStreamSynchronize(st), "set sources");
+}
+
+extern "C" rt_status rt_set_source_options(rt_ctx *c, const double *dir, const int *gate,
+                                           int where, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    if (where != RT_HOST && where != RT_DEVICE) return RT_ERR_INVALID;
+    DevPtrs &P = c->d;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P.ns == 0) return RT_OK;
+    rt_status s;
+    if (dir) {
+        if ((s = copy_in(c, P.sdir, dir, sizeof(double) * 3 * P.ns, where, st))) return s;
+    } else {
+        cudaMemsetAsync(P.sdir, 0, sizeof(double) * 3 * P.ns, st);
+    }
+    if (gate) {
+        if ((s = copy_in(c, P.sgate, gate, sizeof(int) * P.ns, where, st))) return s;
+    } else {
+        cudaMemsetAsync(P.sgate, 0, sizeof(int) * P.ns, st);
+    }
+    if ((s = rt_cuda_check(c, cudaStreamSynchronize(st), "source options"))) return s;
+    std::vector<int> g(P.ns);
+    cudaMemcpy(g.data(), P.sgate, sizeof(int) * P.ns, cudaMemcpyDeviceToHost);
+    P.gated = 0;
+    for (int v : g) P.gated |= v != 0;
+    return rt_cuda_check(c, cudaGetLastError(), "source options");
+}
+
+// quantised coordinate of a box position (floor of x / L * 2^20, clamped into the box)
+static long long host_quantise(double x, double L) {
+    double f = x / L;
+    f = f * (double)RT_Q;
+    double fl = floor(f);
+    long long q = (long long)fl;
+    if (!(fl >= 0.0)) q = 0;
+    if (q > RT_Q - 1) q = RT_Q - 1;
+    return q;
+}
+
+extern "C" rt_status rt_set_barrier(rt_ctx *c, int box, int axis, const double *centre,
+                                    double radius) {
+    if (!c) return RT_ERR_INVALID;
+    DevPtrs &P = c->d;
+    if (box < 0 || box >= P.nb) return RT_ERR_INVALID;
+    Barrier B{-1, 0, 0, 0, 0};
+    if (radius > 0.0) {
+        if (axis < 0 || axis > 2 || !centre) return RT_ERR_INVALID;
+        double L = c->box_L_h[box];
+        B.axis = axis;
+        B.p2 = 2 * host_quantise(centre[axis], L) + 1;
+        B.c1 = 2 * host_quantise(centre[(axis + 1) % 3], L);
+        B.c2 = 2 * host_quantise(centre[(axis + 2) % 3], L);
+        B.r2 = llround(2.0 * radius / L * (double)RT_Q);
+        if (B.r2 >= (1ll << 23)) return RT_ERR_INVALID;   // keeps the exact test in 128 bits
+    }
+    c->bar_h[box] = B;
+    cudaMemcpy(P.bar + box, &B, sizeof(Barrier), cudaMemcpyHostToDevice);
+    P.any_bar = 0;
+    for (const Barrier &x : c->bar_h) P.any_bar |= x.axis >= 0;
+    return rt_cuda_check(c, cudaGetLastError(), "barrier");
 }
 
 extern "C" rt_status rt_build_neighbours(rt_ctx *c, void *stream) {

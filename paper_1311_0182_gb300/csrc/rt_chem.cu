@@ -218,7 +218,21 @@ __global__ void k_budget_fin(DevPtrs P, int phase, const double *src_emit) {
         s1 += P.bpart[2 * ch + 1];
     }
     if (phase == 0) {
-        P.tally[4 * b + 0] += s0 + src_emit[b];
+        // the box's source photons of this step: sources switched off by their gate send
+        // nothing (a directed source sends ndot dt_em per emission, an isotropic one n_ec
+        // packets of ndot dt_em / n_ec)
+        double src = 0.0;
+        if (!P.gated) {
+            src = src_emit[b];
+        } else {
+            for (int j = 0; j < P.ns; ++j) {
+                if (P.sbox[j] != b) continue;
+                if (P.sgate[j] && !(P.xHI[P.snbr[(long long)j * P.kn]] < 0.5)) continue;
+                for (int nu = 0; nu < P.nfs; ++nu)
+                    src += P.ndot[(long long)j * P.nfs + nu] * P.dt_em * (double)P.K;
+            }
+        }
+        P.tally[4 * b + 0] += s0 + src;
         return;
     }
     P.tally[4 * b + 1] += s0;

@@ -79,6 +79,38 @@ struct HopScratch {           // per-hop scratch: [0] free packets, [1] n + free
     unsigned char *vstat;
 };
 
+// Artificial photon barrier of a box (Sec. 4): a disk perpendicular to coordinate `axis`, in
+// doubled quantised units: plane at the odd coordinate p2, centre (c1, c2) in the next two
+// axes (cyclic order), radius r2.  axis < 0: none.
+struct Barrier {
+    int axis;
+    long long p2, c1, c2, r2;
+};
+
+// Does the straight path from a to b cross the barrier?  The plane separates a and b, and
+// the crossing point lies within the radius: exact in 128-bit integers (|terms| < 2^91).
+__host__ __device__ __forceinline__ bool barrier_crosses(const Barrier &B, int ax, int ay, int az,
+                                                         int bx, int by, int bz) {
+    if (B.axis < 0) return false;
+    long long a[3] = {ax, ay, az}, b[3] = {bx, by, bz};
+    int i0 = B.axis, i1 = (B.axis + 1) % 3, i2 = (B.axis + 2) % 3;
+    long long sa = 2 * a[i0] - B.p2, sb = 2 * b[i0] - B.p2;   // odd: never 0
+    if ((sa < 0) == (sb < 0)) return false;
+    long long D = sa - sb;
+    __int128 y = (__int128)(2 * a[i1] - B.c1) * D + (__int128)sa * (2 * (b[i1] - a[i1]));
+    __int128 z = (__int128)(2 * a[i2] - B.c2) * D + (__int128)sa * (2 * (b[i2] - a[i2]));
+    __int128 rD = (__int128)B.r2 * D;
+    return (unsigned __int128)(y * y) + (unsigned __int128)(z * z) <=
+           (unsigned __int128)(rD * rD);
+}
+
+// the kernels call it out of line: its 128-bit arithmetic would otherwise raise the register
+// pressure of every hop kernel, and it runs only in boxes with a barrier
+static __device__ __noinline__ bool barrier_crosses_call(const Barrier &B, int ax, int ay,
+                                                         int az, int bx, int by, int bz) {
+    return barrier_crosses(B, ax, ay, az, bx, by, bz);
+}
+
 struct DevPtrs {              // plain pointers handed to kernels (by value)
     // sizes and parameters
     long long n;
@@ -112,6 +144,11 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     // neighbours
     int *nbr, *snbr;
     long long *h2, *sh2;
+    double *sdir;             // [ns * 3] fixed direction of a directed source (0: isotropic)
+    int *sgate;               // [ns] 1: emits only while its nearest gas particle is ionised
+    Barrier *bar;             // [nb] photon barriers
+    int any_bar;              // some box has a barrier
+    int gated;                // some source has a gate
     float *fdx, *fdy, *fdz;   // forward offsets q_j - q_i, [n * kn]
     int *rev_off;
     unsigned *rev_ent;        // (i << 5) | k
@@ -167,6 +204,7 @@ struct rt_ctx {
     std::vector<long long> box_off_h;
     std::vector<double> box_L_h;
     std::vector<int> gridG_h;
+    std::vector<Barrier> bar_h;    // host copy of the barriers
     int cell_occ = 9;              // particles per cell of the kNN grids in use
     long long grid_cap = 0;        // cells allocated (the finest grid that can be chosen)
     bool grid_tuned = false;       // occupancy chosen (or fixed by the configuration)

@@ -159,6 +159,38 @@ __global__ void k_rev_sort(DevPtrs P) {
     }
 }
 
+// Timing probe of the occupancy search: the kNN search of virtual-particle-like points, one
+// per fourth particle, up to 0.44 smoothing lengths from it in a hashed direction, bounded
+// (by 1.5 h, which holds its n_ngb neighbours) like the virtual particles' search.  Writes one
+// word no one reads, so that the search is not dropped.
+__global__ void __launch_bounds__(256) k_knn_probe(DevPtrs P, unsigned long long *sink) {
+    __shared__ int sdelta[8][32];
+    int lane = threadIdx.x & 31;
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc = 0;
+    for (long long w = w0; 4 * w < P.n; w += nw) {
+        long long i = 4 * w;
+        int b = P.pbox[i];
+        long long H = (long long)sqrt((double)P.h2[i]);
+        unsigned long long hsh = mix64((unsigned long long)i);
+        int o[3];
+        for (int a = 0; a < 3; ++a) {
+            int u = (int)((hsh >> (16 * a)) & 0xffff) - 32768;       // in [-2^15, 2^15)
+            o[a] = (int)((long long)u * (H / 4) / 32768);             // |o| < 0.44 H
+        }
+        int qx = min(max(P.qx[i] + o[0], 0), RT_Q - 1);
+        int qy = min(max(P.qy[i] + o[1], 0), RT_Q - 1);
+        int qz = min(max(P.qz[i] + o[2], 0), RT_Q - 1);
+        long long bd = 3 * H / 2 + 2;
+        long long d2;
+        int idx;
+        warp_knn(box_grid(P, b), qx, qy, qz, -1, P.kn, d2, idx, sdelta[threadIdx.x >> 5], bd * bd);
+        acc += (unsigned long long)idx;
+    }
+    if (lane == 0 && acc == 0xffffffffffffffffull) *sink = acc;
+}
+
 static void cell_lists(rt_ctx *c, cudaStream_t st) {
     DevPtrs &P = c->d;
     int tb = 256;
@@ -172,10 +204,10 @@ static void cell_lists(rt_ctx *c, cudaStream_t st) {
 }
 
 // The occupancy of the kNN cell grids (the tile of candidates each search walks) is picked
-// on the particle set itself: the gas-particle kNN pass, the same warp search the virtual
-// particles run, is timed on each candidate grid and the fastest wins.  Done once per
-// context, at its first neighbour build; the result is the same search on another grid, so
-// only the time depends on the choice.
+// on the particle set itself: after the first neighbour build, the search of points placed
+// like virtual particles (the hot use of the grids) is timed on each candidate grid and the
+// fastest wins.  Done once per context; any grid gives the same exact neighbours, so only the
+// time depends on the choice.
 static void tune_grid(rt_ctx *c, cudaStream_t st) {
     static const int cand[] = {5, 7, 9, 12, 16};
     DevPtrs &P = c->d;
@@ -189,7 +221,8 @@ static void tune_grid(rt_ctx *c, cudaStream_t st) {
         rt_set_grid(c, occ);
         cell_lists(c, st);
         cudaEventRecord(e0, st);
-        k_knn<<<rt_blocks(P.n * 32, tb, 152 * 64), tb, 0, st>>>(P, 0);
+        k_knn_probe<<<rt_blocks((P.n / 4 + 1) * 32, tb, 152 * 64), tb, 0, st>>>(
+            P, (unsigned long long *)&P.cnt[CNT_N - 1]);   // an unused counter as the sink
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -199,6 +232,7 @@ static void tune_grid(rt_ctx *c, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     rt_set_grid(c, best);
+    cell_lists(c, st);
     c->grid_tuned = true;
 }
 
@@ -208,7 +242,6 @@ rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
     int tb = 256;
     unsigned nbk = (unsigned)((n + tb - 1) / tb);
     int *cnt = P.seg_cnt, *fill = P.seg_fill;
-    if (!c->grid_tuned) tune_grid(c, st);
     // cell lists
     cell_lists(c, st);
     // neighbours of particles and sources
@@ -223,6 +256,7 @@ rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
     rt_scan_exclusive(c, cnt, P.rev_off, n + 1, nullptr, nullptr, st);
     k_rev_fill<<<nbe, tb, 0, st>>>(P, fill);
     k_rev_sort<<<nbk, tb, 0, st>>>(P);
+    if (!c->grid_tuned) tune_grid(c, st);   // needs the smoothing lengths just computed
     return rt_cuda_check(c, cudaGetLastError(), "neighbour build");
 }
 

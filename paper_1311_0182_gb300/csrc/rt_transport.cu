@@ -345,9 +345,20 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
     int e = (int)(tt % (unsigned)P.nec);
     FreeBuf F = P.fr[fcur];
     int b = P.sbox[j];
-    double N = __ddiv_rn(__dmul_rn(P.ndot[(long long)j * P.nfs + nu], P.dt_em), (double)P.nec);
-    double d[3];
-    rot_apply(P.Rs + ((long long)j * P.K + k) * 9, c_axd[P.ax_ec] + 3 * e, d);
+    // a gated source emits only while its nearest gas particle is more than half ionised; a
+    // directed source sends one packet per emission and frequency (cone 0) along its direction
+    const double *dir = P.sdir + 3 * (long long)j;
+    bool directed = dir[0] != 0.0 || dir[1] != 0.0 || dir[2] != 0.0;
+    bool on = !P.sgate[j] || P.xHI[P.snbr[(long long)j * P.kn]] < 0.5;
+    double nd = P.ndot[(long long)j * P.nfs + nu];
+    double N = 0.0, d[3];
+    if (directed) {
+        if (on && e == 0) N = __dmul_rn(nd, P.dt_em);
+        d[0] = dir[0]; d[1] = dir[1]; d[2] = dir[2];
+    } else {
+        if (on) N = __ddiv_rn(__dmul_rn(nd, P.dt_em), (double)P.nec);
+        rot_apply(P.Rs + ((long long)j * P.K + k) * 9, c_axd[P.ax_ec] + 3 * e, d);
+    }
     F.box[p] = b;
     F.qx[p] = P.sqx[j]; F.qy[p] = P.sqy[j]; F.qz[p] = P.sqz[j];
     for (int a = 0; a < P.kn; ++a) F.nbr[p * P.kn + a] = P.snbr[(long long)j * P.kn + a];
@@ -575,6 +586,18 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         int nu = F.nu[f];
         long long j = F.nbr[f * P.kn + lane];
         int b = P.pbox[j];
+        long long key = j * P.nf + nu;
+        Real **V = (Real **)P.st_v;
+        if (P.any_bar && barrier_crosses_call(P.bar[b], F.qx[f], F.qy[f], F.qz[f], P.qx[j], P.qy[j],
+                                         P.qz[j])) {
+            // the share crosses the barrier: removed (counted escaped); the staged
+            // contribution is empty
+            atomicAdd(&P.esc_fx[b], esc_fixed(w, P, b));
+            P.st_key[s] = (int)key;
+            P.st_bin[s] = -1;            // the receiver side skips it
+            atomicAdd(&P.seg_cnt[key], 1);
+            continue;
+        }
         Real t = (Real)(P.qx[j] - F.qx[f]) * d0 + (Real)(P.qy[j] - F.qy[f]) * d1 +
                  (Real)(P.qz[j] - F.qz[f]) * d2;
         Real l = t * box_unit<Real>(P, b);
@@ -582,10 +605,8 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         Real A, T;
         split_absorbed<Real>(w, tau, A, T);
         int bt = bin_fast<Real>(P.Rf + j * 9, P.R + j * 9, P.ax_rc, NRC, d0, d1, d2);
-        long long key = j * P.nf + nu;
         P.st_key[s] = (int)key;
         P.st_bin[s] = bt;
-        Real **V = (Real **)P.st_v;
         V[0][s] = T;
         V[1][s] = T * d0;
         V[2][s] = T * d1;
@@ -738,10 +759,14 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         }
         if (!found) axis_offset(d0, d1, d2, H, Dx, Dy, Dz);
         int vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
-        if (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) {
+        // outside the box: the photons escape (vstat 1); on a path through the barrier they
+        // are removed, counted with the escapes (vstat 3)
+        int gone = (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) ? 1
+                 : (P.any_bar && barrier_crosses_call(P.bar[box], qx, qy, qz, vx, vy, vz)) ? 3 : 0;
+        if (gone) {
             if (lane == 0) {
                 esc_r[r] = esc_fixed(N, P, box);
-                vstat[r] = 1;
+                vstat[r] = (unsigned char)gone;
                 Fo.box[r] = box;
                 ((Real *)Fo.N)[r] = Real(0);
             }
@@ -1001,11 +1026,18 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                 unsigned word = 0u;
                 int si = 0;
                 float fx = 0.f, fy = 0.f, fz = 0.f;
+                unsigned xb = 0u;   // 1u << 31: the edge's path crosses the box's barrier
                 if (e < e1) {   // the edge's data is loaded with its word (one memory round)
                     word = bmr[e];
                     si = (int)(P.rev_ent[e] >> 5);
                     fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
                     if (word) bmr[e] = 0u;
+                    if (word && P.any_bar) {
+                        int jx = P.qx[j], jy = P.qy[j], jz = P.qz[j];
+                        if (barrier_crosses_call(P.bar[box], jx - (int)fx, jy - (int)fy,
+                                                 jz - (int)fz, jx, jy, jz))
+                            xb = 1u << 31;
+                    }
                 }
                 int cw = __popc(word);
                 int incl = cw;
@@ -1019,7 +1051,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                 // the chunk's edges in shared memory; contribution c belongs to the edge whose
                 // range [excl, excl + cw) holds it
                 se[threadIdx.x] = make_float4(fx, fy, fz, __int_as_float(si));
-                sw2[threadIdx.x] = make_uint2(word, (unsigned)excl);
+                sw2[threadIdx.x] = make_uint2(word, (unsigned)excl | xb);
                 int carry = 0;   // owner of the last contribution of the previous chunk
                 for (int cb = 0; cb < total; cb += G) {
                     bool st = cw > 0 && excl >= cb && excl < cb + G;
@@ -1031,13 +1063,21 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                     carry = __shfl_sync(gmask, own, G - 1, G);
                     int c = cb + gl;
                     int mybin = -1;
-                    if (c < total) {
-                        float4 ed = se[gbase + own];
+                    bool keep = c < total;
+                    Real w, d0, d1, d2, clk, eps;
+                    float4 ed;
+                    if (keep) {
+                        ed = se[gbase + own];
                         uint2 ow = sw2[gbase + own];
-                        int bsrc = __fns(ow.x, 0, c - (int)ow.y + 1);
+                        int bsrc = __fns(ow.x, 0, c - (int)(ow.y & 0x7fffffffu) + 1);
                         long long ridx = (long long)__float_as_int(ed.w) * P.S + (long long)nu * G + bsrc;
-                        Real w, d0, d1, d2, clk, eps;
                         rec_load(P.rec, ridx, w, d0, d1, d2, clk, eps);
+                        if (ow.y >> 31) {   // through the barrier: removed (counted escaped)
+                            atomicAdd(&P.esc_fx[box], esc_fixed(w, P, box));
+                            keep = false;
+                        }
+                    }
+                    if (keep) {
                         Real t = (Real)ed.x * d0 + (Real)ed.y * d1 + (Real)ed.z * d2;
                         Real l = t * u;
                         Real A, T;
@@ -1065,11 +1105,13 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                 int mybin = -1;
                 if (c < fc) {
                     int s = P.seg_idx[so + c];
-                    mybin = P.st_bin[s];
-                    for (int f = 0; f < 6; ++f) sv[f][threadIdx.x] = V[f][s];
-                    sA.add(V[6][s]);
-                    sAE.add(V[7][s]);
-                    sW.add(V[8][s]);
+                    mybin = P.st_bin[s];           // -1: removed by a barrier
+                    if (mybin >= 0) {
+                        for (int f = 0; f < 6; ++f) sv[f][threadIdx.x] = V[f][s];
+                        sA.add(V[6][s]);
+                        sAE.add(V[7][s]);
+                        sW.add(V[8][s]);
+                    }
                 }
                 merge_chunk(mybin);
             }
@@ -1122,8 +1164,8 @@ __global__ void k_hop_counts(DevPtrs P, int nxt, int fnxt, const int *lens,
     for (long long r = t0; r < nreq; r += stride) {
         unsigned char s = vstat[r];
         live += (s == 0);
-        if (s == 1) {
-            ++nesc;
+        if (s == 1 || s == 3) {
+            nesc += (s == 1);
             unsigned long long v = esc_r[r];
             int b = F.box[r];
             // aggregate equal boxes within the warp before the atomic

@@ -22,7 +22,7 @@ SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_
            "rt_get_rotations", "rt_get_cone_masks", "rt_get_cone_masks_noalloc", "rt_get_slots",
            "rt_set_slots",
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
-           "rt_get_profile", "rt_last_error"]
+           "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier"]
 
 
 class RTError(RuntimeError):
@@ -64,6 +64,8 @@ def load(build_if_missing: bool = False):
     L.rt_destroy.argtypes = [vp]
     L.rt_set_particles.argtypes = [vp] + [vp] * 7 + [i, vp]
     L.rt_set_sources.argtypes = [vp] + [vp] * 7 + [i, vp]
+    L.rt_set_source_options.argtypes = [vp, vp, vp, i, vp]
+    L.rt_set_barrier.argtypes = [vp, i, i, vp, d]
     L.rt_build_neighbours.argtypes = [vp, vp]
     L.rt_assign_cones.argtypes = [vp, ll, vp]
     L.rt_merge.argtypes = [vp, vp]
@@ -183,11 +185,29 @@ class Context:
         self._check(self.L.rt_set_sources(self.h, *[p for p, _ in ptrs], where, self._s()),
                     "rt_set_sources")
 
+    def set_source_options(self, direction=None, gate=None):
+        """Per source: fixed emission direction [ns, 3] (zero rows: isotropic) and gate [ns]."""
+        dp = _ptr(direction) if direction is not None else (None, RT_HOST)
+        gp = _ptr(gate) if gate is not None else (None, RT_HOST)
+        where = dp[1] if direction is not None else gp[1]
+        self._check(self.L.rt_set_source_options(self.h, dp[0], gp[0], where, self._s()),
+                    "rt_set_source_options")
+
+    def set_barrier(self, box, axis, centre, radius):
+        c = np.ascontiguousarray(centre, dtype=np.float64)
+        self._check(self.L.rt_set_barrier(self.h, int(box), int(axis), c.ctypes.data,
+                                          float(radius)), "rt_set_barrier")
+
     def load_workload(self, wl):
         f = lambda k, dt=np.float64: np.ascontiguousarray(wl[k], dtype=dt)
         self.set_particles(f("x"), f("y"), f("z"), f("n_H"), f("N_H"), f("x_HI"), f("T"))
         self.set_sources(f("src_box", np.int32), f("src_x"), f("src_y"), f("src_z"),
                          f("src_ndot"), f("sigma"), f("eps"))
+        if "src_dir" in wl or "src_gate" in wl:
+            self.set_source_options(f("src_dir") if "src_dir" in wl else None,
+                                    f("src_gate", np.int32) if "src_gate" in wl else None)
+        for (b, axis, centre, radius) in wl.get("barriers", []):
+            self.set_barrier(b, axis, centre, radius)
 
     def build_neighbours(self):
         self._check(self.L.rt_build_neighbours(self.h, self._s()), "rt_build_neighbours")

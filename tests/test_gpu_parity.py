@@ -492,3 +492,24 @@ def test_grid_occupancy_search_changes_nothing_but_time():
             g.step(step)
     x = ctxs[5].state()["x_HI"]
     assert all(np.array_equal(g.state()["x_HI"], x) for g in ctxs.values())
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_shadow_workload_against_the_oracle(fp32):
+    """The shadow test of Sec. 4 at 16^3 (directed front emitters, gated boundary emitters,
+    the disk barrier): 14 steps, by which the front has passed the barrier and the boundary
+    emitters have switched on.  FP64 follows the oracle to rounding; FP32 within the bars."""
+    wl = W.shadow(n_side=16, n_front=20, n_bnd=10)
+    g, o = _pair(wl, transport_fp32=fp32)
+    for step in range(14):
+        g.step(step)
+        assert o.step(step) == 0
+    xg, xo = g.state()["x_HI"], o.state()["x_HI"]
+    assert _xhi_ok(xg, xo).all()
+    if not fp32:
+        assert np.max(np.abs(xg / xo - 1)) < 1e-9
+    assert np.allclose(g.state()["T"], o.state()["T"], rtol=1e-3)
+    bg, bo = g.budget()[0], o.budget()[0]
+    assert bo[2] > 0.01 * bo[0]                      # the barrier removed photons
+    assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
+    assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
