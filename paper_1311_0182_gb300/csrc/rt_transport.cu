@@ -667,7 +667,8 @@ __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long l
 }
 
 // Virtual particles (Sec. 2.1): one warp per request.
-template <typename Real, int NRC>
+// BAR: some box has a barrier (a separate instance keeps the test out of the common case)
+template <typename Real, int NRC, bool BAR>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur, const int *lens,
                                                  long long step, int hop,
                                                  unsigned long long *esc_r,
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         // outside the box: the photons escape (vstat 1); on a path through the barrier they
         // are removed, counted with the escapes (vstat 3)
         int gone = (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) ? 1
-                 : (P.any_bar && barrier_crosses_call(P.bar[box], qx, qy, qz, vx, vy, vz)) ? 3 : 0;
+                 : (BAR && barrier_crosses_call(P.bar[box], qx, qy, qz, vx, vy, vz)) ? 3 : 0;
         if (gone) {
             if (lane == 0) {
                 esc_r[r] = esc_fixed(N, P, box);
@@ -1337,8 +1338,12 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 1)));
         LAUNCH(KT_EXPAND, 1, (k_expand<<<(unsigned)((n + nfr + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
-                                  P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
+        if (P.any_bar)
+            LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+                                      P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
+        else
+            LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+                                      P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
         LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
         LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
         LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));
