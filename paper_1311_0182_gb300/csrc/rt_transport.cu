@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(256) k_freeA(DevPtrs P, int fcur, const int *l
 
 // Free packets with cone members: stage one contribution per member, in (packet, neighbour)
 // order at the positions given by the scan of the member counts.
-template <typename Real, int NRC>
+template <typename Real, int NRC, bool BAR>
 __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *lens,
                                                const unsigned *fmask, const int *stoff) {
     int lane = threadIdx.x & 31;
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         int b = P.pbox[j];
         long long key = j * P.nf + nu;
         Real **V = (Real **)P.st_v;
-        if (P.any_bar && barrier_crosses_call(P.bar[b], F.qx[f], F.qy[f], F.qz[f], P.qx[j], P.qy[j],
+        if (BAR && barrier_crosses_call(P.bar[b], F.qx[f], F.qy[f], F.qz[f], P.qx[j], P.qy[j],
                                          P.qz[j])) {
             // the share crosses the barrier: removed (counted escaped); the staged
             // contribution is empty
@@ -958,7 +958,7 @@ __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long
 // cone.  Contributions are computed in parallel and merged in their fixed order by a
 // broadcast loop (the lane owning the target cone adds).  Groups come from the work list;
 // the next buffer's occupancy words were cleared before the launch.
-template <typename Real, int G>
+template <typename Real, int G, bool BAR>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int cur, int stamp, const int *wl_n) {
     // contributions of the current chunk, one per lane: 6 values (T, T d, T clock, T eps); and
     // per reception cone of each group, the mask of the chunk's lanes that feed it
@@ -1033,7 +1033,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                     si = (int)(P.rev_ent[e] >> 5);
                     fx = P.rdx[e]; fy = P.rdy[e]; fz = P.rdz[e];
                     if (word) bmr[e] = 0u;
-                    if (word && P.any_bar) {
+                    if (BAR && word) {
                         int jx = P.qx[j], jy = P.qy[j], jz = P.qz[j];
                         if (barrier_crosses_call(P.bar[box], jx - (int)fx, jy - (int)fy,
                                                  jz - (int)fz, jx, jy, jz))
@@ -1331,7 +1331,10 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         LAUNCH_ON(s2, KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
         LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
         cudaEventRecord(evFree, s2);
-        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+        if (P.any_bar)
+            LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+        else
+            LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur, stamp)));
         cudaEventRecord(evA, st);
         cudaStreamWaitEvent(st, evFree, 0);
@@ -1352,7 +1355,10 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
         cudaMemsetAsync(P.occ[nxt], 0, sizeof(unsigned) * nkey, s2);
         cudaMemsetAsync(P.act[nxt], 0, sizeof(unsigned) * nkey, s2);
-        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
+        if (P.any_bar)
+            LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
+        else
+            LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
         cudaEventRecord(evB, s2);
         cudaStreamWaitEvent(st, evB, 0);
         LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, nxt, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
