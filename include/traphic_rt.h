@@ -130,8 +130,8 @@ rt_status rt_set_source_options(rt_ctx *ctx, const double *dir, const int *gate,
    `axis` (0, 1, 2), removes every packet whose straight path from sender to receiver (or to
    its virtual particle) crosses it.  Removed photons are counted as escaped.  The plane is
    placed half a quantisation cell above the centre's cell, so no particle lies on it; the
-   test is exact integer arithmetic.  radius <= 0 removes the barrier.  Errors:
-   RT_ERR_INVALID. */
+   test is exact integer arithmetic.  radius <= 0 removes the barrier.  Synchronises the
+   device.  Errors: RT_ERR_INVALID. */
 rt_status rt_set_barrier(rt_ctx *ctx, int box, int axis, const double *centre, double radius);
 
 /* rt_build_neighbours -- exact n_ngb nearest neighbours of every particle and source within

@@ -654,6 +654,7 @@ extern "C" rt_status rt_set_barrier(rt_ctx *c, int box, int axis, const double *
         if (B.r2 >= (1ll << 23)) return RT_ERR_INVALID;   // keeps the exact test in 128 bits
     }
     c->bar_h[box] = B;
+    cudaDeviceSynchronize();   // no hop kernel of this context may be reading the barriers
     cudaMemcpy(P.bar + box, &B, sizeof(Barrier), cudaMemcpyHostToDevice);
     P.any_bar = 0;
     for (const Barrier &x : c->bar_h) P.any_bar |= x.axis >= 0;

@@ -244,7 +244,9 @@ rt_status rt_cuda_check(rt_ctx *c, cudaError_t e, const char *what);
 void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
                        int *d_total, cudaStream_t st, int *tmp = nullptr);
 rt_status rt_knn_build(rt_ctx *c, cudaStream_t st);
-void rt_set_grid(rt_ctx *c, int occupancy);   // per-box cell grids for a target occupancy
+// per-box cell grids for a target occupancy; host-synchronous copies: no kernel that reads
+// the grids may be in flight
+void rt_set_grid(rt_ctx *c, int occupancy);
 rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st);
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);

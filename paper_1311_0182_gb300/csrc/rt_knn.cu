@@ -212,6 +212,9 @@ static void tune_grid(rt_ctx *c, cudaStream_t st) {
     static const int cand[] = {5, 7, 9, 12, 16};
     DevPtrs &P = c->d;
     int tb = 256;
+    // rt_set_grid rewrites the grid description with plain copies, which do not wait for
+    // kernels on the caller's (possibly non-blocking) stream: let the neighbour build finish
+    cudaStreamSynchronize(st);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -513,3 +513,49 @@ def test_shadow_workload_against_the_oracle(fp32):
     assert bo[2] > 0.01 * bo[0]                      # the barrier removed photons
     assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
     assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
+
+
+def test_full_size_on_a_non_blocking_stream():
+    """The timed 64^3 workload on a non-blocking stream (as the bench runs it): the neighbour
+    lists (built, then the grid occupancy searched) match brute force at sampled particles, and
+    two steps agree bit for bit with the same steps on the default stream."""
+    import torch
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg2()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g = rt.context_for(wl, stream=s)
+    nbr, h2, _, _ = g.neighbours()
+    q = g.quantised()
+    k = wl["params"]["n_ngb"]
+    rng = np.random.default_rng(1)
+    idx = np.arange(g.n)
+    for i in rng.choice(g.n, 48, replace=False):
+        d2 = ((q - q[i]) ** 2).sum(1)
+        keep = idx != i
+        order = np.lexsort((idx[keep], d2[keep]))[:k]
+        assert np.array_equal(nbr[i], idx[keep][order])
+    d = rt.context_for(wl)
+    with torch.cuda.stream(s):
+        for step in range(2):
+            g.step(step)
+    for step in range(2):
+        d.step(step)
+    assert np.array_equal(g.state()["x_HI"], d.state()["x_HI"])
+
+
+def test_app_a_convergence_with_resolution_and_time_step():
+    """App. A: the Stromgren sphere with transported recombination radiation converges with
+    particle number and RT time step.  After one t_rec, the I-fronts of 32^3 and 64^3 runs, and
+    of runs with dt = 1 and 0.1 Myr (dt_em = 0.1 dt), lie within one smoothing length of each
+    other, and the recombination intensity inside R_S/2 agrees to 25 %."""
+    from paper_1311_0182_gb300 import convergence as CV
+    a = CV.run(n_side=32, dt_myr=1.0, t_rec=1.0)
+    b = CV.run(n_side=64, dt_myr=1.0, t_rec=1.0)
+    c = CV.run(n_side=32, dt_myr=0.1, t_rec=1.0)
+    h = a["mean_h_over_RS"]
+    assert abs(a["front_over_RS"] - b["front_over_RS"]) < h
+    assert abs(a["front_over_RS"] - c["front_over_RS"]) < h
+    ia = np.array([p["intensity"] for p in a["profile"][:4]])
+    ib = np.array([p["intensity"] for p in b["profile"][:4]])
+    assert np.all(np.abs(ia / ib - 1) < 0.25)
