@@ -7,7 +7,7 @@ count, RT time step (emission step 0.1 dt, as in App. A) and number of transmiss
 recombination-radiation intensity, the photons of the recombination bin passing each particle
 per step over its smoothing area (the paper's intensity diagnostic, Sec. 3), in shells of R_S/8.
 
-    python -m paper_1311_0182_gb300.convergence   # the App. A sweeps, one JSON line per run
+    python -m paper_1311_0182_gb300.convergence [t/t_rec] [--quick]   # one JSON line per run
 """
 from __future__ import annotations
 
@@ -65,12 +65,20 @@ def run(n_side: int = 32, dt_myr: float = 1.0, n_tc: int = 8, t_rec: float = 4.0
 SWEEPS = ([dict(n_side=n, dt_myr=0.1) for n in (32, 64, 128)] +
           [dict(n_side=64, dt_myr=d) for d in (0.01, 1.0)] +
           [dict(n_side=64, dt_myr=0.1, n_tc=c) for c in (64, 128)])
+# the same three questions at a cost of minutes: resolution at dt = 1 Myr, time step and cones
+# at 32^3
+SWEEPS_QUICK = ([dict(n_side=n, dt_myr=1.0) for n in (32, 64, 128)] +
+                [dict(n_side=32, dt_myr=d) for d in (0.01, 0.1)] +
+                [dict(n_side=32, dt_myr=1.0, n_tc=c) for c in (64, 128)])
 
 
 def main(argv=None):
+    """python -m paper_1311_0182_gb300.convergence [t / t_rec] [--quick]"""
     argv = sys.argv[1:] if argv is None else argv
-    t_rec = float(argv[0]) if argv else 4.0
-    for kw in SWEEPS:
+    quick = "--quick" in argv
+    nums = [a for a in argv if not a.startswith("--")]
+    t_rec = float(nums[0]) if nums else 4.0
+    for kw in (SWEEPS_QUICK if quick else SWEEPS):
         print(json.dumps(run(t_rec=t_rec, **kw)), flush=True)
 
 
