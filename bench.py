@@ -269,13 +269,13 @@ def fp64_path(args, stream, **over):
     with torch.cuda.stream(stream):
         ctx.load_workload(wl)
         ctx.build_neighbours()
-        for s in range(args.warmup):
+        for s in range(args.warmup + 1):    # the main run's warm-up and its profiled step
             ctx.step(s)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         for s in range(steps):
-            ctx.step(args.warmup + s)
+            ctx.step(args.warmup + 1 + s)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
