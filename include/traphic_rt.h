@@ -175,8 +175,19 @@ rt_status rt_transport(rt_ctx *ctx, long long step, void *stream);
 rt_status rt_chemistry(rt_ctx *ctx, void *stream);
 
 /* rt_step -- one RT step: rt_assign_cones, rt_merge, rt_emit, rt_transport, rt_chemistry and
-   the photon budget.  Returns the first non-OK status. */
+   the photon budget.  Returns the first non-OK status.  Synchronises `stream` once, at the end.
+   By default (rt_set_graph) the whole step runs as one CUDA graph launched on `stream`: the
+   hop loop is a conditional while node whose last kernel decides on the device whether
+   another hop runs, so no host round trip separates hops.  The graph is captured on the
+   first call and again whenever a parameter it holds changes (configuration, barriers,
+   source options, kNN grid).  The hop-by-hop path runs instead while kernels are timed
+   (rt_set_profiling) or hop_cap is 0; both give bit-identical results.  After an error
+   status from the graph the chemistry of that step has run on incomplete absorptions (the
+   hop-by-hop path stops before it); the state of a failed step is not meant to be used. */
 rt_status rt_step(rt_ctx *ctx, long long step, void *stream);
+/* rt_set_graph -- on != 0 (default): rt_step runs as a captured CUDA graph; 0: it drives the
+   hop loop from the host, one synchronisation per hop. */
+rt_status rt_set_graph(rt_ctx *ctx, int on);
 
 /* rt_get_state / rt_set_state -- x_HI, T, pending recombination photons N_rec and their
    excess energy eps_rec ([n] each; NULL skips a field). */

@@ -3,9 +3,13 @@
 The HII region of Sec. 3 (workload 1 geometry: 13.2 kpc box, n_H = 1e-3, T = 1e4 K, a 5e48
 s^-1 source at 13.6 eV) is run on the GPU to a given multiple of t_rec with a chosen particle
 count, RT time step (emission step 0.1 dt, as in App. A) and number of transmission cones
-(N_EC = N_RC = 8).  The result is the radial profile of the neutral fraction and of the
-recombination-radiation intensity, the photons of the recombination bin passing each particle
-per step over its smoothing area (the paper's intensity diagnostic, Sec. 3), in shells of R_S/8.
+(N_EC = N_RC = 8).  The result is the radial profile, in shells of R_S/8, of the neutral
+fraction, of the recombination-radiation intensity (the photons of the recombination bin
+passing each gas particle per step over its smoothing area: a per-area form of the paper's
+diagnostic, which records the photons passing each SPH particle per step, Sec. 3) and of the
+diffuse-to-source ratio of those counts.  Photons carried by virtual particles pass no gas
+particle and are not counted, so the intensity drops as narrow cones (large N_TC) send more
+photons through virtual particles.
 
     python -m paper_1311_0182_gb300.convergence [t/t_rec] [--quick]   # one JSON line per run
 """
@@ -27,8 +31,11 @@ def run(n_side: int = 32, dt_myr: float = 1.0, n_tc: int = 8, t_rec: float = 4.0
         transport_fp32: int = 1, stream=None) -> dict:
     from . import rt
     dt = dt_myr * W.MYR
+    # narrow transmission cones leave most cones empty: room for one virtual particle per
+    # (particle, reception cone) and per extra factor of 8 in the cone count
+    free_cap = n_side ** 3 * 8 * max(1, n_tc // 8)
     wl = W.cfg1(n_side=n_side, dt=dt, dt_em=0.1 * dt, n_tc=n_tc, rec_mode=W.REC_TRANSPORT,
-                transport_fp32=transport_fp32)
+                transport_fp32=transport_fp32, free_cap=free_cap)
     ctx = rt.context_for(wl, stream=stream)
     steps = int(round(t_rec * T_REC_MYR / dt_myr))
     for s in range(steps):
@@ -46,8 +53,12 @@ def run(n_side: int = 32, dt_myr: float = 1.0, n_tc: int = 8, t_rec: float = 4.0
     for a, b in zip(edges[:-1], edges[1:]):
         m = (r >= a) & (r < b)
         if m.any():
+            # diffuse-to-source ratio: photons of the recombination bin over those of the
+            # source bins passing the shell's particles (Sec. 3)
+            src = float(pas[m, :-1].sum())
             prof.append({"r_over_RS": [float(a), float(b)], "x_HI": float(x[m].mean()),
-                         "intensity": float(inten[m].mean())})
+                         "intensity": float(inten[m].mean()),
+                         "diffuse_to_source": float(pas[m, -1].sum()) / src if src > 0 else None})
     # front: where the shell-averaged x_HI crosses 0.5
     front = None
     for p, q in zip(prof[:-1], prof[1:]):

@@ -80,13 +80,17 @@ static cudaEvent_t ev_take(rt_ctx *c) {
 }
 
 void kt_begin(rt_ctx *c, int id, cudaStream_t st) {
-    if (!((c->prof >> id) & 1)) return;
+    if (c->capturing || !((c->prof >> id) & 1)) return;
     cudaEvent_t e0 = ev_take(c), e1 = ev_take(c);
     cudaEventRecord(e0, st);
     c->ev_pending.push_back({id, {e0, e1}});
 }
 
 void kt_end(rt_ctx *c, int id, cudaStream_t st, int nlaunch) {
+    if (c->capturing) {   // counted per step (and per hop) when the graph runs
+        (c->in_hop_body ? c->graph_launch_hop : c->graph_launch_step)[id] += nlaunch;
+        return;
+    }
     c->launches += nlaunch;
     c->kstat[id].launches += nlaunch;
     if (!((c->prof >> id) & 1)) return;
@@ -108,6 +112,12 @@ static const char *KT_NAMES[KT_N] = {
     "expand_requests", "free_c_stage", "virtual_particles", "seg_fill", "seg_sort",
     "phase_b_merge", "hop_counts", "hop_lens", "drop_free", "chemistry", "budget", "knn_build",
     "worklist", "cone_masks"};
+
+extern "C" rt_status rt_set_graph(rt_ctx *c, int on) {
+    if (!c) return RT_ERR_INVALID;
+    c->use_graph = on != 0;
+    return RT_OK;
+}
 
 extern "C" rt_status rt_set_profiling(rt_ctx *c, int on) {
     if (!c) return RT_ERR_INVALID;
@@ -392,6 +402,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         ok = false;
     for (int k = 0; k < 4; ++k)
         if (cudaEventCreateWithFlags(&c->hev[k], cudaEventDisableTiming) != cudaSuccess) ok = false;
+    // the stream the step graph is captured on (it never runs work itself)
+    if (cudaStreamCreateWithFlags(&c->st_cap, cudaStreamNonBlocking) != cudaSuccess) ok = false;
     if (!ok) {
         rt_destroy(c);
         return RT_ERR_OOM;
@@ -418,7 +430,6 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         cudaMemcpy(P.bar, nob.data(), sizeof(Barrier) * n_boxes, cudaMemcpyHostToDevice);
         c->bar_h = nob;
     }
-    cudaMemset(P.touched, 0xff, sizeof(int) * nkey);
     x->src_emit_h.assign(n_boxes, 0.0);
     x->box_NH_h.assign(n_boxes, 0.0);
     cudaError_t e = cudaDeviceSynchronize();
@@ -432,6 +443,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
 
 extern "C" rt_status rt_destroy(rt_ctx *c) {
     if (!c) return RT_OK;
+    cudaDeviceSynchronize();
+    rt_graph_destroy(c);
+    if (c->st_cap) cudaStreamDestroy(c->st_cap);
     for (size_t k = 0; k < c->allocs.size(); ++k) cudaFree(c->allocs[k]);
     if (c->scan_tmp) cudaFree(c->scan_tmp);
     if (c->scan_tmp2) cudaFree(c->scan_tmp2);
@@ -729,6 +743,9 @@ extern "C" rt_status rt_step(rt_ctx *c, long long step, void *stream) {
     rt_status s = need_built(c);
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    // the captured step graph, unless kernels are being timed one by one (events cannot sit
+    // inside the graph's conditional hop loop) or the hop cap allows no hop
+    if (c->use_graph && c->prof == 0 && c->cfg.hop_cap > 0) return rt_step_graph(c, step, st);
     if ((s = rt_run_step_parts(c, 0, step, st))) return s;
     if ((s = rt_run_step_parts(c, 1, step, st))) return s;
     if ((s = rt_emit(c, step, stream))) return s;

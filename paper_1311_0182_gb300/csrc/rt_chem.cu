@@ -167,8 +167,9 @@ __device__ double block_sum(double v, double *sh) {
 // phase 0: the recombination photons of the last chemistry step;
 // phase 1: the absorptions, and the photons held in slots.
 template <typename Real>
-__global__ void k_budget_part(DevPtrs P, int phase, int cur) {
+__global__ void k_budget_part(DevPtrs P, int phase) {
     __shared__ double sh[32];
+    const int cur = (int)P.cnt[CNT_CUR];
     int ch = blockIdx.x;
     long long i0 = P.bch_lo[ch], i1 = P.bch_lo[ch + 1];
     if (phase == 0) {
@@ -244,8 +245,8 @@ __global__ void k_budget_fin(DevPtrs P, int phase, const double *src_emit) {
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st) {
     DevPtrs &P = c->d;
     kt_begin(c, KT_BUDGET, st);
-    if (P.fp32) k_budget_part<float><<<P.nbch, 256, 0, st>>>(P, phase, c->cur);
-    else k_budget_part<double><<<P.nbch, 256, 0, st>>>(P, phase, c->cur);
+    if (P.fp32) k_budget_part<float><<<P.nbch, 256, 0, st>>>(P, phase);
+    else k_budget_part<double><<<P.nbch, 256, 0, st>>>(P, phase);
     k_budget_fin<<<(P.nb + 127) / 128, 128, 0, st>>>(P, phase, c->src_emit);
     kt_end(c, KT_BUDGET, st);
     return rt_cuda_check(c, cudaGetLastError(), "budget");

@@ -43,8 +43,18 @@ enum {
     CNT_STG = 14,       // staged free-packet contributions, summed over hops
     CNT_WLS = 15,       // receiver work-list entries, summed over hops
     CNT_OUT = 16,       // occupied slots written by the receiver side, summed over hops
-    CNT_N = 24
+    // hop state: kept on the device so that a captured graph replays the hop loop unchanged
+    // (19: unused)
+    CNT_CUR = 17,       // slot buffer holding the current packets (0 or 1)
+    CNT_FCUR = 18,      // free-packet buffer of the current hop (0 or 1)
+    CNT_HOP = 20,       // hops done in this step
+    CNT_STEP = 21,      // step number (random streams of the rotations and virtual particles)
+    CNT_DROP = 22,      // 1: the hop cap stopped the loop with packets still moving
+    CNT_PKFREE = 23,    // largest request count of a hop in this step
+    CNT_PKACT = 24,     // largest active-slot count after a hop in this step
+    CNT_N = 32
 };
+
 
 // fixed-point scales of the virtual-particle deposits (relative to the receiver's neutral
 // atoms N_HI at the start of the step) and of the escaped tally (relative to the box's
@@ -167,7 +177,7 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     unsigned *bm;             // receiver-ordered cone bitmaps [nu * n * kn + p], p = reverse position
     int *revpos;              // position of forward entry (i, k) in the reverse lists
     unsigned *emp;            // empty-cone bits [n * nf]
-    int *touched;             // hop stamp per (j, nu)
+    int *touched;             // per (j, nu): 1 when a gas sender wrote a bitmap word this hop
     // requests
     int *reqcnt, *reqoff;     // [n + F_cap]
     unsigned long long *req;  // [F_cap]
@@ -185,6 +195,14 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     int ax_rc, ax_ec;         // index of the reception / emission direction set in c_axes*
     int *worklist;            // (particle, nu) keys a hop's receiver side has to visit
 };
+
+// the low word of a device counter, loaded where it is used (volatile: the load is neither
+// hoisted nor kept in a register across the caller's loops)
+__device__ __forceinline__ unsigned cnt_word(const DevPtrs &P, int k) {
+    unsigned v;
+    asm volatile("ld.global.b32 %0, [%1];" : "=r"(v) : "l"(P.cnt + k));
+    return v;
+}
 
 // kernel identities for the launch counter and the optional per-kernel timer
 enum {
@@ -215,7 +233,7 @@ struct rt_ctx {
     int cur = 0;                  // slot buffer holding the current packets
     int fcur = 0;                 // free buffer of the current hop
     long long nfree_h = 0;        // free packets of the current hop (host copy)
-    long long hop_global = 0;
+    long long step_dev = -1ll << 63;  // step number held in the device counters (LLONG_MIN: unknown)
     long long stats[RT_NSTATS] = {0};
     std::string err;
     // scan scratch
@@ -234,6 +252,17 @@ struct rt_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
     size_t ev_next = 0;
+    // the whole step as one CUDA graph (conditional while node around the hop body); rebuilt
+    // when the kernel parameters it captured change
+    bool use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t st_cap = nullptr;     // capture stream
+    DevPtrs graph_P;                   // parameters the graph was captured with
+    int graph_hop_cap = -1;
+    long long graph_launch_step[KT_N] = {0}, graph_launch_hop[KT_N] = {0};
+    bool capturing = false;            // launches counted into graph_launch_* while capturing
+    bool in_hop_body = false;
     double *src_emit = nullptr;   // device [nb]: source photons of one step per box
     std::vector<double> src_emit_h, box_NH_h;
 };
@@ -248,6 +277,9 @@ rt_status rt_knn_build(rt_ctx *c, cudaStream_t st);
 // the grids may be in flight
 void rt_set_grid(rt_ctx *c, int occupancy);
 rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st);
+// one whole step through the captured graph (captured again when its parameters changed)
+rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st);
+void rt_graph_destroy(rt_ctx *c);
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);
 void rt_host_axis_set(int n, double *out);

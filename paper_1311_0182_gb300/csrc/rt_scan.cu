@@ -1,8 +1,8 @@
 // rt_scan.cu -- exclusive prefix sum of int32 counts (cell lists, reverse lists, per-hop
 // requests and receiver segments).  Three kernels: per-block scan, a single-block scan of
 // the block totals, and the add-back.  `d_len` (optional) is a device-side element count;
-// entries at or beyond it read as zero, so a launch sized for a capacity scans only the live
-// part without a host round trip.
+// the scan covers only the entries before it (the output beyond it is left as it was), so a
+// launch sized for a capacity scans the live part without a host round trip.
 #include "rt_internal.cuh"
 
 #define SCAN_BLOCK 1024
@@ -40,17 +40,26 @@ __global__ void k_scan_blocks(const int *in, int *out, long long n, const int *d
     __shared__ int sh[33];
     long long len = d_len ? (long long)*d_len : n;
     if (len > n) len = n;
-    long long i = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    long long b0 = (long long)blockIdx.x * SCAN_BLOCK;
+    if (b0 >= len) {   // the whole block lies beyond the live part
+        if (threadIdx.x == 0) btot[blockIdx.x] = 0;
+        return;
+    }
+    long long i = b0 + threadIdx.x;
     int v = (i < len) ? in[i] : 0;
     int tot;
     int r = block_excl_scan(v, sh, &tot);
-    if (i < n) out[i] = r;
+    if (i < len) out[i] = r;
     if (threadIdx.x == 0) btot[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_totals(int *btot, long long nblocks, int *d_total) {
+__global__ void k_scan_totals(int *btot, long long nblocks, const int *d_len, int *d_total) {
     __shared__ int sh[33];
     int carry = 0;
+    if (d_len) {
+        long long lb = ((long long)*d_len + SCAN_BLOCK - 1) / SCAN_BLOCK;
+        if (lb < nblocks) nblocks = lb;
+    }
     for (long long base = 0; base < nblocks; base += SCAN_BLOCK) {
         long long i = base + threadIdx.x;
         int v = i < nblocks ? btot[i] : 0;
@@ -62,9 +71,11 @@ __global__ void k_scan_totals(int *btot, long long nblocks, int *d_total) {
     if (threadIdx.x == 0 && d_total) *d_total = carry;
 }
 
-__global__ void k_scan_add(int *out, long long n, const int *btot) {
+__global__ void k_scan_add(int *out, long long n, const int *d_len, const int *btot) {
+    long long len = d_len ? (long long)*d_len : n;
+    if (len > n) len = n;
     long long i = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    if (i < n) out[i] += btot[blockIdx.x];
+    if (i < len) out[i] += btot[blockIdx.x];
 }
 
 // tmp: block-total scratch of at least scan_tmp_n ints (default: the context's); two scans in
@@ -75,6 +86,6 @@ void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const in
     if (nb < 1) nb = 1;
     if (!tmp) tmp = c->scan_tmp;
     k_scan_blocks<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, out, n, d_len, tmp);
-    k_scan_totals<<<1, SCAN_BLOCK, 0, st>>>(tmp, nb, d_total);
-    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, tmp);
+    k_scan_totals<<<1, SCAN_BLOCK, 0, st>>>(tmp, nb, d_len, d_total);
+    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, d_len, tmp);
 }

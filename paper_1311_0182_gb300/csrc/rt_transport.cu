@@ -17,6 +17,8 @@
 //      (sender, slot); then the staged free-packet contributions in (packet, neighbour) order.
 //      No floating-point atomics: every sum has one fixed order.
 #include <algorithm>
+#include <climits>
+#include <cstring>
 
 #include "rt_knn.cuh"
 
@@ -225,8 +227,9 @@ __device__ __forceinline__ unsigned long long esc_fixed(float N, const DevPtrs &
 // ------------------------------------------------------------------------------------------
 // per-step kernels
 // ------------------------------------------------------------------------------------------
-__global__ void k_rotate(DevPtrs P, long long step) {
+__global__ void k_rotate(DevPtrs P) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long step = P.cnt[CNT_STEP];
     long long nsrc = (long long)P.ns * P.K;
     if (i < P.n) {
         double R[9];
@@ -245,9 +248,10 @@ __global__ void k_rotate(DevPtrs P, long long step) {
 
 // Start of step: clock reset and re-binning of held packets into the new reception cones.
 template <typename Real, int NRC>
-__global__ void k_rebin(DevPtrs P, int cur) {
+__global__ void k_rebin(DevPtrs P) {
     long long key = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (key >= P.n * P.nf) return;
+    int cur = (int)P.cnt[CNT_CUR];
     unsigned o = P.occ[cur][key];
     if (!o) { P.act[cur][key] = 0; return; }
     long long i = (unsigned)key / (unsigned)P.nf;   // keys < 2^31: 32-bit division
@@ -286,9 +290,10 @@ __global__ void k_rebin(DevPtrs P, int cur) {
 
 // Recombination emission into the reception cones, counter reset, frozen n_HI.
 template <typename Real, int NRC>
-__global__ void k_emit_rec(DevPtrs P, int cur) {
+__global__ void k_emit_rec(DevPtrs P) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    int cur = (int)P.cnt[CNT_CUR];
     int b = P.pbox[i];
     double nm = P.norm[b];
     for (int nu = 0; nu < P.nf; ++nu) {
@@ -332,9 +337,10 @@ __global__ void k_emit_rec(DevPtrs P, int cur) {
     P.act[cur][key] = a;
 }
 
-// Source packets of the step: K emissions x n_freq_src bins x n_ec cones per source.
+// Source packets of the step: K emissions x n_freq_src bins x n_ec cones per source, written
+// to free buffer 0 (the first hop's).
 template <typename Real>
-__global__ void k_emit_src(DevPtrs P, int fcur) {
+__global__ void k_emit_src(DevPtrs P) {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long per_src = (long long)P.K * P.nfs * P.nec;
     if (p >= (long long)P.ns * per_src) return;
@@ -343,7 +349,7 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
     int k = (int)(tt / (unsigned)(P.nfs * P.nec));
     int nu = (int)((tt / (unsigned)P.nec) % (unsigned)P.nfs);
     int e = (int)(tt % (unsigned)P.nec);
-    FreeBuf F = P.fr[fcur];
+    FreeBuf F = P.fr[0];
     int b = P.sbox[j];
     // a gated source emits only while its nearest gas particle is more than half ionised; a
     // directed source sends one packet per emission and frequency (cone 0) along its direction
@@ -376,16 +382,18 @@ __global__ void k_emit_src(DevPtrs P, int fcur) {
 // The original implementation of recombination radiation (Sec. 2.2): particle i emits, K
 // times a step, n_ec packets of N_rec / (K n_ec) photons along its emission axes, rotated at
 // random before each emission; they are free packets at the particle's position with its
-// neighbour list, written after the source packets (index base + (i K + k) n_ec + e).
+// neighbour list, written to free buffer 0 after the source packets (index
+// base + (i K + k) n_ec + e).
 // Particles without recombination photons leave packets of N = 0, which never move.
 template <typename Real>
-__global__ void k_emit_rec_cones(DevPtrs P, int fcur, long long base, long long step) {
+__global__ void k_emit_rec_cones(DevPtrs P, long long base) {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long per = (long long)P.K * P.nec;
     if (p >= P.n * per) return;
+    long long step = P.cnt[CNT_STEP];
     long long i = p / per;
     int k = (int)((p % per) / P.nec), e = (int)(p % P.nec);
-    FreeBuf F = P.fr[fcur];
+    FreeBuf F = P.fr[0];
     long long f = base + p;
     int b = P.pbox[i];
     double Nr = P.Nrec[i];
@@ -415,8 +423,10 @@ __global__ void k_emit_rec_cones(DevPtrs P, int fcur, long long base, long long 
 // neighbours (lane = neighbour k: cone membership, ballot).  For each (frequency, neighbour)
 // the bits of the packets whose cone holds the neighbour go to the neighbour's receiver-ordered
 // bitmap word; empty cones become virtual-particle requests.
+// cur: the slot buffer holding the hop's packets.  Receivers of a bitmap word are flagged in
+// `touched` (cleared again by the work-list kernel).
 template <typename Real, int NRC>
-__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int cur, int stamp) {
+__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int cur) {
     int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
                 if (unu != cur_nu) {
                     if (valid && word) {
                         P.bm[(long long)cur_nu * nrev + rp] = word;
-                        P.touched[(long long)nb * P.nf + cur_nu] = stamp;
+                        P.touched[(long long)nb * P.nf + cur_nu] = 1;
                     }
                     word = 0u;
                     cur_nu = unu;
@@ -517,7 +527,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
         // each (frequency, neighbour) word is written once: a plain store
         if (valid && word) {
             P.bm[(long long)cur_nu * nrev + rp] = word;
-            P.touched[(long long)nb * P.nf + cur_nu] = stamp;
+            P.touched[(long long)nb * P.nf + cur_nu] = 1;
         }
         if (lane < P.nf) P.emp[i * P.nf + lane] = emp_acc;
         if (lane == 0) P.reqcnt[i] = nreq;
@@ -621,29 +631,29 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
 }
 
 // request list: gas slots with empty cones (particle order, slot order), then free packets
+// (grid-stride: a launch sized for the free-packet capacity covers any count)
 __global__ void k_expand(DevPtrs P, const int *lens) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nfree = lens[0];
-    if (t < P.n) {
-        int c = P.reqcnt[t];
-        if (!c) return;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < P.n + nfree;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (!P.reqcnt[t]) continue;
         long long o = P.reqoff[t];
-        for (int nu = 0; nu < P.nf; ++nu) {
-            unsigned e = P.emp[t * P.nf + nu];
-            while (e) {
-                int b = __ffs(e) - 1;
-                e &= e - 1u;
-                if (o < P.F_cap) P.req[o] = (unsigned long long)(t * P.S + (long long)nu * P.nrc + b);
-                else atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
-                ++o;
+        if (t < P.n) {
+            for (int nu = 0; nu < P.nf; ++nu) {
+                unsigned e = P.emp[t * P.nf + nu];
+                while (e) {
+                    int b = __ffs(e) - 1;
+                    e &= e - 1u;
+                    if (o < P.F_cap) P.req[o] = (unsigned long long)(t * P.S + (long long)nu * P.nrc + b);
+                    else atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
+                    ++o;
+                }
             }
+        } else {
+            long long f = t - P.n;
+            if (o < P.F_cap) P.req[o] = RT_FREE_BIT | (unsigned long long)f;
+            else atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
         }
-    } else if (t < P.n + nfree) {
-        long long f = t - P.n;
-        if (!P.reqcnt[t]) return;
-        long long o = P.reqoff[t];
-        if (o < P.F_cap) P.req[o] = RT_FREE_BIT | (unsigned long long)f;
-        else atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
     }
 }
 
@@ -668,10 +678,12 @@ __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long l
 
 // Virtual particles (Sec. 2.1): one warp per request.
 // BAR: some box has a barrier (a separate instance keeps the test out of the common case)
+// cur, fcur: the hop's slot and free-packet buffers (launch parameters, so that buffer
+// pointers are re-read from the parameter space instead of being held in registers); the
+// step and hop of the random draws are read from the device counters where they are used.
 template <typename Real, int NRC, bool BAR>
-__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur, const int *lens,
-                                                 long long step, int hop,
-                                                 unsigned long long *esc_r,
+__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
+                                                 const int *lens, unsigned long long *esc_r,
                                                  unsigned char *vstat) {
     __shared__ int sdelta[8][32];   // kNN batch bookkeeping, one row per warp
     int lane = threadIdx.x & 31;
@@ -737,7 +749,8 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         bool found = false;
         for (int a0 = 0; a0 < 64 && !found; a0 += 32) {
             unsigned a = (unsigned)(a0 + lane);
-            uint4 u = philox4x32_10(make_uint4((unsigned)step, ((unsigned)hop << 8) | a,
+            // counter: (step, hop << 8 | draw, packet id); step and hop from the device counters
+            uint4 u = philox4x32_10(make_uint4(cnt_word(P, CNT_STEP), (cnt_word(P, CNT_HOP) << 8) | a,
                                                (unsigned)fid, (unsigned)(fid >> 32)), key);
             // floor(u * span / 2^32) - H, |e| <= H < 2^21: 32-bit integers (a 64-bit integer to
             // float conversion would run on the FP64 pipe)
@@ -893,18 +906,25 @@ __global__ void k_seg_sort(DevPtrs P) {
 
 // The receiver groups with work this hop: receivers touched by a gas sender, receivers of
 // staged free-packet contributions, and particles holding waiting packets.  Block-level
-// compaction with one atomic per block; the order of the list does not matter.
-__global__ void __launch_bounds__(256) k_worklist(DevPtrs P, int cur, int stamp, int *wl_n) {
+// compaction with one atomic per block; the order of the list does not matter.  An entry is
+// the key, with bit 31 set when a gas sender touched it (the flag is cleared here).  The next
+// slot buffer's occupancy and activity words are cleared here for the receiver side.
+__global__ void __launch_bounds__(256) k_worklist(DevPtrs P, int cur, int *wl_n) {
     __shared__ int wcount[8], wbase[8], bbase;
     long long nkey = P.n * P.nf;
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned *occ_n = P.occ[cur ^ 1], *act_n = P.act[cur ^ 1];
     for (long long k0 = (long long)blockIdx.x * blockDim.x; k0 < nkey;
          k0 += (long long)gridDim.x * blockDim.x) {
         long long key = k0 + threadIdx.x;
-        bool f = false;
-        if (key < nkey)
-            f = P.touched[key] == stamp || P.seg_cnt[key] > 0 ||
-                (P.occ[cur][key] & ~P.act[cur][key]) != 0u;
+        bool f = false, t = false;
+        if (key < nkey) {
+            t = P.touched[key] != 0;
+            if (t) P.touched[key] = 0;
+            f = t || P.seg_cnt[key] > 0 || (P.occ[cur][key] & ~P.act[cur][key]) != 0u;
+            occ_n[key] = 0u;
+            act_n[key] = 0u;
+        }
         unsigned m = __ballot_sync(FULLMASK, f);
         if (lane == 0) wcount[w] = __popc(m);
         __syncthreads();
@@ -914,7 +934,9 @@ __global__ void __launch_bounds__(256) k_worklist(DevPtrs P, int cur, int stamp,
             bbase = t ? atomicAdd(wl_n, t) : 0;
         }
         __syncthreads();
-        if (f) P.worklist[bbase + wbase[w] + __popc(m & ((1u << lane) - 1u))] = (int)key;
+        if (f)
+            P.worklist[bbase + wbase[w] + __popc(m & ((1u << lane) - 1u))] =
+                (int)((unsigned)key | (t ? 0x80000000u : 0u));
         __syncthreads();
     }
 }
@@ -957,9 +979,10 @@ __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long
 // Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
 // cone.  Contributions are computed in parallel and merged in their fixed order by a
 // broadcast loop (the lane owning the target cone adds).  Groups come from the work list;
-// the next buffer's occupancy words were cleared before the launch.
+// the next buffer's occupancy words were cleared by the work-list kernel.
+// cur: the slot buffer holding the hop's packets.
 template <typename Real, int G, bool BAR>
-__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int cur, int stamp, const int *wl_n) {
+__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int cur, const int *wl_n) {
     // contributions of the current chunk, one per lane: 6 values (T, T d, T clock, T eps); and
     // per reception cone of each group, the mask of the chunk's lanes that feed it
     __shared__ Real sv[6][256];
@@ -978,11 +1001,12 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
     long long gstride = ((long long)gridDim.x * blockDim.x) / G;
     int nxt = cur ^ 1;
     for (long long gi = g0; gi < ng; gi += gstride) {
-        long long key = P.worklist[gi];
+        unsigned wv = (unsigned)P.worklist[gi];
+        long long key = wv & 0x7fffffffu;
+        bool touched = (wv >> 31) != 0u;
         long long j = (unsigned)key / (unsigned)P.nf;
         int nu = (int)((unsigned)key % (unsigned)P.nf);
         unsigned park = P.occ[cur][key] & ~P.act[cur][key];
-        bool touched = P.touched[key] == stamp;
         int fc = P.seg_cnt[key];
         Slots<Real> So(P, cur), Sn(P, nxt);
         long long sidx = j * P.S + (long long)nu * G + gl;
@@ -1207,38 +1231,78 @@ __global__ void k_hop_counts(DevPtrs P, int nxt, int fnxt, const int *lens,
     }
 }
 
-// bookkeeping between kernels of a hop (single thread)
-__global__ void k_hop_lens(DevPtrs P, int *lens, int phase) {
-    if (phase == 0) {            // before the hop: scan lengths
+// bookkeeping of the hop loop (single thread)
+enum { HL_BEGIN = 0, HL_REQ = 1, HL_END = 2, HL_EMIT = 3, HL_TRANSPORT = 4, HL_STEP = 5 };
+// in_graph: the launch is a node of the step graph, and `handle` the conditional it sets
+// (HL_BEGIN: the buffer switch; HL_END: the hop loop)
+__global__ void k_hop_lens(DevPtrs P, int *lens, int phase, long long arg, int in_graph,
+                           cudaGraphConditionalHandle handle) {
+    long long *cnt = P.cnt;
+    if (phase == HL_BEGIN) {            // before the hop: counters, scan length
+        cnt[CNT_ACTIVE] = 0;
+        cnt[CNT_LIVE] = 0;
         lens[1] = (int)(P.n + lens[0]);
-    } else if (phase == 1) {     // after the request scan: n_req
+        // in the graph: which of the four copies of the hop (slot and free-packet buffers) runs
+        if (in_graph) cudaGraphSetConditional(handle, (unsigned)(cnt[CNT_CUR] | (cnt[CNT_FCUR] << 1)));
+    } else if (phase == HL_REQ) {       // after the request scan: n_req
         long long nr = lens[2];
         if (nr > P.F_cap) {
-            atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
+            atomicOr((unsigned long long *)&cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
         }
-        P.cnt[CNT_NREQ] = nr;
-        P.cnt[CNT_VIRT] += nr < P.F_cap ? nr : P.F_cap;
+        cnt[CNT_NREQ] = nr;
+        cnt[CNT_VIRT] += nr < P.F_cap ? nr : P.F_cap;
         if (lens[3] > P.ST_cap)
-            atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_STAGE_CAP);
-    } else {                     // after the hop: the requests become the next free packets
+            atomicOr((unsigned long long *)&cnt[CNT_ERR], (unsigned long long)ERRB_STAGE_CAP);
+    } else if (phase == HL_END) {       // after the hop (arg = hop cap)
         long long nr = lens[2];
         lens[0] = (int)(nr < P.F_cap ? nr : P.F_cap);
-        P.cnt[CNT_STG] += lens[3];
-        P.cnt[CNT_WLS] += lens[4];
+        cnt[CNT_STG] += lens[3];
+        cnt[CNT_WLS] += lens[4];
+        if (nr > cnt[CNT_PKFREE]) cnt[CNT_PKFREE] = nr;
+        if (cnt[CNT_ACTIVE] > cnt[CNT_PKACT]) cnt[CNT_PKACT] = cnt[CNT_ACTIVE];
+        cnt[CNT_CUR] ^= 1;              // the receivers' buffers hold the next hop's packets
+        cnt[CNT_FCUR] ^= 1;
+        long long hop = ++cnt[CNT_HOP];
+        // another hop while packets still move and no error stopped the step; at the hop cap
+        // the free packets in flight are dropped (counted escaped) and the step reports it
+        bool moving = cnt[CNT_ACTIVE] != 0 || cnt[CNT_LIVE] != 0;
+        bool more = moving && cnt[CNT_ERR] == 0;
+        if (more && hop >= arg) {
+            more = false;
+            cnt[CNT_DROP] = 1;
+        }
+        if (in_graph) cudaGraphSetConditional(handle, more ? 1u : 0u);
+    } else if (phase == HL_EMIT) {      // emission (arg = packets): free buffer 0 holds them
+        lens[0] = (int)arg;
+        cnt[CNT_FCUR] = 0;
+    } else if (phase == HL_TRANSPORT) { // start of the hop loop (arg = hop cap)
+        cnt[CNT_VIRT] = 0;
+        cnt[CNT_VESC] = 0;
+        cnt[CNT_GAS] = 0;
+        for (int k = CNT_ACTP; k <= CNT_OUT; ++k) cnt[k] = 0;
+        cnt[CNT_HOP] = 0;
+        cnt[CNT_PKFREE] = 0;
+        cnt[CNT_PKACT] = 0;
+        cnt[CNT_DROP] = arg <= 0 ? 1 : 0;
+    } else {                            // HL_STEP: the step number (arg)
+        cnt[CNT_STEP] = arg;
     }
 }
 
-// Hop cap reached: the free packets still in flight leave the box (counted escaped).
+// Hop cap reached: the free packets still in flight leave the box (counted escaped).  Does
+// nothing unless the hop loop set the drop flag.
 template <typename Real>
-__global__ void k_drop_free(DevPtrs P, int fcur, const int *lens) {
-    long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= lens[0]) return;
-    FreeBuf F = P.fr[fcur];
-    Real N = ((Real *)F.N)[f];
-    if (N > Real(0)) {
-        int b = F.box[f];
-        atomicAdd(&P.esc_fx[b], esc_fixed(N, P, b));
-        ((Real *)F.N)[f] = Real(0);
+__global__ void k_drop_free(DevPtrs P, const int *lens) {
+    if (!P.cnt[CNT_DROP]) return;
+    FreeBuf F = P.fr[(int)P.cnt[CNT_FCUR]];
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < lens[0];
+         f += (long long)gridDim.x * blockDim.x) {
+        Real N = ((Real *)F.N)[f];
+        if (N > Real(0)) {
+            int b = F.box[f];
+            atomicAdd(&P.esc_fx[b], esc_fixed(N, P, b));
+            ((Real *)F.N)[f] = Real(0);
+        }
     }
 }
 
@@ -1254,142 +1318,99 @@ __global__ void k_drop_free(DevPtrs P, int fcur, const int *lens) {
     } while (0)
 #define LAUNCH(id, n, ...) LAUNCH_ON(st, id, n, __VA_ARGS__)
 
+// the step number the rotations and virtual particles draw with (kept on the device)
+static void set_step(rt_ctx *c, long long step, cudaStream_t st) {
+    if (c->step_dev == step && step != LLONG_MIN) return;
+    LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(c->d, c->hop.lens, HL_STEP, step, 0, 0)));
+    c->step_dev = step;
+}
+
+// One hop.  Two streams: st: gas senders, the request list, virtual particles, the hop counts.
+// s2: free-packet senders and staging, receiver segments, work list, receiver side.  s2 starts
+// after everything before this hop on st; the work list waits for the gas senders (touched
+// flags, bitmaps, records); the request scan and its length check wait for the free-packet
+// cone tests; the hop counts wait for the receiver side.  nfr bounds the free packets of the
+// hop (their count is on the device); cur and fcur are the hop's slot and free-packet buffers.
+// The bookkeeping kernels before and after (k_hop_lens HL_BEGIN, HL_END) are not part of it.
 template <typename Real, int NRC>
-static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st) {
+static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcur) {
     DevPtrs &P = c->d;
-    const int tb = 256;
-    long long n = P.n;
-    long long nkey = n * P.nf;
     HopScratch &H = c->hop;
-    if (part == 0) {  // rotations
-        long long t = n + (long long)P.ns * P.K;
-        LAUNCH(KT_ROTATE, 1, (k_rotate<<<(unsigned)((t + tb - 1) / tb), tb, 0, st>>>(P, step)));
-        return rt_cuda_check(c, cudaGetLastError(), "rotate");
-    }
-    if (part == 1) {  // re-bin held packets
-        LAUNCH(KT_REBIN, 1, (k_rebin<Real, NRC><<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P, c->cur)));
-        return rt_cuda_check(c, cudaGetLastError(), "rebin");
-    }
-    if (part == 2) {  // emission
-        LAUNCH(KT_EMIT_REC, 1, (k_emit_rec<Real, NRC><<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(P, c->cur)));
-        long long np_s = (long long)P.ns * P.K * P.nfs * P.nec;
-        long long np_r = P.rec_mode == RT_REC_EMISSION_CONES ? n * P.K * P.nec : 0;
-        long long np = np_s + np_r;
-        if (np > P.F_cap) return rt_fail(c, RT_ERR_CAPACITY, "source packets exceed free_cap");
-        c->fcur = 0;
-        if (np_s > 0)
-            LAUNCH(KT_EMIT_SRC, 1, (k_emit_src<Real><<<(unsigned)((np_s + tb - 1) / tb), tb, 0, st>>>(P, c->fcur)));
-        if (np_r > 0)
-            LAUNCH(KT_EMIT_SRC, 1, (k_emit_rec_cones<Real><<<(unsigned)((np_r + tb - 1) / tb), tb, 0, st>>>(P, c->fcur, np_s, step)));
-        int npi = (int)np;
-        cudaMemcpyAsync(H.lens, &npi, sizeof(int), cudaMemcpyHostToDevice, st);
-        c->nfree_h = np;
-        return rt_cuda_check(c, cudaGetLastError(), "emit");
-    }
-    if (part == 3) {  // cone masks of the held packets only (inspection)
-        cudaMemsetAsync(P.bm, 0, sizeof(unsigned) * n * P.kn * P.nf, st);
-        c->bm_dirty = true;
-        int stamp = (int)(++c->hop_global);
-        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur, stamp)));
-        return rt_cuda_check(c, cudaGetLastError(), "cone masks");
-    }
-    // part 4: the hop loop
+    const int tb = 256, gb = 152 * 64;
+    long long n = P.n, nkey = n * P.nf;
+    cudaStream_t s2 = c->st2;
+    cudaEvent_t evFork = c->hev[0], evA = c->hev[1], evFree = c->hev[2], evB = c->hev[3];
+    if (nfr < 1) nfr = 1;
+    cudaEventRecord(evFork, st);
+    cudaStreamWaitEvent(s2, evFork, 0);
+    cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, s2);
+    cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, s2);
+    LAUNCH_ON(s2, KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
+    LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
+    cudaEventRecord(evFree, s2);
+    if (P.any_bar)
+        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+    else
+        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+    LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
+    cudaEventRecord(evA, st);
+    cudaStreamWaitEvent(st, evFree, 0);
+    LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
+    LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_REQ, 0, 0, 0)));
+    LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
+    if (P.any_bar)
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+    else
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+    LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
+    LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
+    LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));
+    cudaMemsetAsync(H.lens + 4, 0, sizeof(int), s2);
+    cudaStreamWaitEvent(s2, evA, 0);
+    LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, H.lens + 4)));
+    if (P.any_bar)
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+    else
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+    cudaEventRecord(evB, s2);
+    cudaStreamWaitEvent(st, evB, 0);
+    LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, cur ^ 1, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
+}
+
+// cone bitmaps and receiver flags back to zero (as every hop leaves them)
+static void clear_cone_bits(rt_ctx *c, cudaStream_t st) {
+    DevPtrs &P = c->d;
+    cudaMemsetAsync(P.bm, 0, sizeof(unsigned) * P.n * P.kn * P.nf, st);
+    cudaMemsetAsync(P.touched, 0, sizeof(int) * P.n * P.nf, st);
+}
+
+// start of the hop loop: cone bits cleared if an inspection pass left some, counters reset
+static void transport_begin(rt_ctx *c, cudaStream_t st) {
+    DevPtrs &P = c->d;
     if (c->bm_dirty) {
-        cudaMemsetAsync(P.bm, 0, sizeof(unsigned) * n * P.kn * P.nf, st);
+        clear_cone_bits(c, st);
         c->bm_dirty = false;
     }
-    cudaMemsetAsync(&P.cnt[CNT_VIRT], 0, 2 * sizeof(long long), st);
-    cudaMemsetAsync(&P.cnt[CNT_GAS], 0, sizeof(long long), st);
-    cudaMemsetAsync(&P.cnt[CNT_ACTP], 0, 6 * sizeof(long long), st);
-    rt_status status = RT_OK;
-    long long hops = 0, peak_free = 0, peak_act = 0;
-    const int gb = 152 * 64;
-    for (int hop = 0;; ++hop) {
-        if (hop >= c->cfg.hop_cap) {
-            LAUNCH(KT_DROP, 1, (k_drop_free<Real><<<rt_blocks(P.F_cap, tb, 1 << 20), tb, 0, st>>>(P, c->fcur, H.lens)));
-            status = rt_fail(c, RT_ERR_HOP_LIMIT, "hop loop reached hop_cap");
-            break;
-        }
-        int stamp = (int)(++c->hop_global);
-        int cur = c->cur, nxt = cur ^ 1, fcur = c->fcur;
-        // Two streams.  st: gas senders, the request list, virtual particles, the hop counts.
-        // s2: free-packet senders and staging, receiver segments, work list, receiver side.
-        // s2 starts after everything before this hop on st; the work list waits for the gas
-        // senders (touched stamps, bitmaps, records); the request scan and its length check
-        // wait for the free-packet cone tests; the hop counts wait for the receiver side.
-        cudaStream_t s2 = c->st2;
-        cudaEvent_t evFork = c->hev[0], evA = c->hev[1], evFree = c->hev[2], evB = c->hev[3];
-        cudaMemsetAsync(&P.cnt[CNT_ACTIVE], 0, sizeof(long long), st);
-        cudaMemsetAsync(&P.cnt[CNT_LIVE], 0, sizeof(long long), st);
-        // free packets of this hop: known on the host from the last hop's counters
-        long long nfr = std::max<long long>(c->nfree_h, 1);
-        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 0)));
-        cudaEventRecord(evFork, st);
-        cudaStreamWaitEvent(s2, evFork, 0);
-        cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, s2);
-        cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, s2);
-        LAUNCH_ON(s2, KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
-        LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
-        cudaEventRecord(evFree, s2);
-        if (P.any_bar)
-            LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
-        else
-            LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
-        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur, stamp)));
-        cudaEventRecord(evA, st);
-        cudaStreamWaitEvent(st, evFree, 0);
-        LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
-        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 1)));
-        LAUNCH(KT_EXPAND, 1, (k_expand<<<(unsigned)((n + nfr + tb - 1) / tb), tb, 0, st>>>(P, H.lens)));
-        if (P.any_bar)
-            LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
-                                      P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
-        else
-            LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
-                                      P, cur, fcur, H.lens, step, hop, H.esc_r, H.vstat)));
-        LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
-        LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
-        LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));
-        cudaMemsetAsync(H.lens + 4, 0, sizeof(int), s2);
-        cudaStreamWaitEvent(s2, evA, 0);
-        LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
-        cudaMemsetAsync(P.occ[nxt], 0, sizeof(unsigned) * nkey, s2);
-        cudaMemsetAsync(P.act[nxt], 0, sizeof(unsigned) * nkey, s2);
-        if (P.any_bar)
-            LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
-        else
-            LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, stamp, H.lens + 4)));
-        cudaEventRecord(evB, s2);
-        cudaStreamWaitEvent(st, evB, 0);
-        LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, nxt, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
-        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, 2)));
-        c->cur = nxt;
-        c->fcur = fcur ^ 1;
-        ++hops;
-        cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
-        rt_status hs = rt_cuda_check(c, cudaStreamSynchronize(st), "hop");
-        if (hs != RT_OK) return hs;
-        kt_resolve(c);
-        if (c->cnt_h[CNT_ERR]) break;
-        c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], P.F_cap);
-        if (c->cnt_h[CNT_NREQ] > peak_free) peak_free = c->cnt_h[CNT_NREQ];
-        if (c->cnt_h[CNT_ACTIVE] > peak_act) peak_act = c->cnt_h[CNT_ACTIVE];
-        if (c->cnt_h[CNT_ACTIVE] == 0 && c->cnt_h[CNT_LIVE] == 0) break;
-    }
-    cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    kt_resolve(c);
+    LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, c->hop.lens, HL_TRANSPORT, c->cfg.hop_cap, 0, 0)));
+}
+
+// after the hop loop (the counters are in cnt_h): statistics, modelled bytes, status
+static rt_status transport_end(rt_ctx *c, bool fp32) {
+    DevPtrs &P = c->d;
+    long long hops = c->cnt_h[CNT_HOP];
     // the active packets of the first hop were made by the emission: add them to the model
     // counts below (CNT_ACTS/ACTP count those produced by each hop's receiver side)
     {
-        const double R = sizeof(Real), kn = P.kn;
+        const double R = fp32 ? 4.0 : 8.0, kn = P.kn;
         double actp = (double)c->cnt_h[CNT_ACTP], acts = (double)c->cnt_h[CNT_ACTS];
         double gcon = (double)c->cnt_h[CNT_GCON], stg = (double)c->cnt_h[CNT_STG];
         double wls = (double)c->cnt_h[CNT_WLS], outs = (double)c->cnt_h[CNT_OUT];
         double vreq = (double)c->cnt_h[CNT_VIRT];
         // algorithmic bytes: each input read once and each output written once
         c->kstat[KT_PHASE_A].bytes += actp * (kn * (4 + 4 + 12) + P.nf * 4) + acts * 12 * R +
-                                      gcon * 8 + (double)hops * (double)n * 4;
+                                      gcon * 8 + (double)hops * (double)P.n * 4;
         c->kstat[KT_PHASE_B].bytes += wls * (16 + 8 + 48 + kn * 4) + gcon * (16 + 6 * R + 4) +
                                       stg * (8 + 9 * R) + outs * 6 * R;
         c->kstat[KT_VIRTUAL].bytes += vreq * (8 + 6 * R + 40 + kn * (16 + 4 * R + 16 + 4) +
@@ -1398,8 +1419,8 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     c->stats[0] = hops;
     c->stats[1] = c->cnt_h[CNT_VIRT];
     c->stats[2] = c->cnt_h[CNT_VESC];
-    c->stats[5] = peak_free;
-    c->stats[6] = peak_act;
+    c->stats[5] = c->cnt_h[CNT_PKFREE];
+    c->stats[6] = c->cnt_h[CNT_PKACT];
     c->stats[7] = c->cnt_h[CNT_GCON];
     c->stats[8] = c->cnt_h[CNT_ACTP];
     c->stats[9] = c->cnt_h[CNT_ACTS];
@@ -1410,8 +1431,260 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     if (e & ERRB_FREE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "free packets exceeded free_cap");
     if (e & ERRB_STAGE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "staged contributions exceeded capacity");
     if (e & ERRB_RANGE) return rt_fail(c, RT_ERR_RANGE, "virtual deposit overflowed its accumulator");
-    return status;
+    if (c->cnt_h[CNT_DROP]) return rt_fail(c, RT_ERR_HOP_LIMIT, "hop loop reached hop_cap");
+    return RT_OK;
 }
+
+template <typename Real, int NRC>
+static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st) {
+    DevPtrs &P = c->d;
+    const int tb = 256;
+    long long n = P.n;
+    long long nkey = n * P.nf;
+    HopScratch &H = c->hop;
+    if (part == 0) {  // rotations
+        if (!c->capturing) set_step(c, step, st);
+        long long t = n + (long long)P.ns * P.K;
+        LAUNCH(KT_ROTATE, 1, (k_rotate<<<(unsigned)((t + tb - 1) / tb), tb, 0, st>>>(P)));
+        return rt_cuda_check(c, cudaGetLastError(), "rotate");
+    }
+    if (part == 1) {  // re-bin held packets
+        LAUNCH(KT_REBIN, 1, (k_rebin<Real, NRC><<<(unsigned)((nkey + tb - 1) / tb), tb, 0, st>>>(P)));
+        return rt_cuda_check(c, cudaGetLastError(), "rebin");
+    }
+    if (part == 2) {  // emission
+        long long np_s = (long long)P.ns * P.K * P.nfs * P.nec;
+        long long np_r = P.rec_mode == RT_REC_EMISSION_CONES ? n * P.K * P.nec : 0;
+        long long np = np_s + np_r;
+        if (np > P.F_cap) return rt_fail(c, RT_ERR_CAPACITY, "source packets exceed free_cap");
+        if (!c->capturing) set_step(c, step, st);
+        LAUNCH(KT_EMIT_REC, 1, (k_emit_rec<Real, NRC><<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(P)));
+        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_EMIT, np, 0, 0)));
+        c->fcur = 0;
+        if (np_s > 0)
+            LAUNCH(KT_EMIT_SRC, 1, (k_emit_src<Real><<<(unsigned)((np_s + tb - 1) / tb), tb, 0, st>>>(P)));
+        if (np_r > 0)
+            LAUNCH(KT_EMIT_SRC, 1, (k_emit_rec_cones<Real><<<(unsigned)((np_r + tb - 1) / tb), tb, 0, st>>>(P, np_s)));
+        c->nfree_h = np;
+        return rt_cuda_check(c, cudaGetLastError(), "emit");
+    }
+    if (part == 3) {  // cone masks of the held packets only (inspection)
+        clear_cone_bits(c, st);
+        c->bm_dirty = true;
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur)));
+        return rt_cuda_check(c, cudaGetLastError(), "cone masks");
+    }
+    // part 4: the hop loop, driven from the host (one synchronisation per hop)
+    set_step(c, step, st);
+    transport_begin(c, st);
+    for (int hop = 0;; ++hop) {
+        if (hop >= c->cfg.hop_cap) {
+            LAUNCH(KT_DROP, 1, (k_drop_free<Real><<<rt_blocks(P.F_cap, tb, 152 * 64), tb, 0, st>>>(P, H.lens)));
+            break;
+        }
+        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_BEGIN, 0, 0, 0)));
+        hop_core<Real, NRC>(c, st, c->nfree_h, c->cur, c->fcur);
+        LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_END, c->cfg.hop_cap, 0, 0)));
+        c->cur ^= 1;
+        c->fcur ^= 1;
+        cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+        rt_status hs = rt_cuda_check(c, cudaStreamSynchronize(st), "hop");
+        if (hs != RT_OK) return hs;
+        kt_resolve(c);
+        if (c->cnt_h[CNT_ERR]) break;
+        c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], P.F_cap);
+        if (c->cnt_h[CNT_ACTIVE] == 0 && c->cnt_h[CNT_LIVE] == 0) break;
+    }
+    cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+    rt_status hs = rt_cuda_check(c, cudaStreamSynchronize(st), "hop loop");
+    if (hs != RT_OK) return hs;
+    kt_resolve(c);
+    return transport_end(c, sizeof(Real) == 4);
+}
+
+// ---- the whole step as one CUDA graph --------------------------------------------------
+// Prologue (rotations, re-binning, emission, emitted-photon tally, counter reset), a
+// conditional while node whose body is one hop (its last kernel decides whether another hop
+// runs), and the epilogue (drop at the hop cap, chemistry, end-of-step tally).  Captured on
+// the context's own streams.  What changes from step to step or hop to hop is on the device:
+// the step and hop numbers (read where they are used), and the buffer pair of the hop, which
+// selects one of four captured copies of the hop through a switch node, so that inside a
+// copy the buffers are launch parameters.  One capture serves every step.
+static void graph_destroy(rt_ctx *c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+}
+
+static rt_status capture_segment(rt_ctx *c, cudaGraph_t *out, rt_status (*body)(rt_ctx *, cudaStream_t)) {
+    cudaStream_t sc = c->st_cap;
+    cudaError_t e = cudaStreamBeginCapture(sc, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return rt_cuda_check(c, e, "graph capture");
+    rt_status s = body(c, sc);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(sc, &g);
+    if (s != RT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e2 != cudaSuccess) return rt_cuda_check(c, e2, "graph capture");
+    *out = g;
+    return RT_OK;
+}
+
+template <typename Real, int NRC>
+static rt_status seg_prologue(rt_ctx *c, cudaStream_t st) {
+    rt_status s;
+    if ((s = run_parts<Real, NRC>(c, 0, 0, st))) return s;
+    if ((s = run_parts<Real, NRC>(c, 1, 0, st))) return s;
+    if ((s = run_parts<Real, NRC>(c, 2, 0, st))) return s;
+    if ((s = rt_budget_launch(c, 0, st))) return s;
+    LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(c->d, c->hop.lens, HL_TRANSPORT, c->cfg.hop_cap, 0, 0)));
+    return rt_cuda_check(c, cudaGetLastError(), "graph prologue");
+}
+
+template <typename Real>
+static rt_status seg_epilogue(rt_ctx *c, cudaStream_t st) {
+    LAUNCH(KT_DROP, 1, (k_drop_free<Real><<<rt_blocks(c->d.F_cap, 256, 152 * 64), 256, 0, st>>>(c->d, c->hop.lens)));
+    rt_status s;
+    if ((s = rt_chem_launch(c, st))) return s;
+    if ((s = rt_budget_launch(c, 1, st))) return s;
+    return rt_cuda_check(c, cudaGetLastError(), "graph epilogue");
+}
+
+// a single-thread bookkeeping kernel as an explicit node of a graph
+static cudaError_t add_lens_node(rt_ctx *c, cudaGraphNode_t *node, cudaGraph_t g,
+                                 const cudaGraphNode_t *dep, int phase, long long arg,
+                                 cudaGraphConditionalHandle handle) {
+    DevPtrs P = c->d;
+    int *lens = c->hop.lens;
+    int in_graph = 1;
+    void *args[] = {&P, &lens, &phase, &arg, &in_graph, &handle};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_hop_lens;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    c->graph_launch_hop[KT_HOP_LENS] += 1;
+    return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp);
+}
+
+// The while node's body: HL_BEGIN (sets the buffer switch) -> a switch node over the four
+// (slot buffer, free-packet buffer) pairs, each body one capture of the hop with those buffers
+// as launch parameters -> HL_END (sets the loop condition).
+template <typename Real, int NRC>
+static cudaError_t build_hop_body(rt_ctx *c, cudaGraph_t body, cudaGraphConditionalHandle loop) {
+    cudaGraphNode_t nbeg, nsw, nend;
+    cudaGraphConditionalHandle sw;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&sw, body, 0, 0);
+    if (e == cudaSuccess) e = add_lens_node(c, &nbeg, body, nullptr, HL_BEGIN, 0, sw);
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = sw;
+        cp.conditional.type = cudaGraphCondTypeSwitch;
+        cp.conditional.size = 4;
+        e = cudaGraphAddNode(&nsw, body, &nbeg, nullptr, 1, &cp);
+    }
+    c->in_hop_body = true;
+    long long once[KT_N];
+    for (int par = 0; par < 4 && e == cudaSuccess; ++par) {
+        e = cudaStreamBeginCaptureToGraph(c->st_cap, cp.conditional.phGraph_out[par], nullptr,
+                                          nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        hop_core<Real, NRC>(c, c->st_cap, c->d.F_cap, par & 1, par >> 1);
+        cudaGraph_t b = cp.conditional.phGraph_out[par];
+        e = cudaStreamEndCapture(c->st_cap, &b);
+        // one copy runs per hop: its launches are counted once
+        if (par == 0) memcpy(once, c->graph_launch_hop, sizeof(once));
+        else memcpy(c->graph_launch_hop, once, sizeof(once));
+    }
+    if (e == cudaSuccess) e = add_lens_node(c, &nend, body, &nsw, HL_END, c->cfg.hop_cap, loop);
+    c->in_hop_body = false;
+    return e;
+}
+
+template <typename Real, int NRC>
+static rt_status capture_step(rt_ctx *c) {
+    graph_destroy(c);
+    for (int k = 0; k < KT_N; ++k) c->graph_launch_step[k] = c->graph_launch_hop[k] = 0;
+    c->capturing = true;
+    cudaGraph_t pro = nullptr, epi = nullptr, g = nullptr;
+    rt_status s = capture_segment(c, &pro, seg_prologue<Real, NRC>);
+    if (s == RT_OK) s = capture_segment(c, &epi, seg_epilogue<Real>);
+    cudaError_t e = cudaSuccess;
+    if (s == RT_OK) {
+        cudaGraphNode_t npro, nloop, nepi;
+        cudaGraphConditionalHandle loop;
+        e = cudaGraphCreate(&g, 0);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&npro, g, nullptr, 0, pro);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams cp = {};
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = loop;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&nloop, g, &npro, nullptr, 1, &cp);
+        }
+        if (e == cudaSuccess) e = build_hop_body<Real, NRC>(c, cp.conditional.phGraph_out[0], loop);
+        if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&nepi, g, &nloop, 1, epi);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    }
+    c->capturing = false;
+    c->in_hop_body = false;
+    if (pro) cudaGraphDestroy(pro);
+    if (epi) cudaGraphDestroy(epi);
+    if (s != RT_OK || e != cudaSuccess) {
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        if (g) cudaGraphDestroy(g);
+        c->graph_exec = nullptr;
+        cudaGetLastError();
+        return s != RT_OK ? s : rt_cuda_check(c, e, "graph build");
+    }
+    c->graph = g;
+    c->graph_P = c->d;
+    c->graph_hop_cap = c->cfg.hop_cap;
+    return RT_OK;
+}
+
+template <typename Real, int NRC>
+static rt_status step_graph(rt_ctx *c, long long step, cudaStream_t st) {
+    bool stale = !c->graph_exec || c->graph_hop_cap != c->cfg.hop_cap ||
+                 memcmp(&c->graph_P, &c->d, sizeof(DevPtrs)) != 0;
+    rt_status s;
+    if (stale && (s = capture_step<Real, NRC>(c))) return s;
+    set_step(c, step, st);
+    if (c->bm_dirty) {
+        clear_cone_bits(c, st);
+        c->bm_dirty = false;
+    }
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, st);
+    if (e != cudaSuccess) return rt_cuda_check(c, e, "graph launch");
+    cudaMemcpyAsync(c->cnt_h, c->d.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
+    if ((s = rt_cuda_check(c, cudaStreamSynchronize(st), "graph step"))) return s;
+    long long hops = c->cnt_h[CNT_HOP];
+    for (int k = 0; k < KT_N; ++k) {
+        long long l = c->graph_launch_step[k] + hops * c->graph_launch_hop[k];
+        c->kstat[k].launches += l;
+        c->launches += l;
+    }
+    c->cur = (int)c->cnt_h[CNT_CUR];
+    c->fcur = (int)c->cnt_h[CNT_FCUR];
+    c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], c->d.F_cap);
+    c->stats[3] = c->cnt_h[CNT_SUB];
+    c->stats[4] = c->cnt_h[CNT_FLOOR];
+    return transport_end(c, sizeof(Real) == 4);
+}
+
+rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st) {
+    int nrc = c->d.nrc;
+    if (c->d.fp32) return nrc == 8 ? step_graph<float, 8>(c, step, st) : step_graph<float, 32>(c, step, st);
+    return nrc == 8 ? step_graph<double, 8>(c, step, st) : step_graph<double, 32>(c, step, st);
+}
+
+void rt_graph_destroy(rt_ctx *c) { graph_destroy(c); }
 
 rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st) {
     int nrc = c->d.nrc;

@@ -22,7 +22,8 @@ SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_
            "rt_get_rotations", "rt_get_cone_masks", "rt_get_cone_masks_noalloc", "rt_get_slots",
            "rt_set_slots",
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
-           "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier"]
+           "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier",
+           "rt_set_graph"]
 
 
 class RTError(RuntimeError):
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = False):
     L.rt_get_stats.argtypes = [vp, vp]
     L.rt_axis_set.argtypes = [i, vp]
     L.rt_set_profiling.argtypes = [vp, i]
+    L.rt_set_graph.argtypes = [vp, i]
     L.rt_get_profile.argtypes = [vp, vp, i, vp, vp, vp, vp]
     L.rt_last_error.argtypes = [vp]
     L.rt_last_error.restype = C.c_char_p
@@ -232,8 +234,12 @@ class Context:
     def chemistry(self):
         self._check(self.L.rt_chemistry(self.h, self._s()), "rt_chemistry")
 
-    def step(self, step):
-        self._check(self.L.rt_step(self.h, step, self._s()), "rt_step")
+    def step(self, step, allow_hop_limit=False):
+        st = self.L.rt_step(self.h, step, self._s())
+        if st == 4 and allow_hop_limit:
+            return st
+        self._check(st, "rt_step")
+        return st
 
     # -- state ---------------------------------------------------------------------------------
     def state(self):
@@ -317,6 +323,10 @@ class Context:
         self._check(self.L.rt_get_deposits(self.h, a.ctypes.data, e.ctypes.data, ps.ctypes.data,
                                            RT_HOST, self._s()), "rt_get_deposits")
         return a, e, ps
+
+    def set_graph(self, on=True):
+        """step() as one captured CUDA graph (True, the default) or hop by hop from the host."""
+        self._check(self.L.rt_set_graph(self.h, 1 if on else 0), "rt_set_graph")
 
     def profile(self, on=True):
         """Time kernels with CUDA events: True every kernel, False none, or an iterable of

@@ -209,7 +209,7 @@ def _lognormal_field(G, sigma_ln, slope, rng):
     kk = np.sqrt(kx * kx + ky * ky + kz * kz)
     amp = np.where(kk > 0, np.power(np.maximum(kk, 1e-12), slope / 2.0), 0.0)
     noise = rng.standard_normal((G, G, G))
-    f = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=(G, G, G))
+    f = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=(G, G, G), axes=(0, 1, 2))
     f = (f - f.mean()) / f.std() * sigma_ln
     rho = np.exp(f)
     return rho / rho.mean()

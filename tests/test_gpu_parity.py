@@ -369,6 +369,75 @@ def test_hop_cap_reports_and_conserves():
     assert abs(bg[0] - bg[1:].sum()) <= 1e-9 * bg[0]
 
 
+def _graph_pair(wl):
+    from paper_1311_0182_gb300 import rt
+    a = rt.context_for(wl)
+    b = rt.context_for(wl)
+    b.set_graph(False)
+    return a, b
+
+
+def _same_results(a, b):
+    sa, sb = a.state(), b.state()
+    for k in ("x_HI", "T", "N_rec", "eps_rec"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(a.budget(), b.budget())
+    for x, y in zip(a.deposits(), b.deposits()):
+        assert np.array_equal(x, y)
+    # (the kNN grid occupancy is chosen by timing and may differ; results do not depend on it)
+    sta, stb = a.stats(), b.stats()
+    sta.pop("cell_occupancy")
+    stb.pop("cell_occupancy")
+    assert sta == stb
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("name", ["cfg2_24", "shadow", "original"])
+def test_step_graph_equals_hop_by_hop_loop(name, fp32):
+    """rt_step as one captured CUDA graph (a conditional while node around the hop, a switch
+    node over the four buffer pairs) gives the same bits as the host-driven hop loop, with the
+    same kernel launch counts (the graph launches the hop-cap drop every step; the loop only
+    at the cap): the HII region at 24^3 (32 cones, 8 frequency bins), the shadow workload
+    (barrier, directed and gated emitters) and the original recombination implementation."""
+    wl = {"cfg2_24": lambda: W.cfg2(n_side=24, transport_fp32=fp32),
+          "shadow": lambda: W.shadow(n_side=16, n_front=20, n_bnd=10, transport_fp32=fp32),
+          "original": lambda: W.cfg1(rec_mode=W.REC_EMISSION_CONES, transport_fp32=fp32)}[name]()
+    a, b = _graph_pair(wl)
+    for step in range(5):
+        a.step(step)
+        b.step(step)
+        assert a.stats()["hops"] > 0
+        _same_results(a, b)
+    ka, kb = a.kernel_times(), b.kernel_times()
+    ka.pop("drop_free", None)
+    kb.pop("drop_free", None)
+    assert {k: v["launches"] for k, v in ka.items()} == {k: v["launches"] for k, v in kb.items()}
+
+
+def test_step_graph_at_the_hop_cap_and_after_a_barrier_change():
+    """The graph stops at the hop cap with the same status, drop and budget as the host loop;
+    a barrier removed between steps (a changed kernel choice) makes the graph capture again."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg1(hop_cap=5)
+    wl["x_HI"][:] = 1e-3
+    a, b = _graph_pair(wl)
+    for step in range(2):
+        assert a.step(step, allow_hop_limit=True) == 4
+        assert b.step(step, allow_hop_limit=True) == 4
+        _same_results(a, b)
+    bg = a.budget()[0]
+    assert bg[2] > 0 and abs(bg[0] - bg[1:].sum()) <= 1e-9 * bg[0]
+    wl = W.shadow(n_side=16, n_front=20, n_bnd=10)
+    a, b = _graph_pair(wl)
+    for step in range(6):
+        if step == 3:
+            for c in (a, b):
+                c.set_barrier(0, 0, [0.0, 0.0, 0.0], 0.0)
+        a.step(step)
+        b.step(step)
+        _same_results(a, b)
+
+
 def test_free_packet_capacity_is_an_error_not_a_fault():
     from paper_1311_0182_gb300 import rt
     wl = W.cfg1(free_cap=300)
