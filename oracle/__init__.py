@@ -45,6 +45,7 @@ class Config(C.Structure):
         ("rec_mode", C.c_int), ("evolve_T", C.c_int), ("seed", C.c_uint64),
         ("hop_cap", C.c_int), ("sub_cap", C.c_int), ("cool_flags", C.c_int),
         ("T_floor", C.c_double), ("eps_rr_fixed", C.c_double), ("sigma_rec", C.c_double),
+        ("rec_shared_bin", C.c_int),
     ]
 
 
@@ -89,6 +90,8 @@ def lib():
             L.orc_cone_masks.argtypes = [vp, P(u32)]
             L.orc_get_slots.argtypes = [vp, P(d)]
             L.orc_set_slots.argtypes = [vp, P(d)]
+            L.orc_get_shared_sigma.argtypes = [vp, P(d)]
+            L.orc_set_shared_sigma.argtypes = [vp, P(d)]
             L.orc_get_state.argtypes = [vp, P(d), P(d), P(d), P(d)]
             L.orc_set_state.argtypes = [vp, P(d), P(d), P(d), P(d)]
             L.orc_get_deposits.argtypes = [vp, P(d), P(d), P(d)]
@@ -108,7 +111,7 @@ def make_config(p: dict) -> Config:
         n_freq_src=p["n_freq_src"], dt=p["dt"], dt_em=p["dt_em"], rec_mode=p["rec_mode"],
         evolve_T=p["evolve_T"], seed=p["seed"], hop_cap=p["hop_cap"], sub_cap=p["sub_cap"],
         cool_flags=p["cool_flags"], T_floor=p["T_floor"], eps_rr_fixed=p["eps_rr_fixed"],
-        sigma_rec=p["sigma_rec"])
+        sigma_rec=p["sigma_rec"], rec_shared_bin=p.get("rec_shared_bin", 0))
 
 
 # --- building blocks ----------------------------------------------------------------------
@@ -198,7 +201,8 @@ class Sim:
         self.cfg = make_config(p)
         self.n = int(wl["box_off"][-1])
         self.nb = len(wl["box_L"])
-        self.nf = p["n_freq_src"] + 1
+        # a shared bin (Sec. 2.2) carries the recombination photons in source bin 0
+        self.nf = p["n_freq_src"] + (0 if p.get("rec_shared_bin", 0) else 1)
         self.S = self.nf * p["n_rc"]
         self.K = max(1, int(round(p["dt"] / p["dt_em"])))
         self.ns = len(wl["src_box"])
@@ -298,6 +302,16 @@ class Sim:
     def set_slots(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
         self.L.orc_set_slots(self.h, _p(f, C.c_double))
+
+    def shared_sigma(self):
+        """Shared bin: G = sum N sigma of each slot of bin 0, [n, n_rc]."""
+        G = np.zeros((self.n, self.params["n_rc"]))
+        self.L.orc_get_shared_sigma(self.h, _p(G, C.c_double))
+        return G
+
+    def set_shared_sigma(self, G):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        self.L.orc_set_shared_sigma(self.h, _p(G, C.c_double))
 
     def state(self):
         out = [np.zeros(self.n) for _ in range(4)]

@@ -450,6 +450,7 @@ typedef struct {
     int32_t nbr[MAXK]; /* global gas indices */
     int64_t h2;
     double N, d[3], clock, eps;
+    double sig;        /* cross-section of its photons, cm^2 */
     int nu;
     uint64_t fid;
 } freep_t; /* a packet not held by a gas particle: a source packet or a virtual particle */
@@ -499,6 +500,11 @@ struct orc_sim {
     double *R, *Rs;
     double axes_rc[3 * 32], axes_ec[3 * 32];
     double *sl[6], *nx[6];
+    /* shared frequency bin (Sec. 2.2, last paragraph): recombination photons travel in source
+       bin 0 (rbin = 0), and each slot of that bin carries G = sum N sigma of the photons merged
+       into it ([n*n_rc], current and next hop); without it rbin is the extra last bin */
+    int rbin;
+    double *sg, *nsg;
     double *abs_, *absE, *pass, *nHI, *Nrec, *epsrec;
     double *tally; /* [nb*4] running sums (Neumaier compensated with tallc) */
     double *tallc;
@@ -540,11 +546,13 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
         return NULL;
     if ((cfg->n_rc != 8 && cfg->n_rc != 32) || (cfg->n_ec != 8 && cfg->n_ec != 32))
         return NULL;
+    if (cfg->rec_shared_bin && cfg->n_freq_src < 1) return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->cfg = *cfg;
     s->nb = n_boxes;
     s->n = box_off[n_boxes];
-    s->nf = cfg->n_freq_src + 1;
+    s->nf = cfg->n_freq_src + (cfg->rec_shared_bin ? 0 : 1);
+    s->rbin = cfg->rec_shared_bin ? 0 : cfg->n_freq_src;
     s->S = s->nf * cfg->n_rc;
     long long K = (long long)llround(cfg->dt / cfg->dt_em);
     s->K = K < 1 ? 1 : (int)K;
@@ -587,13 +595,13 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
     s->sgate = (int *)calloc((size_t)(n_src + 1), sizeof(int));
     s->bar = (barrier_t *)calloc((size_t)n_boxes, sizeof(barrier_t));
     for (int b = 0; b < n_boxes; ++b) s->bar[b].axis = -1;
-    s->sigma = (double *)malloc(sizeof(double) * (size_t)s->nf);
-    s->eps = (double *)malloc(sizeof(double) * (size_t)s->nf);
+    s->sigma = (double *)malloc(sizeof(double) * (size_t)(nfs + 1));
+    s->eps = (double *)malloc(sizeof(double) * (size_t)(nfs + 1));
     for (int f = 0; f < nfs; ++f) {
         s->sigma[f] = sigma[f];
         s->eps[f] = eps[f];
     }
-    s->sigma[nfs] = cfg->sigma_rec;
+    s->sigma[nfs] = cfg->sigma_rec;   /* the recombination bin (unused with a shared bin) */
     s->eps[nfs] = 0.0;
     orc_axis_set(cfg->n_rc, s->axes_rc);
     orc_axis_set(cfg->n_ec, s->axes_ec);
@@ -608,6 +616,10 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
     for (int f = 0; f < 6; ++f) {
         s->sl[f] = (double *)calloc((size_t)(n * s->S), sizeof(double));
         s->nx[f] = (double *)calloc((size_t)(n * s->S), sizeof(double));
+    }
+    if (cfg->rec_shared_bin) {
+        s->sg = (double *)calloc((size_t)(n * cfg->n_rc), sizeof(double));
+        s->nsg = (double *)calloc((size_t)(n * cfg->n_rc), sizeof(double));
     }
     s->abs_ = (double *)calloc((size_t)(n * s->nf), sizeof(double));
     s->pass = (double *)calloc((size_t)(n * s->nf), sizeof(double));
@@ -631,6 +643,7 @@ void orc_destroy(orc_sim *s) {
     for (int b = 0; b < s->nb; ++b) grid_free(&s->grids[b]);
     free(s->grids); free(s->R); free(s->Rs);
     for (int f = 0; f < 6; ++f) { free(s->sl[f]); free(s->nx[f]); }
+    free(s->sg); free(s->nsg);
     free(s->abs_); free(s->pass); free(s->absE); free(s->nHI); free(s->Nrec);
     free(s->epsrec); free(s->tally); free(s->tallc); free(s->cur.p); free(s->nxt.p);
     free(s);
@@ -775,11 +788,17 @@ static int slot_active(const orc_sim *s, long long i, int sl, double *clock) {
 void orc_rebin(orc_sim *s) {
     int S = s->S, nrc = s->cfg.n_rc;
     double *tmp = (double *)malloc(sizeof(double) * 6 * (size_t)S);
+    double gold[32];
     for (long long i = 0; i < s->n; ++i) {
         for (int f = 0; f < 6; ++f)
             for (int sl = 0; sl < S; ++sl) {
                 tmp[f * S + sl] = s->sl[f][i * S + sl];
                 s->sl[f][i * S + sl] = 0.0;
+            }
+        if (s->sg)
+            for (int b = 0; b < nrc; ++b) {
+                gold[b] = s->sg[i * nrc + b];
+                s->sg[i * nrc + b] = 0.0;
             }
         for (int sl = 0; sl < S; ++sl) {
             double N = tmp[sl];
@@ -795,6 +814,7 @@ void orc_rebin(orc_sim *s) {
             s->sl[3][p] += M[2];
             s->sl[4][p] += 0.0;
             s->sl[5][p] += tmp[5 * S + sl];
+            if (s->sg && nu == 0) s->sg[i * nrc + b] += gold[sl];
         }
     }
     free(tmp);
@@ -811,7 +831,9 @@ void orc_rebin(orc_sim *s) {
        source in the first hop.
    Absorption and pass counters restart, and the neutral density seen by the transport
    is frozen at its value at the start of the step (operator split, Sec. 2.1).
-   With rec_mode ORC_REC_EMISSION_CONES, (1) is replaced by (3) below. */
+   With rec_mode ORC_REC_EMISSION_CONES, (1) is replaced by (3) below.
+   With a shared bin (Sec. 2.2, last paragraph) the recombination photons go into source bin
+   0 instead of a bin of their own, and add N sigma_rec to the slot's cross-section sum. */
 void orc_emit(orc_sim *s, long long step) {
     int S = s->S, nrc = s->cfg.n_rc, nfs = s->cfg.n_freq_src;
     for (long long i = 0; i < s->n * s->nf; ++i) { s->abs_[i] = 0.0; s->pass[i] = 0.0; }
@@ -826,12 +848,13 @@ void orc_emit(orc_sim *s, long long step) {
         for (int b = 0; b < nrc; ++b) {
             double A[3];
             rotate_axis(s->R + 9 * i, s->axes_rc + 3 * b, A);
-            long long p = i * S + nfs * nrc + b;
+            long long p = i * S + s->rbin * nrc + b;
             s->sl[0][p] += e;
             s->sl[1][p] += e * A[0];
             s->sl[2][p] += e * A[1];
             s->sl[3][p] += e * A[2];
             s->sl[5][p] += e * s->epsrec[i];
+            if (s->sg) s->sg[i * nrc + b] += e * s->cfg.sigma_rec;
             tally_add(s, s->box[i], 0, e);
         }
     }
@@ -866,6 +889,7 @@ void orc_emit(orc_sim *s, long long step) {
                     }
                     p.clock = 0.0;
                     p.eps = s->eps[nu];
+                    p.sig = s->sigma[nu];
                     p.nu = nu;
                     p.fid = (1ull << 62) | idx;
                     tally_add(s, p.box, 0, p.N);
@@ -879,7 +903,7 @@ void orc_emit(orc_sim *s, long long step) {
        leave it in the first hop through its own neighbours.  Packet identities follow
        (particle, emission, cone) whether or not a particle emits. */
     if (s->cfg.rec_mode == ORC_REC_EMISSION_CONES) {
-        int nrb = s->nf - 1;                       /* the recombination frequency bin */
+        int nrb = s->rbin;                         /* the recombination frequency bin */
         for (long long i = 0; i < s->n; ++i) {
             double Nr = s->Nrec[i];
             if (!(Nr > 0.0)) continue;
@@ -898,6 +922,7 @@ void orc_emit(orc_sim *s, long long step) {
                     rotate_axis(R, s->axes_ec + 3 * e, p.d);
                     p.clock = 0.0;
                     p.eps = s->epsrec[i];
+                    p.sig = s->cfg.sigma_rec;
                     p.nu = nrb;
                     p.fid = (2ull << 62) | (uint64_t)((i * s->K + k) * nec + e);
                     tally_add(s, p.box, 0, p.N);
@@ -921,13 +946,14 @@ static void split_absorbed(double N, double tau, double *A, double *T) {
     }
 }
 
-/* Deliver w photons of a packet (direction d, clock, eps, frequency nu) from a sender
-   at integer position qs to gas neighbour j (Sec. 2.1): optical depth
-   tau = sigma_nu n_HI,j l with l the distance projected on the propagation direction,
+/* Deliver w photons of a packet (direction d, clock, eps, cross-section sig, frequency nu)
+   from a sender at integer position qs to gas neighbour j (Sec. 2.1): optical depth
+   tau = sig n_HI,j l with l the distance projected on the propagation direction (sig is the
+   bin's grey cross-section sigma_nu, or in a shared bin the packet's photon-weighted mean),
    absorbed N_in (1 - exp(-tau)), the rest arriving at j after l/c and merged into the
    reception cone of its direction. */
 static void deliver(orc_sim *s, const int64_t *qs, long long j, double w, const double d[3],
-                    double clock, double eps, int nu) {
+                    double clock, double eps, double sig, int nu) {
     int nrc = s->cfg.n_rc, S = s->S;
     int b = s->box[j];
     if (barrier_crosses(&s->bar[b], qs, s->q + 3 * j)) {   /* removed (Sec. 4): leaves the box */
@@ -939,7 +965,7 @@ static void deliver(orc_sim *s, const int64_t *qs, long long j, double w, const 
     double t = (double)(qj[0] - qs[0]) * d[0] + (double)(qj[1] - qs[1]) * d[1] +
                (double)(qj[2] - qs[2]) * d[2];
     double l = t * u;
-    double tau = (s->sigma[nu] * s->nHI[j]) * l;
+    double tau = (sig * s->nHI[j]) * l;
     double A, T;
     split_absorbed(w, tau, &A, &T);
     s->abs_[j * s->nf + nu] += A;
@@ -954,6 +980,8 @@ static void deliver(orc_sim *s, const int64_t *qs, long long j, double w, const 
     s->nx[3][p] += T * d[2];
     s->nx[4][p] += T * (clock + l / C_LIGHT);
     s->nx[5][p] += T * eps;
+    /* shared bin: the merged packet's cross-section is the photon-weighted mean */
+    if (s->nsg && nu == 0) s->nsg[j * nrc + bb] += T * sig;
 }
 
 /* M4 cubic spline of compact support h (the GADGET form), without its normalisation,
@@ -979,7 +1007,7 @@ static double kernel_w(double q) {
    its clock. */
 static void make_virtual(orc_sim *s, long long step, int hop, int box, const int64_t *qs,
                          int64_t h2, double N, const double d[3], double clock, double eps,
-                         int nu, uint64_t fid) {
+                         double sig, int nu, uint64_t fid) {
     s->st_virtual++;
     uint32_t key[2];
     philox_key(s->cfg.seed, PURPOSE_VIRTUAL, key);
@@ -1041,7 +1069,7 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
     double u = s->box_L[box] / (double)ORC_Q;
     double t = (double)del[0] * d[0] + (double)del[1] * d[1] + (double)del[2] * d[2];
     double l = t * u;
-    double tau = (s->sigma[nu] * nHIv) * l;
+    double tau = (sig * nHIv) * l;
     double A, T;
     split_absorbed(N, tau, &A, &T);
     if (swn > 0.0) {
@@ -1057,6 +1085,7 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
     v.d[0] = d[0]; v.d[1] = d[1]; v.d[2] = d[2];
     v.clock = clock + l / C_LIGHT;
     v.eps = eps;
+    v.sig = sig;
     v.nu = nu;
     v.fid = orc_mix64(fid);
     fl_push(&s->nxt, &v);
@@ -1068,7 +1097,7 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
    order; an empty cone creates a virtual particle. */
 static void send_packet(orc_sim *s, long long step, int hop, int box, const int64_t *qs,
                         const int32_t *nbr, int64_t h2, double N, const double d[3],
-                        double clock, double eps, int nu, uint64_t fid) {
+                        double clock, double eps, double sig, int nu, uint64_t fid) {
     int kn = s->cfg.n_ngb, members[MAXK], m = 0;
     for (int k = 0; k < kn; ++k) {
         const int64_t *qj = s->q + 3 * (long long)nbr[k];
@@ -1076,11 +1105,11 @@ static void send_packet(orc_sim *s, long long step, int hop, int box, const int6
         if (orc_in_cone(del, d, s->cfg.n_tc)) members[m++] = k;
     }
     if (m == 0) {
-        make_virtual(s, step, hop, box, qs, h2, N, d, clock, eps, nu, fid);
+        make_virtual(s, step, hop, box, qs, h2, N, d, clock, eps, sig, nu, fid);
         return;
     }
     double w = N / (double)m;
-    for (int a = 0; a < m; ++a) deliver(s, qs, nbr[members[a]], w, d, clock, eps, nu);
+    for (int a = 0; a < m; ++a) deliver(s, qs, nbr[members[a]], w, d, clock, eps, sig, nu);
 }
 
 /* Transport (Sec. 2.1): every packet whose clock has not reached the end of the step
@@ -1112,11 +1141,14 @@ int orc_transport(orc_sim *s, long long step) {
         }
         /* waiting packets stay where they are */
         for (int f = 0; f < 6; ++f) memset(s->nx[f], 0, sizeof(double) * (size_t)(n * S));
+        if (s->nsg) memset(s->nsg, 0, sizeof(double) * (size_t)(n * nrc));
         for (long long i = 0; i < n; ++i)
             for (int sl = 0; sl < S; ++sl) {
                 long long p = i * S + sl;
-                if (s->sl[0][p] > 0.0 && !slot_active(s, i, sl, NULL))
+                if (s->sl[0][p] > 0.0 && !slot_active(s, i, sl, NULL)) {
                     for (int f = 0; f < 6; ++f) s->nx[f][p] = s->sl[f][p];
+                    if (s->nsg && sl < nrc) s->nsg[i * nrc + sl] = s->sg[i * nrc + sl];
+                }
             }
         s->nxt.n = 0;
         /* gas particles send, in index order */
@@ -1129,21 +1161,26 @@ int orc_transport(orc_sim *s, long long step) {
                 double M[3] = {s->sl[1][p], s->sl[2][p], s->sl[3][p]}, d[3];
                 packet_dir(M, d);
                 double eps = s->sl[5][p] / N;
+                /* shared bin: the packet's mean cross-section; else its bin's */
+                double sig = (s->sg && sl < nrc) ? s->sg[i * nrc + sl] / N : s->sigma[sl / nrc];
                 send_packet(s, step, hop, s->box[i], s->q + 3 * i, s->nbr + i * kn, s->h2[i],
-                            N, d, clock, eps, sl / nrc, (uint64_t)(i * S + sl) + 1);
+                            N, d, clock, eps, sig, sl / nrc, (uint64_t)(i * S + sl) + 1);
             }
         /* then sources (first hop) and virtual particles, in creation order */
         for (long long f = 0; f < s->cur.n; ++f) {
             freep_t *p = &s->cur.p[f];
             if (!(p->N > 0.0)) continue;
             send_packet(s, step, hop, p->box, p->q, p->nbr, p->h2, p->N, p->d, p->clock,
-                        p->eps, p->nu, p->fid);
+                        p->eps, p->sig, p->nu, p->fid);
         }
         for (int f = 0; f < 6; ++f) {
             double *t = s->sl[f];
             s->sl[f] = s->nx[f];
             s->nx[f] = t;
         }
+        double *tg = s->sg;
+        s->sg = s->nsg;
+        s->nsg = tg;
         freelist_t t = s->cur;
         s->cur = s->nxt;
         s->nxt = t;
@@ -1207,6 +1244,14 @@ void orc_get_slots(const orc_sim *s, double *f) {
 void orc_set_slots(orc_sim *s, const double *f) {
     long long m = s->n * s->S;
     for (int k = 0; k < 6; ++k) memcpy(s->sl[k], f + k * m, sizeof(double) * (size_t)m);
+}
+
+void orc_get_shared_sigma(const orc_sim *s, double *G) {
+    if (s->sg) memcpy(G, s->sg, sizeof(double) * (size_t)(s->n * s->cfg.n_rc));
+}
+
+void orc_set_shared_sigma(orc_sim *s, const double *G) {
+    if (s->sg) memcpy(s->sg, G, sizeof(double) * (size_t)(s->n * s->cfg.n_rc));
 }
 
 void orc_get_state(const orc_sim *s, double *x_HI, double *T, double *N_rec,

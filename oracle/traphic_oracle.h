@@ -45,7 +45,11 @@ typedef struct {
     int cool_flags;       /* ORC_COOL_* */
     double T_floor;       /* K */
     double eps_rr_fixed;  /* erg; < 0 selects kT of the emitting gas (Sec. 2.2) */
-    double sigma_rec;     /* grey cross-section of the recombination bin, cm^2 (Sec. 2.2) */
+    double sigma_rec;     /* grey cross-section of the recombination photons, cm^2 (Sec. 2.2) */
+    int rec_shared_bin;   /* 1: recombination photons travel in source bin 0 (no bin of their
+                             own); each packet of that bin carries its photon-weighted mean
+                             cross-section, averaged on every merge (Sec. 2.2, last paragraph);
+                             needs n_freq_src >= 1 */
 } orc_config;
 
 typedef struct orc_sim orc_sim;
@@ -110,6 +114,10 @@ void orc_cone_masks(const orc_sim *s, uint32_t *mask /* [n*S] */);
 /* state access; slot fields are N, Mx, My, Mz, C (= N * clock), E (= N * eps) */
 void orc_get_slots(const orc_sim *s, double *f /* [6*n*S] */);
 void orc_set_slots(orc_sim *s, const double *f);
+/* with rec_shared_bin: the cross-section field G = sum of N sigma of the slots of bin 0,
+   [n*n_rc], slot (i, b) at i*n_rc + b; no-ops otherwise */
+void orc_get_shared_sigma(const orc_sim *s, double *G);
+void orc_set_shared_sigma(orc_sim *s, const double *G);
 void orc_get_state(const orc_sim *s, double *x_HI, double *T, double *N_rec,
                    double *eps_rec);
 void orc_set_state(orc_sim *s, const double *x_HI, const double *T, const double *N_rec,

@@ -557,3 +557,113 @@ def test_barrier_shadow_is_ionised_and_heated_by_recombination_radiation():
     xs, xo, Ts, To = res["RT"]
     assert xs < 1e-2 and xo < 1e-3
     assert 5e3 < Ts < 0.7 * To
+
+
+# --- shared frequency bin (Sec. 2.2, last paragraph) -----------------------------------------
+def _shared_chain(**kw):
+    wl = _chain(**kw)
+    wl["params"]["rec_shared_bin"] = 1
+    return wl
+
+
+def test_shared_bin_mixed_packet_follows_beer_lambert_with_its_mean_cross_section():
+    """A packet of the shared bin holding photons of two cross-sections is attenuated with the
+    photon-weighted mean N_abs = N (1 - exp(-sigma_mean n_HI l)) on every hop, and keeps that
+    mean as it moves on: along the chain the photon count falls as exp(-sigma_mean sum n l).
+    The bin's own cross-section, or a mean lost after the first hop, fails."""
+    wl = _shared_chain()
+    s = oracle.Sim(wl)
+    assert s.nf == 1 and s.S == s.params["n_rc"]       # no bin of their own
+    s.build_neighbours()
+    s.rotate(0)
+    s.emit(0)
+    N0, sig0 = 1e50, wl["sigma"][0]
+    Na, Nb, sb = 0.25 * N0, 0.75 * N0, 2.0 * sig0
+    _put_packet(s, 1, N0, [1.0, 0.0, 0.0])
+    G = np.zeros((s.n, s.params["n_rc"]))
+    b = int(np.nonzero(s.slots()[0][1])[0][0])
+    G[1, b] = Na * sig0 + Nb * sb
+    s.set_shared_sigma(G)
+    assert s.transport(0) == 0
+    a = s.deposits()[0][:, 0]
+    sig_mean = (Na * sig0 + Nb * sb) / N0                 # 1.75 sigma_0
+    q = s.quantised()
+    u = wl["box_L"][0] / (1 << 20)
+    l = np.diff(q[1:, 0]) * u
+    tau = sig_mean * wl["x_HI"][2:] * wl["n_H"][2:] * l
+    N = N0 * np.exp(-np.concatenate([[0.0], np.cumsum(tau)]))
+    assert np.allclose(a[2:-2], N[:-3] - N[1:-2], rtol=1e-12, atol=0)
+    tau0 = sig0 * wl["x_HI"][2:] * wl["n_H"][2:] * l       # with the bin's own sigma: far off
+    N_wrong = N0 * np.exp(-np.concatenate([[0.0], np.cumsum(tau0)]))
+    assert not np.allclose(a[2:-2], N_wrong[:-3] - N_wrong[1:-2], rtol=1e-3)
+    e, ab, esc, fl = s.budget()[0]
+    assert abs(ab + esc - N0) <= 1e-12 * N0
+
+
+def test_shared_bin_recombination_photons_merge_into_bin_0_with_their_cross_section():
+    """With a shared bin the recombination photons of a particle go into its reception cones of
+    source bin 0: per particle the bin gains N_rec photons and N_rec sigma_rec of cross-section
+    sum, on top of the packet already there (photon-weighted merge)."""
+    wl = W.cfg2(n_side=8, rec_shared_bin=1, ionised=False)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    nrc = s.params["n_rc"]
+    assert s.nf == wl["params"]["n_freq_src"] and s.S == s.nf * nrc
+    n = s.n
+    nrec = np.zeros(n)
+    nrec[[5, 77, 300]] = [1e55, 3e54, 7e53]
+    s.set_state(N_rec=nrec, eps_rec=np.full(n, 2 * EV))
+    s.rotate(3)
+    _put_packet(s, 77, 2e54, [0.0, 1.0, 0.0])          # a stellar packet already in bin 0
+    b77 = int(np.nonzero(s.slots()[0][77])[0][0])
+    assert b77 < nrc
+    G = np.zeros((n, nrc))
+    G[77, b77] = 2e54 * wl["sigma"][0]
+    s.set_shared_sigma(G)
+    s.emit(3)
+    f, G = s.slots(), s.shared_sigma()
+    sr, s0 = wl["params"]["sigma_rec"], wl["sigma"][0]
+    for i, extra in ((5, 0.0), (77, 2e54), (300, 0.0)):
+        assert np.allclose(f[0][i, :nrc].sum(), nrec[i] + extra, rtol=1e-14)
+        assert np.all(f[0][i, nrc:] == 0.0)             # the other source bins stay empty
+        assert np.allclose(G[i].sum(), nrec[i] * sr + extra * s0, rtol=1e-14)
+    # the cone holding the stellar packet: the photon-weighted mean of the two cross-sections
+    e = nrec[77] / nrc
+    assert np.isclose(G[77, b77] / f[0][77, b77], (2e54 * s0 + e * sr) / (2e54 + e), rtol=1e-14)
+
+
+def test_shared_bin_conserves_photons_and_keeps_means_between_the_inputs():
+    """Clock-limited steps (c dt < box side) leave packets held at the step end: photons are
+    conserved to 1e-12 and every held packet of the shared bin has a mean cross-section between
+    the bin's own and the recombination photons', some strictly between (merged)."""
+    wl = W.cfg2(n_side=12, rec_shared_bin=1, dt=0.01 * MYR, dt_em=0.01 * MYR)
+    s = _run(wl, 6)
+    e, a, esc, fl = s.budget()[0]
+    assert fl > 0.01 * e
+    assert abs(e - a - esc - fl) <= 1e-12 * e
+    nrc = s.params["n_rc"]
+    N, G = s.slots()[0][:, :nrc], s.shared_sigma()
+    m = N > 0
+    sig = G[m] / N[m]
+    lo, hi = sorted([wl["sigma"][0], wl["params"]["sigma_rec"]])
+    assert np.all(sig >= lo * (1 - 1e-13)) and np.all(sig <= hi * (1 + 1e-13))
+    assert np.any((sig > lo * 1.01) & (sig < hi * 0.99))
+    assert np.all(G[~m] == 0.0)
+
+
+def test_shared_and_separate_bins_agree_when_the_spectra_match():
+    """Sec. 2.2: one bin for stellar and recombination photons is appropriate when the two
+    spectra in it are alike.  In the Stromgren workload (13.6 eV source, sigma equal to the
+    recombination photons') the shared and the separate bin give radial medians of x_HI within
+    3 % of each other after 20 steps, while case A differs by more than 10 % somewhere."""
+    res = {}
+    for name, kw in (("sep", {}), ("shared", dict(rec_shared_bin=1)),
+                     ("A", dict(rec_mode=W.REC_CASE_A))):
+        res[name] = _run(W.cfg1(**kw), 20).state()["x_HI"]
+    wl = W.cfg1()
+    pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
+    r = np.linalg.norm(pos - 0.5 * wl["box_L"][0], axis=1) / KPC
+    shells = [(0, 2), (2, 3), (3, 4), (4, 5), (5, 6)]
+    med = {m: np.array([np.median(x[(r >= a) & (r < b)]) for a, b in shells]) for m, x in res.items()}
+    assert np.all(np.abs(med["shared"] / med["sep"] - 1) < 0.03)
+    assert np.max(np.abs(med["A"] / med["sep"] - 1)) > 0.10
