@@ -67,7 +67,8 @@ typedef struct {
     int n_ec;             /* emission cones per source (8 or 32) */
     int n_tc;             /* transmission cones: cone solid angle 4 pi / n_tc, n_tc >= 2 */
     int n_rc;             /* reception cones per particle (8 or 32) */
-    int n_freq_src;       /* source frequency bins (>= 0); one recombination bin is added */
+    int n_freq_src;       /* source frequency bins (>= 0); one recombination bin is added
+                             unless rec_shared_bin is set */
     double dt;            /* RT step, s */
     double dt_em;         /* source emission step, s (dt / dt_em rounded = emissions per step) */
     int rec_mode;         /* rt_rec_mode */
@@ -79,10 +80,16 @@ typedef struct {
     int cool_flags;       /* RT_COOL_* */
     double T_floor;       /* K */
     double eps_rr_fixed;  /* excess energy of recombination photons, erg; < 0: kT of emitter */
-    double sigma_rec;     /* grey cross-section of the recombination bin, cm^2 */
+    double sigma_rec;     /* grey cross-section of the recombination photons, cm^2 */
     long long free_cap;   /* capacity of free packets per hop (0: library default) */
     int cell_occupancy;   /* particles per cell of the kNN grids; 0: chosen by timing the
                              neighbour search over 5, 7, 9, 12 and 16 in rt_build_neighbours */
+    int rec_shared_bin;   /* 1: one frequency bin for stellar and recombination photons (Sec.
+                             2.2, last paragraph): recombination photons travel in source bin 0
+                             and there is no recombination bin (n_freq_src bins in all, so
+                             n_freq_src >= 1); every packet of bin 0 carries the photon-weighted
+                             mean cross-section of its photons, averaged again on every merge,
+                             and is attenuated with it.  0: a recombination bin of its own. */
 } rt_config;
 
 /* rt_create -- validate cfg, allocate every device buffer for n_boxes boxes whose particle
@@ -228,8 +235,18 @@ rt_status rt_get_cone_masks_noalloc(rt_ctx *ctx, unsigned *mask, int where, void
 /* held packets: 6 fields [6 * n * S] (N, Mx, My, Mz, C = N*clock, E = N*eps), physical units */
 rt_status rt_get_slots(rt_ctx *ctx, double *f, int where, void *stream);
 rt_status rt_set_slots(rt_ctx *ctx, const double *f, int where, void *stream);
+/* rt_get_shared_sigma / rt_set_shared_sigma -- with rec_shared_bin (Sec. 2.2, last paragraph:
+   one bin for stellar and recombination photons, cross-sections averaged on merging): the
+   cross-section sum G = sum N sigma (cm^2 x photons) of each held packet of bin 0, [n * n_rc],
+   packet (i, b) at i * n_rc + b; a packet's mean cross-section is G / N.  Get writes 0 for
+   empty slots; set writes the field as given (call it after rt_set_slots, which decides which
+   slots are held).  Synchronous on `stream`.  Errors: RT_ERR_INVALID (also without a shared
+   bin), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_get_shared_sigma(rt_ctx *ctx, double *G, int where, void *stream);
+rt_status rt_set_shared_sigma(rt_ctx *ctx, const double *G, int where, void *stream);
 /* absorptions of the current step: photons [n * nf], energy [n * nf] (erg), photons passing
-   each particle [n * nf] (the intensity diagnostic of Sec. 3); nf = n_freq_src + 1 */
+   each particle [n * nf] (the intensity diagnostic of Sec. 3); nf = n_freq_src + 1, or
+   n_freq_src with rec_shared_bin */
 rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass, int where,
                           void *stream);
 /* statistics of the last rt_transport/rt_chemistry, out[RT_NSTATS] (host): hops, virtual

@@ -202,7 +202,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     if (cfg->n_ngb < 1 || cfg->n_ngb > RT_MAXK || cfg->n_tc < 2 || cfg->n_freq_src < 0 ||
         (cfg->n_rc != 8 && cfg->n_rc != 32) || (cfg->n_ec != 8 && cfg->n_ec != 32) ||
         !(cfg->dt > 0.0) || !(cfg->dt_em > 0.0) || cfg->hop_cap < 1 || cfg->sub_cap < 1 ||
-        cfg->rec_mode < 0 || cfg->rec_mode > 3)
+        cfg->rec_mode < 0 || cfg->rec_mode > 3 || cfg->rec_shared_bin < 0 ||
+        cfg->rec_shared_bin > 1 || (cfg->rec_shared_bin && cfg->n_freq_src < 1))
         return RT_ERR_INVALID;
     if (box_off[0] != 0) return RT_ERR_INVALID;
     for (int b = 0; b < n_boxes; ++b) {
@@ -229,7 +230,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     P.nb = n_boxes;
     P.ns = n_src;
     P.nfs = cfg->n_freq_src;
-    P.nf = cfg->n_freq_src + 1;
+    P.shared = cfg->rec_shared_bin;
+    P.nf = cfg->n_freq_src + (P.shared ? 0 : 1);
+    P.rbin = P.shared ? 0 : P.nf - 1;
     P.nrc = cfg->n_rc;
     P.nec = cfg->n_ec;
     P.ntc = cfg->n_tc;
@@ -244,6 +247,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     P.T_floor = cfg->T_floor;
     P.eps_rr_fixed = cfg->eps_rr_fixed;
     P.eunit = P.fp32 ? 1.602176634e-12 : 1.0;
+    P.sunit = P.fp32 ? 1e-18 : 1.0;
     P.rec_mode = cfg->rec_mode;
     P.evolve_T = cfg->evolve_T;
     P.sub_cap = cfg->sub_cap;
@@ -317,9 +321,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.sbox, int, n_src + 1);
     A(P.sqx, int, n_src + 1); A(P.sqy, int, n_src + 1); A(P.sqz, int, n_src + 1);
     A(P.ndot, double, (long long)n_src * P.nfs + 1);
-    A(P.sigma, double, P.nf);
-    A(P.eps, double, P.nf);
-    A(P.sigmaf, float, P.nf);
+    A(P.sigma, double, P.nfs + 1);
+    A(P.eps, double, P.nfs + 1);
+    A(P.sigmaf, float, P.nfs + 1);
     A(P.box_uf, float, n_boxes);
     A(P.escf, float, n_boxes);
     A(P.nbr, int, n * P.kn);
@@ -344,6 +348,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.Rs, double, 9 * ((long long)n_src * P.K + 1));
     for (int b = 0; b < 2; ++b) {
         for (int f = 0; f < 6; ++f) P.sl[b][f] = dalloc(c, R * nslot, &ok);
+        if (P.shared) P.slG[b] = dalloc(c, R * n * P.nrc, &ok);
         A(P.occ[b], unsigned, nkey);
         A(P.act[b], unsigned, nkey);
     }
@@ -366,10 +371,12 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         F.N = dalloc(c, R * fc, &ok); F.dx = dalloc(c, R * fc, &ok);
         F.dy = dalloc(c, R * fc, &ok); F.dz = dalloc(c, R * fc, &ok);
         F.clock = dalloc(c, R * fc, &ok); F.eps = dalloc(c, R * fc, &ok);
+        if (P.shared) F.sig = dalloc(c, R * fc, &ok);
     }
     A(P.st_key, int, P.ST_cap);
     A(P.st_bin, int, P.ST_cap);
     for (int f = 0; f < 9; ++f) P.st_v[f] = dalloc(c, R * P.ST_cap, &ok);
+    if (P.shared) P.st_v[9] = dalloc(c, R * P.ST_cap, &ok);
     long long segn = std::max<long long>(nkey, ncell) + 1;
     A(P.seg_cnt, int, segn);
     A(P.seg_off, int, segn);
@@ -583,7 +590,7 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
         cudaFree(t);
         if (P.nfs) cudaMemcpy(P.ndot, ndh.data(), sizeof(double) * P.ns * P.nfs, cudaMemcpyHostToDevice);
     }
-    std::vector<double> sg(P.nf), ep(P.nf);
+    std::vector<double> sg(P.nfs + 1), ep(P.nfs + 1);
     if (P.nfs > 0) {
         if (where == RT_HOST) {
             memcpy(sg.data(), sigma, sizeof(double) * P.nfs);
@@ -595,10 +602,11 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
     }
     sg[P.nfs] = c->cfg.sigma_rec;
     ep[P.nfs] = 0.0;
-    cudaMemcpy(P.sigma, sg.data(), sizeof(double) * P.nf, cudaMemcpyHostToDevice);
+    // entry nfs: the recombination photons' (their bin's, unless the bin is shared)
+    cudaMemcpy(P.sigma, sg.data(), sizeof(double) * (P.nfs + 1), cudaMemcpyHostToDevice);
     std::vector<float> sgf(sg.begin(), sg.end());
-    cudaMemcpy(P.sigmaf, sgf.data(), sizeof(float) * P.nf, cudaMemcpyHostToDevice);
-    cudaMemcpy(P.eps, ep.data(), sizeof(double) * P.nf, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.sigmaf, sgf.data(), sizeof(float) * (P.nfs + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(P.eps, ep.data(), sizeof(double) * (P.nfs + 1), cudaMemcpyHostToDevice);
     // source photons of one step per box, summed packet by packet as they are emitted
     rt_ctx &xe = *c;
     std::fill(xe.src_emit_h.begin(), xe.src_emit_h.end(), 0.0);
@@ -973,6 +981,52 @@ extern "C" rt_status rt_set_slots(rt_ctx *c, const double *f, int where, void *s
     s = rt_cuda_check(c, cudaStreamSynchronize(st), "set slots");
     cudaFree(t);
     return s;
+}
+
+// the cross-section sums of the shared frequency bin (bin 0), [n * nrc], in cm^2 x photons
+template <typename Real>
+__global__ void k_shared_sigma_io(DevPtrs P, int cur, double *f, int to_dev) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.n * P.nrc) return;
+    long long i = t / P.nrc;
+    int b = (int)(t % P.nrc);
+    double nm = P.norm[P.pbox[i]];
+    Real *G = (Real *)P.slG[cur];
+    if (to_dev) {
+        G[t] = (Real)(f[t] / nm / P.sunit);
+    } else {
+        bool occ = (P.occ[cur][i * P.nf] >> b) & 1u;
+        f[t] = occ ? (double)G[t] * nm * P.sunit : 0.0;
+    }
+}
+
+static rt_status shared_sigma_io(rt_ctx *c, double *f, int to_dev, int where, void *stream) {
+    if (!c || !f || (where != RT_HOST && where != RT_DEVICE)) return RT_ERR_INVALID;
+    if (!c->d.shared) return rt_fail(c, RT_ERR_INVALID, "no shared frequency bin in this context");
+    cudaStream_t st = (cudaStream_t)stream;
+    long long m = c->d.n * c->d.nrc;
+    double *t = dtmp<double>(m);
+    if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
+    rt_status s = RT_OK;
+    if (to_dev && (s = copy_in(c, t, f, sizeof(double) * m, where, st))) {
+        cudaFree(t);
+        return s;
+    }
+    unsigned nb = (unsigned)((m + 255) / 256);
+    if (c->d.fp32) k_shared_sigma_io<float><<<nb, 256, 0, st>>>(c->d, c->cur, t, to_dev);
+    else k_shared_sigma_io<double><<<nb, 256, 0, st>>>(c->d, c->cur, t, to_dev);
+    if (!to_dev) s = copy_out(c, f, t, sizeof(double) * m, where, st);
+    rt_status s2 = rt_cuda_check(c, cudaStreamSynchronize(st), "shared sigma");
+    cudaFree(t);
+    return s ? s : s2;
+}
+
+extern "C" rt_status rt_get_shared_sigma(rt_ctx *c, double *G, int where, void *stream) {
+    return shared_sigma_io(c, G, 0, where, stream);
+}
+
+extern "C" rt_status rt_set_shared_sigma(rt_ctx *c, const double *G, int where, void *stream) {
+    return shared_sigma_io(c, const_cast<double *>(G), 1, where, stream);
 }
 
 __global__ void k_deposits(DevPtrs P, double *a, double *e, double *ps) {

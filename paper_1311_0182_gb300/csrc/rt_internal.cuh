@@ -70,6 +70,8 @@ struct FreeBuf {  // packets not held by gas particles: source packets and virtu
     long long *h2;
     unsigned long long *fid;
     void *N, *dx, *dy, *dz, *clock, *eps;  // Real [cap]
+    void *sig;                // Real [cap]: cross-section of the photons in units of sunit
+                              // (shared frequency bin only, else null)
 };
 
 struct Grid {                 // per-box uniform cell lists (device arrays)
@@ -129,6 +131,12 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     double dt, dt_em, sigma_rec, T_floor, eps_rr_fixed;
     double eunit;             // energy unit of the slot field E: 1 erg (FP64), 1 eV (FP32)
     int rec_mode, evolve_T, sub_cap, cool_flags;
+    // shared frequency bin (Sec. 2.2, last paragraph): recombination photons in source bin
+    // rbin = 0 (else rbin = nf - 1, a bin of their own); each slot of bin 0 carries
+    // G = sum N sigma (slG, Real [n * nrc], slot (i, b) at i * nrc + b) in units of
+    // sunit * the slot's photon unit: 1 cm^2 (FP64), 1e-18 cm^2 (FP32)
+    int shared, rbin;
+    double sunit;
     unsigned long long seed;
     long long F_cap, ST_cap;
     // boxes
@@ -169,8 +177,10 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     float *Rf;
     // slots (double-buffered): 6 Real fields + occupancy/activity words per (i, nu)
     void *sl[2][6];
+    void *slG[2];             // shared bin: cross-section sums of bin 0 (null otherwise)
     unsigned *occ[2], *act[2];
-    // phase-A records, one per slot, 8 Real each (w, dx, dy, dz, clock, eps, unused, unused):
+    // phase-A records, one per slot, 8 Real each (w, dx, dy, dz, clock, eps, sigma, unused;
+    // sigma in units of sunit, written for bin 0 with a shared bin only):
     // the receiver side reads a record as one aligned 32-byte (FP32) or 64-byte (FP64) piece;
     // and transposed cone bitmaps
     void *rec;
@@ -186,7 +196,8 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     int *st_key;              // receiver key j*nf+nu
     long long *st_ord;        // ordering key f*kn + k
     int *st_bin;
-    void *st_v[9];            // T, T dx, T dy, T dz, T clock, T eps, A, A eps, w (Real)
+    void *st_v[10];           // T, T dx, T dy, T dz, T clock, T eps, A, A eps, w, T sigma (Real;
+                              // the last with a shared bin only)
     int *seg_cnt, *seg_off, *seg_fill, *seg_idx;
     // accumulators
     double *abs, *absE, *pass;                // [n * nf]

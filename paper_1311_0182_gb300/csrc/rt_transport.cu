@@ -152,32 +152,44 @@ template <typename Real> struct Slots {
     }
 };
 
-// phase-A record of a slot: (w, d, clock, eps) in one aligned piece of 8 Real
+// phase-A record of a slot: (w, d, clock, eps) in one aligned piece of 8 Real, and with `sg`
+// (a slot of a shared frequency bin) the packet's mean cross-section in the seventh
 __device__ __forceinline__ void rec_store(void *rec, long long s, float w, float d0, float d1,
-                                          float d2, float c, float e) {
+                                          float d2, float c, float e, bool sg, float sig) {
     float4 *p = (float4 *)rec + 2 * s;
     p[0] = make_float4(w, d0, d1, d2);
-    *(float2 *)(p + 1) = make_float2(c, e);
+    if (sg) p[1] = make_float4(c, e, sig, 0.0f);
+    else *(float2 *)(p + 1) = make_float2(c, e);
 }
 __device__ __forceinline__ void rec_store(void *rec, long long s, double w, double d0, double d1,
-                                          double d2, double c, double e) {
+                                          double d2, double c, double e, bool sg, double sig) {
     double2 *p = (double2 *)rec + 4 * s;
     p[0] = make_double2(w, d0);
     p[1] = make_double2(d1, d2);
     p[2] = make_double2(c, e);
+    if (sg) p[3] = make_double2(sig, 0.0);
 }
 __device__ __forceinline__ void rec_load(const void *rec, long long s, float &w, float &d0,
-                                         float &d1, float &d2, float &c, float &e) {
+                                         float &d1, float &d2, float &c, float &e, bool sg,
+                                         float &sig) {
     const float4 *p = (const float4 *)rec + 2 * s;
     float4 a = p[0];
-    float2 b = *(const float2 *)(p + 1);
-    w = a.x; d0 = a.y; d1 = a.z; d2 = a.w; c = b.x; e = b.y;
+    w = a.x; d0 = a.y; d1 = a.z; d2 = a.w;
+    if (sg) {
+        float4 b = p[1];
+        c = b.x; e = b.y; sig = b.z;
+    } else {
+        float2 b = *(const float2 *)(p + 1);
+        c = b.x; e = b.y;
+    }
 }
 __device__ __forceinline__ void rec_load(const void *rec, long long s, double &w, double &d0,
-                                         double &d1, double &d2, double &c, double &e) {
+                                         double &d1, double &d2, double &c, double &e, bool sg,
+                                         double &sig) {
     const double2 *p = (const double2 *)rec + 4 * s;
     double2 a = p[0], b = p[1], d = p[2];
     w = a.x; d0 = a.y; d1 = b.x; d2 = b.y; c = d.x; e = d.y;
+    if (sg) sig = p[3].x;
 }
 
 // unit direction of a packet from its summed momentum M (the luminosity-weighted mean
@@ -209,6 +221,14 @@ template <> __device__ __forceinline__ float box_unit<float>(const DevPtrs &P, i
 template <typename Real> __device__ __forceinline__ Real sigma_of(const DevPtrs &P, int nu);
 template <> __device__ __forceinline__ double sigma_of<double>(const DevPtrs &P, int nu) { return P.sigma[nu]; }
 template <> __device__ __forceinline__ float sigma_of<float>(const DevPtrs &P, int nu) { return P.sigmaf[nu]; }
+// the cross-section of a bin in the unit of the shared-bin fields (sunit)
+template <typename Real> __device__ __forceinline__ Real sigma_units(const DevPtrs &P, int nu);
+template <> __device__ __forceinline__ double sigma_units<double>(const DevPtrs &P, int nu) {
+    return P.sigma[nu] / P.sunit;
+}
+template <> __device__ __forceinline__ float sigma_units<float>(const DevPtrs &P, int nu) {
+    return (float)(P.sigma[nu] / P.sunit);
+}
 template <typename Real> __device__ __forceinline__ Real to_real(long long v);
 template <> __device__ __forceinline__ double to_real<double>(long long v) { return (double)v; }
 template <> __device__ __forceinline__ float to_real<float>(long long v) { return i64_to_f(v); }
@@ -258,13 +278,16 @@ __global__ void k_rebin(DevPtrs P) {
     int nu = (int)((unsigned)key % (unsigned)P.nf);
     Slots<Real> S(P, cur);
     long long s0 = i * P.S + (long long)nu * NRC;
-    Real nN[NRC], nX[NRC], nY[NRC], nZ[NRC], nE[NRC];
-    Real oN[NRC], oX[NRC], oY[NRC], oZ[NRC], oE[NRC];
+    Real nN[NRC], nX[NRC], nY[NRC], nZ[NRC], nE[NRC], nG[NRC];
+    Real oN[NRC], oX[NRC], oY[NRC], oZ[NRC], oE[NRC], oG[NRC];
+    // a shared frequency bin carries the cross-section sums of bin 0 along
+    Real *SG = (P.shared && nu == 0) ? (Real *)P.slG[cur] + i * NRC : nullptr;
     for (int b = 0; b < NRC; ++b) {
-        nN[b] = nX[b] = nY[b] = nZ[b] = nE[b] = Real(0);
+        nN[b] = nX[b] = nY[b] = nZ[b] = nE[b] = nG[b] = Real(0);
         if ((o >> b) & 1) {
             oN[b] = S.N[s0 + b]; oX[b] = S.X[s0 + b]; oY[b] = S.Y[s0 + b];
             oZ[b] = S.Z[s0 + b]; oE[b] = S.E[s0 + b];
+            oG[b] = SG ? SG[b] : Real(0);
         }
     }
     const double *Rd = P.R + i * 9;
@@ -275,6 +298,7 @@ __global__ void k_rebin(DevPtrs P) {
         packet_dir(oX[b], oY[b], oZ[b], d0, d1, d2);
         int nb = bin_fast<Real>(Rf, Rd, P.ax_rc, NRC, d0, d1, d2);
         nN[nb] += oN[b]; nX[nb] += oX[b]; nY[nb] += oY[b]; nZ[nb] += oZ[b]; nE[nb] += oE[b];
+        nG[nb] += oG[b];
     }
     unsigned no = 0;
     for (int b = 0; b < NRC; ++b) {
@@ -282,6 +306,7 @@ __global__ void k_rebin(DevPtrs P) {
             no |= 1u << b;
             S.N[s0 + b] = nN[b]; S.X[s0 + b] = nX[b]; S.Y[s0 + b] = nY[b];
             S.Z[s0 + b] = nZ[b]; S.C[s0 + b] = Real(0); S.E[s0 + b] = nE[b];
+            if (SG) SG[b] = nG[b];
         }
     }
     P.occ[cur][key] = no;
@@ -314,11 +339,14 @@ __global__ void k_emit_rec(DevPtrs P) {
     double e_phys = Nr / (double)NRC;
     Real e = (Real)(e_phys / nm);
     Real epsr = (Real)(P.epsrec[i] / P.eunit);
-    int nu = P.nf - 1;
+    int nu = P.rbin;       // the recombination bin, or source bin 0 when the bin is shared
     long long key = i * P.nf + nu;
     unsigned o = P.occ[cur][key], a = P.act[cur][key];
     Slots<Real> S(P, cur);
     long long s0 = i * P.S + (long long)nu * NRC;
+    // shared bin: each cone gains e sigma_rec of cross-section sum
+    Real *SG = P.shared ? (Real *)P.slG[cur] + i * NRC : nullptr;
+    Real eg = e * (Real)(P.sigma_rec / P.sunit);
     const double *R = P.R + i * 9;
     for (int bb = 0; bb < NRC; ++bb) {
         double A[3];
@@ -327,9 +355,11 @@ __global__ void k_emit_rec(DevPtrs P) {
         if ((o >> bb) & 1) {
             S.N[s] += e; S.X[s] += e * (Real)A[0]; S.Y[s] += e * (Real)A[1];
             S.Z[s] += e * (Real)A[2]; S.E[s] += e * epsr;
+            if (SG) SG[bb] += eg;
         } else {
             S.N[s] = e; S.X[s] = e * (Real)A[0]; S.Y[s] = e * (Real)A[1];
             S.Z[s] = e * (Real)A[2]; S.C[s] = Real(0); S.E[s] = e * epsr;
+            if (SG) SG[bb] = eg;
         }
         if (e > Real(0)) { o |= 1u << bb; a |= 1u << bb; }
     }
@@ -375,6 +405,7 @@ __global__ void k_emit_src(DevPtrs P) {
     ((Real *)F.dz)[p] = (Real)d[2];
     ((Real *)F.clock)[p] = Real(0);
     ((Real *)F.eps)[p] = (Real)(P.eps[nu] / P.eunit);
+    if (P.shared) ((Real *)F.sig)[p] = sigma_units<Real>(P, nu);
     F.nu[p] = nu;
     F.fid[p] = (1ull << 62) | (unsigned long long)p;
 }
@@ -411,7 +442,8 @@ __global__ void k_emit_rec_cones(DevPtrs P, long long base) {
     ((Real *)F.dz)[f] = (Real)d[2];
     ((Real *)F.clock)[f] = Real(0);
     ((Real *)F.eps)[f] = (Real)(P.epsrec[i] / P.eunit);
-    F.nu[f] = P.nf - 1;
+    if (P.shared) ((Real *)F.sig)[f] = (Real)(P.sigma_rec / P.sunit);
+    F.nu[f] = P.rbin;
     F.fid[f] = (2ull << 62) | (unsigned long long)p;
 }
 
@@ -425,7 +457,8 @@ __global__ void k_emit_rec_cones(DevPtrs P, long long base) {
 // bitmap word; empty cones become virtual-particle requests.
 // cur: the slot buffer holding the hop's packets.  Receivers of a bitmap word are flagged in
 // `touched` (cleared again by the work-list kernel).
-template <typename Real, int NRC>
+// SH: the shared frequency bin (a separate instance keeps its code out of the common case)
+template <typename Real, int NRC, bool SH>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int cur) {
     int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -479,11 +512,14 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
             int ob = has ? __fns(ow, 0, t - oex + 1) : 0;
             long long s = i * P.S + (long long)onu * NRC + ob;
             Real N = Real(0), d0 = Real(1), d1 = Real(0), d2 = Real(0), C = Real(0), E = Real(0);
+            Real sgr = Real(0);
+            bool sgs = SH && onu == 0;   // a slot of the shared bin: its mean cross-section
             if (has) {
                 N = S.N[s];
                 packet_dir(S.X[s], S.Y[s], S.Z[s], d0, d1, d2);
                 C = S.C[s];
                 E = S.E[s];
+                if (sgs) sgr = ((Real *)P.slG[cur])[i * NRC + ob] / N;
             }
             int nb_chunk = min(32, total - cb);
             int my_cm = 0;
@@ -496,7 +532,8 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
                 if (lane == u) { my_mask = m; my_cm = __popc(m); }
             }
             ncon += (lane < nb_chunk) ? my_cm : 0;
-            if (has && my_cm > 0) rec_store(P.rec, s, N / (Real)my_cm, d0, d1, d2, C / N, E / N);
+            if (has && my_cm > 0)
+                rec_store(P.rec, s, N / (Real)my_cm, d0, d1, d2, C / N, E / N, sgs, sgr);
             // empty cones of this chunk, folded into the per-frequency words
             bool empty = has && my_cm == 0;
             unsigned emb = __ballot_sync(FULLMASK, empty);
@@ -571,7 +608,7 @@ __global__ void __launch_bounds__(256) k_freeA(DevPtrs P, int fcur, const int *l
 
 // Free packets with cone members: stage one contribution per member, in (packet, neighbour)
 // order at the positions given by the scan of the member counts.
-template <typename Real, int NRC, bool BAR>
+template <typename Real, int NRC, bool BAR, bool SH>
 __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *lens,
                                                const unsigned *fmask, const int *stoff) {
     int lane = threadIdx.x & 31;
@@ -594,6 +631,9 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         Real d0 = ((Real *)F.dx)[f], d1 = ((Real *)F.dy)[f], d2 = ((Real *)F.dz)[f];
         Real clk = ((Real *)F.clock)[f], eps = ((Real *)F.eps)[f];
         int nu = F.nu[f];
+        // the packet's cross-section: its own mean in a shared bin, else its bin's
+        bool sgs = SH && nu == 0;
+        Real sg = sgs ? ((Real *)F.sig)[f] : Real(0);
         long long j = F.nbr[f * P.kn + lane];
         int b = P.pbox[j];
         long long key = j * P.nf + nu;
@@ -611,7 +651,8 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         Real t = (Real)(P.qx[j] - F.qx[f]) * d0 + (Real)(P.qy[j] - F.qy[f]) * d1 +
                  (Real)(P.qz[j] - F.qz[f]) * d2;
         Real l = t * box_unit<Real>(P, b);
-        Real tau = (sigma_of<Real>(P, nu) * ((Real *)P.nHIr)[j]) * l;
+        Real sig = sgs ? sg * (Real)P.sunit : sigma_of<Real>(P, nu);
+        Real tau = (sig * ((Real *)P.nHIr)[j]) * l;
         Real A, T;
         split_absorbed<Real>(w, tau, A, T);
         int bt = bin_fast<Real>(P.Rf + j * 9, P.R + j * 9, P.ax_rc, NRC, d0, d1, d2);
@@ -626,6 +667,7 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
         V[6][s] = A;
         V[7][s] = A * eps;
         V[8][s] = w;
+        if (sgs) V[9][s] = T * sg;
         atomicAdd(&P.seg_cnt[key], 1);
     }
 }
@@ -677,11 +719,12 @@ __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long l
 }
 
 // Virtual particles (Sec. 2.1): one warp per request.
-// BAR: some box has a barrier (a separate instance keeps the test out of the common case)
+// BAR: some box has a barrier (a separate instance keeps the test out of the common case);
+// SH: the shared frequency bin (likewise)
 // cur, fcur: the hop's slot and free-packet buffers (launch parameters, so that buffer
 // pointers are re-read from the parameter space instead of being held in registers); the
 // step and hop of the random draws are read from the device counters where they are used.
-template <typename Real, int NRC, bool BAR>
+template <typename Real, int NRC, bool BAR, bool SH>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
                                                  const int *lens, unsigned long long *esc_r,
                                                  unsigned char *vstat) {
@@ -708,6 +751,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         long long h2;
         Real N, d0, d1, d2, clk, eps;
         unsigned long long fid;
+        Real sg = Real(0);          // shared bin: the packet's mean cross-section (sunit)
         const int *snb;             // the sender's neighbour list (bounds the kNN search)
         if (!(code & RT_FREE_BIT)) {
             long long i = (unsigned)code / (unsigned)P.S;   // slot codes < 2^31
@@ -720,6 +764,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             packet_dir(S.X[code], S.Y[code], S.Z[code], d0, d1, d2);
             clk = S.C[code] / N;
             eps = S.E[code] / N;
+            if (SH && nu == 0) sg = ((Real *)P.slG[cur])[i * NRC + s] / N;
             fid = code + 1ull;
             snb = P.nbr + i * P.kn;
         } else {
@@ -731,11 +776,13 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             clk = ((Real *)Fi.clock)[f];
             eps = ((Real *)Fi.eps)[f];
             nu = Fi.nu[f];
+            if (SH && nu == 0) sg = ((Real *)Fi.sig)[f];
             fid = Fi.fid[f];
             snb = Fi.nbr + f * P.kn;
         }
         long long boff = P.box_off[box];
-        Real sig = sigma_of<Real>(P, nu), bu = box_unit<Real>(P, box);
+        bool sgs = SH && nu == 0;
+        Real sig = sgs ? sg * (Real)P.sunit : sigma_of<Real>(P, nu), bu = box_unit<Real>(P, box);
         int sqx = 0, sqy = 0, sqz = 0;
         if (lane < P.kn) {
             int q = snb[lane];
@@ -867,6 +914,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             ((Real *)Fo.dx)[r] = d0; ((Real *)Fo.dy)[r] = d1; ((Real *)Fo.dz)[r] = d2;
             ((Real *)Fo.clock)[r] = clk + l / (Real)C_LIGHT;
             ((Real *)Fo.eps)[r] = eps;
+            if (sgs) ((Real *)Fo.sig)[r] = sg;
             Fo.nu[r] = nu;
             Fo.fid[r] = mix64(fid);
         }
@@ -981,11 +1029,12 @@ __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long
 // broadcast loop (the lane owning the target cone adds).  Groups come from the work list;
 // the next buffer's occupancy words were cleared by the work-list kernel.
 // cur: the slot buffer holding the hop's packets.
-template <typename Real, int G, bool BAR>
+template <typename Real, int G, bool BAR, bool SH>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int cur, const int *wl_n) {
-    // contributions of the current chunk, one per lane: 6 values (T, T d, T clock, T eps); and
-    // per reception cone of each group, the mask of the chunk's lanes that feed it
-    __shared__ Real sv[6][256];
+    // contributions of the current chunk, one per lane: 6 values (T, T d, T clock, T eps), and
+    // T sigma in a shared frequency bin; and per reception cone of each group, the mask of the
+    // chunk's lanes that feed it
+    __shared__ Real sv[SH ? 7 : 6][256];
     __shared__ unsigned sm[256];
     // the current chunk of reverse edges: offset and sender; bitmap word and first
     // contribution; and per contribution chunk, the edge lane where each range starts
@@ -1010,13 +1059,18 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
         int fc = P.seg_cnt[key];
         Slots<Real> So(P, cur), Sn(P, nxt);
         long long sidx = j * P.S + (long long)nu * G + gl;
-        KSum<Real> aN, aX, aY, aZ, aC, aE, sA, sAE, sW;
+        // a group of the shared frequency bin also merges the cross-section sums
+        bool sgs = SH && nu == 0;
+        long long gidx = j * G + gl;
+        KSum<Real> aN, aX, aY, aZ, aC, aE, aG, sA, sAE, sW;
         if ((park >> gl) & 1u) {
             aN.init(So.N[sidx]); aX.init(So.X[sidx]); aY.init(So.Y[sidx]);
             aZ.init(So.Z[sidx]); aC.init(So.C[sidx]); aE.init(So.E[sidx]);
+            aG.init(sgs ? ((Real *)P.slG[cur])[gidx] : Real(0));
         } else {
             aN.init(Real(0)); aX.init(Real(0)); aY.init(Real(0));
             aZ.init(Real(0)); aC.init(Real(0)); aE.init(Real(0));
+            aG.init(Real(0));
         }
         sA.init(Real(0)); sAE.init(Real(0)); sW.init(Real(0));
         int box = P.pbox[j];
@@ -1036,6 +1090,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                 m &= m - 1u;
                 aN.add(sv[0][t2]); aX.add(sv[1][t2]); aY.add(sv[2][t2]);
                 aZ.add(sv[3][t2]); aC.add(sv[4][t2]); aE.add(sv[5][t2]);
+                if (sgs) aG.add(sv[SH ? 6 : 0][t2]);
             }
             __syncwarp(gmask);
         };
@@ -1089,14 +1144,14 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                     int c = cb + gl;
                     int mybin = -1;
                     bool keep = c < total;
-                    Real w, d0, d1, d2, clk, eps;
+                    Real w, d0, d1, d2, clk, eps, sgc = Real(0);
                     float4 ed;
                     if (keep) {
                         ed = se[gbase + own];
                         uint2 ow = sw2[gbase + own];
                         int bsrc = __fns(ow.x, 0, c - (int)(ow.y & 0x7fffffffu) + 1);
                         long long ridx = (long long)__float_as_int(ed.w) * P.S + (long long)nu * G + bsrc;
-                        rec_load(P.rec, ridx, w, d0, d1, d2, clk, eps);
+                        rec_load(P.rec, ridx, w, d0, d1, d2, clk, eps, sgs, sgc);
                         if (ow.y >> 31) {   // through the barrier: removed (counted escaped)
                             atomicAdd(&P.esc_fx[box], esc_fixed(w, P, box));
                             keep = false;
@@ -1106,7 +1161,9 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                         Real t = (Real)ed.x * d0 + (Real)ed.y * d1 + (Real)ed.z * d2;
                         Real l = t * u;
                         Real A, T;
-                        split_absorbed<Real>(w, sig_nhi * l, A, T);
+                        // in a shared bin each packet carries its own mean cross-section
+                        Real sn = sgs ? (sgc * (Real)P.sunit) * ((Real *)P.nHIr)[j] : sig_nhi;
+                        split_absorbed<Real>(w, sn * l, A, T);
                         sA.add(A);
                         sAE.add(A * eps);
                         sW.add(w);
@@ -1117,6 +1174,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                         sv[3][threadIdx.x] = T * d2;
                         sv[4][threadIdx.x] = T * (clk + l / (Real)C_LIGHT);
                         sv[5][threadIdx.x] = T * eps;
+                        if (sgs) sv[SH ? 6 : 0][threadIdx.x] = T * sgc;
                     }
                     merge_chunk(mybin);
                 }
@@ -1133,6 +1191,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
                     mybin = P.st_bin[s];           // -1: removed by a barrier
                     if (mybin >= 0) {
                         for (int f = 0; f < 6; ++f) sv[f][threadIdx.x] = V[f][s];
+                        if (sgs) sv[SH ? 6 : 0][threadIdx.x] = V[9][s];
                         sA.add(V[6][s]);
                         sAE.add(V[7][s]);
                         sW.add(V[8][s]);
@@ -1150,6 +1209,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
         if (occ) {
             Sn.N[sidx] = N; Sn.X[sidx] = aX.get(); Sn.Y[sidx] = aY.get();
             Sn.Z[sidx] = aZ.get(); Sn.C[sidx] = aC.get(); Sn.E[sidx] = aE.get();
+            if (sgs) ((Real *)P.slG[nxt])[gidx] = aG.get();
         }
         Real a = sA.get(), ae = sAE.get(), w = sW.get();
 #pragma unroll
@@ -1348,21 +1408,31 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     LAUNCH_ON(s2, KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
     LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
     cudaEventRecord(evFree, s2);
-    if (P.any_bar)
-        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+    // instances: the common case; with a barrier; with a shared frequency bin (whose instance
+    // also takes the barrier test, which is a no-op in boxes without one)
+    if (P.shared)
+        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true, true><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+    else if (P.any_bar)
+        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
     else
-        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
-    LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
+        LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
+    if (P.shared)
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, true><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
+    else
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, false><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
     cudaEventRecord(evA, st);
     cudaStreamWaitEvent(st, evFree, 0);
     LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
     LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_REQ, 0, 0, 0)));
     LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
-    if (P.any_bar)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+    if (P.shared)
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+    else if (P.any_bar)
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     else
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
     LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
@@ -1370,10 +1440,12 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     cudaMemsetAsync(H.lens + 4, 0, sizeof(int), s2);
     cudaStreamWaitEvent(s2, evA, 0);
     LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, H.lens + 4)));
-    if (P.any_bar)
-        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+    if (P.shared)
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, true><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+    else if (P.any_bar)
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
     else
-        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
     cudaEventRecord(evB, s2);
     cudaStreamWaitEvent(st, evB, 0);
     LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, cur ^ 1, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
@@ -1471,7 +1543,10 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     if (part == 3) {  // cone masks of the held packets only (inspection)
         clear_cone_bits(c, st);
         c->bm_dirty = true;
-        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur)));
+        if (P.shared)
+            LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, true><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur)));
+        else
+            LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, false><<<rt_blocks(n * 32, tb, 152 * 64), tb, 0, st>>>(P, c->cur)));
         return rt_cuda_check(c, cudaGetLastError(), "cone masks");
     }
     // part 4: the hop loop, driven from the host (one synchronisation per hop)

@@ -23,7 +23,7 @@ SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_
            "rt_set_slots",
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
            "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier",
-           "rt_set_graph"]
+           "rt_set_graph", "rt_get_shared_sigma", "rt_set_shared_sigma"]
 
 
 class RTError(RuntimeError):
@@ -40,6 +40,7 @@ class Config(C.Structure):
         ("seed", C.c_ulonglong), ("hop_cap", C.c_int), ("sub_cap", C.c_int),
         ("cool_flags", C.c_int), ("T_floor", C.c_double), ("eps_rr_fixed", C.c_double),
         ("sigma_rec", C.c_double), ("free_cap", C.c_longlong), ("cell_occupancy", C.c_int),
+        ("rec_shared_bin", C.c_int),
     ]
 
 
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = False):
     L.rt_get_cone_masks_noalloc.argtypes = [vp, vp, i, vp]
     L.rt_get_slots.argtypes = [vp, vp, i, vp]
     L.rt_set_slots.argtypes = [vp, vp, i, vp]
+    L.rt_get_shared_sigma.argtypes = [vp, vp, i, vp]
+    L.rt_set_shared_sigma.argtypes = [vp, vp, i, vp]
     L.rt_get_deposits.argtypes = [vp, vp, vp, vp, i, vp]
     L.rt_get_stats.argtypes = [vp, vp]
     L.rt_axis_set.argtypes = [i, vp]
@@ -106,7 +109,8 @@ def make_config(p: dict) -> Config:
         evolve_T=p["evolve_T"], transport_fp32=p.get("transport_fp32", 0), seed=p["seed"],
         hop_cap=p["hop_cap"], sub_cap=p["sub_cap"], cool_flags=p["cool_flags"],
         T_floor=p["T_floor"], eps_rr_fixed=p["eps_rr_fixed"], sigma_rec=p["sigma_rec"],
-        free_cap=p.get("free_cap", 0), cell_occupancy=p.get("cell_occupancy", 0))
+        free_cap=p.get("free_cap", 0), cell_occupancy=p.get("cell_occupancy", 0),
+        rec_shared_bin=p.get("rec_shared_bin", 0))
 
 
 def _ptr(a):
@@ -142,7 +146,7 @@ class Context:
         self.n = int(self.box_off[-1])
         self.nb = len(self.box_L)
         self.ns = len(wl["src_box"])
-        self.nf = p["n_freq_src"] + 1
+        self.nf = p["n_freq_src"] + (0 if p.get("rec_shared_bin", 0) else 1)
         self.S = self.nf * p["n_rc"]
         self.K = max(1, int(round(p["dt"] / p["dt_em"])))
         self.stream = stream
@@ -315,6 +319,18 @@ class Context:
         f = np.ascontiguousarray(f, dtype=np.float64)
         self._check(self.L.rt_set_slots(self.h, f.ctypes.data, RT_HOST, self._s()),
                     "rt_set_slots")
+
+    def shared_sigma(self):
+        """Shared frequency bin: the cross-section sums N sigma of bin 0's packets, [n, n_rc]."""
+        G = np.zeros((self.n, self.params["n_rc"]))
+        self._check(self.L.rt_get_shared_sigma(self.h, G.ctypes.data, RT_HOST, self._s()),
+                    "rt_get_shared_sigma")
+        return G
+
+    def set_shared_sigma(self, G):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        self._check(self.L.rt_set_shared_sigma(self.h, G.ctypes.data, RT_HOST, self._s()),
+                    "rt_set_shared_sigma")
 
     def deposits(self):
         a = np.zeros((self.n, self.nf))

@@ -392,16 +392,18 @@ def _same_results(a, b):
 
 
 @pytest.mark.parametrize("fp32", [0, 1])
-@pytest.mark.parametrize("name", ["cfg2_24", "shadow", "original"])
+@pytest.mark.parametrize("name", ["cfg2_24", "shadow", "original", "shared"])
 def test_step_graph_equals_hop_by_hop_loop(name, fp32):
     """rt_step as one captured CUDA graph (a conditional while node around the hop, a switch
     node over the four buffer pairs) gives the same bits as the host-driven hop loop, with the
     same kernel launch counts (the graph launches the hop-cap drop every step; the loop only
     at the cap): the HII region at 24^3 (32 cones, 8 frequency bins), the shadow workload
-    (barrier, directed and gated emitters) and the original recombination implementation."""
+    (barrier, directed and gated emitters), the original recombination implementation and the
+    shared frequency bin."""
     wl = {"cfg2_24": lambda: W.cfg2(n_side=24, transport_fp32=fp32),
           "shadow": lambda: W.shadow(n_side=16, n_front=20, n_bnd=10, transport_fp32=fp32),
-          "original": lambda: W.cfg1(rec_mode=W.REC_EMISSION_CONES, transport_fp32=fp32)}[name]()
+          "original": lambda: W.cfg1(rec_mode=W.REC_EMISSION_CONES, transport_fp32=fp32),
+          "shared": lambda: W.cfg2(n_side=16, rec_shared_bin=1, transport_fp32=fp32)}[name]()
     a, b = _graph_pair(wl)
     for step in range(5):
         a.step(step)
@@ -628,3 +630,84 @@ def test_app_a_convergence_with_resolution_and_time_step():
     ia = np.array([p["intensity"] for p in a["profile"][:4]])
     ib = np.array([p["intensity"] for p in b["profile"][:4]])
     assert np.all(np.abs(ia / ib - 1) < 0.25)
+
+
+# --- shared frequency bin (Sec. 2.2, last paragraph) ---------------------------------------------
+def _shared_chain(n_part=40, spacing=0.1 * W.KPC):
+    """Particles on a line with two neighbours each, one shared frequency bin: a packet sent
+    along +x reaches only the next particle."""
+    L = (n_part + 1) * spacing
+    wl = W.tiny(n=n_part, n_ngb=2, L=L, n_tc=64, rec_shared_bin=1)
+    yz = np.full(n_part, 0.5 * L)
+    wl.update(x=(np.arange(n_part) + 0.5) * spacing, y=yz.copy(), z=yz.copy(),
+              n_H=np.full(n_part, 1e-3), N_H=np.full(n_part, 1e-3 * spacing ** 3),
+              x_HI=np.full(n_part, 1e-2), T=np.full(n_part, 1e4), src_box=np.zeros(0, np.int32),
+              src_x=np.zeros(0), src_y=np.zeros(0), src_z=np.zeros(0), src_ndot=np.zeros(0))
+    return wl
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_shared_bin_mixed_packet_against_the_oracle(fp32):
+    """A packet of the shared bin holding photons of two cross-sections (the bin's own and twice
+    it) moves down a chain: every deposit, the cross-section field and the budget match the
+    oracle (FP64 to rounding, FP32 within 1e-5)."""
+    wl = _shared_chain()
+    g, o = _pair(wl, transport_fp32=fp32)
+    assert g.nf == 1 and g.S == wl["params"]["n_rc"]
+    g.assign_cones(0)
+    g.emit(0)
+    o.rotate(0)
+    o.emit(0)
+    N0, s0 = 1e50, wl["sigma"][0]
+    d = np.array([1.0, 0.0, 0.0])
+    b = oracle.recv_bin(o.rotations()[0][1].reshape(3, 3), oracle.axis_set(wl["params"]["n_rc"]), d)
+    f = np.zeros((6, g.n, g.S))
+    f[0, 1, b] = N0
+    f[1:4, 1, b] = N0 * d
+    G = np.zeros((g.n, wl["params"]["n_rc"]))
+    G[1, b] = 0.25 * N0 * s0 + 0.75 * N0 * 2 * s0
+    for c in (g, o):
+        c.set_slots(f)
+        c.set_shared_sigma(G)
+    assert np.allclose(g.shared_sigma(), G, rtol=1e-6 if fp32 else 0, atol=0)
+    g.transport(0)
+    assert o.transport(0) == 0
+    ag, ao = g.deposits()[0][:, 0], o.deposits()[0][:, 0]
+    assert ao[2:-2].min() > 0
+    assert np.allclose(ag, ao, rtol=1e-12 if not fp32 else 1e-5, atol=1e-6 * ao.max() if fp32 else 0)
+    for c in (g, o):                 # the library folds the step's absorptions into the budget here
+        c.chemistry()
+    bg, bo = g.budget()[0], o.budget()[0]
+    assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * N0)
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+@pytest.mark.parametrize("clock_limited", [False, True])
+def test_shared_frequency_bin_against_the_oracle(fp32, clock_limited):
+    """The HII region (1e5 K blackbody in 8 bins, 32 cones, T evolving) with the recombination
+    photons in source bin 0, their cross-sections averaged on merge.  With clock-limited steps
+    (c dt < box side) packets are held across steps and re-binned with their cross-section
+    sums.  FP64: x_HI, T and the cross-section field of the held packets as the oracle's to
+    rounding; FP32: x_HI and T within the bars; budgets within 1e-6."""
+    kw = dict(dt=0.01 * W.MYR, dt_em=0.01 * W.MYR) if clock_limited else {}
+    wl = W.cfg2(n_side=16, rec_shared_bin=1, **kw)
+    g, o = _pair(wl, transport_fp32=fp32)
+    for step in range(4):
+        g.step(step)
+        assert o.step(step) == 0
+    sg, so = g.state(), o.state()
+    ok = _xhi_ok(sg["x_HI"], so["x_HI"])
+    relT = np.abs(sg["T"] / so["T"] - 1)
+    assert so["N_rec"].max() > 0
+    if fp32 == 0:
+        assert ok.all() and (relT < 1e-3).all()
+        assert np.max(np.abs(sg["x_HI"] / so["x_HI"] - 1)) < 1e-9
+        Gg, Go = g.shared_sigma(), o.shared_sigma()
+        if clock_limited:
+            assert np.count_nonzero(Go) > 1000
+        assert np.allclose(Gg, Go, rtol=1e-9, atol=1e-9 * np.abs(Go).max())
+    else:
+        assert ok.mean() > 0.99 and (relT < 1e-3).mean() > 0.99
+    bg, bo = g.budget()[0], o.budget()[0]
+    assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
+    assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
