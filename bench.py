@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--original", action="store_true",
                     help="also time the original (emission-cone) recombination implementation")
+    ap.add_argument("--shared", action="store_true",
+                    help="also time one frequency bin shared by stellar and recombination photons")
     return ap.parse_args()
 
 
@@ -225,6 +227,11 @@ def run_ours(args):
         # emission cones, on the same workload and precision
         out["original_recombination"] = fp64_path(
             args, stream, transport_fp32=int(args.precision == "fp32"), rec_mode=3)
+    if args.shared:
+        # stellar and recombination photons in one frequency bin (Sec. 2.2, last paragraph),
+        # on the same workload and precision
+        out["shared_frequency_bin"] = fp64_path(
+            args, stream, transport_fp32=int(args.precision == "fp32"), rec_shared_bin=1)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
@@ -320,8 +327,15 @@ def fp64_path(args, stream, **over):
         ms = e0.elapsed_time(e1)
     n = int(wl["box_off"][-1])
     ctx.close()
+    pr = wl["params"]
+    R = 4 if pr["transport_fp32"] else 8
+    nrc = pr["n_rc"]
+    S = (pr["n_freq_src"] + (0 if pr.get("rec_shared_bin", 0) else 1)) * nrc
+    # packet storage: two slot buffers of 6 fields, the sender records (8 values a slot) and,
+    # with a shared bin, two buffers of bin-0 cross-section sums
+    slot_bytes = n * R * (2 * 6 * S + 8 * S + (2 * nrc if pr.get("rec_shared_bin", 0) else 0))
     return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
-            "ms_per_step": ms / steps, "steps": steps,
+            "ms_per_step": ms / steps, "steps": steps, "packet_storage_bytes": slot_bytes,
             "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
 
 
