@@ -461,13 +461,25 @@ __global__ void k_emit_rec_cones(DevPtrs P, long long base) {
 template <typename Real, int NRC, bool SH>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int cur) {
     int lane = threadIdx.x & 31;
-    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     Slots<Real> S(P, cur);
     float cf = 1.0f - 2.0f / (float)P.ntc;
     long long nrev = P.n * P.kn;
     long long ncon = 0;
-    for (long long i = w0; i < P.n; i += nw) {
+    // each block takes one contiguous chunk of particles; its warps pull particles from it
+    // through a shared counter, so that they finish together (particles hold from none to
+    // hundreds of packets)
+    __shared__ int snext;
+    long long chunk = (P.n + gridDim.x - 1) / gridDim.x;
+    long long ib0 = (long long)blockIdx.x * chunk;
+    long long ib1 = ib0 + chunk < P.n ? ib0 + chunk : P.n;
+    if (threadIdx.x == 0) snext = 0;
+    __syncthreads();
+    auto next_particle = [&]() {
+        long long v = 0;
+        if (lane == 0) v = ib0 + atomicAdd(&snext, 1);
+        return __shfl_sync(FULLMASK, v, 0);
+    };
+    for (long long i = next_particle(); i < ib1; i = next_particle()) {
         unsigned aw = (lane < P.nf) ? P.act[cur][i * P.nf + lane] : 0u;
         if (__ballot_sync(FULLMASK, aw != 0u) == 0u) {
             if (lane == 0) P.reqcnt[i] = 0;
@@ -732,8 +744,6 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     int lane = threadIdx.x & 31;
     long long nreq = lens[2];
     if (nreq > P.F_cap) nreq = P.F_cap;
-    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     FreeBuf Fi = P.fr[fcur], Fo = P.fr[fcur ^ 1];
     Slots<Real> S(P, cur);
     uint2 key = philox_key(P.seed, 3u);
@@ -741,12 +751,28 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     // values and the sender's neighbour positions are loaded before the position draws; the
     // four per-neighbour inputs of the interpolation and deposit are gathered together; the
     // values returned by the deposit atomics are checked one request later.
-    unsigned long long code_next = w0 < nreq ? P.req[w0] : 0ull;
+    // Each block takes one contiguous chunk of the requests, and its warps pull requests from
+    // the chunk through a shared counter, one ahead: the warps of a block finish together
+    // (request costs vary), and blocks still retire one by one, which lets the receiver side
+    // on the other stream in.  Results do not depend on which warp takes a request.
+    __shared__ int snext;
+    long long chunk = (nreq + gridDim.x - 1) / gridDim.x;
+    long long rb0 = (long long)blockIdx.x * chunk;
+    long long rb1 = rb0 + chunk < nreq ? rb0 + chunk : nreq;
+    if (threadIdx.x == 0) snext = 0;
+    __syncthreads();
+    long long r_first = 0;
+    if (lane == 0) r_first = rb0 + atomicAdd(&snext, 1);
+    r_first = __shfl_sync(FULLMASK, r_first, 0);
+    unsigned long long code_next = r_first < rb1 ? P.req[r_first] : 0ull;
     unsigned long long pend_a = 0ull, pend_e = 0ull;   // words before this lane's last adds
     bool bad = false;
-    for (long long r = w0; r < nreq; r += nw) {
+    for (long long r = r_first, rn; r < rb1; r = rn) {
         unsigned long long code = code_next;
-        if (r + nw < nreq) code_next = P.req[r + nw];
+        rn = 0;
+        if (lane == 0) rn = rb0 + atomicAdd(&snext, 1);
+        rn = __shfl_sync(FULLMASK, rn, 0);
+        if (rn < rb1) code_next = P.req[rn];
         int box, qx, qy, qz, nu;
         long long h2;
         Real N, d0, d1, d2, clk, eps;
@@ -1046,10 +1072,21 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
     unsigned base = (threadIdx.x & 31) & ~(unsigned)(G - 1);
     unsigned gmask = (G == 32) ? FULLMASK : (((1u << G) - 1u) << base);
     long long ng = *wl_n;
-    long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    long long gstride = ((long long)gridDim.x * blockDim.x) / G;
     int nxt = cur ^ 1;
-    for (long long gi = g0; gi < ng; gi += gstride) {
+    // each block takes one contiguous chunk of the work list; its groups pull entries from it
+    // through a shared counter, so that they finish together
+    __shared__ int snext;
+    long long chunk = (ng + gridDim.x - 1) / gridDim.x;
+    long long gb0 = (long long)blockIdx.x * chunk;
+    long long gb1 = gb0 + chunk < ng ? gb0 + chunk : ng;
+    if (threadIdx.x == 0) snext = 0;
+    __syncthreads();
+    auto next_group = [&]() {
+        long long v = 0;
+        if (gl == 0) v = gb0 + atomicAdd(&snext, 1);
+        return __shfl_sync(gmask, v, 0, G);
+    };
+    for (long long gi = next_group(); gi < gb1; gi = next_group()) {
         unsigned wv = (unsigned)P.worklist[gi];
         long long key = wv & 0x7fffffffu;
         bool touched = (wv >> 31) != 0u;
