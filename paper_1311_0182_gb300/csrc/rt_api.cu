@@ -8,7 +8,7 @@
 #include <mutex>
 #include <string>
 
-#include "rt_internal.cuh"
+#include "rt_knn.cuh"
 
 rt_status rt_fail(rt_ctx *c, rt_status s, const std::string &msg) {
     if (c) c->err = msg;
@@ -343,6 +343,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.grid.start, int, ncell + 1);
     c->grid_cap = ncell;
     A(P.grid.items, int4, n);
+    A(P.grid.tab, int, KNN_TAB_N);
     A(P.R, double, 9 * n);
     A(P.Rf, float, 9 * n);
     A(P.Rs, double, 9 * ((long long)n_src * P.K + 1));
@@ -418,6 +419,11 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     std::vector<double> u(n_boxes);
     for (int b = 0; b < n_boxes; ++b) u[b] = box_L[b] / (double)RT_Q;
     cudaMemcpy(P.box_off, box_off, sizeof(long long) * (n_boxes + 1), cudaMemcpyHostToDevice);
+    {
+        int tab[KNN_TAB_N];
+        knn_offset_table(tab);
+        cudaMemcpy(P.grid.tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(P.box_bch, box_bch.data(), sizeof(int) * (n_boxes + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(P.bch_lo, bch_lo.data(), sizeof(long long) * (P.nbch + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(P.box_L, box_L, sizeof(double) * n_boxes, cudaMemcpyHostToDevice);

@@ -17,7 +17,7 @@
 
 #define RT_Q 1048576          // 2^20 quantisation cells per box side
 #define RT_BUDGET_CHUNK 4096
-#define RT_OCC_MIN 5           // finest kNN grid the occupancy search tries
+#define RT_OCC_MIN 2           // finest kNN grid the occupancy search tries
 #define RT_MAXK 32            // maximum neighbours per particle
 #define RT_FREE_BIT (1ull << 63)
 
@@ -81,6 +81,7 @@ struct Grid {                 // per-box uniform cell lists (device arrays)
     int *start;               // [ncells + 1] offsets into items
     int4 *items;              // (qx, qy, qz, local index) sorted by cell
     long long ncells;
+    int *tab;                 // cell offsets of the kNN search, nearest first (rt_knn.cuh)
 };
 
 struct HopScratch {           // per-hop scratch: [0] free packets, [1] n + free, [2] requests, [3] staged

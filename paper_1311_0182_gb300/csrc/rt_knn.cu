@@ -1,6 +1,10 @@
 // rt_knn.cu -- quantisation, per-box cell lists, exact kNN of particles and sources, and the
 // receiver-sorted reverse neighbour lists (Sec. 2.1: a packet at particle i is passed to the
 // neighbours within i's smoothing volume, the n_ngb nearest particles).
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
 #include "rt_knn.cuh"
 
 __global__ void k_quantise(DevPtrs P, const double *x, const double *y, const double *z) {
@@ -69,12 +73,33 @@ __global__ void k_cell_fill(DevPtrs P, int *fill) {
     P.grid.items[pos] = make_int4(P.qx[i], P.qy[i], P.qz[i], (int)(i - P.box_off[b]));
 }
 
+void knn_offset_table(int *out) {
+    struct E { int d, r2, code; };
+    std::vector<E> es;
+    for (int ox = -KNN_TAB_R; ox <= KNN_TAB_R; ++ox)
+        for (int oy = -KNN_TAB_R; oy <= KNN_TAB_R; ++oy)
+            for (int oz = -KNN_TAB_R; oz <= KNN_TAB_R; ++oz) {
+                int o[3] = {ox, oy, oz}, d = 0;
+                for (int a = 0; a < 3; ++a) {
+                    int m = std::abs(o[a]) - 1;
+                    if (m > 0) d += m * m;
+                }
+                int code = (ox + 4) | (oy + 4) << 4 | (oz + 4) << 8 | d << 12;
+                es.push_back({d, ox * ox + oy * oy + oz * oz, code});
+            }
+    std::stable_sort(es.begin(), es.end(), [](const E &a, const E &b) {
+        return a.d != b.d ? a.d < b.d : a.r2 < b.r2;
+    });
+    for (int k = 0; k < KNN_TAB_N; ++k) out[k] = es[k].code;
+}
+
 __device__ __forceinline__ BoxGrid box_grid(const DevPtrs &P, int b) {
     BoxGrid g;
     g.G = P.grid.G[b];
     g.cs = P.grid.cs[b];
     g.coff = P.grid.coff[b];
     g.start = P.grid.start;
+    g.tab = P.grid.tab;
     g.items = P.grid.items;
     return g;
 }
@@ -209,7 +234,7 @@ static void cell_lists(rt_ctx *c, cudaStream_t st) {
 // fastest wins.  Done once per context; any grid gives the same exact neighbours, so only the
 // time depends on the choice.
 static void tune_grid(rt_ctx *c, cudaStream_t st) {
-    static const int cand[] = {5, 7, 9, 12, 16};
+    static const int cand[] = {2, 3, 4, 5, 7, 9};
     DevPtrs &P = c->d;
     int tb = 256;
     // rt_set_grid rewrites the grid description with plain copies, which do not wait for

@@ -1,10 +1,12 @@
 // rt_knn.cuh -- exact k-nearest-neighbour search by one warp over a box's uniform cell list.
 //
 // The result is the k smallest (squared quantised distance, local index) pairs, a unique set,
-// held sorted across the lanes: lane l has the l-th nearest.  The search visits the 3x3x3 block
-// of cells around the query, then growing shells of cells (skipping cells that cannot hold a
-// point at or below the current k-th distance) until the k-th distance is below the distance
-// to the outside of the visited block.
+// held sorted across the lanes: lane l has the l-th nearest.  The search first visits the cells
+// within Chebyshev radius KNN_TAB_R of the query's cell, 32 at a time, nearest first (a fixed
+// table of offsets sorted by the smallest distance a cell at that offset can have), skipping
+// every cell farther than the current k-th distance, and stops as soon as no remaining cell can
+// be nearer; when the k-th distance still reaches beyond that block, growing shells of cells
+// follow until it is below the distance to the outside of the visited block.
 //
 // A pair is one 64-bit key, d2 * 2^22 + index: quantised offsets are below 2^20 per axis, so
 // d2 < 3 * 2^40 < 2^42, and a box holds fewer than 2^22 particles (checked when the context
@@ -61,11 +63,20 @@ __device__ __forceinline__ void warp_insert(unsigned long long &t, unsigned long
     if (t > c) t = (lane == 0 || p < c) ? c : p;
 }
 
+// the table of cell offsets: all of [-KNN_TAB_R, KNN_TAB_R]^3, each entry
+// (ox + 4) | (oy + 4) << 4 | (oz + 4) << 8 | dmin << 12, sorted by dmin, then by |o|^2, where
+// dmin = sum_a max(|o_a| - 1, 0)^2: a point in the query's cell is at least dmin * cs^2 from
+// any point of the cell at offset o (squared quantised units)
+#define KNN_TAB_R 3
+#define KNN_TAB_N 343
+void knn_offset_table(int *out);   // host: fills KNN_TAB_N entries
+
 struct BoxGrid {
     int G, cs;
     long long coff;
     const int *start;
     const int4 *items;
+    const int *tab;           // the offset table (device)
 };
 
 __device__ __forceinline__ int cell_coord(int v, int cs, int G) {
@@ -154,21 +165,16 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
     }
 }
 
-// Exact kNN of point q (quantised, inside [0, RT_Q)^3) among the box's points, excluding the
-// point with local index `exclude` (-1: none).  Lane l < kn returns the l-th nearest.
-// `bound` is an upper bound on the squared distance of the kn-th neighbour (KNN_INF when none
-// is known): points and cells beyond it are skipped, which leaves the result unchanged.
-// sdelta: 32 ints of shared memory owned by the calling warp.
-// Returns false when the box holds fewer than kn candidates.
-__device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
-                                long long &out_d2, int &out_idx, int *sdelta,
-                                long long bound = KNN_INF) {
-    unsigned long long t = KNN_KEY_NONE, kth = KNN_KEY_NONE;
-    unsigned long long bkey = bound >= (1ll << 42) ? KNN_KEY_NONE - 1ull
-                                                   : knn_key(bound, (int)KNN_IDX_MASK);
+// Shells of cells at Chebyshev radius r0, r0 + 1, ... around the query's cell, merged into the
+// running list t (k-th key kth), until the k-th distance is below the distance from q to the
+// outside of the visited block (every cell of radius < r0 has been visited or shown not to
+// matter).  r0 = 1 visits the whole 3x3x3 block first.
+__device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
+                                  int r0, long long bound, unsigned long long bkey,
+                                  unsigned long long &t, unsigned long long &kth, int *sdelta) {
     int G = g.G, cs = g.cs;
     int cx = cell_coord(qx, cs, G), cy = cell_coord(qy, cs, G), cz = cell_coord(qz, cs, G);
-    for (int r = 1; r <= G; ++r) {
+    for (int r = r0; r <= G; ++r) {
         // the columns (x, y) of the shell at Chebyshev radius r (r = 1: the whole 3x3x3 block)
         int side = 2 * r + 1;
         int ncol = side * side;
@@ -236,6 +242,54 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
         if (b < 0) break;
         if (kth != KNN_KEY_NONE && (long long)(kth >> KNN_IDX_BITS) < b * b) break;
     }
+}
+
+// Exact kNN of point q (quantised, inside [0, RT_Q)^3) among the box's points, excluding the
+// point with local index `exclude` (-1: none).  Lane l < kn returns the l-th nearest.
+// `bound` is an upper bound on the squared distance of the kn-th neighbour (KNN_INF when none
+// is known): points and cells beyond it are skipped, which leaves the result unchanged.
+// sdelta: 32 ints of shared memory owned by the calling warp.
+// Returns false when the box holds fewer than kn candidates.
+__device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
+                                long long &out_d2, int &out_idx, int *sdelta,
+                                long long bound = KNN_INF) {
+    unsigned long long t = KNN_KEY_NONE, kth = KNN_KEY_NONE;
+    unsigned long long bkey = bound >= (1ll << 42) ? KNN_KEY_NONE - 1ull
+                                                   : knn_key(bound, (int)KNN_IDX_MASK);
+    int G = g.G, cs = g.cs;
+    int cx = cell_coord(qx, cs, G), cy = cell_coord(qy, cs, G), cz = cell_coord(qz, cs, G);
+    const long long cs2 = (long long)cs * cs;
+    // cells outside the table are at Chebyshev radius > KNN_TAB_R: dmin >= KNN_TAB_R^2
+    const int dout = KNN_TAB_R * KNN_TAB_R;
+    bool done = false;
+    for (int e0 = 0; e0 < KNN_TAB_N; e0 += 32) {
+        // cells farther than the current k-th distance (or the bound) cannot help
+        long long lim = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> KNN_IDX_BITS);
+        if (bound < lim) lim = bound;
+        // the table is sorted by dmin: once the next entry (and every cell outside the table)
+        // is beyond the limit, nothing nearer remains
+        int dnext = __ldg(g.tab + e0) >> 12;
+        if (lim < KNN_INF && (long long)min(dnext, dout) * cs2 > lim) {
+            done = true;
+            break;
+        }
+        int rs = 0, rc = 0;
+        int k = e0 + (int)(threadIdx.x & 31);
+        if (k < KNN_TAB_N) {
+            int e = __ldg(g.tab + k);
+            int ix = cx + (e & 15) - 4, iy = cy + ((e >> 4) & 15) - 4, iz = cz + ((e >> 8) & 15) - 4;
+            if (ix >= 0 && iy >= 0 && iz >= 0 && ix < G && iy < G && iz < G) {
+                int lx = ix * cs, ly = iy * cs, lz = iz * cs;
+                if (box_d2(qx, qy, qz, lx, ly, lz, lx + cs - 1, ly + cs - 1, lz + cs - 1) <= lim) {
+                    long long c = g.coff + ((long long)ix * G + iy) * G + iz;
+                    rs = g.start[c];
+                    rc = g.start[c + 1] - rs;
+                }
+            }
+        }
+        knn_visit(g, qx, qy, qz, exclude, kn, rs, rc, bkey, t, kth, sdelta);
+    }
+    if (!done) knn_shells(g, qx, qy, qz, exclude, kn, KNN_TAB_R + 1, bound, bkey, t, kth, sdelta);
     if (t == KNN_KEY_NONE) {
         out_d2 = KNN_INF;
         out_idx = 0x7fffffff;

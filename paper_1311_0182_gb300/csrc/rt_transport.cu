@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         int kidx;
         BoxGrid g;
         g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
-        g.start = P.grid.start; g.items = P.grid.items;
+        g.start = P.grid.start; g.items = P.grid.items; g.tab = P.grid.tab;
         warp_knn(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2);
         long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
         bool valid = lane < P.kn;

@@ -551,11 +551,11 @@ def test_grid_occupancy_search_changes_nothing_but_time():
     from paper_1311_0182_gb300 import rt
     wl = W.cfg2(n_side=20)
     ctxs = {occ: rt.context_for(dict(wl, params=dict(wl["params"], cell_occupancy=occ)))
-            for occ in (0, 5, 16)}
-    assert ctxs[0].stats()["cell_occupancy"] in (5, 7, 9, 12, 16)
+            for occ in (0, 2, 5, 16)}
+    assert ctxs[0].stats()["cell_occupancy"] in (2, 3, 4, 5, 7, 9)
     assert ctxs[5].stats()["cell_occupancy"] == 5
     ref = ctxs[5].neighbours()
-    for occ in (0, 16):
+    for occ in (0, 2, 16):
         for a, b in zip(ctxs[occ].neighbours(), ref):
             assert np.array_equal(a, b)
     for g in ctxs.values():
