@@ -2,6 +2,10 @@
 
 sm_103a only.  -fmad=false keeps every floating-point expression rounded as written (the exact
 decisions of the method depend on it); FP32 fused multiply-adds are written out explicitly.
+-ftz=true flushes subnormal FP32 results to zero: on the FP32 transport path a photon count
+below FLT_MIN (about 1e-38 of a box's source photons per step) becomes 0, so its share counts
+as absorbed where it is, and the packet, which carries nothing, is not transported further.
+FP64 arithmetic (the FP64 path, the chemistry, every exact decision) is not affected.
 """
 from __future__ import annotations
 
@@ -17,7 +21,7 @@ SOURCES = ["rt_api.cu", "rt_knn.cu", "rt_scan.cu", "rt_transport.cu", "rt_chem.c
 HEADERS = ["rt_internal.cuh", "rt_knn.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler",
+FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-ftz=true", "-Xcompiler",
                 "-fPIC,-ffp-contract=off", "-Xptxas", "-warn-spills"]
 
 

@@ -19,7 +19,7 @@
 #define KNN_IDX_MASK ((1ull << KNN_IDX_BITS) - 1ull)
 #define KNN_KEY_NONE 0xffffffffffffffffull
 // merge by insertion when at most this many candidates of a batch pass the k-th key
-#define KNN_INSERT_MAX 24
+#define KNN_INSERT_MAX 16
 
 __device__ __forceinline__ unsigned long long knn_key(long long d2, int idx) {
     return ((unsigned long long)d2 << KNN_IDX_BITS) | (unsigned long long)idx;

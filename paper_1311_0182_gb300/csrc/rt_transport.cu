@@ -206,13 +206,20 @@ __device__ __forceinline__ void packet_dir(float Mx, float My, float Mz, float &
                                            float &d2) {
     float s = fmaxf(fabsf(Mx), fmaxf(fabsf(My), fabsf(Mz)));
     if (s > 0.0f) {
-        float a = Mx / s, b = My / s, c = Mz / s;
-        float nn = sqrtf(a * a + b * b + c * c);
-        d0 = a / nn; d1 = b / nn; d2 = c / nn;
+        float is = __frcp_rn(s);
+        float a = Mx * is, b = My * is, c = Mz * is;
+        float rn = rsqrtf(a * a + b * b + c * c);
+        d0 = a * rn; d1 = b * rn; d2 = c * rn;
     } else {
         d0 = 1.0f; d1 = 0.0f; d2 = 0.0f;
     }
 }
+
+// a / b: IEEE division on the FP64 path (the oracle's arithmetic), a times the correctly
+// rounded reciprocal on the FP32 path
+template <typename Real> __device__ __forceinline__ Real rdiv(Real a, Real b);
+template <> __device__ __forceinline__ double rdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float rdiv<float>(float a, float b) { return a * __frcp_rn(b); }
 
 // precision-matched constants: FP64 values on the FP64 path, FP32 copies on the FP32 path
 template <typename Real> __device__ __forceinline__ Real box_unit(const DevPtrs &P, int b);
@@ -545,7 +552,8 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
             }
             ncon += (lane < nb_chunk) ? my_cm : 0;
             if (has && my_cm > 0)
-                rec_store(P.rec, s, N / (Real)my_cm, d0, d1, d2, C / N, E / N, sgs, sgr);
+                rec_store(P.rec, s, rdiv<Real>(N, (Real)my_cm), d0, d1, d2, rdiv<Real>(C, N),
+                          rdiv<Real>(E, N), sgs, sgr);
             // empty cones of this chunk, folded into the per-frequency words
             bool empty = has && my_cm == 0;
             unsigned emb = __ballot_sync(FULLMASK, empty);
