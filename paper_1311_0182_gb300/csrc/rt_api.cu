@@ -396,9 +396,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(x->hop.esc_r, unsigned long long, fc);
     A(x->hop.vstat, unsigned char, fc);
 #undef A
-    // the scan scratch, sized for the largest scan (no allocation later)
-    long long maxscan = std::max(std::max(n + fc, segn), std::max(n * P.kn, ncell + 1));
-    c->scan_tmp_n = (maxscan + 1023) / 1024 + 1;
+    // the scan scratch: one partial sum per block of a scan (no allocation later)
+    c->scan_tmp_n = RT_SCAN_NB;
     if (cudaMalloc(&c->scan_tmp, sizeof(int) * c->scan_tmp_n) != cudaSuccess) ok = false;
     if (cudaMalloc(&c->scan_tmp2, sizeof(int) * c->scan_tmp_n) != cudaSuccess) ok = false;
     if (cudaMallocHost(&c->cnt_h, sizeof(long long) * CNT_N) != cudaSuccess) ok = false;

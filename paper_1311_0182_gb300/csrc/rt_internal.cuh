@@ -20,6 +20,7 @@
 #define RT_OCC_MIN 2           // finest kNN grid the occupancy search tries
 #define RT_MAXK 32            // maximum neighbours per particle
 #define RT_FREE_BIT (1ull << 63)
+#define RT_SCAN_NB 608         // blocks of every prefix-sum launch (4 per SM)
 
 // error bits of the sticky device error word
 enum { ERRB_FREE_CAP = 1, ERRB_STAGE_CAP = 2, ERRB_RANGE = 4, ERRB_KNN = 8 };

@@ -1,8 +1,7 @@
 // rt_scan.cu -- exclusive prefix sum of int32 counts (cell lists, reverse lists, per-hop
-// requests and receiver segments).  Three kernels: per-block scan, a single-block scan of
-// the block totals, and the add-back.  `d_len` (optional) is a device-side element count;
-// the scan covers only the entries before it (the output beyond it is left as it was), so a
-// launch sized for a capacity scans the live part without a host round trip.
+// requests and receiver segments).  `d_len` (optional) is a device-side element count; the
+// scan covers only the entries before it (the output beyond it is left as it was), so a
+// launch made for a capacity scans the live part without a host round trip.
 #include "rt_internal.cuh"
 
 #define SCAN_BLOCK 1024
@@ -35,57 +34,68 @@ __device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
     return r;
 }
 
-__global__ void k_scan_blocks(const int *in, int *out, long long n, const int *d_len,
-                              int *btot) {
-    __shared__ int sh[33];
+// Two kernels on a fixed grid of SCAN_NB blocks: block b owns one contiguous range of the
+// live part; the first kernel sums each range, the second scans it in tiles of SCAN_BLOCK,
+// starting from the sum of the ranges before it.  No launch is sized by the capacity.
+#define SCAN_NB RT_SCAN_NB
+
+__device__ __forceinline__ void scan_range(long long len, long long &b0, long long &b1) {
+    long long per = (len + SCAN_NB - 1) / SCAN_NB;
+    per = (per + SCAN_BLOCK - 1) / SCAN_BLOCK * SCAN_BLOCK;   // whole tiles per block
+    b0 = (long long)blockIdx.x * per;
+    b1 = b0 + per < len ? b0 + per : len;
+}
+
+__device__ __forceinline__ long long scan_len(long long n, const int *d_len) {
     long long len = d_len ? (long long)*d_len : n;
-    if (len > n) len = n;
-    long long b0 = (long long)blockIdx.x * SCAN_BLOCK;
-    if (b0 >= len) {   // the whole block lies beyond the live part
-        if (threadIdx.x == 0) btot[blockIdx.x] = 0;
-        return;
-    }
-    long long i = b0 + threadIdx.x;
-    int v = (i < len) ? in[i] : 0;
+    return len < n ? len : n;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sum(const int *in, long long n,
+                                                         const int *d_len, int *btot) {
+    __shared__ int sh[33];
+    long long b0, b1;
+    scan_range(scan_len(n, d_len), b0, b1);
+    int v = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += SCAN_BLOCK) v += in[i];
     int tot;
-    int r = block_excl_scan(v, sh, &tot);
-    if (i < len) out[i] = r;
+    block_excl_scan(v, sh, &tot);
     if (threadIdx.x == 0) btot[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_totals(int *btot, long long nblocks, const int *d_len, int *d_total) {
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_fin(const int *in, int *out, long long n,
+                                                         const int *d_len, const int *btot,
+                                                         int *d_total) {
     __shared__ int sh[33];
-    int carry = 0;
-    if (d_len) {
-        long long lb = ((long long)*d_len + SCAN_BLOCK - 1) / SCAN_BLOCK;
-        if (lb < nblocks) nblocks = lb;
+    long long b0, b1;
+    scan_range(scan_len(n, d_len), b0, b1);
+    // the sum of the ranges before this block (and of all of them, for the total)
+    int before = 0, all = 0;
+    for (int k = threadIdx.x; k < SCAN_NB; k += SCAN_BLOCK) {
+        int t = btot[k];
+        all += t;
+        if (k < (int)blockIdx.x) before += t;
     }
-    for (long long base = 0; base < nblocks; base += SCAN_BLOCK) {
+    int tb, ta;
+    block_excl_scan(before, sh, &tb);
+    block_excl_scan(all, sh, &ta);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && d_total) *d_total = ta;
+    int carry = tb;
+    for (long long base = b0; base < b1; base += SCAN_BLOCK) {
         long long i = base + threadIdx.x;
-        int v = i < nblocks ? btot[i] : 0;
+        int v = i < b1 ? in[i] : 0;
         int tot;
         int r = block_excl_scan(v, sh, &tot);
-        if (i < nblocks) btot[i] = r + carry;
+        if (i < b1) out[i] = carry + r;
         carry += tot;
     }
-    if (threadIdx.x == 0 && d_total) *d_total = carry;
 }
 
-__global__ void k_scan_add(int *out, long long n, const int *d_len, const int *btot) {
-    long long len = d_len ? (long long)*d_len : n;
-    if (len > n) len = n;
-    long long i = (long long)blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    if (i < len) out[i] += btot[blockIdx.x];
-}
-
-// tmp: block-total scratch of at least scan_tmp_n ints (default: the context's); two scans in
-// flight at once need two.  n never exceeds what rt_create sized scan_tmp_n for.
+// tmp: block-total scratch of at least SCAN_NB ints (default: the context's); two scans in
+// flight at once need two.
 void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
                        int *d_total, cudaStream_t st, int *tmp) {
-    long long nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    if (nb < 1) nb = 1;
     if (!tmp) tmp = c->scan_tmp;
-    k_scan_blocks<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, out, n, d_len, tmp);
-    k_scan_totals<<<1, SCAN_BLOCK, 0, st>>>(tmp, nb, d_len, d_total);
-    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(out, n, d_len, tmp);
+    k_scan_sum<<<SCAN_NB, SCAN_BLOCK, 0, st>>>(in, n, d_len, tmp);
+    k_scan_fin<<<SCAN_NB, SCAN_BLOCK, 0, st>>>(in, out, n, d_len, tmp, d_total);
 }

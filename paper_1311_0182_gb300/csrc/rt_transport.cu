@@ -693,8 +693,20 @@ __global__ void __launch_bounds__(256) k_freeC(DevPtrs P, int fcur, const int *l
 }
 
 // request list: gas slots with empty cones (particle order, slot order), then free packets
-// (grid-stride: a launch sized for the free-packet capacity covers any count)
+// (grid-stride: a launch sized for the free-packet capacity covers any count).  Its first
+// thread also books the hop's request count and checks the capacities (after the request
+// scan and the staging scan).
 __global__ void k_expand(DevPtrs P, const int *lens) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long *cnt = P.cnt;
+        long long nr = lens[2];
+        if (nr > P.F_cap)
+            atomicOr((unsigned long long *)&cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
+        cnt[CNT_NREQ] = nr;
+        cnt[CNT_VIRT] += nr < P.F_cap ? nr : P.F_cap;
+        if (lens[3] > P.ST_cap)
+            atomicOr((unsigned long long *)&cnt[CNT_ERR], (unsigned long long)ERRB_STAGE_CAP);
+    }
     long long nfree = lens[0];
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < P.n + nfree;
          t += (long long)gridDim.x * blockDim.x) {
@@ -1337,7 +1349,7 @@ __global__ void k_hop_counts(DevPtrs P, int nxt, int fnxt, const int *lens,
 }
 
 // bookkeeping of the hop loop (single thread)
-enum { HL_BEGIN = 0, HL_REQ = 1, HL_END = 2, HL_EMIT = 3, HL_TRANSPORT = 4, HL_STEP = 5 };
+enum { HL_BEGIN = 0, HL_END = 2, HL_EMIT = 3, HL_TRANSPORT = 4, HL_STEP = 5 };
 // in_graph: the launch is a node of the step graph, and `handle` the conditional it sets
 // (HL_BEGIN: the buffer switch; HL_END: the hop loop)
 __global__ void k_hop_lens(DevPtrs P, int *lens, int phase, long long arg, int in_graph,
@@ -1349,15 +1361,6 @@ __global__ void k_hop_lens(DevPtrs P, int *lens, int phase, long long arg, int i
         lens[1] = (int)(P.n + lens[0]);
         // in the graph: which of the four copies of the hop (slot and free-packet buffers) runs
         if (in_graph) cudaGraphSetConditional(handle, (unsigned)(cnt[CNT_CUR] | (cnt[CNT_FCUR] << 1)));
-    } else if (phase == HL_REQ) {       // after the request scan: n_req
-        long long nr = lens[2];
-        if (nr > P.F_cap) {
-            atomicOr((unsigned long long *)&cnt[CNT_ERR], (unsigned long long)ERRB_FREE_CAP);
-        }
-        cnt[CNT_NREQ] = nr;
-        cnt[CNT_VIRT] += nr < P.F_cap ? nr : P.F_cap;
-        if (lens[3] > P.ST_cap)
-            atomicOr((unsigned long long *)&cnt[CNT_ERR], (unsigned long long)ERRB_STAGE_CAP);
     } else if (phase == HL_END) {       // after the hop (arg = hop cap)
         long long nr = lens[2];
         lens[0] = (int)(nr < P.F_cap ? nr : P.F_cap);
@@ -1451,7 +1454,7 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     cudaMemsetAsync(P.seg_cnt, 0, sizeof(int) * nkey, s2);
     cudaMemsetAsync(P.seg_fill, 0, sizeof(int) * nkey, s2);
     LAUNCH_ON(s2, KT_FREE_A, 1, (k_freeA<Real><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stcnt)));
-    LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
+    LAUNCH_ON(s2, KT_SCAN, 2, (rt_scan_exclusive(c, H.stcnt, H.stoff, nfr, H.lens, H.lens + 3, s2, c->scan_tmp2)));
     cudaEventRecord(evFree, s2);
     // instances: the common case; with a barrier; with a shared frequency bin (whose instance
     // also takes the barrier test, which is a no-op in boxes without one)
@@ -1467,8 +1470,7 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, false><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
     cudaEventRecord(evA, st);
     cudaStreamWaitEvent(st, evFree, 0);
-    LAUNCH(KT_SCAN, 3, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
-    LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_REQ, 0, 0, 0)));
+    LAUNCH(KT_SCAN, 2, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
     LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
     if (P.shared)
         LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
@@ -1479,7 +1481,7 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     else
         LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
-    LAUNCH_ON(s2, KT_SCAN, 3, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
+    LAUNCH_ON(s2, KT_SCAN, 2, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
     LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
     LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));
     cudaMemsetAsync(H.lens + 4, 0, sizeof(int), s2);
