@@ -143,6 +143,19 @@ void rt_upload_axes() {
 // Resident 256-thread blocks per SM asked of the hop kernels: four (64 registers a thread)
 // for FP32 packets; three for FP64, whose wider values would otherwise spill.
 #define HOP_MINB(Real) (sizeof(Real) == 4 ? 4 : 3)
+// Largest grids (blocks) of the sender side, the virtual particles and the receiver side;
+// each block takes a contiguous chunk of the live items.  Set by a measured sweep on the 64^3
+// HII-region step: fewer, longer-lived blocks than one per 32 items, while still several
+// blocks per SM turn over during a launch.
+#ifndef GRID_A
+#define GRID_A (152 * 16)
+#endif
+#ifndef GRID_V
+#define GRID_V (152 * 32)
+#endif
+#ifndef GRID_B
+#define GRID_B (152 * 8)
+#endif
 
 template <typename Real> struct Slots {
     Real *N, *X, *Y, *Z, *C, *E;
@@ -1465,21 +1478,21 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     else
         LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
     if (P.shared)
-        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, true><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, true><<<rt_blocks(n * 32, tb, GRID_A), tb, 0, st>>>(P, cur)));
     else
-        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, false><<<rt_blocks(n * 32, tb, gb), tb, 0, st>>>(P, cur)));
+        LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, false><<<rt_blocks(n * 32, tb, GRID_A), tb, 0, st>>>(P, cur)));
     cudaEventRecord(evA, st);
     cudaStreamWaitEvent(st, evFree, 0);
     LAUNCH(KT_SCAN, 2, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
     LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
     if (P.shared)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true><<<rt_blocks(P.F_cap * 32, tb, GRID_V), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     else if (P.any_bar)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false><<<rt_blocks(P.F_cap * 32, tb, GRID_V), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     else
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false><<<rt_blocks(P.F_cap * 32, tb, gb), tb, 0, st>>>(
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false><<<rt_blocks(P.F_cap * 32, tb, GRID_V), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     LAUNCH_ON(s2, KT_SCAN, 2, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
     LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
@@ -1488,11 +1501,11 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     cudaStreamWaitEvent(s2, evA, 0);
     LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, H.lens + 4)));
     if (P.shared)
-        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, true><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, true><<<rt_blocks(nkey * NRC, tb, GRID_B), tb, 0, s2>>>(P, cur, H.lens + 4)));
     else if (P.any_bar)
-        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, false><<<rt_blocks(nkey * NRC, tb, GRID_B), tb, 0, s2>>>(P, cur, H.lens + 4)));
     else
-        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false, false><<<rt_blocks(nkey * NRC, tb, 152 * 32), tb, 0, s2>>>(P, cur, H.lens + 4)));
+        LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false, false><<<rt_blocks(nkey * NRC, tb, GRID_B), tb, 0, s2>>>(P, cur, H.lens + 4)));
     cudaEventRecord(evB, s2);
     cudaStreamWaitEvent(st, evB, 0);
     LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, cur ^ 1, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
