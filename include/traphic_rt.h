@@ -84,6 +84,14 @@ typedef struct {
     long long free_cap;   /* capacity of free packets per hop (0: library default) */
     int cell_occupancy;   /* particles per cell of the kNN grids; 0: chosen by timing the
                              neighbour search over 5, 7, 9, 12 and 16 in rt_build_neighbours */
+    int tune_launch;      /* 1: the grid sizes of the three main hop kernels (sender side,
+                             virtual particles, receiver side) are chosen by timing the first
+                             rt_step or rt_transport, which then runs hop by hop from the host
+                             whatever rt_set_graph says; 0: built-in sizes.  Results do not
+                             depend on the choice. */
+    int launch_grid[3];   /* grid sizes (blocks) of those three kernels; 0: built-in or tuned.
+                             Any nonzero entry switches the tuning off (> 0 values are used,
+                             zeros keep the built-in size). */
     int rec_shared_bin;   /* 1: one frequency bin for stellar and recombination photons (Sec.
                              2.2, last paragraph): recombination photons travel in source bin 0
                              and there is no recombination bin (n_freq_src bins in all, so
@@ -254,8 +262,10 @@ rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass,
    packets in a hop, peak active slots in a hop; then summed over the hops of the last
    transport: gas-to-gas contributions, particles with a packet able to move, packets able to
    move, staged free-packet contributions, receiver work-list entries, occupied slots written
-   by the receiver side; then the cell occupancy of the kNN grids in use; out[14..15] are 0 */
-#define RT_NSTATS 16
+   by the receiver side; then the cell occupancy of the kNN grids in use; then the grid sizes
+   (blocks) of the sender side, the virtual particles and the receiver side in use;
+   out[17..19] are 0 */
+#define RT_NSTATS 20
 rt_status rt_get_stats(rt_ctx *ctx, long long *out);
 /* the isotropic cone direction set with n directions (8 or 32), [n * 3] host */
 rt_status rt_axis_set(int n, double *out);

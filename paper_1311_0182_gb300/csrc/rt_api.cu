@@ -280,6 +280,15 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         return RT_ERR_INVALID;
     }
     c->cell_occ = cfg->cell_occupancy > 0 ? cfg->cell_occupancy : 9;
+    // launch sizes of the hop kernels given by the caller: no tuning
+    for (int k = 0; k < 3; ++k) {
+        if (cfg->launch_grid[k] < 0) {
+            delete c;
+            return RT_ERR_INVALID;
+        }
+        c->grid_hop[k] = cfg->launch_grid[k];
+        if (cfg->launch_grid[k] > 0) c->launch_tuned = true;
+    }
     c->grid_tuned = cfg->cell_occupancy > 0;
     long long ncell = 0;
     for (int b = 0; b < n_boxes; ++b) {
@@ -409,6 +418,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         ok = false;
     for (int k = 0; k < 4; ++k)
         if (cudaEventCreateWithFlags(&c->hev[k], cudaEventDisableTiming) != cudaSuccess) ok = false;
+    for (int k = 0; k < 6; ++k)
+        if (cudaEventCreate(&c->tev[k]) != cudaSuccess) ok = false;
     // the stream the step graph is captured on (it never runs work itself)
     if (cudaStreamCreateWithFlags(&c->st_cap, cudaStreamNonBlocking) != cudaSuccess) ok = false;
     if (!ok) {
@@ -468,6 +479,8 @@ extern "C" rt_status rt_destroy(rt_ctx *c) {
     }
     for (int k = 0; k < 4; ++k)
         if (c->hev[k]) cudaEventDestroy(c->hev[k]);
+    for (int k = 0; k < 6; ++k)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return RT_OK;
@@ -758,7 +771,10 @@ extern "C" rt_status rt_step(rt_ctx *c, long long step, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     // the captured step graph, unless kernels are being timed one by one (events cannot sit
     // inside the graph's conditional hop loop) or the hop cap allows no hop
-    if (c->use_graph && c->prof == 0 && c->cfg.hop_cap > 0) return rt_step_graph(c, step, st);
+    // (the first step that tunes the launch sizes runs hop by hop as well)
+    bool tune = c->cfg.tune_launch && !c->launch_tuned;
+    if (!tune && c->use_graph && c->prof == 0 && c->cfg.hop_cap > 0)
+        return rt_step_graph(c, step, st);
     if ((s = rt_run_step_parts(c, 0, step, st))) return s;
     if ((s = rt_run_step_parts(c, 1, step, st))) return s;
     if ((s = rt_emit(c, step, stream))) return s;
@@ -1069,6 +1085,7 @@ extern "C" rt_status rt_get_stats(rt_ctx *c, long long *out) {
     if (!c || !out) return RT_ERR_INVALID;
     for (int k = 0; k < RT_NSTATS; ++k) out[k] = c->stats[k];
     out[13] = c->cell_occ;
+    rt_launch_grids(c, out + 14);
     return RT_OK;
 }
 

@@ -276,6 +276,15 @@ struct rt_ctx {
     long long graph_launch_step[KT_N] = {0}, graph_launch_hop[KT_N] = {0};
     bool capturing = false;            // launches counted into graph_launch_* while capturing
     bool in_hop_body = false;
+    // grid sizes (blocks) of the sender side, the virtual particles and the receiver side
+    // (0: the built-in ones), chosen by timing the first hop loop when cfg.tune_launch is set:
+    // its hops cycle through the candidates, each of the three kernels is timed with events,
+    // and the candidate with the least time per item wins
+    int grid_hop[3] = {0, 0, 0};
+    bool launch_tuned = false;
+    bool tuning = false;
+    double tune_ms[3][4] = {}, tune_items[3][4] = {};
+    cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double *src_emit = nullptr;   // device [nb]: source photons of one step per box
     std::vector<double> src_emit_h, box_NH_h;
 };
@@ -293,6 +302,8 @@ rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st
 // one whole step through the captured graph (captured again when its parameters changed)
 rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st);
 void rt_graph_destroy(rt_ctx *c);
+// the grid sizes (blocks) of the sender side, the virtual particles and the receiver side
+void rt_launch_grids(const rt_ctx *c, long long out[3]);
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);
 void rt_host_axis_set(int n, double *out);

@@ -40,7 +40,7 @@ class Config(C.Structure):
         ("seed", C.c_ulonglong), ("hop_cap", C.c_int), ("sub_cap", C.c_int),
         ("cool_flags", C.c_int), ("T_floor", C.c_double), ("eps_rr_fixed", C.c_double),
         ("sigma_rec", C.c_double), ("free_cap", C.c_longlong), ("cell_occupancy", C.c_int),
-        ("rec_shared_bin", C.c_int),
+        ("tune_launch", C.c_int), ("launch_grid", C.c_int * 3), ("rec_shared_bin", C.c_int),
     ]
 
 
@@ -110,6 +110,8 @@ def make_config(p: dict) -> Config:
         hop_cap=p["hop_cap"], sub_cap=p["sub_cap"], cool_flags=p["cool_flags"],
         T_floor=p["T_floor"], eps_rr_fixed=p["eps_rr_fixed"], sigma_rec=p["sigma_rec"],
         free_cap=p.get("free_cap", 0), cell_occupancy=p.get("cell_occupancy", 0),
+        tune_launch=p.get("tune_launch", 0),
+        launch_grid=(C.c_int * 3)(*p.get("launch_grid", (0, 0, 0))),
         rec_shared_bin=p.get("rec_shared_bin", 0))
 
 
@@ -380,11 +382,12 @@ class Context:
                 for k in range(32) if names[k] and la[k] > 0}
 
     def stats(self):
-        out = (C.c_longlong * 16)()
+        out = (C.c_longlong * 20)()
         self._check(self.L.rt_get_stats(self.h, out), "rt_get_stats")
         keys = ["hops", "virtual", "escaped_virtual", "subcycles", "floor_hits", "peak_free",
                 "peak_active", "gas_contrib", "senders", "moving_packets", "staged_contrib",
-                "receiver_groups", "receiver_outputs", "cell_occupancy"]
+                "receiver_groups", "receiver_outputs", "cell_occupancy", "grid_send",
+                "grid_virtual", "grid_receive"]
         return dict(zip(keys, list(out)))
 
 

@@ -384,10 +384,12 @@ def _same_results(a, b):
     assert np.array_equal(a.budget(), b.budget())
     for x, y in zip(a.deposits(), b.deposits()):
         assert np.array_equal(x, y)
-    # (the kNN grid occupancy is chosen by timing and may differ; results do not depend on it)
+    # (the kNN grid occupancy and the launch sizes are chosen by timing and may differ; results
+    # do not depend on them)
     sta, stb = a.stats(), b.stats()
-    sta.pop("cell_occupancy")
-    stb.pop("cell_occupancy")
+    for k in ("cell_occupancy", "grid_send", "grid_virtual", "grid_receive"):
+        sta.pop(k)
+        stb.pop(k)
     assert sta == stb
 
 
@@ -438,6 +440,25 @@ def test_step_graph_at_the_hop_cap_and_after_a_barrier_change():
         a.step(step)
         b.step(step)
         _same_results(a, b)
+
+
+def test_launch_size_tuning_changes_nothing_but_time():
+    """With tune_launch the first step times the sender side, the virtual particles and the
+    receiver side on grids of 152 x {8, 16, 32, 64} blocks, hop by hop, and keeps per kernel
+    the least time per item; sizes given in the configuration switch the tuning off.  The
+    results agree bit for bit whatever the sizes."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg2(n_side=20)
+    a = rt.context_for(wl, tune_launch=1)
+    b = rt.context_for(wl, tune_launch=0, launch_grid=(152, 304, 456))
+    for step in range(3):
+        a.step(step)
+        b.step(step)
+        _same_results(a, b)
+    sa, sb = a.stats(), b.stats()
+    for k in ("grid_send", "grid_virtual", "grid_receive"):
+        assert sa[k] in (1216, 2432, 4864, 9728)
+    assert (sb["grid_send"], sb["grid_virtual"], sb["grid_receive"]) == (152, 304, 456)
 
 
 def test_free_packet_capacity_is_an_error_not_a_fault():
