@@ -44,6 +44,10 @@ def parse():
                     help="also time the original (emission-cone) recombination implementation")
     ap.add_argument("--shared", action="store_true",
                     help="also time one frequency bin shared by stellar and recombination photons")
+    ap.add_argument("--on-the-spot", action="store_true",
+                    help="also time the same workload without recombination transport (case B "
+                         "on the spot), and with it in a shared bin against on the spot with one "
+                         "bin fewer")
     return ap.parse_args()
 
 
@@ -237,6 +241,14 @@ def run_ours(args):
         # on the same workload and precision
         out["shared_frequency_bin"] = fp64_path(
             args, stream, transport_fp32=int(args.precision == "fp32"), rec_shared_bin=1)
+    if args.on_the_spot:
+        # the cost of transporting recombination radiation (Sec. 1, Sec. 2.2): on the spot,
+        # with the same slots (a recombination bin that stays empty) and with the shared-bin
+        # layout (no recombination bin)
+        fp = int(args.precision == "fp32")
+        out["on_the_spot"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1)
+        out["on_the_spot_shared_layout"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1,
+                                                     rec_shared_bin=1)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
