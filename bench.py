@@ -44,6 +44,9 @@ def parse():
                     help="also time the original (emission-cone) recombination implementation")
     ap.add_argument("--shared", action="store_true",
                     help="also time one frequency bin shared by stellar and recombination photons")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time workload 4: 512 independent boxes of uneven size in the same "
+                         "launches, FP32 transport and all FP64")
     ap.add_argument("--on-the-spot", action="store_true",
                     help="also time the same workload without recombination transport (case B "
                          "on the spot), and with it in a shared bin against on the spot with one "
@@ -249,6 +252,8 @@ def run_ours(args):
         out["on_the_spot"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1)
         out["on_the_spot_shared_layout"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1,
                                                      rec_shared_bin=1)
+    if args.batched:
+        out["batched_boxes"] = batched(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
@@ -354,6 +359,44 @@ def fp64_path(args, stream, **over):
     return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
             "ms_per_step": ms / steps, "steps": steps, "packet_storage_bytes": slot_bytes,
             "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
+
+
+def batched(args, stream, warmup=2, steps=3):
+    """Workload 4: 512 independent boxes of 8^3 to 40^3 particles (log-uniform count),
+    lognormal densities, one central source each, T evolving, 8 cones, advanced together in
+    the same launches (the step graph), FP32 transport and all FP64."""
+    import torch
+    from paper_1311_0182_gb300 import rt, workloads as W
+    wl = W.cfg4()
+    n = int(wl["box_off"][-1])
+    out = {"workload": "512 boxes, 8^3-40^3 particles each (log-uniform), lognormal density, "
+                       "central source, 8 cones, 2 frequency bins, T evolving",
+           "particles": n, "boxes": len(wl["box_L"]), "warmup": warmup, "steps": steps}
+    for fp in (1, 0):
+        ctx = rt.Context(wl, stream=stream, transport_fp32=fp)
+        with torch.cuda.stream(stream):
+            ctx.load_workload(wl)
+            ctx.build_neighbours()
+            for s in range(warmup):
+                ctx.step(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for s in range(warmup, warmup + steps):
+                ctx.step(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        st = ctx.stats()
+        b = ctx.budget()
+        out["fp32" if fp else "fp64"] = {
+            "value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
+            "ms_per_step": ms / steps, "hops_last_step": st["hops"],
+            "virtual_last_step": st["virtual"],
+            "worst_box_budget_closure": float(np.max(np.abs(b[:, 0] - b[:, 1:].sum(1)) / b[:, 0]))}
+        ctx.close()
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def precision_errors(args, stream, steps=10):
