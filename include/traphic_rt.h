@@ -243,6 +243,20 @@ rt_status rt_get_cone_masks_noalloc(rt_ctx *ctx, unsigned *mask, int where, void
 /* held packets: 6 fields [6 * n * S] (N, Mx, My, Mz, C = N*clock, E = N*eps), physical units */
 rt_status rt_get_slots(rt_ctx *ctx, double *f, int where, void *stream);
 rt_status rt_set_slots(rt_ctx *ctx, const double *f, int where, void *stream);
+/* rt_save_state -- checkpoint between steps (the paper has none; GADGET snapshots are implied):
+   what a step carries into the next one, byte for byte -- the packets held by the particles
+   (slots with their occupancy and activity words, and the cross-section sums of a shared bin),
+   x_HI, T, the recombination photons waiting to be emitted and their energy, and the photon
+   budget.  With buf NULL, *bytes receives the size needed; otherwise buf (host, *bytes long)
+   receives the checkpoint and *bytes its size.  Waits for all work on the device.  Errors:
+   RT_ERR_STATE before rt_build_neighbours, RT_ERR_INVALID (buffer too small), RT_ERR_CUDA.
+   rt_load_state -- restore a checkpoint into a context of the same configuration and particle
+   set whose neighbours are built (a fresh context built from the same inputs gives the same
+   neighbour lists, rotations and random streams, so a resumed run repeats an uninterrupted one
+   bit for bit).  Errors: RT_ERR_INVALID (not a checkpoint, another configuration, short
+   buffer), RT_ERR_STATE, RT_ERR_CUDA. */
+rt_status rt_save_state(rt_ctx *ctx, void *buf, size_t *bytes);
+rt_status rt_load_state(rt_ctx *ctx, const void *buf, size_t bytes);
 /* rt_get_shared_sigma / rt_set_shared_sigma -- with rec_shared_bin (Sec. 2.2, last paragraph:
    one bin for stellar and recombination photons, cross-sections averaged on merging): the
    cross-section sum G = sum N sigma (cm^2 x photons) of each held packet of bin 0, [n * n_rc],

@@ -816,6 +816,101 @@ extern "C" rt_status rt_get_budget(rt_ctx *c, double *out, void *stream) {
     return copy_out(c, out, c->d.tally, sizeof(double) * 4 * c->d.nb, RT_HOST, (cudaStream_t)stream);
 }
 
+// ---- checkpoint / resume ------------------------------------------------------------------
+// A checkpoint taken between steps holds what a step carries into the next one, byte for byte:
+// the packets held by the particles (the current slot buffer with its occupancy and activity
+// words, and the cross-section sums of a shared bin), the particle state (x_HI, T, and the
+// recombination photons and their energy waiting to be emitted), the photon budget and the
+// fixed-point escape word.  Everything else (rotations, deposits, bitmaps, free packets) is
+// rebuilt or cleared by the next step.  The header records the sizes it was taken with.
+struct CkptHeader {
+    char magic[8];
+    int version, fp32, shared, nf, S, nrc, nb, pad;
+    long long n, bytes;
+};
+
+static const char CKPT_MAGIC[8] = {'T', 'R', 'P', 'H', 'C', 'K', 'P', '1'};
+
+struct CkptPart {
+    void *dev;
+    size_t bytes;
+};
+
+static std::vector<CkptPart> ckpt_parts(rt_ctx *c) {
+    DevPtrs &P = c->d;
+    size_t R = P.fp32 ? 4 : 8, nslot = (size_t)P.n * P.S, nkey = (size_t)P.n * P.nf;
+    std::vector<CkptPart> v;
+    for (int f = 0; f < 6; ++f) v.push_back({P.sl[c->cur][f], R * nslot});
+    v.push_back({P.occ[c->cur], sizeof(unsigned) * nkey});
+    v.push_back({P.act[c->cur], sizeof(unsigned) * nkey});
+    if (P.shared) v.push_back({P.slG[c->cur], R * (size_t)P.n * P.nrc});
+    for (double *a : {P.xHI, P.T, P.Nrec, P.epsrec}) v.push_back({a, sizeof(double) * (size_t)P.n});
+    v.push_back({P.tally, sizeof(double) * 4 * (size_t)P.nb});
+    v.push_back({P.esc_fx, sizeof(unsigned long long) * (size_t)P.nb});
+    return v;
+}
+
+static CkptHeader ckpt_header(rt_ctx *c) {
+    DevPtrs &P = c->d;
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = 1;
+    h.fp32 = P.fp32; h.shared = P.shared; h.nf = P.nf; h.S = P.S; h.nrc = P.nrc; h.nb = P.nb;
+    h.n = P.n;
+    size_t b = sizeof(CkptHeader);
+    for (auto &q : ckpt_parts(c)) b += q.bytes;
+    h.bytes = (long long)b;
+    return h;
+}
+
+extern "C" rt_status rt_save_state(rt_ctx *c, void *buf, size_t *bytes) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    if (!bytes) return RT_ERR_INVALID;
+    CkptHeader h = ckpt_header(c);
+    if (!buf) {
+        *bytes = (size_t)h.bytes;
+        return RT_OK;
+    }
+    if (*bytes < (size_t)h.bytes)
+        return rt_fail(c, RT_ERR_INVALID, "rt_save_state: buffer of " + std::to_string(*bytes) +
+                                              " bytes, " + std::to_string(h.bytes) + " needed");
+    // every queued step on every stream has finished before the copies
+    if ((s = rt_cuda_check(c, cudaDeviceSynchronize(), "save state"))) return s;
+    char *o = (char *)buf;
+    memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    for (auto &q : ckpt_parts(c)) {
+        if ((s = rt_cuda_check(c, cudaMemcpy(o, q.dev, q.bytes, cudaMemcpyDeviceToHost), "save state")))
+            return s;
+        o += q.bytes;
+    }
+    *bytes = (size_t)h.bytes;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_load_state(rt_ctx *c, const void *buf, size_t bytes) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    if (!buf || bytes < sizeof(CkptHeader)) return RT_ERR_INVALID;
+    CkptHeader h = ckpt_header(c), g;
+    memcpy(&g, buf, sizeof(g));
+    if (memcmp(g.magic, CKPT_MAGIC, 8) != 0 || g.version != 1)
+        return rt_fail(c, RT_ERR_INVALID, "rt_load_state: not a checkpoint of this library");
+    if (g.fp32 != h.fp32 || g.shared != h.shared || g.nf != h.nf || g.S != h.S ||
+        g.nrc != h.nrc || g.nb != h.nb || g.n != h.n || g.bytes != h.bytes || bytes < (size_t)h.bytes)
+        return rt_fail(c, RT_ERR_INVALID, "rt_load_state: checkpoint of another configuration");
+    if ((s = rt_cuda_check(c, cudaDeviceSynchronize(), "load state"))) return s;
+    const char *o = (const char *)buf + sizeof(CkptHeader);
+    for (auto &q : ckpt_parts(c)) {
+        if ((s = rt_cuda_check(c, cudaMemcpy(q.dev, o, q.bytes, cudaMemcpyHostToDevice), "load state")))
+            return s;
+        o += q.bytes;
+    }
+    return RT_OK;
+}
+
 extern "C" rt_status rt_get_neighbours(rt_ctx *c, int *nbr, long long *h2, int *src_nbr,
                                        long long *src_h2, int where, void *stream) {
     rt_status s = need_built(c);

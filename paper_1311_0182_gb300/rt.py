@@ -23,7 +23,8 @@ SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_
            "rt_set_slots",
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
            "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier",
-           "rt_set_graph", "rt_get_shared_sigma", "rt_set_shared_sigma"]
+           "rt_set_graph", "rt_get_shared_sigma", "rt_set_shared_sigma", "rt_save_state",
+           "rt_load_state"]
 
 
 class RTError(RuntimeError):
@@ -86,6 +87,8 @@ def load(build_if_missing: bool = False):
     L.rt_get_slots.argtypes = [vp, vp, i, vp]
     L.rt_set_slots.argtypes = [vp, vp, i, vp]
     L.rt_get_shared_sigma.argtypes = [vp, vp, i, vp]
+    L.rt_save_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.rt_load_state.argtypes = [vp, vp, C.c_size_t]
     L.rt_set_shared_sigma.argtypes = [vp, vp, i, vp]
     L.rt_get_deposits.argtypes = [vp, vp, vp, vp, i, vp]
     L.rt_get_stats.argtypes = [vp, vp]
@@ -321,6 +324,21 @@ class Context:
         f = np.ascontiguousarray(f, dtype=np.float64)
         self._check(self.L.rt_set_slots(self.h, f.ctypes.data, RT_HOST, self._s()),
                     "rt_set_slots")
+
+    def save_state(self) -> bytes:
+        """Checkpoint between steps (rt_save_state): the held packets, particle state and budget."""
+        n = C.c_size_t(0)
+        self._check(self.L.rt_save_state(self.h, None, C.byref(n)), "rt_save_state")
+        buf = (C.c_char * n.value)()
+        self._check(self.L.rt_save_state(self.h, C.cast(buf, C.c_void_p), C.byref(n)),
+                    "rt_save_state")
+        return bytes(buf)
+
+    def load_state(self, data: bytes):
+        """Restore a checkpoint of a context with the same configuration and particles."""
+        buf = C.create_string_buffer(data, len(data))
+        self._check(self.L.rt_load_state(self.h, C.cast(buf, C.c_void_p), len(data)),
+                    "rt_load_state")
 
     def shared_sigma(self):
         """Shared frequency bin: the cross-section sums N sigma of bin 0's packets, [n, n_rc]."""

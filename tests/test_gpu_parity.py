@@ -461,6 +461,38 @@ def test_launch_size_tuning_changes_nothing_but_time():
     assert (sb["grid_send"], sb["grid_virtual"], sb["grid_receive"]) == (152, 304, 456)
 
 
+@pytest.mark.parametrize("case", ["fp64", "fp32", "shared_clock_limited"])
+def test_checkpoint_resume_repeats_the_run_bit_for_bit(case):
+    """rt_save_state after two steps, rt_load_state into a fresh context built from the same
+    inputs, two more steps: the same bits as four uninterrupted steps (state, budget,
+    deposits, held packets).  With clock-limited steps packets are held across the checkpoint.
+    A checkpoint of another configuration is refused."""
+    from paper_1311_0182_gb300 import rt
+    kw = {"fp64": dict(transport_fp32=0), "fp32": dict(transport_fp32=1),
+          "shared_clock_limited": dict(transport_fp32=1, rec_shared_bin=1, dt=0.01 * W.MYR,
+                                       dt_em=0.01 * W.MYR)}[case]
+    wl = W.cfg2(n_side=16, **kw)
+    a = rt.context_for(wl)
+    b = rt.context_for(wl)
+    for step in range(2):
+        a.step(step)
+        b.step(step)
+    ck = b.save_state()
+    b.close()
+    c = rt.context_for(wl)
+    c.load_state(ck)
+    if case == "shared_clock_limited":
+        assert np.count_nonzero(c.slots()[0]) > 1000 and np.count_nonzero(c.shared_sigma()) > 1000
+    for step in range(2, 4):
+        a.step(step)
+        c.step(step)
+    _same_results(a, c)
+    assert np.array_equal(a.slots(), c.slots())
+    other = rt.context_for(W.cfg2(n_side=16, transport_fp32=1 - kw["transport_fp32"]))
+    with pytest.raises(rt.RTError):
+        other.load_state(ck)
+
+
 def test_free_packet_capacity_is_an_error_not_a_fault():
     from paper_1311_0182_gb300 import rt
     wl = W.cfg1(free_cap=300)
