@@ -203,7 +203,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
         (cfg->n_rc != 8 && cfg->n_rc != 32) || (cfg->n_ec != 8 && cfg->n_ec != 32) ||
         !(cfg->dt > 0.0) || !(cfg->dt_em > 0.0) || cfg->hop_cap < 1 || cfg->sub_cap < 1 ||
         cfg->rec_mode < 0 || cfg->rec_mode > 3 || cfg->rec_shared_bin < 0 ||
-        cfg->rec_shared_bin > 1 || (cfg->rec_shared_bin && cfg->n_freq_src < 1))
+        cfg->rec_shared_bin > 1 || (cfg->rec_shared_bin && cfg->n_freq_src < 1) ||
+        cfg->launch_grid[0] < 0 || cfg->launch_grid[1] < 0 || cfg->launch_grid[2] < 0 ||
+        cfg->cell_occupancy < 0)
         return RT_ERR_INVALID;
     if (box_off[0] != 0) return RT_ERR_INVALID;
     for (int b = 0; b < n_boxes; ++b) {
@@ -282,10 +284,6 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     c->cell_occ = cfg->cell_occupancy > 0 ? cfg->cell_occupancy : 9;
     // launch sizes of the hop kernels given by the caller: no tuning
     for (int k = 0; k < 3; ++k) {
-        if (cfg->launch_grid[k] < 0) {
-            delete c;
-            return RT_ERR_INVALID;
-        }
         c->grid_hop[k] = cfg->launch_grid[k];
         if (cfg->launch_grid[k] > 0) c->launch_tuned = true;
     }

@@ -59,6 +59,18 @@ def test_invalid_configuration_is_rejected_without_touching_a_gpu(lib):
     assert e.value.status == 5
 
 
+def test_options_are_validated_before_any_device_work(lib):
+    """A shared frequency bin needs a source bin to share; launch sizes and the kNN grid
+    occupancy cannot be negative; the flags are 0 or 1."""
+    from paper_1311_0182_gb300 import rt, workloads as W
+    wl = W.cfg1()
+    for bad in (dict(rec_shared_bin=1, n_freq_src=0), dict(rec_shared_bin=2),
+                dict(launch_grid=(0, -1, 0)), dict(cell_occupancy=-3), dict(rec_mode=4)):
+        with pytest.raises(rt.RTError) as e:
+            rt.Context(dict(wl, params=dict(wl["params"], **bad)))
+        assert e.value.status == 1, bad
+
+
 def test_box_too_large_for_the_knn_keys_is_rejected(lib):
     """The kNN search packs a box-local index into 22 bits: a box of 2^22 particles is refused
     before any device work."""
