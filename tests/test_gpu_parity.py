@@ -668,6 +668,51 @@ def test_full_size_on_a_non_blocking_stream():
     assert np.array_equal(g.state()["x_HI"], d.state()["x_HI"])
 
 
+@pytest.mark.parametrize("fp32", [1, 0])
+def test_full_size_chemistry_sampled_against_the_oracle(fp32):
+    """The timed 64^3 workload in the bench's launch sizes: after a step's transport, the
+    chemistry of 300 sampled particles (200 at random, 100 with the most absorptions), computed
+    one by one by the oracle from the same absorbed photons and energy and the same x_HI and T,
+    matches the GPU's.  FP64 path: to 1e-9.  Mixed path, whose rate fits run in FP32: x_HI
+    and T to 1e-4; the recombination photons to emit (an integral of the difference
+    alpha_A - alpha_B of two FP32 fits times the electron density) to 1e-3, the bar of the fields
+    they feed.  Both paths compare those photons per particle where the gas is at least 1 %
+    ionised, and summed over the sample: in nearly neutral gas they scale with 1 - x_HI, which
+    x_HI to a relative tolerance does not fix (the summed inputs already differ in their last
+    bits)."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg2(transport_fp32=fp32)
+    g = rt.context_for(wl)
+    g.step(0)                        # recombination photons to emit in the next step
+    g.assign_cones(1)
+    g.merge()
+    g.emit(1)
+    g.transport(1)
+    before = g.state()
+    a, e, _ = g.deposits()
+    g.chemistry()
+    after = g.state()
+    phot, heat = a.sum(1), e.sum(1)
+    rng = np.random.default_rng(4)
+    idx = np.concatenate([rng.choice(g.n, 200, replace=False), np.argsort(phot)[-100:]])
+    assert phot[idx].max() > 0
+    tol = 1e-4 if fp32 else 1e-9
+    tol_rec = 1e-3 if fp32 else 1e-9
+    sum_g = sum_o = 0.0
+    for i in idx:
+        x, T, nrec, _, _ = oracle.chem_particle(wl["params"], wl["n_H"][i], wl["N_H"][i],
+                                                phot[i], heat[i], before["x_HI"][i],
+                                                before["T"][i])
+        xg, Tg, ng = after["x_HI"][i], after["T"][i], after["N_rec"][i]
+        assert abs(xg - x) <= max(tol * x, 1e-7 if x < 1e-4 else 0.0), (i, xg, x)
+        assert abs(Tg - T) <= tol * T, (i, Tg, T)
+        if 1.0 - x > 0.01:
+            assert abs(ng - nrec) <= tol_rec * max(nrec, 1e-300) + 1e-300, (i, ng, nrec)
+        sum_g += ng
+        sum_o += nrec
+    assert sum_o > 0 and abs(sum_g - sum_o) <= tol_rec * sum_o
+
+
 def test_app_a_convergence_with_resolution_and_time_step():
     """App. A: the Stromgren sphere with transported recombination radiation converges with
     particle number and RT time step.  After one t_rec, the I-fronts of 32^3 and 64^3 runs, and
