@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="also time workload 4: 512 independent boxes of uneven size in the same "
                          "launches, FP32 transport and all FP64")
+    ap.add_argument("--paper-workloads", action="store_true",
+                    help="also time workload 3 (128^3 with a dense clump) and workload 5 (256^3 "
+                         "clustered volume, 256 sources), FP32 transport")
     ap.add_argument("--on-the-spot", action="store_true",
                     help="also time the same workload without recombination transport (case B "
                          "on the spot), and with it in a shared bin against on the spot with one "
@@ -254,6 +257,8 @@ def run_ours(args):
                                                      rec_shared_bin=1)
     if args.batched:
         out["batched_boxes"] = batched(args, stream)
+    if args.paper_workloads:
+        out["paper_workloads"] = paper_workloads(stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
@@ -396,6 +401,43 @@ def batched(args, stream, warmup=2, steps=3):
             "worst_box_budget_closure": float(np.max(np.abs(b[:, 0] - b[:, 1:].sum(1)) / b[:, 0]))}
         ctx.close()
     out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def paper_workloads(stream, warmup=1, steps=2):
+    """Workload 3 (128^3 equal-mass particles with a clump 200x denser, 5 kpc from a
+    3e51 s^-1 source; 8 cones, grey bin, 0.1 Myr steps) and workload 5 (256^3 particles sampled
+    from a lognormal field, 256 sources in its densest 1 %; 8 cones, 1 Myr steps), FP32
+    transport, from their initial states."""
+    import torch
+    from paper_1311_0182_gb300 import rt, workloads as W
+    out = {}
+    for name, make in (("workload3_clump_128^3", W.cfg3), ("workload5_clustered_256^3", W.cfg5)):
+        wl = make(transport_fp32=1)
+        n = int(wl["box_off"][-1])
+        ctx = rt.Context(wl, stream=stream)
+        with torch.cuda.stream(stream):
+            ctx.load_workload(wl)
+            ctx.build_neighbours()
+            for s in range(warmup):
+                ctx.step(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for s in range(warmup, warmup + steps):
+                ctx.step(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        st = ctx.stats()
+        b = ctx.budget()
+        out[name] = {"particles": n, "sources": len(wl["src_box"]), "warmup": warmup,
+                     "steps": steps, "value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
+                     "ms_per_step": ms / steps, "hops_last_step": st["hops"],
+                     "virtual_last_step": st["virtual"], "cell_occupancy": st["cell_occupancy"],
+                     "budget_closure": float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])}
+        ctx.close()
+        del wl
     return out
 
 

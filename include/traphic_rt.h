@@ -42,7 +42,10 @@ typedef enum {
     RT_ERR_OOM = 2,       /* device allocation failed */
     RT_ERR_CUDA = 3,      /* a CUDA runtime call failed */
     RT_ERR_HOP_LIMIT = 4, /* hop loop reached hop_cap; unfinished free packets counted escaped */
-    RT_ERR_KNN = 5,       /* a box holds fewer than n_ngb + 1 particles */
+    RT_ERR_KNN = 5,       /* a box holds fewer than n_ngb + 1 particles, or (in a box of more
+                             than 2^22 particles) an n_ngb-th neighbour lies farther than the
+                             kNN keys order exactly: 2^20 / sqrt(3) of the box's 2^20
+                             quantisation cells */
     RT_ERR_CAPACITY = 6,  /* more free packets (sources + virtual particles) in a hop than free_cap */
     RT_ERR_STATE = 7,     /* call out of order, e.g. rt_transport before rt_build_neighbours */
     RT_ERR_RANGE = 8      /* a virtual-particle deposit overflowed its fixed-point accumulator */
@@ -104,7 +107,7 @@ typedef struct {
    ranges are box_off[0..n_boxes] (host, box_off[0] = 0) with side lengths box_L (host, cm),
    and n_src sources.  Sizes only: particle and source data come with rt_set_particles and
    rt_set_sources.  On success *out owns the allocations.  Limits: a box holds at most
-   2^22 - 1 particles, all boxes together fewer than 2^27.  Errors: RT_ERR_INVALID (also
+   2^24 particles, all boxes together fewer than 2^27.  Errors: RT_ERR_INVALID (also
    beyond those limits), RT_ERR_KNN, RT_ERR_OOM, RT_ERR_CUDA (*out is NULL). */
 rt_status rt_create(const rt_config *cfg, int n_boxes, const long long *box_off,
                     const double *box_L, int n_src, rt_ctx **out);

@@ -211,7 +211,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     for (int b = 0; b < n_boxes; ++b) {
         if (box_off[b + 1] < box_off[b] + cfg->n_ngb + 1) return RT_ERR_KNN;
         // the kNN search packs a box-local index into 22 bits
-        if (box_off[b + 1] - box_off[b] >= (1ll << 22)) return RT_ERR_INVALID;
+        if (box_off[b + 1] - box_off[b] > (1ll << 24)) return RT_ERR_INVALID;
         if (!(box_L[b] > 0.0)) return RT_ERR_INVALID;
     }
     long long n = box_off[n_boxes];
@@ -711,7 +711,9 @@ extern "C" rt_status rt_build_neighbours(rt_ctx *c, void *stream) {
     cudaMemcpyAsync(&err, &c->d.cnt[CNT_ERR], sizeof(long long), cudaMemcpyDeviceToHost, st);
     s = rt_cuda_check(c, cudaStreamSynchronize(st), "neighbour build");
     if (s) return s;
-    if (err & ERRB_KNN) return rt_fail(c, RT_ERR_KNN, "a box holds too few particles");
+    if (err & ERRB_KNN)
+        return rt_fail(c, RT_ERR_KNN, "a box holds too few particles, or a neighbour lies "
+                                      "beyond the kNN key range");
     c->built = true;
     return RT_OK;
 }

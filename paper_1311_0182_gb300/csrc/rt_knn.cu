@@ -100,6 +100,7 @@ __device__ __forceinline__ BoxGrid box_grid(const DevPtrs &P, int b) {
     g.coff = P.grid.coff[b];
     g.start = P.grid.start;
     g.tab = P.grid.tab;
+    g.ib = knn_index_bits(P.box_off[b + 1] - P.box_off[b]);
     g.items = P.grid.items;
     return g;
 }

@@ -8,21 +8,30 @@
 // be nearer; when the k-th distance still reaches beyond that block, growing shells of cells
 // follow until it is below the distance to the outside of the visited block.
 //
-// A pair is one 64-bit key, d2 * 2^22 + index: quantised offsets are below 2^20 per axis, so
-// d2 < 3 * 2^40 < 2^42, and a box holds fewer than 2^22 particles (checked when the context
-// is created).  Key order is the (d2, index) order, and one compare or shuffle pair moves it.
+// A pair is one 64-bit key, d2 * 2^ib + index, with ib index bits per box: 22 for a box of up
+// to 2^22 particles, 24 up to 2^24 (the most a box may hold, checked when the context is
+// created).  Quantised offsets are below 2^20 per axis, so d2 < 3 * 2^40 < 2^42: with 22 index
+// bits d2 always fits.  With 24, d2 is saturated at 2^40 - 2, which only points farther apart
+// than 2^20 / sqrt(3) of the box's 2^20 cells reach; a search whose k-th neighbour is that far
+// reports failure instead of a possibly wrong order.  Key order is the (d2, index) order, and
+// one compare or shuffle pair moves it.
 #pragma once
 #include "rt_internal.cuh"
 
 #define KNN_INF 0x7fffffffffffffffll
-#define KNN_IDX_BITS 22
-#define KNN_IDX_MASK ((1ull << KNN_IDX_BITS) - 1ull)
+#define KNN_IB_SMALL 22        // index bits of a box of up to 2^22 particles
+#define KNN_IB_LARGE 24        // index bits of a larger box (up to 2^24 particles)
 #define KNN_KEY_NONE 0xffffffffffffffffull
 // merge by insertion when at most this many candidates of a batch pass the k-th key
 #define KNN_INSERT_MAX 16
 
-__device__ __forceinline__ unsigned long long knn_key(long long d2, int idx) {
-    return ((unsigned long long)d2 << KNN_IDX_BITS) | (unsigned long long)idx;
+// the largest d2 a key with ib index bits holds
+__device__ __forceinline__ long long knn_d2max(int ib) { return (1ll << (64 - ib)) - 2; }
+
+__device__ __forceinline__ unsigned long long knn_key(long long d2, int idx, int ib) {
+    long long m = knn_d2max(ib);
+    if (d2 > m) d2 = m;
+    return ((unsigned long long)d2 << ib) | (unsigned long long)idx;
 }
 
 // bitonic sort (ascending) of one key per lane across the warp
@@ -77,7 +86,12 @@ struct BoxGrid {
     const int *start;
     const int4 *items;
     const int *tab;           // the offset table (device)
+    int ib;                   // index bits of the keys (KNN_IB_SMALL or KNN_IB_LARGE)
 };
+
+__device__ __forceinline__ int knn_index_bits(long long box_particles) {
+    return box_particles > (1ll << KNN_IB_SMALL) ? KNN_IB_LARGE : KNN_IB_SMALL;
+}
 
 __device__ __forceinline__ int cell_coord(int v, int cs, int G) {
     int c = v / cs;
@@ -141,7 +155,7 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
         unsigned long long ck = KNN_KEY_NONE;
         if (it.w >= 0 && it.w != exclude) {
             long long dx = it.x - qx, dy = it.y - qy, dz = it.z - qz;
-            ck = knn_key(dx * dx + dy * dy + dz * dz, it.w);
+            ck = knn_key(dx * dx + dy * dy + dz * dz, it.w, g.ib);
         }
         bool pass = ck < kth && ck <= bkey;
         unsigned m = __ballot_sync(FULLMASK, pass);
@@ -179,7 +193,7 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
         int side = 2 * r + 1;
         int ncol = side * side;
         // cells farther than the current k-th distance (or the bound) cannot help
-        long long prune = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> KNN_IDX_BITS);
+        long long prune = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> g.ib);
         if (bound < prune) prune = bound;
         for (int cb = 0; cb < ncol; cb += 32) {
             int col = cb + (threadIdx.x & 31);
@@ -240,7 +254,7 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
             }
         }
         if (b < 0) break;
-        if (kth != KNN_KEY_NONE && (long long)(kth >> KNN_IDX_BITS) < b * b) break;
+        if (kth != KNN_KEY_NONE && (long long)(kth >> g.ib) < b * b) break;
     }
 }
 
@@ -249,13 +263,15 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
 // `bound` is an upper bound on the squared distance of the kn-th neighbour (KNN_INF when none
 // is known): points and cells beyond it are skipped, which leaves the result unchanged.
 // sdelta: 32 ints of shared memory owned by the calling warp.
-// Returns false when the box holds fewer than kn candidates.
+// Returns false when the box holds fewer than kn candidates, or when the kn-th distance
+// saturated the key (the order among the farthest candidates is then not certain).
 __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
                                 long long &out_d2, int &out_idx, int *sdelta,
                                 long long bound = KNN_INF) {
     unsigned long long t = KNN_KEY_NONE, kth = KNN_KEY_NONE;
-    unsigned long long bkey = bound >= (1ll << 42) ? KNN_KEY_NONE - 1ull
-                                                   : knn_key(bound, (int)KNN_IDX_MASK);
+    const int ib = g.ib;
+    unsigned long long bkey = bound >= knn_d2max(ib) ? KNN_KEY_NONE - 1ull
+                                                     : knn_key(bound, (1 << ib) - 1, ib);
     int G = g.G, cs = g.cs;
     int cx = cell_coord(qx, cs, G), cy = cell_coord(qy, cs, G), cz = cell_coord(qz, cs, G);
     const long long cs2 = (long long)cs * cs;
@@ -264,7 +280,7 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
     bool done = false;
     for (int e0 = 0; e0 < KNN_TAB_N; e0 += 32) {
         // cells farther than the current k-th distance (or the bound) cannot help
-        long long lim = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> KNN_IDX_BITS);
+        long long lim = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> ib);
         if (bound < lim) lim = bound;
         // the table is sorted by dmin: once the next entry (and every cell outside the table)
         // is beyond the limit, nothing nearer remains
@@ -294,8 +310,8 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
         out_d2 = KNN_INF;
         out_idx = 0x7fffffff;
     } else {
-        out_d2 = (long long)(t >> KNN_IDX_BITS);
-        out_idx = (int)(t & KNN_IDX_MASK);
+        out_d2 = (long long)(t >> ib);
+        out_idx = (int)(t & ((1ull << ib) - 1ull));
     }
-    return kth != KNN_KEY_NONE;
+    return kth != KNN_KEY_NONE && (long long)(kth >> ib) < knn_d2max(ib);
 }

@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     r_first = __shfl_sync(FULLMASK, r_first, 0);
     unsigned long long code_next = r_first < rb1 ? P.req[r_first] : 0ull;
     unsigned long long pend_a = 0ull, pend_e = 0ull;   // words before this lane's last adds
-    bool bad = false;
+    bool bad = false, bad_knn = false;
     for (long long r = r_first, rn; r < rb1; r = rn) {
         unsigned long long code = code_next;
         rn = 0;
@@ -910,7 +910,13 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         BoxGrid g;
         g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
         g.start = P.grid.start; g.items = P.grid.items; g.tab = P.grid.tab;
-        warp_knn(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2);
+        g.ib = knn_index_bits(P.box_off[box + 1] - boff);
+        if (!warp_knn(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2)) {
+            // a k-th neighbour beyond the key range: reported; indices kept inside the box
+            bad_knn = true;
+            long long nbx = P.box_off[box + 1] - boff;
+            if (kidx < 0 || kidx >= nbx) { kidx = 0; kd2 = 0; }
+        }
         long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
         bool valid = lane < P.kn;
         long long j = valid ? boff + kidx : 0;
@@ -980,6 +986,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     }
     bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
     if (bad) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
+    if (bad_knn) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_KNN);
 }
 
 // receiver segments of the staged contributions
@@ -1599,6 +1606,8 @@ static rt_status transport_end(rt_ctx *c, bool fp32) {
     if (e & ERRB_FREE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "free packets exceeded free_cap");
     if (e & ERRB_STAGE_CAP) return rt_fail(c, RT_ERR_CAPACITY, "staged contributions exceeded capacity");
     if (e & ERRB_RANGE) return rt_fail(c, RT_ERR_RANGE, "virtual deposit overflowed its accumulator");
+    if (e & ERRB_KNN)
+        return rt_fail(c, RT_ERR_KNN, "a virtual particle's n_ngb-th neighbour lies beyond the kNN key range");
     if (c->cnt_h[CNT_DROP]) return rt_fail(c, RT_ERR_HOP_LIMIT, "hop loop reached hop_cap");
     return RT_OK;
 }

@@ -72,19 +72,19 @@ def test_options_are_validated_before_any_device_work(lib):
 
 
 def test_box_too_large_for_the_knn_keys_is_rejected(lib):
-    """The kNN search packs a box-local index into 22 bits: a box of 2^22 particles is refused
-    before any device work."""
+    """The kNN search packs a box-local index into 24 bits: a box of 2^24 + 1 particles is
+    refused before any device work."""
     from paper_1311_0182_gb300 import rt, workloads as W
     wl = W.cfg1()
-    big = dict(wl, box_off=np.array([0, 1 << 22]), box_L=np.array([1.0]))
+    big = dict(wl, box_off=np.array([0, (1 << 24) + 1]), box_L=np.array([1.0]))
     with pytest.raises(rt.RTError) as e:
         rt.Context(big)
     assert e.value.status == 1
-    # one particle fewer passes the validation and then needs a device (checked where none is
-    # present: with a GPU it would allocate a 4M-particle context)
+    # 2^24 (workload 5 in one box) passes the validation and then needs a device (checked where
+    # none is present: with a GPU it would allocate a 16.7M-particle context)
     import torch
     if not torch.cuda.is_available():
-        ok = dict(wl, box_off=np.array([0, (1 << 22) - 1]), box_L=np.array([1.0]))
+        ok = dict(wl, box_off=np.array([0, 1 << 24]), box_L=np.array([1.0]))
         with pytest.raises(rt.RTError) as e:
             rt.Context(ok)
         assert e.value.status == 3
