@@ -233,6 +233,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     P.ns = n_src;
     P.nfs = cfg->n_freq_src;
     P.shared = cfg->rec_shared_bin;
+    for (int b = 0; b < n_boxes; ++b)
+        if (box_off[b + 1] - box_off[b] > (1ll << 22)) P.kwide = 1;
     P.nf = cfg->n_freq_src + (P.shared ? 0 : 1);
     P.rbin = P.shared ? 0 : P.nf - 1;
     P.nrc = cfg->n_rc;

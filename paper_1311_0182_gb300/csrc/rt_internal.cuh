@@ -168,6 +168,7 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     int *sgate;               // [ns] 1: emits only while its nearest gas particle is ionised
     Barrier *bar;             // [nb] photon barriers
     int any_bar;              // some box has a barrier
+    int kwide;                // some box holds more than 2^22 particles (24-bit kNN keys)
     int gated;                // some source has a gate
     float *fdx, *fdy, *fdz;   // forward offsets q_j - q_i, [n * kn]
     int *rev_off;

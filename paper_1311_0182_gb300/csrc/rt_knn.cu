@@ -100,7 +100,6 @@ __device__ __forceinline__ BoxGrid box_grid(const DevPtrs &P, int b) {
     g.coff = P.grid.coff[b];
     g.start = P.grid.start;
     g.tab = P.grid.tab;
-    g.ib = knn_index_bits(P.box_off[b + 1] - P.box_off[b]);
     g.items = P.grid.items;
     return g;
 }
@@ -122,7 +121,11 @@ __global__ void __launch_bounds__(256) k_knn(DevPtrs P, int sources) {
         }
         long long d2;
         int idx;
-        bool ok = warp_knn(box_grid(P, b), qx, qy, qz, ex, P.kn, d2, idx, sdelta[threadIdx.x >> 5]);
+        bool ok = knn_wide_box(P.box_off[b + 1] - P.box_off[b])
+                      ? warp_knn<KNN_IB_LARGE>(box_grid(P, b), qx, qy, qz, ex, P.kn, d2, idx,
+                                               sdelta[threadIdx.x >> 5])
+                      : warp_knn<KNN_IB_SMALL>(box_grid(P, b), qx, qy, qz, ex, P.kn, d2, idx,
+                                               sdelta[threadIdx.x >> 5]);
         if (!ok) {
             if (lane == 0) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_KNN);
             continue;
@@ -211,7 +214,12 @@ __global__ void __launch_bounds__(256) k_knn_probe(DevPtrs P, unsigned long long
         long long bd = 3 * H / 2 + 2;
         long long d2;
         int idx;
-        warp_knn(box_grid(P, b), qx, qy, qz, -1, P.kn, d2, idx, sdelta[threadIdx.x >> 5], bd * bd);
+        if (knn_wide_box(P.box_off[b + 1] - P.box_off[b]))
+            warp_knn<KNN_IB_LARGE>(box_grid(P, b), qx, qy, qz, -1, P.kn, d2, idx,
+                                   sdelta[threadIdx.x >> 5], bd * bd);
+        else
+            warp_knn<KNN_IB_SMALL>(box_grid(P, b), qx, qy, qz, -1, P.kn, d2, idx,
+                                   sdelta[threadIdx.x >> 5], bd * bd);
         acc += (unsigned long long)idx;
     }
     if (lane == 0 && acc == 0xffffffffffffffffull) *sink = acc;

@@ -25,13 +25,14 @@
 // merge by insertion when at most this many candidates of a batch pass the k-th key
 #define KNN_INSERT_MAX 16
 
-// the largest d2 a key with ib index bits holds
-__device__ __forceinline__ long long knn_d2max(int ib) { return (1ll << (64 - ib)) - 2; }
+// the largest d2 a key with IB index bits holds
+template <int IB> __device__ __forceinline__ long long knn_d2max() { return (1ll << (64 - IB)) - 2; }
 
-__device__ __forceinline__ unsigned long long knn_key(long long d2, int idx, int ib) {
-    long long m = knn_d2max(ib);
-    if (d2 > m) d2 = m;
-    return ((unsigned long long)d2 << ib) | (unsigned long long)idx;
+template <int IB>
+__device__ __forceinline__ unsigned long long knn_key(long long d2, int idx) {
+    // with 22 index bits every d2 (< 3 * 2^40) fits; with 24 it saturates
+    if (IB > KNN_IB_SMALL && d2 > knn_d2max<IB>()) d2 = knn_d2max<IB>();
+    return ((unsigned long long)d2 << IB) | (unsigned long long)idx;
 }
 
 // bitonic sort (ascending) of one key per lane across the warp
@@ -86,11 +87,12 @@ struct BoxGrid {
     const int *start;
     const int4 *items;
     const int *tab;           // the offset table (device)
-    int ib;                   // index bits of the keys (KNN_IB_SMALL or KNN_IB_LARGE)
 };
 
-__device__ __forceinline__ int knn_index_bits(long long box_particles) {
-    return box_particles > (1ll << KNN_IB_SMALL) ? KNN_IB_LARGE : KNN_IB_SMALL;
+// Exact kNN with the key width of the box: the searches of one launch that may meet boxes of
+// more than 2^22 particles are compiled with 24 index bits, the others with 22
+__device__ __forceinline__ bool knn_wide_box(long long box_particles) {
+    return box_particles > (1ll << KNN_IB_SMALL);
 }
 
 __device__ __forceinline__ int cell_coord(int v, int cs, int G) {
@@ -133,6 +135,7 @@ __device__ __forceinline__ int4 knn_fetch(const BoxGrid &g, int base, int total,
 // top list t; kth is the key held by lane kn - 1 (uniform), bkey the largest key allowed.
 // The items of the next batch of 32 are loaded before the current batch is merged, so the
 // load latency overlaps the merge.
+template <int IB>
 __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
                                  int rs, int rc, unsigned long long bkey, unsigned long long &t,
                                  unsigned long long &kth, int *sdelta) {
@@ -155,7 +158,7 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
         unsigned long long ck = KNN_KEY_NONE;
         if (it.w >= 0 && it.w != exclude) {
             long long dx = it.x - qx, dy = it.y - qy, dz = it.z - qz;
-            ck = knn_key(dx * dx + dy * dy + dz * dz, it.w, g.ib);
+            ck = knn_key<IB>(dx * dx + dy * dy + dz * dz, it.w);
         }
         bool pass = ck < kth && ck <= bkey;
         unsigned m = __ballot_sync(FULLMASK, pass);
@@ -183,6 +186,7 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
 // running list t (k-th key kth), until the k-th distance is below the distance from q to the
 // outside of the visited block (every cell of radius < r0 has been visited or shown not to
 // matter).  r0 = 1 visits the whole 3x3x3 block first.
+template <int IB>
 __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
                                   int r0, long long bound, unsigned long long bkey,
                                   unsigned long long &t, unsigned long long &kth, int *sdelta) {
@@ -193,7 +197,7 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
         int side = 2 * r + 1;
         int ncol = side * side;
         // cells farther than the current k-th distance (or the bound) cannot help
-        long long prune = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> g.ib);
+        long long prune = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> IB);
         if (bound < prune) prune = bound;
         for (int cb = 0; cb < ncol; cb += 32) {
             int col = cb + (threadIdx.x & 31);
@@ -235,9 +239,9 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
                     }
                 }
             }
-            knn_visit(g, qx, qy, qz, exclude, kn, rs0, rc0, bkey, t, kth, sdelta);
+            knn_visit<IB>(g, qx, qy, qz, exclude, kn, rs0, rc0, bkey, t, kth, sdelta);
             if (__any_sync(FULLMASK, rc1 > 0))
-                knn_visit(g, qx, qy, qz, exclude, kn, rs1, rc1, bkey, t, kth, sdelta);
+                knn_visit<IB>(g, qx, qy, qz, exclude, kn, rs1, rc1, bkey, t, kth, sdelta);
         }
         // distance from q to the outside of the visited block [c - r, c + r]^3
         long long b = -1;
@@ -254,7 +258,7 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
             }
         }
         if (b < 0) break;
-        if (kth != KNN_KEY_NONE && (long long)(kth >> g.ib) < b * b) break;
+        if (kth != KNN_KEY_NONE && (long long)(kth >> IB) < b * b) break;
     }
 }
 
@@ -265,13 +269,13 @@ __device__ inline void knn_shells(const BoxGrid &g, int qx, int qy, int qz, int 
 // sdelta: 32 ints of shared memory owned by the calling warp.
 // Returns false when the box holds fewer than kn candidates, or when the kn-th distance
 // saturated the key (the order among the farthest candidates is then not certain).
+template <int IB>
 __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int exclude, int kn,
                                 long long &out_d2, int &out_idx, int *sdelta,
                                 long long bound = KNN_INF) {
     unsigned long long t = KNN_KEY_NONE, kth = KNN_KEY_NONE;
-    const int ib = g.ib;
-    unsigned long long bkey = bound >= knn_d2max(ib) ? KNN_KEY_NONE - 1ull
-                                                     : knn_key(bound, (1 << ib) - 1, ib);
+    unsigned long long bkey = bound >= knn_d2max<IB>() ? KNN_KEY_NONE - 1ull
+                                                       : knn_key<IB>(bound, (1 << IB) - 1);
     int G = g.G, cs = g.cs;
     int cx = cell_coord(qx, cs, G), cy = cell_coord(qy, cs, G), cz = cell_coord(qz, cs, G);
     const long long cs2 = (long long)cs * cs;
@@ -280,7 +284,7 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
     bool done = false;
     for (int e0 = 0; e0 < KNN_TAB_N; e0 += 32) {
         // cells farther than the current k-th distance (or the bound) cannot help
-        long long lim = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> ib);
+        long long lim = kth == KNN_KEY_NONE ? KNN_INF : (long long)(kth >> IB);
         if (bound < lim) lim = bound;
         // the table is sorted by dmin: once the next entry (and every cell outside the table)
         // is beyond the limit, nothing nearer remains
@@ -303,15 +307,15 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
                 }
             }
         }
-        knn_visit(g, qx, qy, qz, exclude, kn, rs, rc, bkey, t, kth, sdelta);
+        knn_visit<IB>(g, qx, qy, qz, exclude, kn, rs, rc, bkey, t, kth, sdelta);
     }
-    if (!done) knn_shells(g, qx, qy, qz, exclude, kn, KNN_TAB_R + 1, bound, bkey, t, kth, sdelta);
+    if (!done) knn_shells<IB>(g, qx, qy, qz, exclude, kn, KNN_TAB_R + 1, bound, bkey, t, kth, sdelta);
     if (t == KNN_KEY_NONE) {
         out_d2 = KNN_INF;
         out_idx = 0x7fffffff;
     } else {
-        out_d2 = (long long)(t >> ib);
-        out_idx = (int)(t & ((1ull << ib) - 1ull));
+        out_d2 = (long long)(t >> IB);
+        out_idx = (int)(t & ((1ull << IB) - 1ull));
     }
-    return kth != KNN_KEY_NONE && (long long)(kth >> ib) < knn_d2max(ib);
+    return kth != KNN_KEY_NONE && (IB == KNN_IB_SMALL || (long long)(kth >> IB) < knn_d2max<IB>());
 }

@@ -765,11 +765,12 @@ __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long l
 
 // Virtual particles (Sec. 2.1): one warp per request.
 // BAR: some box has a barrier (a separate instance keeps the test out of the common case);
-// SH: the shared frequency bin (likewise)
+// SH: the shared frequency bin (likewise); IB: index bits of the kNN keys (24 when a box holds
+// more than 2^22 particles)
 // cur, fcur: the hop's slot and free-packet buffers (launch parameters, so that buffer
 // pointers are re-read from the parameter space instead of being held in registers); the
 // step and hop of the random draws are read from the device counters where they are used.
-template <typename Real, int NRC, bool BAR, bool SH>
+template <typename Real, int NRC, bool BAR, bool SH, int IB>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
                                                  const int *lens, unsigned long long *esc_r,
                                                  unsigned char *vstat) {
@@ -910,8 +911,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         BoxGrid g;
         g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
         g.start = P.grid.start; g.items = P.grid.items; g.tab = P.grid.tab;
-        g.ib = knn_index_bits(P.box_off[box + 1] - boff);
-        if (!warp_knn(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2)) {
+        if (!warp_knn<IB>(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2)) {
             // a k-th neighbour beyond the key range: reported; indices kept inside the box
             bad_knn = true;
             long long nbx = P.box_off[box + 1] - boff;
@@ -1499,14 +1499,21 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     LAUNCH(KT_SCAN, 2, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
     LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
     if (tm) cudaEventRecord(c->tev[2], st);
-    if (P.shared)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
+    const int IS = KNN_IB_SMALL, IL = KNN_IB_LARGE;
+    if (P.kwide && P.shared)   // boxes above 2^22 particles: the general instance, 24-bit keys
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true, IL><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
+                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+    else if (P.kwide)
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false, IL><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
+                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+    else if (P.shared)
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     else if (P.any_bar)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     else
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
+        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
     if (tm) cudaEventRecord(c->tev[3], st);
     LAUNCH_ON(s2, KT_SCAN, 2, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
