@@ -667,3 +667,49 @@ def test_shared_and_separate_bins_agree_when_the_spectra_match():
     med = {m: np.array([np.median(x[(r >= a) & (r < b)]) for a, b in shells]) for m, x in res.items()}
     assert np.all(np.abs(med["shared"] / med["sep"] - 1) < 0.03)
     assert np.max(np.abs(med["A"] / med["sep"] - 1)) > 0.10
+
+
+def test_chemistry_converges_to_its_rate_equations():
+    """Sec. 2.1 chemistry: with the step cut into many short calls at a fixed photoionisation and
+    photoheating rate per neutral atom, the oracle's update (electron density frozen within a
+    subcycle, exact exponential for x_HI, explicit step for u) converges at first order to a
+    stiff integration (scipy Radau) of the rate equations
+        dx/dt = alpha_A n_e (1 - x) - (Gamma + beta n_e) x,
+        du/dt = x n_H H - n_e n_HII L_rec,A - n_e n_HI L_cex,   u = 1.5 k T n_H (1 + x_HII),
+    and its recombination photons to the integral of (alpha_A - alpha_B) n_e n_HII V.  A neutral
+    cold particle is ionised and heated through the step.  A dropped term, a wrong sign, a case-B
+    coefficient or a wrong normalisation converges elsewhere and fails."""
+    from scipy.integrate import solve_ivp
+    nH, L = 1e-3, 0.2 * KPC
+    NH = nH * L ** 3
+    x0, T0 = 0.9, 100.0
+    Gam = 2e-12
+    H = Gam * 3.0 * EV
+    dt = 0.5 * MYR
+
+    def rhs(t, y):
+        x, u, _ = y
+        xII = 1.0 - x
+        r = oracle.rates(u / (1.5 * K_B * nH * (1.0 + xII)))
+        ne = xII * nH
+        return [r["alpha_A"] * ne * xII - (Gam + r["beta"] * ne) * x,
+                x * nH * H - ne * xII * nH * r["Lrec_A"] - ne * x * nH * r["L_cex"],
+                (r["alpha_A"] - r["alpha_B"]) * ne * xII * NH]
+
+    u0 = 1.5 * K_B * T0 * nH * (2.0 - x0)
+    sol = solve_ivp(rhs, (0.0, dt), [x0, u0, 0.0], method="Radau", rtol=1e-10,
+                    atol=[1e-14, 1e-12 * u0, 1.0])
+    xr, ur, nr_ref = sol.y[:, -1]
+    Tr = ur / (1.5 * K_B * nH * (2.0 - xr))
+    assert xr < 1e-3 and Tr > 5e3                     # ionised and heated within the step
+    errs = []
+    for n_calls in (1000, 4000):
+        p = _params(dt=dt / n_calls, evolve_T=1, rec_mode=W.REC_TRANSPORT, sub_cap=100000)
+        x, T, nrec = x0, T0, 0.0
+        for _ in range(n_calls):
+            h = dt / n_calls
+            x, T, n, _, _ = oracle.chem_particle(p, nH, NH, Gam * x * NH * h, H * x * NH * h, x, T)
+            nrec += n
+        errs.append(max(abs(x / xr - 1), abs(T / Tr - 1), abs(nrec / nr_ref - 1)))
+    assert errs[1] < 5e-3
+    assert 2.5 < errs[0] / errs[1] < 6.0               # first order in the call length
