@@ -809,3 +809,55 @@ def test_shared_frequency_bin_against_the_oracle(fp32, clock_limited):
     bg, bo = g.budget()[0], o.budget()[0]
     assert np.allclose(bg, bo, rtol=1e-6, atol=1e-6 * bo[0])
     assert abs(bg[0] - bg[1:].sum()) <= 1e-6 * bg[0]
+
+
+def test_box_above_2_22_particles_uses_24_bit_keys():
+    """A box of 2^22 + 1000 particles takes the kNN instances with 24 index bits: sampled
+    neighbour lists equal brute force and a step conserves photons.  In a box that size, a
+    particle whose 32nd neighbour lies across the box cannot be ordered by the keys and the
+    neighbour build says so (RT_ERR_KNN); the same geometry in a small box, with 22 index bits,
+    builds."""
+    from paper_1311_0182_gb300 import rt
+    n = (1 << 22) + 1000
+    L = 13.2 * W.KPC
+    rng = np.random.default_rng(9)
+    pos = rng.uniform(0.0, L, size=(n, 3))
+    params = W.default_params(seed=9, n_ec=8, n_tc=8, n_rc=8, dt=0.05 * W.MYR, dt_em=0.05 * W.MYR,
+                              transport_fp32=1)
+    wl = W._pack(params, [L], [0, n], pos, np.full(n, 1e-3), np.full(n, 1e-3 * L ** 3 / n),
+                 np.full(n, 0.5), np.full(n, 1e4), [0], np.array([[0.5 * L] * 3]), [[1e50]],
+                 [6.3e-18], [0.0])
+    g = rt.context_for(wl)
+    nbr, h2, _, _ = g.neighbours()
+    q = g.quantised()
+    idx = np.arange(n)
+    for i in rng.choice(n, 12, replace=False):
+        d2 = ((q - q[i]) ** 2).sum(1)
+        d2[i] = np.iinfo(np.int64).max
+        cand = np.nonzero(d2 <= np.partition(d2, 31)[31])[0]      # ties at the 32nd kept
+        order = cand[np.lexsort((cand, d2[cand]))][:32]
+        assert np.array_equal(nbr[i], order)
+        assert h2[i] == d2[order[-1]]
+    g.step(0)
+    b = g.budget()[0]
+    assert g.stats()["virtual"] > 0 and abs(b[0] - b[1:].sum()) <= 1e-6 * b[0]
+    g.close()
+    # one particle alone in the far corner, the rest spread over the octant [0, 0.4 L)^3 (about
+    # 15 times the mean density, so the cell grid stays usable): the far particle's 32nd
+    # neighbour is more than a box side away
+    far = np.full((1, 3), np.nextafter(L, 0.0))
+    for m, expect_error in ((n, True), (2000, False)):
+        p = np.concatenate([rng.uniform(0.0, 0.4 * L, size=(m - 1, 3)), far])
+        w2 = W._pack(params, [L], [0, m], p, np.full(m, 1e-3), np.full(m, 1e-3 * L ** 3 / m),
+                     np.full(m, 0.5), np.full(m, 1e4), [0], np.array([[0.2 * L] * 3]), [[1e50]],
+                     [6.3e-18], [0.0])
+        c = rt.Context(w2)
+        c.load_workload(w2)
+        if expect_error:
+            with pytest.raises(rt.RTError) as e:
+                c.build_neighbours()
+            assert e.value.status == 5
+        else:
+            c.build_neighbours()
+            assert c.neighbours()[1][-1] > (1 << 40)      # its 32nd neighbour is across the box
+        c.close()
