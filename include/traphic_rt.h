@@ -174,7 +174,9 @@ rt_status rt_merge(rt_ctx *ctx, void *stream);
 
 /* rt_emit -- emission at the start of step `step` (Sec. 2.1, Sec. 2.2, Fig. 1c,d): the
    recombination photons of the last chemistry step go N_rec/n_rc into each reception cone of
-   the recombination bin along its rotated axis, merged with the packets there; the sources
+   the recombination bin (source bin 0 with rec_shared_bin, where they add N_rec/n_rc sigma_rec
+   to the cone's cross-section sum) along its rotated axis, merged with the packets there (with
+   rec_mode RT_REC_EMISSION_CONES they leave as separate packets instead); the sources
    emit dt/dt_em times n_ec packets per frequency bin along their rotated emission axes.
    Also restarts the absorption counters and freezes n_HI for the transport. */
 rt_status rt_emit(rt_ctx *ctx, long long step, void *stream);
@@ -198,8 +200,9 @@ rt_status rt_chemistry(rt_ctx *ctx, void *stream);
    hop loop is a conditional while node whose last kernel decides on the device whether
    another hop runs, so no host round trip separates hops.  The graph is captured on the
    first call and again whenever a parameter it holds changes (configuration, barriers,
-   source options, kNN grid).  The hop-by-hop path runs instead while kernels are timed
-   (rt_set_profiling) or hop_cap is 0; both give bit-identical results.  After an error
+   source options, kNN grid, launch sizes).  The hop-by-hop path runs instead while kernels
+   are timed (rt_set_profiling), when hop_cap is 0, and for the first step when tune_launch
+   chooses the launch sizes; both give bit-identical results.  After an error
    status from the graph the chemistry of that step has run on incomplete absorptions (the
    hop-by-hop path stops before it); the state of a failed step is not meant to be used. */
 rt_status rt_step(rt_ctx *ctx, long long step, void *stream);
