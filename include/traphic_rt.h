@@ -119,7 +119,10 @@ rt_status rt_destroy(rt_ctx *ctx);
    context: positions (cm, per box in [0, L_b)), hydrogen number density n_H (cm^-3),
    hydrogen atoms per particle N_H, neutral fraction x_HI and temperature T (K).  Resets the
    packets held by the particles, the recombination photons pending and the neighbour lists
-   (call rt_build_neighbours again).  Errors: RT_ERR_INVALID, RT_ERR_CUDA. */
+   (call rt_build_neighbours again).  Positions outside [0, L_b) are moved onto the box's edge.
+   Errors: RT_ERR_INVALID (also for a non-finite position, a non-positive or non-finite density
+   or atom count, x_HI outside [0, 1] or a non-positive temperature: the context then holds no
+   particles until a valid call), RT_ERR_CUDA. */
 rt_status rt_set_particles(rt_ctx *ctx, const double *x, const double *y, const double *z,
                            const double *n_H, const double *N_H, const double *x_HI,
                            const double *T, int where, void *stream);
@@ -127,7 +130,10 @@ rt_status rt_set_particles(rt_ctx *ctx, const double *x, const double *y, const 
 /* rt_set_sources -- copy the sources: box index (int [n_src]), position ([n_src] each, cm),
    photon rates ndot ([n_src * n_freq_src], row per source, s^-1), and per source frequency
    bin the grey cross-section sigma (cm^2) and excess energy eps (erg) ([n_freq_src]) (Sec.
-   2.1: each packet carries one bin; the bin's spectrum is a grey cross-section). */
+   2.1: each packet carries one bin; the bin's spectrum is a grey cross-section).  Errors:
+   RT_ERR_INVALID (also for a non-finite position, a negative photon rate, a non-positive
+   cross-section or a negative excess energy: the context then holds no sources until a valid
+   call), RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_set_sources(rt_ctx *ctx, const int *box, const double *x, const double *y,
                          const double *z, const double *ndot, const double *sigma,
                          const double *eps, int where, void *stream);
@@ -211,7 +217,9 @@ rt_status rt_step(rt_ctx *ctx, long long step, void *stream);
 rt_status rt_set_graph(rt_ctx *ctx, int on);
 
 /* rt_get_state / rt_set_state -- x_HI, T, pending recombination photons N_rec and their
-   excess energy eps_rec ([n] each; NULL skips a field). */
+   excess energy eps_rec ([n] each; NULL skips a field).  rt_set_state returns RT_ERR_INVALID
+   for x_HI outside [0, 1], a non-positive temperature, or negative or non-finite photons or
+   energy; the rejected values are then in place and the state must be set again. */
 rt_status rt_get_state(rt_ctx *ctx, double *x_HI, double *T, double *N_rec, double *eps_rec,
                        int where, void *stream);
 rt_status rt_set_state(rt_ctx *ctx, const double *x_HI, const double *T, const double *N_rec,

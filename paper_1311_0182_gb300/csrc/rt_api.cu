@@ -525,6 +525,45 @@ static void set_norms(rt_ctx *c) {
     cudaMemcpy(x.src_emit, x.src_emit_h.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
 }
 
+// ---- input validation ---------------------------------------------------------------------
+// Values the method cannot use, found on the device copies (host and device inputs alike):
+// non-finite positions; non-positive or non-finite densities and atom counts; neutral
+// fractions outside [0, 1]; non-positive or non-finite temperatures; negative or non-finite
+// recombination photons and energies.  Reads only; a NULL array is not checked.
+__global__ void k_check_inputs(long long n, const double *x, const double *y, const double *z,
+                               const double *nH, const double *NH, const double *xHI,
+                               const double *T, const double *Nrec, const double *epsrec,
+                               long long *bad) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool ok = true;
+    if (x) ok = ok && isfinite(x[i]) && isfinite(y[i]) && isfinite(z[i]);
+    if (nH) ok = ok && nH[i] > 0.0 && isfinite(nH[i]);
+    if (NH) ok = ok && NH[i] > 0.0 && isfinite(NH[i]);
+    if (xHI) ok = ok && xHI[i] >= 0.0 && xHI[i] <= 1.0;
+    if (T) ok = ok && T[i] > 0.0 && isfinite(T[i]);
+    if (Nrec) ok = ok && Nrec[i] >= 0.0 && isfinite(Nrec[i]);
+    if (epsrec) ok = ok && epsrec[i] >= 0.0 && isfinite(epsrec[i]);
+    if (!ok) atomicOr((unsigned long long *)bad, 1ull);
+}
+
+static const int CNT_CHECK = CNT_N - 2;   // device word of the input checks
+
+// true when every value passes (synchronises st)
+static bool inputs_ok(rt_ctx *c, long long n, const double *x, const double *y, const double *z,
+                      const double *nH, const double *NH, const double *xHI, const double *T,
+                      const double *Nrec, const double *epsrec, cudaStream_t st) {
+    long long *flag = c->d.cnt + CNT_CHECK;
+    cudaMemsetAsync(flag, 0, sizeof(long long), st);
+    if (n > 0)
+        k_check_inputs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y, z, nH, NH, xHI, T,
+                                                                    Nrec, epsrec, flag);
+    long long bad = 0;
+    cudaMemcpyAsync(&bad, flag, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return bad == 0;
+}
+
 extern "C" rt_status rt_set_particles(rt_ctx *c, const double *x, const double *y,
                                       const double *z, const double *n_H, const double *N_H,
                                       const double *x_HI, const double *T, int where,
@@ -545,6 +584,14 @@ extern "C" rt_status rt_set_particles(rt_ctx *c, const double *x, const double *
         (s = copy_in(c, P.T, T, nb, where, st))) {
         cudaFree(tx);
         return s;
+    }
+    if (!inputs_ok(c, P.n, tx, ty, tz, P.nH, P.NH, P.xHI, P.T, nullptr, nullptr, st)) {
+        cudaFree(tx);
+        c->have_particles = false;
+        c->built = false;
+        return rt_fail(c, RT_ERR_INVALID,
+                       "rt_set_particles: a non-finite position, a non-positive density or atom "
+                       "count, x_HI outside [0, 1] or a non-positive temperature");
     }
     rt_launch_quantise(c, tx, ty, tz, st);
     cudaStreamSynchronize(st);
@@ -603,6 +650,13 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
             cudaFree(t);
             return s;
         }
+        if (!inputs_ok(c, P.ns, t, t + P.ns, t + 2 * P.ns, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, nullptr, st)) {
+            cudaFree(t);
+            c->have_sources = false;
+            c->built = false;
+            return rt_fail(c, RT_ERR_INVALID, "rt_set_sources: a non-finite position");
+        }
         rt_launch_quantise_src(c, t, t + P.ns, t + 2 * P.ns, st);
         cudaStreamSynchronize(st);
         cudaFree(t);
@@ -618,6 +672,21 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
             cudaMemcpy(ep.data(), eps, sizeof(double) * P.nfs, cudaMemcpyDeviceToHost);
         }
     }
+    for (int f = 0; f < P.nfs; ++f)
+        if (!(sg[f] > 0.0) || !std::isfinite(sg[f]) || !(ep[f] >= 0.0) || !std::isfinite(ep[f]))
+        {
+            c->have_sources = false;
+            c->built = false;
+            return rt_fail(c, RT_ERR_INVALID, "rt_set_sources: a non-positive cross-section or a "
+                                              "negative excess energy");
+        }
+    for (double v : ndh)
+        if (!(v >= 0.0) || !std::isfinite(v))
+        {
+            c->have_sources = false;
+            c->built = false;
+            return rt_fail(c, RT_ERR_INVALID, "rt_set_sources: a negative photon rate");
+        }
     sg[P.nfs] = c->cfg.sigma_rec;
     ep[P.nfs] = 0.0;
     // entry nfs: the recombination photons' (their bin's, unless the bin is shared)
@@ -810,6 +879,13 @@ extern "C" rt_status rt_set_state(rt_ctx *c, const double *x_HI, const double *T
         (s = copy_in(c, c->d.Nrec, N_rec, b, where, st)) ||
         (s = copy_in(c, c->d.epsrec, eps_rec, b, where, st)))
         return s;
+    DevPtrs &P = c->d;
+    if (!inputs_ok(c, P.n, nullptr, nullptr, nullptr, nullptr, nullptr, x_HI ? P.xHI : nullptr,
+                   T ? P.T : nullptr, N_rec ? P.Nrec : nullptr, eps_rec ? P.epsrec : nullptr, st))
+        return rt_fail(c, RT_ERR_INVALID,
+                       "rt_set_state: x_HI outside [0, 1], a non-positive temperature, or negative "
+                       "recombination photons or energy (the rejected values are in place: set "
+                       "the state again before the next step)");
     return RT_OK;
 }
 

@@ -861,3 +861,46 @@ def test_box_above_2_22_particles_uses_24_bit_keys():
             c.build_neighbours()
             assert c.neighbours()[1][-1] > (1 << 40)      # its 32nd neighbour is across the box
         c.close()
+
+
+def test_invalid_inputs_are_refused_with_a_status():
+    """Host-side fault injection: a NaN density, a negative atom count, x_HI above 1, a zero
+    temperature, a NaN position, a negative photon rate or a zero cross-section is refused with
+    RT_ERR_INVALID before any step uses it; the context then needs valid inputs again and works
+    with them."""
+    from paper_1311_0182_gb300 import rt
+    wl = W.cfg1(n_side=12)
+    g = rt.Context(wl)
+    f = lambda k: np.ascontiguousarray(wl[k], dtype=np.float64)
+    good = [f(k) for k in ("x", "y", "z", "n_H", "N_H", "x_HI", "T")]
+    for k, val in ((3, np.nan), (4, -1.0), (5, 1.5), (6, 0.0), (0, np.nan)):
+        bad = [a.copy() for a in good]
+        bad[k][7] = val
+        with pytest.raises(rt.RTError) as e:
+            g.set_particles(*bad)
+        assert e.value.status == 1, (k, val)
+        with pytest.raises(rt.RTError) as e:        # no particles until a valid call
+            g.build_neighbours()
+        assert e.value.status == 7
+    g.set_particles(*good)
+    src = [np.ascontiguousarray(wl["src_box"], dtype=np.int32), f("src_x"), f("src_y"),
+           f("src_z"), f("src_ndot"), f("sigma"), f("eps")]
+    for k, val in ((4, -5e48), (5, 0.0)):
+        bad = [a.copy() for a in src]
+        bad[k][0] = val
+        with pytest.raises(rt.RTError) as e:
+            g.set_sources(*bad)
+        assert e.value.status == 1, (k, val)
+    g.set_sources(*src)
+    g.build_neighbours()
+    g.step(0)
+    x = g.state()["x_HI"].copy()
+    x[3] = -0.1
+    with pytest.raises(rt.RTError) as e:
+        g.set_state(x_HI=x)
+    assert e.value.status == 1
+    x[3] = 0.5
+    g.set_state(x_HI=x)
+    g.step(1)
+    b = g.budget()[0]
+    assert abs(b[0] - b[1:].sum()) <= 1e-9 * b[0]
