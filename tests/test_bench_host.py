@@ -1,0 +1,73 @@
+"""Host logic of the benchmark (no GPU): the roofline arithmetic, the committed DRAM traffic
+(taken only when the CUDA sources match the profiled ones, scaled by particle count), the
+per-kernel shares of a step and the clock samples' summary."""
+import os
+import types
+
+import numpy as np
+
+import bench
+
+
+def test_roofline_is_algorithmic_bytes_over_event_time(monkeypatch):
+    monkeypatch.setattr(bench, "peaks", lambda: (6684.1, "measured"))
+    monkeypatch.setattr(bench, "committed_traffic", lambda k, n: None)
+    kt = {"virtual_particles": {"ms": 10.0, "launches": 10, "bytes": 6.6841e9},
+          "phase_a_send": {"ms": 2.0, "launches": 10, "bytes": 1e9},
+          "hop_lens": {"ms": 20.0, "launches": 30, "bytes": 0.0}}
+    r = bench.roofline(None, kt, 50.0, types.SimpleNamespace(n_side=64))
+    # the dominant modelled kernel, not the slowest kernel without a bytes model
+    assert r["kernel"] == "virtual_particles"
+    assert np.isclose(r["ms_per_launch"], 1.0)
+    assert np.isclose(r["achieved"], 668.41)              # 6.6841e8 bytes in 1 ms
+    assert np.isclose(r["frac"], 0.1)
+    assert np.isclose(r["share_of_step"], 0.2)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
+
+
+def _fake_tree(tmp_path, table_hash):
+    csrc = tmp_path / "paper_1311_0182_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for fn in ("rt_transport.cu", "rt_internal.cuh", "rt_knn.cuh"):
+        (csrc / fn).write_text("// " + fn + "\n")
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic_per_launch.md").write_text(
+        "| kernel | DRAM bytes per launch | particles in capture | source hash |\n"
+        "|---|---|---|---|\n"
+        f"| virtual_particles | 200000000 | 262144 | {table_hash} |\n")
+
+
+def test_traffic_is_taken_only_for_the_profiled_sources(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    _fake_tree(tmp_path, "0" * 16)
+    h = bench.source_hash()
+    assert bench.committed_traffic("virtual_particles", 64) is None      # other sources
+    (tmp_path / "profiles" / "traffic_per_launch.md").unlink()
+    os.rmdir(tmp_path / "profiles")
+    import shutil
+    shutil.rmtree(tmp_path / "paper_1311_0182_gb300")
+    _fake_tree(tmp_path, h)
+    assert bench.committed_traffic("virtual_particles", 64) == 2e8
+    assert bench.committed_traffic("virtual_particles", 32) == 2e8 / 8   # scaled by particles
+    assert bench.committed_traffic("phase_b_merge", 64) is None
+
+
+def test_kernel_shares_sum_to_one():
+    kt = {"a": {"ms": 3.0, "launches": 1}, "b": {"ms": 1.0, "launches": 2},
+          "c": {"ms": 0.0, "launches": 5}}
+    sh = bench.kernel_shares(kt)
+    assert list(sh) == ["a", "b"]                       # sorted by time, idle kernels left out
+    assert np.isclose(sum(v["share"] for v in sh.values()), 1.0)
+
+
+def test_clock_summary_reports_throttle_reasons():
+    c = bench.Clocks()
+    c.proc = types.SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0)
+    row = lambda sm, *flags: ["0", str(sm), "2070", "900.5", "0x0"] + list(flags)
+    c.rows = [row(2070, "Not Active", "Not Active", "Not Active", "Not Active"),
+              row(1995, "Not Active", "Not Active", "Not Active", "Active"),
+              row(2070, "Not Active", "Not Active", "Not Active", "Not Active"),
+              ["1", "300", "2070", "10", "0x0", "Active", "Active", "Active", "Active"]]
+    out = c.stop(dev=0)
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]           # the other GPU's row is not counted
