@@ -11,10 +11,13 @@
  * 2011), the reading taken is stated at the function that implements it.
  *
  * Parity unpinned (no printed number or closed form fixes them; checked only through
- * photon conservation and the physical limits): the equal split among cone members,
- * the photon-weighted merged clock, the virtual-particle placement/interpolation/
- * absorption share, the chemistry subcycling and the cooling coefficients other than
- * the recombination coefficients.
+ * photon conservation and the physical limits): the virtual-particle placement/
+ * interpolation/absorption share and the cooling coefficients other than the
+ * recombination coefficients.  The equal split among cone members and the
+ * photon-weighted merge of arriving packets are readings the paper does not fix; a
+ * brute-force computation of one hop on tiny boxes checks that this code does what they
+ * say.  The chemistry update is checked by its convergence to a stiff integration of its
+ * own rate equations.
  */
 #include "traphic_oracle.h"
 

@@ -395,6 +395,112 @@ def test_clock_stops_packet_after_c_dt():
     assert np.all(s.slots()[4] == 0.0)
 
 
+def _one_hop_box(seed, n=12, n_tc=8, n_emit=5):
+    """A box of n particles, each the neighbour of all the others (n_ngb = n - 1), with packets
+    planted at n_emit of them, pointing within a few degrees of one common direction (so that
+    arrivals share reception cones), each with a non-empty transmission cone, clocks already
+    started, and dt short enough that every packet stops after one hop.  Returns None when
+    some neighbour lies within 1e-9 of a cone's edge in cos, or too few emitters qualify."""
+    rng = np.random.default_rng(seed)
+    L = 1.0 * KPC
+    wl = W.tiny(n=n, seed=seed, n_ngb=n - 1, L=L, n_tc=n_tc)
+    wl.update(x_HI=rng.uniform(0.0, 0.9, n), src_box=np.zeros(0, np.int32), src_x=np.zeros(0),
+              src_y=np.zeros(0), src_z=np.zeros(0), src_ndot=np.zeros(0))
+    s = oracle.Sim(wl)
+    q = s.quantised().astype(np.float64)
+    u = L / (1 << 20)
+    cmin = 1.0 - 2.0 / n_tc
+    d0 = rng.normal(size=3)
+    d0 /= np.linalg.norm(d0)
+    pk = []
+    for e in rng.permutation(n):
+        d = d0 + rng.normal(0.0, 0.05, 3)
+        d /= np.linalg.norm(d)
+        members, l = [], []
+        for j in range(n):
+            if j == e:
+                continue
+            delta = q[j] - q[e]
+            cosang = delta @ d / np.linalg.norm(delta)
+            if abs(cosang - cmin) < 1e-9:
+                return None
+            if cosang > cmin:
+                members.append(j)
+                l.append((delta @ d) * u)
+        if not members:
+            continue
+        pk.append(dict(e=e, d=d, members=members, l=np.array(l), N=rng.uniform(1e48, 1e50),
+                       eps=rng.uniform(1.0, 5.0) * EV))
+        if len(pk) == n_emit:
+            break
+    if len(pk) < n_emit:
+        return None
+    dt = 0.5 * min(p["l"].min() for p in pk) / 2.99792458e10
+    for p in pk:
+        p["clock"] = rng.uniform(0.0, 0.3) * dt
+    wl["params"]["dt"] = wl["params"]["dt_em"] = dt
+    return wl, pk
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_one_hop_splits_equally_among_cone_members_and_merges_photon_weighted(seed):
+    """Brute force on tiny boxes (Sec. 2.1): a packet of N photons shares them equally among the
+    k neighbours inside its transmission cone; each share loses 1 - exp(-sigma n_HI l) on the way
+    (l the hop projected on the packet's direction) and arrives in the reception cone of its
+    direction at the receiver, where the arrivals merge.  The merged packet's photons, momentum
+    and energy are the sums; its clock is the photon-weighted mean of the arriving clocks, each
+    the sender's clock plus l / c."""
+    made = None
+    for k in range(20):
+        made = _one_hop_box(1000 * seed + k)
+        if made is not None:
+            break
+    wl, pk = made
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    s.rotate(0)
+    s.emit(0)
+    axes = oracle.axis_set(wl["params"]["n_rc"])
+    R = s.rotations()[0]
+    f = np.zeros((6, s.n, s.S))
+    for p in pk:
+        b = oracle.recv_bin(R[p["e"]].reshape(3, 3), axes, p["d"])
+        f[0, p["e"], b] = p["N"]
+        f[1:4, p["e"], b] = p["N"] * p["d"]
+        f[4, p["e"], b] = p["N"] * p["clock"]
+        f[5, p["e"], b] = p["N"] * p["eps"]
+    s.set_slots(f)
+    assert s.transport(0) == 0
+    sigma = wl["sigma"][0]
+    nHI = wl["x_HI"] * wl["n_H"]
+    want = np.zeros((6, s.n, s.S))
+    absorbed = np.zeros(s.n)
+    arrivals = np.zeros((s.n, s.S), int)
+    for p in pk:
+        w = p["N"] / len(p["members"])
+        for j, l in zip(p["members"], p["l"]):
+            T = w * math.exp(-sigma * nHI[j] * l)
+            absorbed[j] += w - T
+            b = oracle.recv_bin(R[j].reshape(3, 3), axes, p["d"])
+            want[0, j, b] += T
+            want[1:4, j, b] += T * p["d"]
+            want[4, j, b] += T * (p["clock"] + l / 2.99792458e10)
+            want[5, j, b] += T * p["eps"]
+            arrivals[j, b] += 1
+    assert arrivals.max() >= 2          # some slot merges packets from two senders
+    got = s.slots()
+    scale = np.abs(want).max(axis=(1, 2), keepdims=True)
+    assert np.all(np.abs(got - want) <= 1e-12 * scale)
+    held = want[0] > 0
+    assert np.allclose(got[4][held] / got[0][held], want[4][held] / want[0][held], rtol=1e-12)
+    assert np.allclose(s.deposits()[0][:, 0], absorbed, rtol=1e-11, atol=1e-12 * absorbed.max())
+    e, ab, esc, fl = s.budget()[0]
+    total = sum(p["N"] for p in pk)
+    assert esc == 0.0 and abs(ab - absorbed.sum()) <= 1e-12 * total
+    st = s.stats()
+    assert st["virtual"] == 0 and st["hops"] == 1   # no empty cone; every packet stopped
+
+
 def _front_radius(s, wl):
     L = wl["box_L"][0]
     pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
