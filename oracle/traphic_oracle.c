@@ -11,9 +11,11 @@
  * 2011), the reading taken is stated at the function that implements it.
  *
  * Parity unpinned (no printed number or closed form fixes them; checked only through
- * photon conservation and the physical limits): the virtual-particle placement/
- * interpolation/absorption share and the cooling coefficients other than the
- * recombination coefficients.  The equal split among cone members and the
+ * photon conservation and the physical limits): where a virtual particle lands, how its
+ * absorptions are shared, and the cooling coefficients other than the recombination
+ * coefficients.  The rest of the virtual-particle step (its interpolated n_HI, projected
+ * length and clock) is checked by invariants of a uniform medium that hold wherever the
+ * point lands.  The equal split among cone members and the
  * photon-weighted merge of arriving packets are readings the paper does not fix; a
  * brute-force computation of one hop on tiny boxes checks that this code does what they
  * say.  The chemistry update is checked by its convergence to a stiff integration of its

@@ -501,6 +501,78 @@ def test_one_hop_splits_equally_among_cone_members_and_merges_photon_weighted(se
     assert st["virtual"] == 0 and st["hops"] == 1   # no empty cone; every packet stopped
 
 
+def _virtual_hop_receivers(seed):
+    """One packet sent into an empty cone in a uniform medium; returns its receiver count."""
+    rng = np.random.default_rng(seed)
+    L = 1.0 * KPC
+    c0 = np.full(3, 0.5)
+    d = np.array([1.0, 0.0, 0.0])
+
+    def dirs(m, cos_lo, cos_hi):
+        ct = rng.uniform(cos_lo, cos_hi, m)
+        ph = rng.uniform(0.0, 2 * np.pi, m)
+        st = np.sqrt(1 - ct ** 2)
+        return np.stack([ct, st * np.cos(ph), st * np.sin(ph)], 1)
+
+    n_ngb = 8
+    behind = c0 + rng.uniform(0.04, 0.05, (n_ngb, 1)) * dirs(n_ngb, -1.0, -0.1)
+    ahead = c0 + rng.uniform(0.09, 0.2, (14, 1)) * dirs(14, 0.8, 1.0)
+    side = c0 + rng.uniform(0.08, 0.15, (10, 1)) * dirs(10, -0.6, 0.6)
+    pos = np.concatenate([[c0], behind, ahead, side]) * L
+    n = len(pos)
+    wl = W.tiny(n=n, seed=seed, n_ngb=n_ngb, L=L, n_tc=8)
+    nH = 1e-3
+    wl.update(x=pos[:, 0].copy(), y=pos[:, 1].copy(), z=pos[:, 2].copy(),
+              n_H=np.full(n, nH), N_H=np.full(n, nH * (0.05 * L) ** 3), x_HI=np.full(n, 0.08),
+              T=np.full(n, 1e4), src_box=np.zeros(0, np.int32), src_x=np.zeros(0),
+              src_y=np.zeros(0), src_z=np.zeros(0), src_ndot=np.zeros(0))
+    wl["params"]["dt"] = wl["params"]["dt_em"] = 1.0   # 1 s: every packet stops at the first gas
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    q = s.quantised().astype(np.float64)
+    nbr = s.neighbours()[0][0]
+    assert set(nbr) == set(range(1, n_ngb + 1))
+    assert all((q[j] - q[0]) @ d < 0 for j in nbr)     # the sender's cone is empty
+    s.rotate(0)
+    s.emit(0)
+    N0 = 1e50
+    _put_packet(s, 0, N0, d)
+    assert s.transport(0) == 0
+    st = s.stats()
+    assert st["virtual"] >= 1 and st["escaped_virtual"] == 0
+    f = s.slots()
+    Nj = f[0].sum(1)
+    recv = np.nonzero(Nj)[0]
+    assert len(recv) >= 1 and 0 not in recv
+    u = L / (1 << 20)
+    lj = ((q[recv] - q[0]) @ d) * u
+    assert np.all(lj > 0)
+    tau = wl["sigma"][0] * 0.08 * nH * lj
+    share = Nj[recv] * np.exp(tau)
+    assert np.allclose(share, N0 / len(recv), rtol=1e-12)
+    assert np.allclose(f[4][recv].sum(1) / Nj[recv], lj / 2.99792458e10, rtol=1e-12)
+    assert np.allclose(f[1:4][:, recv].sum(2), np.outer(d, Nj[recv]), rtol=1e-12, atol=0)
+    e, ab, esc, fl = s.budget()[0]
+    assert esc == 0.0 and abs(ab + Nj.sum() - N0) <= 1e-12 * N0
+    assert abs(s.deposits()[0][:, 0].sum() - ab) <= 1e-12 * N0
+    return len(recv)
+
+
+def test_virtual_particle_hop_in_a_uniform_medium_is_independent_of_its_position():
+    """A packet whose transmission cone holds no neighbour is handed to a virtual particle
+    (Sec. 2.1), drawn at random in the cone.  In a medium of uniform n_HI and V = N_H/n_H
+    the outcome at every receiver depends on where that point landed only through the
+    number k of receivers:
+    - the SPH estimate at the point is exactly the uniform n_HI (the weights are normalised);
+    - the projected lengths of the hops add up, so the optical depth and the clock at
+      receiver j are those of the straight projected path (q_j - q_sender) . d;
+    - the last virtual particle splits what is left equally among its cone members.
+    So N_j exp(tau_j) is the same for every receiver, these sum to the N sent, and every
+    receiver's clock is (q_j - q_sender) . d u / c."""
+    counts = [_virtual_hop_receivers(seed) for seed in range(21, 29)]
+    assert sum(c >= 2 for c in counts) >= 3, counts   # the split is exercised
+
+
 def _front_radius(s, wl):
     L = wl["box_L"][0]
     pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
