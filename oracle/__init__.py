@@ -66,6 +66,9 @@ def lib():
             L.orc_axis_set.argtypes = [C.c_int, P(d)]
             L.orc_rotation.argtypes = [C.c_uint64, u32, u32, u32, u32, P(d)]
             L.orc_in_cone.argtypes = [P(i64), P(d), C.c_int]
+            L.orc_virtual_offset.argtypes = [C.c_uint64, C.c_longlong, C.c_int, C.c_uint64, i64,
+                                             P(d), C.c_int, P(i64)]
+            L.orc_virtual_offset.restype = None
             L.orc_bin.argtypes = [P(d), P(d), C.c_int, P(d)]
             L.orc_rates.argtypes = [d, P(d)]
             L.orc_chem_particle.argtypes = [P(Config), d, d, d, d, P(d), P(d), P(d)]
@@ -144,6 +147,15 @@ def in_cone(delta, d, n_tc) -> bool:
     dl = np.ascontiguousarray(delta, dtype=np.int64)
     dd = np.ascontiguousarray(d, dtype=np.float64)
     return bool(lib().orc_in_cone(_p(dl, C.c_int64), _p(dd, C.c_double), n_tc))
+
+
+def virtual_offset(seed, step, hop, fid, h2, d, n_tc) -> np.ndarray:
+    """Integer offset of a virtual particle from its sender."""
+    out = np.zeros(3, np.int64)
+    dd = np.ascontiguousarray(d, dtype=np.float64)
+    lib().orc_virtual_offset(seed, step, hop, fid, h2, _p(dd, C.c_double), n_tc,
+                             _p(out, C.c_int64))
+    return out
 
 
 def recv_bin(R, axes, d) -> int:

@@ -11,11 +11,11 @@
  * 2011), the reading taken is stated at the function that implements it.
  *
  * Parity unpinned (no printed number or closed form fixes them; checked only through
- * photon conservation and the physical limits): where a virtual particle lands, how its
- * absorptions are shared, and the cooling coefficients other than the recombination
- * coefficients.  The rest of the virtual-particle step (its interpolated n_HI, projected
- * length and clock) is checked by invariants of a uniform medium that hold wherever the
- * point lands.  The equal split among cone members and the
+ * photon conservation and the physical limits): how a virtual particle's absorptions are
+ * shared among its neighbours, and the cooling coefficients other than the recombination
+ * coefficients.  Where a virtual particle lands is checked statistically against the
+ * uniform law of its reading; the rest of its step (its interpolated n_HI, projected length
+ * and clock) by invariants of a uniform medium that hold wherever the point lands.  The equal split among cone members and the
  * photon-weighted merge of arriving packets are readings the paper does not fix; a
  * brute-force computation of one hop on tiny boxes checks that this code does what they
  * say.  The chemistry update is checked by its convergence to a stiff integration of its
@@ -1000,6 +1000,34 @@ static double kernel_w(double q) {
     return 0.0;
 }
 
+/* Where a virtual particle is placed, as an integer offset from its sender (Sec. 2.1;
+   reading at make_virtual): the first of 64 counter-based draws, uniform over the integer
+   points of [-H, H]^3 with H = floor(sqrt(h2)), that lies in the sender's smoothing sphere and
+   in the transmission cone about d; when none does, the point on the axis at H/2. */
+void orc_virtual_offset(uint64_t seed, long long step, int hop, uint64_t fid, int64_t h2,
+                        const double d[3], int n_tc, int64_t del[3]) {
+    uint32_t key[2];
+    philox_key(seed, PURPOSE_VIRTUAL, key);
+    int64_t H = (int64_t)floor(sqrt((double)h2));
+    int64_t span = 2 * H + 1;
+    int found = 0;
+    for (uint32_t a = 0; a < 64 && !found; ++a) {
+        uint32_t ctr[4] = {(uint32_t)step, ((uint32_t)hop << 8) | a, (uint32_t)fid,
+                           (uint32_t)(fid >> 32)},
+                 r[4];
+        orc_philox4x32_10(ctr, key, r);
+        for (int c = 0; c < 3; ++c)
+            del[c] = (int64_t)(((uint64_t)r[c] * (uint64_t)span) >> 32) - H;
+        int64_t r2 = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
+        if (r2 > 0 && r2 <= h2 && orc_in_cone(del, d, n_tc)) found = 1;
+    }
+    if (!found) {
+        double f = 0.5 * (double)H;
+        if (f < 1.0) f = 1.0;
+        for (int c = 0; c < 3; ++c) del[c] = (int64_t)rint(d[c] * f);
+    }
+}
+
 /* Virtual particle (Sec. 2.1): created at random inside the transmission cone, its
    properties SPH-interpolated from its own neighbours, absorptions on the way to it
    shared among those neighbours; it then passes the packet on and is deleted.
@@ -1014,27 +1042,8 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
                          int64_t h2, double N, const double d[3], double clock, double eps,
                          double sig, int nu, uint64_t fid) {
     s->st_virtual++;
-    uint32_t key[2];
-    philox_key(s->cfg.seed, PURPOSE_VIRTUAL, key);
-    int64_t H = (int64_t)floor(sqrt((double)h2));
-    int64_t span = 2 * H + 1;
     int64_t del[3];
-    int found = 0;
-    for (uint32_t a = 0; a < 64 && !found; ++a) {
-        uint32_t ctr[4] = {(uint32_t)step, ((uint32_t)hop << 8) | a, (uint32_t)fid,
-                           (uint32_t)(fid >> 32)},
-                 r[4];
-        orc_philox4x32_10(ctr, key, r);
-        for (int c = 0; c < 3; ++c)
-            del[c] = (int64_t)(((uint64_t)r[c] * (uint64_t)span) >> 32) - H;
-        int64_t r2 = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
-        if (r2 > 0 && r2 <= h2 && orc_in_cone(del, d, s->cfg.n_tc)) found = 1;
-    }
-    if (!found) {
-        double f = 0.5 * (double)H;
-        if (f < 1.0) f = 1.0;
-        for (int c = 0; c < 3; ++c) del[c] = (int64_t)rint(d[c] * f);
-    }
+    orc_virtual_offset(s->cfg.seed, step, hop, fid, h2, d, s->cfg.n_tc, del);
     int64_t qv[3] = {qs[0] + del[0], qs[1] + del[1], qs[2] + del[2]};
     if (qv[0] < 0 || qv[1] < 0 || qv[2] < 0 || qv[0] >= ORC_Q || qv[1] >= ORC_Q ||
         qv[2] >= ORC_Q) {

@@ -63,6 +63,10 @@ void orc_rotation(uint64_t seed, uint32_t purpose, uint32_t c0, uint32_t c1, uin
                   double R[9]);
 int orc_in_cone(const int64_t delta[3], const double d[3], int n_tc);
 int orc_bin(const double R[9], const double *axes, int n_rc, const double d[3]);
+/* offset of a virtual particle from its sender (h2: the sender's squared smoothing length in
+   quantised units; fid: the packet's identity in the generator's counter) */
+void orc_virtual_offset(uint64_t seed, long long step, int hop, uint64_t fid, int64_t h2,
+                        const double d[3], int n_tc, int64_t del[3]);
 /* rate coefficients at T: alpha_A, alpha_B, beta_col, Lrec_A, Lrec_B, L_cex, L_cion, L_ff */
 void orc_rates(double T, double out[8]);
 /* one particle's chemistry update over dt.  On return x and T hold the new state;

@@ -573,6 +573,46 @@ def test_virtual_particle_hop_in_a_uniform_medium_is_independent_of_its_position
     assert sum(c >= 2 for c in counts) >= 3, counts   # the split is exercised
 
 
+@pytest.mark.parametrize("n_tc", [8, 32])
+def test_virtual_particle_lands_uniformly_in_the_cone_part_of_the_smoothing_sphere(n_tc):
+    """The point of a virtual particle (Sec. 2.1, reading: uniform over the part of the sender's
+    smoothing sphere inside the transmission cone).  Uniform in that solid cone means three
+    independent uniform variables: (r/h)^3 on [0, 1], cos(angle to the axis) on [1 - 2/N_TC, 1]
+    and the azimuth about the axis on [0, 2 pi).  A point that no draw finds sits on the axis
+    at h/2; that happens with probability (1 - p)^64, p the accepted fraction of the cube."""
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(9)
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    H = 1000
+    h2 = H * H
+    m = 20000
+    pts = np.array([oracle.virtual_offset(77, 5, 3, 1 + f, h2, d, n_tc) for f in range(m)])
+    fallback = np.rint(d * (0.5 * H)).astype(np.int64)
+    on_axis = np.all(pts == fallback, axis=1)
+    p = (4 / 3 * math.pi / n_tc) / 8.0
+    q = (1 - p) ** 64
+    assert abs(on_axis.mean() - q) < 5 * math.sqrt(q * (1 - q) / m) + 2e-4
+    x = pts[~on_axis].astype(np.float64)
+    r = np.linalg.norm(x, axis=1)
+    assert np.all((r > 0) & (r * r <= h2))
+    c = x @ d / r
+    cmin = 1 - 2 / n_tc
+    assert np.all(c >= cmin - 1e-12)
+    e1 = np.cross(d, [1.0, 0.0, 0.0] if abs(d[0]) < 0.9 else [0.0, 1.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(d, e1)
+    phi = np.arctan2(x @ e2, x @ e1) % (2 * math.pi)
+    for sample, cdf in (((r / H) ** 3, stats.uniform(0, 1).cdf),
+                        (c, stats.uniform(cmin, 1 - cmin).cdf),
+                        (phi, stats.uniform(0, 2 * math.pi).cdf)):
+        assert stats.kstest(sample, cdf).pvalue > 1e-3
+    # the draws depend on every counter field
+    base = oracle.virtual_offset(77, 5, 3, 1, h2, d, n_tc)
+    for args in ((78, 5, 3, 1), (77, 6, 3, 1), (77, 5, 4, 1), (77, 5, 3, 1 + (1 << 32))):
+        assert not np.array_equal(oracle.virtual_offset(*args, h2, d, n_tc), base)
+
+
 def _front_radius(s, wl):
     L = wl["box_L"][0]
     pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
