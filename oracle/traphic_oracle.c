@@ -11,11 +11,11 @@
  * 2011), the reading taken is stated at the function that implements it.
  *
  * Parity unpinned (no printed number or closed form fixes them; checked only through
- * photon conservation and the physical limits): how a virtual particle's absorptions are
- * shared among its neighbours, and the cooling coefficients other than the recombination
+ * the physical limits): the cooling coefficients other than the recombination
  * coefficients.  Where a virtual particle lands is checked statistically against the
- * uniform law of its reading; the rest of its step (its interpolated n_HI, projected length
- * and clock) by invariants of a uniform medium that hold wherever the point lands.  The equal split among cone members and the
+ * uniform law of its reading; the rest of its step (its interpolated n_HI, projected length,
+ * clock and the sharing of its absorptions) by invariants of a uniform medium and by brute
+ * force of whole chains on tiny boxes.  The equal split among cone members and the
  * photon-weighted merge of arriving packets are readings the paper does not fix; a
  * brute-force computation of one hop on tiny boxes checks that this code does what they
  * say.  The chemistry update is checked by its convergence to a stiff integration of its

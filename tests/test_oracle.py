@@ -613,6 +613,112 @@ def test_virtual_particle_lands_uniformly_in_the_cone_part_of_the_smoothing_sphe
         assert not np.array_equal(oracle.virtual_offset(*args, h2, d, n_tc), base)
 
 
+def _m4(x):
+    """M4 cubic spline of support 1 without its normalisation (Monaghan & Lattanzio 1985)."""
+    return np.where(x <= 0.5, 1 - 6 * x ** 2 + 6 * x ** 3, np.where(x <= 1, 2 * (1 - x) ** 3, 0.0))
+
+
+def _virtual_chain_against_brute_force(seed, near):
+    """One packet into an empty cone; returns the number of virtual particles it made."""
+    rng = np.random.default_rng(seed)
+    L = 1.0 * KPC
+    c0 = np.full(3, 0.5)
+    d = np.array([1.0, 0.0, 0.0])
+
+    def dirs(m, lo, hi):
+        ct = rng.uniform(lo, hi, m)
+        ph = rng.uniform(0.0, 2 * np.pi, m)
+        st = np.sqrt(1 - ct ** 2)
+        return np.stack([ct, st * np.cos(ph), st * np.sin(ph)], 1)
+
+    # the sender's k neighbours all lie behind it; a group just beyond its smoothing radius,
+    # near the axis, puts gas close to where the virtual particle lands (small r / h_v);
+    # without it the first virtual particle's cone is often empty too (a chain)
+    k = 16
+    groups = [[c0], c0 + rng.uniform(0.04, 0.05, (k, 1)) * dirs(k, -1.0, -0.1)]
+    if near:
+        groups.append(c0 + rng.uniform(0.051, 0.065, (8, 1)) * dirs(8, 0.8, 1.0))
+    groups += [c0 + rng.uniform(0.07, 0.2, (16, 1)) * dirs(16, 0.5, 1.0),
+               c0 + rng.uniform(0.08, 0.15, (10, 1)) * dirs(10, -0.6, 0.6)]
+    pos = np.concatenate(groups) * L
+    n = len(pos)
+    wl = W.tiny(n=n, seed=seed, n_ngb=k, L=L, n_tc=8)
+    nH = np.exp(rng.normal(math.log(1e-3), 0.7, n))
+    wl.update(x=pos[:, 0].copy(), y=pos[:, 1].copy(), z=pos[:, 2].copy(), n_H=nH,
+              N_H=nH * (0.05 * L) ** 3 * rng.uniform(0.5, 2.0, n), x_HI=rng.uniform(0.01, 0.2, n),
+              T=np.full(n, 1e4), src_box=np.zeros(0, np.int32), src_x=np.zeros(0),
+              src_y=np.zeros(0), src_z=np.zeros(0), src_ndot=np.zeros(0))
+    wl["params"]["dt"] = wl["params"]["dt_em"] = 1.0
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    qi = s.quantised()
+    q = qi.astype(np.float64)
+    nbr, h2s = s.neighbours()[:2]
+    assert all((q[j] - q[0]) @ d < 0 for j in nbr[0])
+    s.rotate(0)
+    s.emit(0)
+    N0 = 1e50
+    _put_packet(s, 0, N0, d)
+    b0 = int(np.nonzero(s.slots()[0][0])[0][0])
+    assert s.transport(0) == 0
+
+    u = L / (1 << 20)
+    sigma = wl["sigma"][0]
+    nHI = wl["x_HI"] * nH
+    V = wl["N_H"] / nH
+    cmin = 1.0 - 2.0 / 8
+    idx = np.arange(n)
+    dep = np.zeros(n)
+    arrived = np.zeros(n)
+    fid, hop, qs, h2, N = b0 + 1, 0, qi[0], int(h2s[0]), N0
+    escaped = 0.0
+    for _ in range(8):
+        qv = qs + oracle.virtual_offset(wl["params"]["seed"], 0, hop, fid, h2, d, 8)
+        if not np.all((qv >= 0) & (qv < (1 << 20))):
+            escaped = N                 # a point outside the box: the photons leave it
+            break
+        d2 = ((qi - qv) ** 2).sum(1)
+        near = np.lexsort((idx, d2))[:k]
+        h2v = int(d2[near[-1]])
+        om = V[near] * _m4(np.sqrt(d2[near] / h2v))
+        l = ((qv - qs) @ d) * u
+        A = N * -math.expm1(-sigma * (om @ nHI[near] / om.sum()) * l)
+        dep[near] += A * om * nHI[near] / (om @ nHI[near])
+        N -= A
+        rel = q[near] - qv
+        cosang = rel @ d / np.maximum(np.linalg.norm(rel, axis=1), 1e-300)
+        assert np.all(np.abs(cosang - cmin) > 1e-9)
+        members = near[cosang > cmin]
+        if len(members):
+            for j in members:
+                lj = ((q[j] - qv) @ d) * u
+                a = (N / len(members)) * -math.expm1(-sigma * nHI[j] * lj)
+                dep[j] += a
+                arrived[j] += N / len(members) - a
+            break
+        qs, h2, hop, fid = qv, h2v, hop + 1, oracle.mix64(fid)
+    else:
+        raise AssertionError("virtual chain longer than 8 hops")
+    assert s.stats()["virtual"] == hop + 1
+    got = s.deposits()[0][:, 0]
+    assert np.allclose(got, dep, rtol=1e-11, atol=1e-13 * N0)
+    assert np.allclose(s.slots()[0].sum(1), arrived, rtol=1e-11, atol=1e-13 * N0)
+    assert abs(s.budget()[0][2] - escaped) <= 1e-12 * N0
+    return hop + 1
+
+
+def test_virtual_particle_shares_absorptions_by_sph_weight_and_neutral_density():
+    """Brute force of a virtual-particle chain in a non-uniform medium (Sec. 2.1, reading 11):
+    the point comes from the pinned placement draw; its neighbours are the n_ngb nearest gas
+    particles (ties to the lower index); n_HI there is the Shepard-normalised SPH estimate with
+    weights V_k W(r_k / h_v), V = N_H / n_H; the photons absorbed on the projected way to it are
+    shared in proportion to V_k W_k n_HI,k; what is left goes to its cone members in equal
+    shares (or to the next virtual particle, one hop later, with the mixed packet identity)."""
+    chains = [_virtual_chain_against_brute_force(seed, near)
+              for seed, near in zip(range(31, 39), [True] * 4 + [False] * 4)]
+    assert max(chains) >= 2, chains     # a chain of virtual particles is exercised
+
+
 def _front_radius(s, wl):
     L = wl["box_L"][0]
     pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
