@@ -3,7 +3,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from paper_1311_0182_gb300 import distributed as D
 from paper_1311_0182_gb300 import workloads as W
