@@ -31,7 +31,6 @@
 #define MAXK 32
 
 static const double K_B = 1.380649e-16;    /* erg/K */
-static const double EV = 1.602176634e-12;  /* erg */
 static const double C_LIGHT = 2.99792458e10; /* cm/s */
 static const double T_HI = 157807.0;       /* K, hydrogen ionisation temperature */
 
