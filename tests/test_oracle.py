@@ -171,6 +171,16 @@ def test_recombination_coefficients_match_paper():
     assert r2["alpha_A"] < r["alpha_A"] and r2["beta"] > r["beta"] and r2["L_cex"] > r["L_cex"]
 
 
+def test_collisional_ionisation_cooling_removes_the_ionisation_energy():
+    """Each collisional ionisation takes the 13.598 eV ionisation energy of hydrogen out of the
+    gas, so its cooling rate coefficient is that energy times the ionisation coefficient; the
+    free-free rate grows as sqrt(T) (constant Gaunt factor)."""
+    for T in (1e4, 3e4, 1e5, 1e6):
+        r = oracle.rates(T)
+        assert abs(r["L_cion"] / r["beta"] / EV / 13.598 - 1) < 2e-4
+        assert abs(oracle.rates(4 * T)["L_ff"] / r["L_ff"] - 2) < 1e-12
+
+
 def test_recombination_heating_energy():
     v, tol = paper_values()["kT_27000K_eV"]
     assert abs(K_B * 27000 / EV / v - 1) < tol
