@@ -1,7 +1,10 @@
 """Host logic of the benchmark (no GPU): the roofline arithmetic, the committed DRAM traffic
 (taken only when the CUDA sources match the profiled ones, scaled by particle count), the
-per-kernel shares of a step and the clock samples' summary."""
+per-kernel shares of a step, the clock samples' summary, and the reference arm's JSON line."""
+import json
 import os
+import subprocess
+import sys
 import types
 
 import numpy as np
@@ -71,3 +74,34 @@ def test_clock_summary_reports_throttle_reasons():
     out = c.stop(dev=0)
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]           # the other GPU's row is not counted
+
+
+def _reference_arm(env_extra):
+    from conftest import ROOT
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                           "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                          cwd=ROOT, env=env, timeout=600)
+
+
+def test_reference_arm_prints_one_contract_line_on_rank_0_only():
+    """The reference arm times the CPU oracle: one JSON line with the contract's keys, its
+    cpu_baseline and e2e describing the same run; the other ranks of a torchrun print nothing."""
+    r = _reference_arm({"RANK": "0"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["value"] > 0 and out["steps"] == 1
+    assert out["metric"] == bench.METRIC and out["higher_is_better"] is True
+    assert "workload" in out["config"]
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
+    e2e = out["e2e"]
+    assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    r1 = _reference_arm({"RANK": "1"})
+    assert r1.returncode == 0 and r1.stdout.strip() == ""
