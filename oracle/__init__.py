@@ -355,6 +355,6 @@ class Sim:
         return out
 
     def stats(self):
-        out = (C.c_longlong * 4)()
+        out = (C.c_longlong * 5)()
         self.L.orc_get_stats(self.h, out)
-        return dict(zip(["hops", "virtual", "escaped_virtual", "subcycles"], list(out)))
+        return dict(zip(["hops", "virtual", "escaped_virtual", "subcycles", "sends"], list(out)))

@@ -514,7 +514,7 @@ struct orc_sim {
     double *tally; /* [nb*4] running sums (Neumaier compensated with tallc) */
     double *tallc;
     freelist_t cur, nxt;
-    long long st_hops, st_virtual, st_escaped_v, st_sub;
+    long long st_hops, st_virtual, st_escaped_v, st_sub, st_sends;
     int built;
 };
 
@@ -1112,6 +1112,7 @@ static void make_virtual(orc_sim *s, long long step, int hop, int box, const int
 static void send_packet(orc_sim *s, long long step, int hop, int box, const int64_t *qs,
                         const int32_t *nbr, int64_t h2, double N, const double d[3],
                         double clock, double eps, double sig, int nu, uint64_t fid) {
+    s->st_sends++;
     int kn = s->cfg.n_ngb, members[MAXK], m = 0;
     for (int k = 0; k < kn; ++k) {
         const int64_t *qj = s->q + 3 * (long long)nbr[k];
@@ -1139,6 +1140,7 @@ int orc_transport(orc_sim *s, long long step) {
     s->st_hops = 0;
     s->st_virtual = 0;
     s->st_escaped_v = 0;
+    s->st_sends = 0;
     for (int hop = 0;; ++hop) {
         long long nact = 0;
         for (long long i = 0; i < n; ++i)
@@ -1304,9 +1306,10 @@ void orc_get_budget(const orc_sim *s, double *out) {
     }
 }
 
-void orc_get_stats(const orc_sim *s, long long out[4]) {
+void orc_get_stats(const orc_sim *s, long long out[5]) {
     out[0] = s->st_hops;
     out[1] = s->st_virtual;
     out[2] = s->st_escaped_v;
     out[3] = s->st_sub;
+    out[4] = s->st_sends;
 }

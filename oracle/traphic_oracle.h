@@ -130,8 +130,9 @@ void orc_get_deposits(const orc_sim *s, double *abs_ /* [n*nf] */, double *absE 
                       double *pass /* [n*nf] */);
 /* per box: emitted, absorbed, escaped, in flight (cumulative photon counts) */
 void orc_get_budget(const orc_sim *s, double *out /* [n_boxes*4] */);
-/* hops, virtual particles, escaped virtuals, chemistry subcycles of the last step */
-void orc_get_stats(const orc_sim *s, long long out[4]);
+/* hops, virtual particles, escaped virtuals, chemistry subcycles, and packets sent (by gas
+   particles, sources and virtual particles) of the last step */
+void orc_get_stats(const orc_sim *s, long long out[5]);
 
 #ifdef __cplusplus
 }

@@ -729,6 +729,37 @@ def test_virtual_particle_shares_absorptions_by_sph_weight_and_neutral_density()
     assert max(chains) >= 2, chains     # a chain of virtual particles is exercised
 
 
+def test_cost_does_not_grow_with_the_number_of_sources():
+    """Packets merge per reception cone at every particle, so the work of a step is bounded by
+    the particles and their cones, not by the sources (Sec. 2.1): in each hop at most
+    n S gas slots send, plus each free packet (a source's first-hop packets and the virtual
+    particles) once.  The same luminosity split over 64 sources clustered where one source
+    sat costs well under twice as many sends, where a method tracing rays per source would
+    cost about 64 times as many."""
+    base = W.cfg1(n_side=16)
+    L = base["box_L"][0]
+    tot = base["src_ndot"].sum()
+    rng = np.random.default_rng(1)
+    p = base["params"]
+    sends = {}
+    for ns in (1, 64):
+        pos = np.array([[0.5, 0.5, 0.5]]) * L if ns == 1 else (0.5 + rng.uniform(-0.02, 0.02, (ns, 3))) * L
+        wl = dict(base, src_box=np.zeros(ns, np.int32), src_x=pos[:, 0].copy(),
+                  src_y=pos[:, 1].copy(), src_z=pos[:, 2].copy(), src_ndot=np.full(ns, tot / ns))
+        s = oracle.Sim(wl)
+        s.build_neighbours()
+        sends[ns] = 0
+        for step in range(4):
+            s.step(step)
+            st = s.stats()
+            bound = st["hops"] * s.n * s.S + ns * p["n_ec"] * p["n_freq_src"] + st["virtual"]
+            assert 0 < st["sends"] <= bound
+            sends[ns] += st["sends"]
+        e, ab, esc, fl = s.budget()[0]
+        assert abs(e - ab - esc - fl) <= 1e-12 * e
+    assert sends[64] < 2 * sends[1], sends
+
+
 def _front_radius(s, wl):
     L = wl["box_L"][0]
     pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
