@@ -729,6 +729,38 @@ def test_virtual_particle_shares_absorptions_by_sph_weight_and_neutral_density()
     assert max(chains) >= 2, chains     # a chain of virtual particles is exercised
 
 
+@pytest.mark.parametrize("n_ec,k_em", [(8, 1), (32, 2), (8, 4)])
+def test_source_emission_is_complete_and_isotropic(n_ec, k_em):
+    """A source emits ndot dt photons per step (Sec. 2.1): K = dt / dt_em emissions, each split
+    equally over N_EC packets along its emission axes, rotated at random before each emission.
+    The axes of each emission sum to zero, so in an optically thin box, with every packet
+    stopping at the first gas it reaches, the photons held afterwards total ndot dt and their
+    momenta cancel."""
+    wl = W.cfg1(n_side=12)
+    n = len(wl["x"])
+    dt = 1.0
+    wl.update(x_HI=np.zeros(n))
+    wl["params"].update(n_ec=n_ec, dt=dt, dt_em=dt / k_em)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    s.rotate(0)
+    s.rebin()
+    s.emit(0)
+    ndot_dt = wl["src_ndot"].sum() * dt
+    assert abs(s.budget()[0][0] - ndot_dt) <= 1e-14 * ndot_dt
+    assert s.transport(0) == 0
+    e, ab, esc, fl = s.budget()[0]
+    assert ab == 0.0 and esc == 0.0
+    f = s.slots()
+    N = f[0].sum()
+    assert abs(N - ndot_dt) <= 1e-13 * ndot_dt
+    assert np.linalg.norm(f[1:4].sum(axis=(1, 2))) <= 1e-12 * ndot_dt
+    Rs = s.rotations()[1]
+    assert len(Rs) == k_em
+    if k_em > 1:
+        assert not np.allclose(Rs[0], Rs[1])     # a fresh rotation before each emission
+
+
 def test_cost_does_not_grow_with_the_number_of_sources():
     """Packets merge per reception cone at every particle, so the work of a step is bounded by
     the particles and their cones, not by the sources (Sec. 2.1): in each hop at most
