@@ -729,6 +729,54 @@ def test_virtual_particle_shares_absorptions_by_sph_weight_and_neutral_density()
     assert max(chains) >= 2, chains     # a chain of virtual particles is exercised
 
 
+@pytest.mark.parametrize("n_rc,shared", [(8, 0), (32, 0), (8, 1)])
+def test_rebin_moves_each_held_packet_to_the_new_cone_of_its_direction(n_rc, shared):
+    """At the start of a step the reception cones are rotated anew (Sec. 2.1) and every packet a
+    particle holds moves, with its photons, momentum and energy, into the cone of the new set
+    nearest its direction; packets landing in one cone merge, and every clock restarts.  In a
+    shared bin the photon-weighted cross-section sum travels with its packet.  Brute force on
+    random packets, the new cone taken as argmax over the rotated axes."""
+    rng = np.random.default_rng(40 + n_rc + shared)
+    wl = W.tiny(n=60, n_ngb=8, n_rc=n_rc, rec_shared_bin=shared)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    s.rotate(0)
+    f = np.zeros((6, s.n, s.S))
+    occ = rng.random((s.n, s.S)) < 0.3
+    N = rng.uniform(1e40, 1e42, (s.n, s.S)) * occ
+    d = rng.normal(size=(s.n, s.S, 3))
+    d /= np.linalg.norm(d, axis=2, keepdims=True)
+    f[0] = N
+    f[1:4] = np.moveaxis(N[..., None] * d * rng.uniform(0.3, 1.0, (s.n, s.S, 1)), 2, 0)
+    f[4] = N * rng.uniform(0.0, 1e13, (s.n, s.S))
+    f[5] = N * rng.uniform(1.0, 5.0, (s.n, s.S)) * EV
+    s.set_slots(f)
+    G = None
+    if shared:
+        G = N[:, :n_rc] * rng.uniform(1e-18, 6e-18, (s.n, n_rc))
+        s.set_shared_sigma(G)
+    s.rotate(1)
+    s.rebin()
+    A = oracle.axis_set(n_rc)
+    R = s.rotations()[0]
+    want = np.zeros_like(f)
+    wantG = np.zeros((s.n, n_rc))
+    for i in range(s.n):
+        Ri = R[i].reshape(3, 3)
+        for sl in np.nonzero(occ[i])[0]:
+            nu = sl // n_rc
+            b = int(np.argmax((Ri @ A.T).T @ f[1:4, i, sl]))
+            want[[0, 1, 2, 3, 5], i, nu * n_rc + b] += f[[0, 1, 2, 3, 5], i, sl]
+            if shared and nu == 0:
+                wantG[i, b] += G[i, sl]
+    got = s.slots()
+    for k in range(6):
+        assert np.allclose(got[k], want[k], rtol=1e-13, atol=1e-13 * np.abs(want[k]).max())
+    assert np.all(got[4] == 0.0)
+    if shared:
+        assert np.allclose(s.shared_sigma(), wantG, rtol=1e-13, atol=0)
+
+
 @pytest.mark.parametrize("n_ec,k_em", [(8, 1), (32, 2), (8, 4)])
 def test_source_emission_is_complete_and_isotropic(n_ec, k_em):
     """A source emits ndot dt photons per step (Sec. 2.1): K = dt / dt_em emissions, each split
