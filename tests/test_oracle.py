@@ -2,7 +2,11 @@
 
 Each test would fail on a plausible mistake in the oracle: a wrong generator constant, a cone of
 the wrong opening angle, a transposed rotation, a dropped N_HI or dt in the rates, a wrong energy
-normalisation, a photon leak, or a wrong recombination coefficient.
+normalisation, a photon leak, a wrong recombination coefficient, an unequal split or a merge
+weighted before absorption, a virtual particle drawn outside its cone or weighted wrongly, a
+packet left in its old cone at the step start, or a source emission of the wrong size.
+Brute-force tests recompute small cases directly from the definitions; copies of the oracle
+with such mistakes planted in them fail those tests.
 """
 import math
 
