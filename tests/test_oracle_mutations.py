@@ -1,0 +1,96 @@
+"""Planted mistakes: each case builds a copy of the CPU oracle with one plausible mistake in it
+(a dropped term, a wrong index, a wrong weight) and checks that the brute-force and invariant
+pins of tests/test_oracle.py fail on it.  No GPU is involved; every planted mistake keeps
+memory accesses in bounds, so the copies run in this process."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle as T
+from conftest import ROOT
+
+ONE_HOP = [lambda: T.test_one_hop_splits_equally_among_cone_members_and_merges_photon_weighted(s)
+           for s in (11, 12, 13)]
+UNIFORM_VP = [T.test_virtual_particle_hop_in_a_uniform_medium_is_independent_of_its_position]
+CHAIN_VP = [T.test_virtual_particle_shares_absorptions_by_sph_weight_and_neutral_density]
+PLACEMENT = [lambda: T.test_virtual_particle_lands_uniformly_in_the_cone_part_of_the_smoothing_sphere(k)
+             for k in (8, 32)]
+REBIN = [lambda: T.test_rebin_moves_each_held_packet_to_the_new_cone_of_its_direction(n, sh)
+         for n, sh in ((8, 0), (32, 0), (8, 1))]
+EMISSION = [lambda: T.test_source_emission_is_complete_and_isotropic(e, k)
+            for e, k in ((8, 1), (32, 2), (8, 4))]
+
+# name: (text in the oracle, its replacement, the pins expected to catch it)
+MUTATIONS = {
+    "split_by_k_plus_1": ("double w = N / (double)m;", "double w = N / (double)(m + 1);", ONE_HOP),
+    "first_member_only": ("for (int a = 0; a < m; ++a) deliver(",
+                          "for (int a = 0; a < 1; ++a) deliver(", ONE_HOP),
+    "clock_without_hop": ("s->nx[4][p] += T * (clock + l / C_LIGHT);",
+                          "s->nx[4][p] += T * clock;", ONE_HOP),
+    "clock_weighted_before_absorption": ("s->nx[4][p] += T * (clock + l / C_LIGHT);",
+                                         "s->nx[4][p] += w * (clock + l / C_LIGHT);", ONE_HOP),
+    "momentum_weighted_before_absorption": ("s->nx[1][p] += T * d[0];",
+                                            "s->nx[1][p] += w * d[0];", ONE_HOP),
+    "energy_weighted_before_absorption": ("s->nx[5][p] += T * eps;",
+                                          "s->nx[5][p] += w * eps;", ONE_HOP),
+    "sph_estimate_unnormalised": ("double nHIv = swn / sw;", "double nHIv = swn / (sw * 1.01);",
+                                  UNIFORM_VP),
+    "sph_estimate_by_count": ("double nHIv = swn / sw;", "double nHIv = swn / (double)kn;",
+                              UNIFORM_VP),
+    "virtual_clock_not_advanced": ("v.clock = clock + l / C_LIGHT;", "v.clock = clock;",
+                                   UNIFORM_VP),
+    "shares_without_neutral_density": ("double Ak = A * ((om[k] * s->nHI[j]) / swn);",
+                                       "double Ak = A * (om[k] / sw);", CHAIN_VP),
+    "weights_without_kernel": ("om[k] = (s->NH[j] / s->nH[j]) * kernel_w(qk);",
+                               "om[k] = (s->NH[j] / s->nH[j]);", CHAIN_VP),
+    "volume_as_atom_count": ("om[k] = (s->NH[j] / s->nH[j]) * kernel_w(qk);",
+                             "om[k] = s->NH[j] * kernel_w(qk);", CHAIN_VP),
+    "kernel_inner_branch": ("if (q <= 0.5) return 1.0 - 6.0 * q * q + 6.0 * q * q * q;",
+                            "if (q <= 0.5) return 1.0 - 6.0 * q * q + 5.0 * q * q * q;", CHAIN_VP),
+    "identity_not_mixed": ("v.fid = orc_mix64(fid);", "v.fid = fid + 1;", CHAIN_VP),
+    "placement_without_cone": ("if (r2 > 0 && r2 <= h2 && orc_in_cone(del, d, n_tc)) found = 1;",
+                               "if (r2 > 0 && r2 <= h2) found = 1;", PLACEMENT),
+    "placement_sphere_2h": ("if (r2 > 0 && r2 <= h2 && orc_in_cone(del, d, n_tc)) found = 1;",
+                            "if (r2 > 0 && r2 <= 4 * h2 && orc_in_cone(del, d, n_tc)) found = 1;",
+                            PLACEMENT),
+    "placement_fallback_at_h": ("double f = 0.5 * (double)H;", "double f = (double)H;", PLACEMENT),
+    "placement_identity_truncated": ("(uint32_t)(fid >> 32)},", "0u},", PLACEMENT),
+    "rebin_keeps_clock": ("            s->sl[4][p] += 0.0;\n",
+                          "            s->sl[4][p] += tmp[4 * S + sl];\n", REBIN),
+    "rebin_keeps_old_slot": ("            long long p = i * S + nu * nrc + b;\n            s->sl[0][p] += N;",
+                             "            long long p = i * S + sl; (void)b;\n            s->sl[0][p] += N;",
+                             REBIN),
+    "rebin_moves_wrong_sum": ("if (s->sg && nu == 0) s->sg[i * nrc + b] += gold[sl];",
+                              "if (s->sg && nu == 0) s->sg[i * nrc + b] += gold[b];", REBIN),
+    "emission_split_by_n_ec_plus_1": (
+        "p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em / (double)nec;",
+        "p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em / (double)(nec + 1);", EMISSION),
+    "single_emission_per_step": (
+        "        for (int k = 0; k < s->K; ++k)\n            for (int nu = 0; nu < nfs; ++nu)",
+        "        for (int k = 0; k < 1; ++k)\n            for (int nu = 0; nu < nfs; ++nu)", EMISSION),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path, monkeypatch):
+    old, new, pins = MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "traphic_oracle.c")).read()
+    assert src.count(old) == 1, name
+    (tmp_path / "traphic_oracle.c").write_text(src.replace(old, new))
+    (tmp_path / "traphic_oracle.h").write_text(
+        open(os.path.join(ROOT, "oracle", "traphic_oracle.h")).read())
+    so = tmp_path / "liborc_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", str(so), str(tmp_path / "traphic_oracle.c"),
+                           "-lm"])
+    monkeypatch.setattr(oracle, "_lib", None)
+    monkeypatch.setattr(oracle, "build", lambda force=False: str(so))
+    caught = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, f"{name}: no pin failed"
