@@ -232,6 +232,13 @@ def test_chemistry_photon_accounting_and_recombination_photons():
     phot = 1e-4 * NH
     x, T, nrec, _, _ = oracle.chem_particle(p, nH, NH, phot, 0.0, 1.0, 1e4)
     assert abs((1 - x) * NH / phot - 1) < 1e-3
+    # partially ionised gas: the rate is per neutral atom, so the absorbed photons still ionise
+    # as many atoms (against the same step without photons, which recombines a little)
+    x0 = 0.3
+    dose = 1e-5 * x0 * NH
+    xa = oracle.chem_particle(p, nH, NH, 0.0, 0.0, x0, 1e4)[0]
+    xb = oracle.chem_particle(p, nH, NH, dose, 0.0, x0, 1e4)[0]
+    assert abs((xa - xb) * NH / dose - 1) < 1e-2
     # fully ionised gas without photons: ground-level recombinations alpha_1 n_e n_HII V dt
     x, T, nrec, _, _ = oracle.chem_particle(p, nH, NH, 0.0, 0.0, 0.0, 1e4)
     r = oracle.rates(1e4)

@@ -21,9 +21,29 @@ REBIN = [lambda: T.test_rebin_moves_each_held_packet_to_the_new_cone_of_its_dire
          for n, sh in ((8, 0), (32, 0), (8, 1))]
 EMISSION = [lambda: T.test_source_emission_is_complete_and_isotropic(e, k)
             for e, k in ((8, 1), (32, 2), (8, 4))]
+CONE = [T.test_transmission_cone_solid_angle]
+BIN = [T.test_reception_bin_is_nearest_rotated_axis]
+RATES = [T.test_recombination_coefficients_match_paper,
+         T.test_collisional_ionisation_cooling_removes_the_ionisation_energy]
+CHEM = [T.test_chemistry_photon_accounting_and_recombination_photons]
+CHAIN = [T.test_beer_lambert_chain]
 
 # name: (text in the oracle, its replacement, the pins expected to catch it)
 MUTATIONS = {
+    "cone_half_the_solid_angle": ("double c = 1.0 - 2.0 / (double)n_tc;",
+                                  "double c = 1.0 - 1.0 / (double)n_tc;", CONE),
+    "rotation_partly_transposed": ("double e0 = R[0] * d[0] + R[3] * d[1] + R[6] * d[2];",
+                                   "double e0 = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];", BIN),
+    "case_b_coefficient_off": ("double aB = 2.753e-14 * pow(lam, 1.500)",
+                               "double aB = 2.953e-14 * pow(lam, 1.500)", RATES),
+    "ionisation_cooling_half_energy": ("double Lci = K_B * T_HI * beta;",
+                                       "double Lci = 0.5 * K_B * T_HI * beta;", RATES),
+    "free_free_wrong_power": ("double Lff = 1.42e-27 * 1.3 * sqrt(T);",
+                              "double Lff = 1.42e-27 * 1.3 * pow(T, 0.45);", RATES),
+    "photoionisation_rate_per_atom_not_neutral": ("Gam = phot / (NHI * dt);",
+                                                  "Gam = phot / (NH * dt);", CHEM),
+    "optical_depth_with_total_density": ("double tau = (sig * s->nHI[j]) * l;",
+                                         "double tau = (sig * s->nH[j]) * l;", CHAIN),
     "split_by_k_plus_1": ("double w = N / (double)m;", "double w = N / (double)(m + 1);", ONE_HOP),
     "first_member_only": ("for (int a = 0; a < m; ++a) deliver(",
                           "for (int a = 0; a < 1; ++a) deliver(", ONE_HOP),
