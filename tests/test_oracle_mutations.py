@@ -27,9 +27,14 @@ RATES = [T.test_recombination_coefficients_match_paper,
          T.test_collisional_ionisation_cooling_removes_the_ionisation_energy]
 CHEM = [T.test_chemistry_photon_accounting_and_recombination_photons]
 CHAIN = [T.test_beer_lambert_chain]
+KNN = [lambda: T.test_knn_grid_equals_brute_force(k) for k in ("uniform", "clustered", "lattice")]
 
 # name: (text in the oracle, its replacement, the pins expected to catch it)
 MUTATIONS = {
+    "knn_ties_to_higher_index": ("return da < db || (da == db && ia < ib);",
+                                 "return da < db || (da == db && ia > ib);", KNN),
+    "knn_distance_without_z": ("return dx * dx + dy * dy + dz * dz;",
+                               "return dx * dx + dy * dy + 0 * dz;", KNN),
     "cone_half_the_solid_angle": ("double c = 1.0 - 2.0 / (double)n_tc;",
                                   "double c = 1.0 - 1.0 / (double)n_tc;", CONE),
     "rotation_partly_transposed": ("double e0 = R[0] * d[0] + R[3] * d[1] + R[6] * d[2];",
