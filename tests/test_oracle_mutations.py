@@ -27,10 +27,16 @@ RATES = [T.test_recombination_coefficients_match_paper,
          T.test_collisional_ionisation_cooling_removes_the_ionisation_energy]
 CHEM = [T.test_chemistry_photon_accounting_and_recombination_photons]
 CHAIN = [T.test_beer_lambert_chain]
+PHILOX = [T.test_philox_known_answers]
+BARRIER = [T.test_barrier_test_is_exact_against_rational_arithmetic]
 KNN = [lambda: T.test_knn_grid_equals_brute_force(k) for k in ("uniform", "clustered", "lattice")]
 
 # name: (text in the oracle, its replacement, the pins expected to catch it)
 MUTATIONS = {
+    "philox_multiplier": ("uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;",
+                          "uint64_t p0 = (uint64_t)0xD2511F55u * (uint64_t)c0;", PHILOX),
+    "barrier_crossing_sign": ("+ (__int128)sa * (2 * (b[i1] - a[i1]));",
+                              "- (__int128)sa * (2 * (b[i1] - a[i1]));", BARRIER),
     "knn_ties_to_higher_index": ("return da < db || (da == db && ia < ib);",
                                  "return da < db || (da == db && ia > ib);", KNN),
     "knn_distance_without_z": ("return dx * dx + dy * dy + dz * dz;",
