@@ -62,9 +62,14 @@ def workload(args):
     return W.cfg2(n_side=args.n_side, transport_fp32=1 if args.precision == "fp32" else 0)
 
 
+def workload_name(n_side: int) -> str:
+    return f"hii_region_{n_side}^3_bb1e5K_8bins_32cones_Tevolving"
+
+
 def workload_config(args, wl):
     p = wl["params"]
-    return {"workload": f"hii_region_{args.n_side}^3_bb1e5K_8bins_32cones_Tevolving",
+    n_side = round(int(wl["box_off"][-1]) ** (1 / 3))
+    return {"workload": workload_name(n_side),
             "particles": int(wl["box_off"][-1]), "n_ngb": p["n_ngb"], "cones": p["n_tc"],
             "freq_bins": p["n_freq_src"] + 1, "dt_myr": p["dt"] / 3.15576e13,
             "start": "seeded mid-expansion HII region (front at 0.8 R_S)",
@@ -227,8 +232,12 @@ def run_ours(args):
                          "same_result_bits": same, "clocks": clocks_h,
                          "note": "host-driven hop loop, one synchronisation per hop; the "
                                  "dominant kernel bracketed with events"}
+    out["roofline"]["hop_loop_model"] = hop_loop_model(st, wl, ms / args.steps)
     out["kernel_shares"] = shares
     out["stats_last_step"] = st
+    out["floor_hits_last_step"] = st["floor_hits"]
+    from paper_1311_0182_gb300.run import ionised_fraction
+    out["ionised_volume_fraction"] = ionised_fraction(ctx.state()["x_HI"], wl["n_H"], wl["N_H"])
     out["budget_closure"] = float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])
     ctx_h.close()
     if not args.no_e2e:
@@ -236,7 +245,8 @@ def run_ours(args):
     ctx.close()
     if not args.no_fp64 and args.precision == "fp32":
         out["fp64_path"] = fp64_path(args, stream)
-        out["fp32_vs_fp64_per_shell"] = precision_errors(args, stream)
+        out["fp32_over_fp64"] = out["value"] / out["fp64_path"]["value"]
+        out["fp32_vs_fp64"] = precision_check(args, stream)
     if args.original:
         # the original implementation of recombination radiation (Sec. 2.2): per-particle
         # emission cones, on the same workload and precision
@@ -256,7 +266,7 @@ def run_ours(args):
         out["on_the_spot_shared_layout"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1,
                                                      rec_shared_bin=1)
     if args.batched:
-        out["batched_boxes"] = batched(args, stream)
+        out["batched_boxes"] = batched(args, stream, world=world, rank=rank)
     if args.paper_workloads:
         out["paper_workloads"] = paper_workloads(stream)
     if rank == 0 and not args.no_cpu_baseline:
@@ -332,6 +342,25 @@ def roofline(ctx, kt, ms_step_total, args):
                             for n, v in kt.items() if v["ms"] > 0}}
 
 
+def hop_loop_model(st: dict, wl: dict, ms_step: float) -> dict:
+    """The per-particle-hop byte model of the whole sweep: per hop and active particle
+    2 S_act 20 B of slots read and written, n_ngb (4 + 4) B of reverse and forward lists, 12 B of
+    position, 8 B of x_HI and n_H, 16 N_f B of tallies; plus about 100 + 8 N_f B per particle of
+    chemistry per step.  The active counts are the device counters of the last timed step
+    (packets able to move and particles holding one, summed over its hops).  Virtual particles
+    are outside this model; the per-kernel models count them."""
+    peak, kind = peaks()
+    p = wl["params"]
+    kn, nf = p["n_ngb"], p["n_freq_src"] + (0 if p.get("rec_shared_bin", 0) else 1)
+    n = int(wl["box_off"][-1])
+    B = (2 * 20 * st["moving_packets"] + (8 * kn + 12 + 8 + 16 * nf) * st["senders"] +
+         (100 + 8 * nf) * n)
+    ach = B / (ms_step / 1e3) / 1e9
+    return {"bytes_per_step": B, "ms_per_step": ms_step, "achieved": ach, "unit": "GB/s",
+            "peak": peak, "frac": ach / peak, "packets_moved": st["moving_packets"],
+            "particle_hops": st["senders"], "peak_kind": kind}
+
+
 def fp64_path(args, stream, **over):
     """The all-FP64 GPU path on the same workload and start state (the comparison path); with
     `over`, the same timing for other parameters."""
@@ -339,7 +368,7 @@ def fp64_path(args, stream, **over):
     from paper_1311_0182_gb300 import rt, workloads as W
     wl = W.cfg2(n_side=args.n_side, **dict(dict(transport_fp32=0), **over))
     ctx = rt.Context(wl, stream=stream)
-    steps = max(1, min(args.steps, 2))
+    steps = max(1, args.steps)
     with torch.cuda.stream(stream):
         ctx.load_workload(wl)
         ctx.build_neighbours()
@@ -367,17 +396,28 @@ def fp64_path(args, stream, **over):
             "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
 
 
-def batched(args, stream, warmup=2, steps=3):
+def batched(args, stream, warmup=2, steps=3, world=1, rank=0):
     """Workload 4: 512 independent boxes of 8^3 to 40^3 particles (log-uniform count),
     lognormal densities, one central source each, T evolving, 8 cones, advanced together in
-    the same launches (the step graph), FP32 transport and all FP64."""
+    the same launches (the step graph), FP32 transport and all FP64.  With several ranks the
+    boxes are split between them (longest-processing-time greedy on particle count), each rank
+    runs its boxes with no collective in the timed region, the time is the slowest rank's and
+    the per-box photon budgets are summed over ranks afterwards."""
     import torch
-    from paper_1311_0182_gb300 import rt, workloads as W
-    wl = W.cfg4()
-    n = int(wl["box_off"][-1])
+    from paper_1311_0182_gb300 import distributed as D, rt, workloads as W
+    wl_all = W.cfg4()
+    n = int(wl_all["box_off"][-1])
+    nb = len(wl_all["box_L"])
+    mine = np.arange(nb)
+    wl = wl_all
+    if world > 1:
+        mine = D.partition_boxes(np.diff(wl_all["box_off"]), world)[rank]
+        wl = D.local_workload(wl_all, mine)
     out = {"workload": "512 boxes, 8^3-40^3 particles each (log-uniform), lognormal density, "
                        "central source, 8 cones, 2 frequency bins, T evolving",
-           "particles": n, "boxes": len(wl["box_L"]), "warmup": warmup, "steps": steps}
+           "particles": n, "boxes": nb, "warmup": warmup, "steps": steps, "ranks": world,
+           "scaling": "strong" if world > 1 else None,
+           "partition": "LPT on particle count; no collective inside the timed steps"}
     for fp in (1, 0):
         ctx = rt.Context(wl, stream=stream, transport_fp32=fp)
         with torch.cuda.stream(stream):
@@ -394,11 +434,15 @@ def batched(args, stream, warmup=2, steps=3):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
         st = ctx.stats()
-        b = ctx.budget()
+        b = np.zeros((nb, 4))
+        b[mine] = ctx.budget()
+        if world > 1:
+            ms = D.max_over_ranks(ms, device="cuda")
+            b = D.sum_over_ranks(b, device="cuda")
         out["fp32" if fp else "fp64"] = {
             "value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
-            "ms_per_step": ms / steps, "hops_last_step": st["hops"],
-            "virtual_last_step": st["virtual"],
+            "ms_per_step": ms / steps, "hops_last_step_rank0": st["hops"],
+            "virtual_last_step_rank0": st["virtual"],
             "worst_box_budget_closure": float(np.max(np.abs(b[:, 0] - b[:, 1:].sum(1)) / b[:, 0]))}
         ctx.close()
     out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
@@ -442,40 +486,48 @@ def paper_workloads(stream, warmup=1, steps=2):
     return out
 
 
-def precision_errors(args, stream, steps=10):
+def precision_check(args, stream, steps=10):
     """FP32-transport path against the all-FP64 path (which follows the oracle to rounding in
-    the parity tests), same workload and start, after `steps` steps: the relative error of x_HI
-    and T per radial shell around the source (shells of 1/16 of the box side)."""
+    the parity tests), same workload and start, run side by side for `steps` steps: the
+    routing-affected particles (absorptions of some step off by more than ROUTE_TOL, see
+    paper_1311_0182_gb300/accuracy.py), the largest relative errors of x_HI and T among all
+    particles and among the others, and per radial shell around the source (shells of 1/16 of
+    the box side) the largest errors and affected counts."""
     import torch
-    import numpy as np
-    from paper_1311_0182_gb300 import rt, workloads as W
-    st = {}
-    for fp in (1, 0):
-        wl = W.cfg2(n_side=args.n_side, transport_fp32=fp)
-        ctx = rt.Context(wl, stream=stream)
-        with torch.cuda.stream(stream):
-            ctx.load_workload(wl)
-            ctx.build_neighbours()
-            for s in range(steps):
-                ctx.step(s)
-        st[fp] = ctx.state()
-        ctx.close()
+    from paper_1311_0182_gb300 import accuracy as ACC, rt, workloads as W
+    wl = W.cfg2(n_side=args.n_side)
+    ctx = {fp: rt.Context(wl, stream=stream, transport_fp32=fp) for fp in (1, 0)}
+    affected = np.zeros(int(wl["box_off"][-1]), bool)
+    with torch.cuda.stream(stream):
+        for c in ctx.values():
+            c.load_workload(wl)
+            c.build_neighbours()
+        for s in range(steps):
+            dep = {}
+            for fp, c in ctx.items():
+                c.step(s)
+                a, e, _ = c.deposits()
+                dep[fp] = (a.sum(1), e.sum(1))
+            ACC.mark_routing_affected(dep[1][0], dep[0][0], dep[1][1], dep[0][1], wl["N_H"],
+                                      affected)
+    st = {fp: c.state() for fp, c in ctx.items()}
+    for c in ctx.values():
+        c.close()
+    out = {"steps": steps, "reference": "all-FP64 GPU path",
+           **ACC.summary(st[1], st[0], affected, steps)}
     pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
     src = np.array([wl["src_x"][0], wl["src_y"][0], wl["src_z"][0]])
-    L = float(wl["box_L"][0])
-    r = np.linalg.norm(pos - src, axis=1) / L
-    out = {"steps": steps, "shell_width_of_box": 1 / 16, "shells": []}
-    for k in range(8):
+    r = np.linalg.norm(pos - src, axis=1) / float(wl["box_L"][0])
+    relx = np.abs(st[1]["x_HI"] / st[0]["x_HI"] - 1)
+    relT = np.abs(st[1]["T"] / st[0]["T"] - 1)
+    shells = []
+    for k in range(9):
         m = (r >= k / 16) & (r < (k + 1) / 16)
-        if not m.any():
-            continue
-        sh = {"r_over_L": [k / 16, (k + 1) / 16], "particles": int(m.sum())}
-        for f in ("x_HI", "T"):
-            a, b = st[1][f][m], st[0][f][m]
-            rel = np.abs(a / b - 1)
-            sh[f] = {"median_rel": float(np.median(rel)), "max_rel": float(rel.max()),
-                     "median_value": float(np.median(b))}
-        out["shells"].append(sh)
+        if m.any():
+            shells.append([round(k / 16, 4), int(m.sum()), int(affected[m].sum()),
+                           float(f"{relx[m].max():.3g}"), float(f"{relT[m].max():.3g}")])
+    out["shells"] = {"columns": ["r_over_L_from", "particles", "routing_affected",
+                                 "x_HI_max_rel", "T_max_rel"], "rows": shells}
     return out
 
 
@@ -588,15 +640,34 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl_args, W.cfg2(n_side=args.n_side)),
+            "config": dict(workload_config(wl_args, wl), transport="fp64 (oracle)",
+                           sample_of=workload_name(args.n_side),
+                           note=f"the oracle times whole steps of the same recipe at {n_side}^3 "
+                                f"particles, a bounded sample of the {args.n_side}^3 workload; "
+                                f"per-particle cost grows with the box (more hops)"),
             "cpu_baseline": {"value": v, "unit": "particle-sweeps/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step a whole RT step of the workload at {n_side}^3"},
             "e2e": {"value": v, "unit": "particle-sweeps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
+def relaunch_on_ranks(n: int) -> int:
+    """`--gpus N` without a launcher: run this same command as N ranks under
+    torch.distributed.run on this node (rendezvous on 127.0.0.1); returns its exit code."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_on_ranks(args.gpus))
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))

@@ -48,7 +48,13 @@ typedef enum {
                              quantisation cells */
     RT_ERR_CAPACITY = 6,  /* more free packets (sources + virtual particles) in a hop than free_cap */
     RT_ERR_STATE = 7,     /* call out of order, e.g. rt_transport before rt_build_neighbours */
-    RT_ERR_RANGE = 8      /* a virtual-particle deposit overflowed its fixed-point accumulator */
+    RT_ERR_RANGE = 8,     /* a virtual-particle deposit overflowed its fixed-point accumulator */
+    RT_ERR_SUBCYCLE_LIMIT = 9 /* the chemistry held some particle's subcycle at the floor
+                                 dt/sub_cap although the 10% energy limit asked for a shorter
+                                 one: that explicit energy step changed u by more than 10%.  The
+                                 step completed and its state is written; the status says that it
+                                 is less accurate there (raise sub_cap).  Numbered 9 because 6 was
+                                 taken by RT_ERR_CAPACITY. */
 } rt_status;
 
 /* Treatment of recombination radiation (Sec. 2.1, last paragraphs; Sec. 2.2) */
@@ -197,14 +203,18 @@ rt_status rt_transport(rt_ctx *ctx, long long step, void *stream);
 
 /* rt_chemistry -- per particle: photoionisation and photoheating rates from the step's
    absorptions, subcycled update of x_HI and T, and the ground-level recombination photons to
-   emit next step (Sec. 2.1, Sec. 2.2). */
+   emit next step (Sec. 2.1, Sec. 2.2).  Subcycles are limited to a 10% change of the energy
+   density, with a floor of dt/sub_cap.  Synchronises `stream`.  Errors: RT_ERR_SUBCYCLE_LIMIT
+   (some subcycle was held at the floor; the state is updated, rt_get_stats counts the floor
+   hits), RT_ERR_CUDA. */
 rt_status rt_chemistry(rt_ctx *ctx, void *stream);
 
 /* rt_step -- one RT step: rt_assign_cones, rt_merge, rt_emit, rt_transport, rt_chemistry and
    the photon budget.  Returns the first non-OK status.  Synchronises `stream` once, at the end.
    By default (rt_set_graph) the whole step runs as one CUDA graph launched on `stream`: the
    hop loop is a conditional while node whose last kernel decides on the device whether
-   another hop runs, so no host round trip separates hops.  The graph is captured on the
+   another hop runs, so no host round trip separates hops.  A transport error takes precedence
+   over RT_ERR_SUBCYCLE_LIMIT, which only reports that the (completed) chemistry hit its floor.  The graph is captured on the
    first call and again whenever a parameter it holds changes (configuration, barriers,
    source options, kNN grid, launch sizes).  The hop-by-hop path runs instead while kernels
    are timed (rt_set_profiling), when hop_cap is 0, and for the first step when tune_launch
@@ -249,7 +259,9 @@ rt_status rt_get_cone_masks(rt_ctx *ctx, unsigned *mask, int where, void *stream
    a file-scope device array of 4,194,304 entries (16 MiB) that every GPU loading the library
    holds until the process exits; n * S beyond that is rejected with RT_ERR_INVALID.  The first
    call on a device looks up the array's device address (cudaGetSymbolAddress, with that
-   device current); make that first call before any stream capture.  All calls share the
+   device current); make that first call before any stream capture.  The address is kept for
+   the rest of the process, so it stays valid only while that device's primary context lives:
+   after cudaDeviceReset on the device, do not call this entry point again.  All calls share the
    array: calls whose work overlaps on the GPU race, so serialise them (one stream, or wait for
    the previous call's copy).  With where == RT_HOST the call synchronises `stream`; with
    RT_DEVICE the copy is queued on `stream`. */
@@ -282,7 +294,9 @@ rt_status rt_get_shared_sigma(rt_ctx *ctx, double *G, int where, void *stream);
 rt_status rt_set_shared_sigma(rt_ctx *ctx, const double *G, int where, void *stream);
 /* absorptions of the current step: photons [n * nf], energy [n * nf] (erg), photons passing
    each particle [n * nf] (the intensity diagnostic of Sec. 3); nf = n_freq_src + 1, or
-   n_freq_src with rec_shared_bin */
+   n_freq_src with rec_shared_bin.  Valid after rt_transport and still after rt_chemistry (the
+   values do not depend on the x_HI the chemistry writes); cleared by the next rt_emit.
+   Allocates a temporary device buffer and synchronises `stream`. */
 rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass, int where,
                           void *stream);
 /* statistics of the last rt_transport/rt_chemistry, out[RT_NSTATS] (host): hops, virtual

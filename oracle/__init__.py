@@ -91,6 +91,7 @@ def lib():
             L.orc_chemistry.argtypes = [vp]
             L.orc_step.argtypes = [vp, C.c_longlong]
             L.orc_cone_masks.argtypes = [vp, P(u32)]
+            L.orc_cone_masks_dir.argtypes = [vp, P(d), P(u32)]
             L.orc_get_slots.argtypes = [vp, P(d)]
             L.orc_set_slots.argtypes = [vp, P(d)]
             L.orc_get_shared_sigma.argtypes = [vp, P(d)]
@@ -295,11 +296,18 @@ class Sim:
     def transport(self, step) -> int:
         return int(self.L.orc_transport(self.h, step))
 
-    def chemistry(self):
-        self.L.orc_chemistry(self.h)
+    def chemistry(self) -> int:
+        return int(self.L.orc_chemistry(self.h))
 
     def step(self, step) -> int:
         return int(self.L.orc_step(self.h, step))
+
+    def cone_masks_given_directions(self, dirs):
+        """Masks of the held packets with their directions given ([n, S, 3])."""
+        dd = np.ascontiguousarray(dirs, dtype=np.float64).reshape(self.n * self.S * 3)
+        m = np.zeros((self.n, self.S), np.uint32)
+        self.L.orc_cone_masks_dir(self.h, _p(dd, C.c_double), _p(m, C.c_uint32))
+        return m
 
     def cone_masks(self):
         m = np.zeros((self.n, self.S), np.uint32)
@@ -355,6 +363,7 @@ class Sim:
         return out
 
     def stats(self):
-        out = (C.c_longlong * 5)()
+        out = (C.c_longlong * 6)()
         self.L.orc_get_stats(self.h, out)
-        return dict(zip(["hops", "virtual", "escaped_virtual", "subcycles", "sends"], list(out)))
+        return dict(zip(["hops", "virtual", "escaped_virtual", "subcycles", "sends", "floor_hits"],
+                        list(out)))

@@ -270,7 +270,13 @@ void orc_chem_particle(const orc_config *cfg, double nH, double NH, double phot,
                 double ht = 0.1 * u / fabs(dudt);
                 if (ht < h) h = ht;
             }
-            if (h < dtmin) { h = dtmin; ++nfloor; }
+            /* the floor binds only when the 10% limit, not the time left in the step, made
+               the subcycle shorter than dt/sub_cap: the subcycle taken then changes u by more
+               than 10% */
+            if (h < dtmin) {
+                if (h < dt - t) ++nfloor;
+                h = dtmin;
+            }
         }
         if (h >= dt - t) { h = dt - t; last = 1; }
         double xn, intII;
@@ -514,7 +520,7 @@ struct orc_sim {
     double *tally; /* [nb*4] running sums (Neumaier compensated with tallc) */
     double *tallc;
     freelist_t cur, nxt;
-    long long st_hops, st_virtual, st_escaped_v, st_sub, st_sends;
+    long long st_hops, st_virtual, st_escaped_v, st_sub, st_sends, st_floor;
     int built;
 };
 
@@ -1206,9 +1212,11 @@ int orc_transport(orc_sim *s, long long step) {
 }
 
 /* Chemistry step of every particle (Sec. 2.1, Sec. 2.2); the recombination photons
-   found here are emitted at the start of the next RT step. */
-void orc_chemistry(orc_sim *s) {
-    long long nsub = 0;
+   found here are emitted at the start of the next RT step.  Returns
+   ORC_ERR_SUBCYCLE_LIMIT when some particle's energy step was held at the subcycle floor
+   dt/sub_cap (the state is still updated). */
+int orc_chemistry(orc_sim *s) {
+    long long nsub = 0, nfloor = 0;
     for (long long i = 0; i < s->n; ++i) {
         double phot = 0.0;
         for (int nu = 0; nu < s->nf; ++nu) phot += s->abs_[i * s->nf + nu];
@@ -1218,8 +1226,11 @@ void orc_chemistry(orc_sim *s) {
         s->Nrec[i] = out[0];
         s->epsrec[i] = s->cfg.eps_rr_fixed >= 0.0 ? s->cfg.eps_rr_fixed : K_B * s->T[i];
         nsub += (long long)out[1];
+        nfloor += (long long)out[2];
     }
     s->st_sub = nsub;
+    s->st_floor = nfloor;
+    return nfloor > 0 ? ORC_ERR_SUBCYCLE_LIMIT : ORC_OK;
 }
 
 int orc_step(orc_sim *s, long long step) {
@@ -1228,8 +1239,8 @@ int orc_step(orc_sim *s, long long step) {
     orc_rebin(s);
     orc_emit(s, step);
     int st = orc_transport(s, step);
-    orc_chemistry(s);
-    return st;
+    int cs = orc_chemistry(s);
+    return st != ORC_OK ? st : cs;
 }
 
 void orc_cone_masks(const orc_sim *s, uint32_t *mask) {
@@ -1241,6 +1252,28 @@ void orc_cone_masks(const orc_sim *s, uint32_t *mask) {
                 long long p = i * S + sl;
                 double M[3] = {s->sl[1][p], s->sl[2][p], s->sl[3][p]}, d[3];
                 packet_dir(M, d);
+                for (int k = 0; k < kn; ++k) {
+                    const int64_t *qj = s->q + 3 * (long long)s->nbr[i * kn + k];
+                    const int64_t *qi = s->q + 3 * i;
+                    int64_t del[3] = {qj[0] - qi[0], qj[1] - qi[1], qj[2] - qi[2]};
+                    if (orc_in_cone(del, d, s->cfg.n_tc)) m |= 1u << k;
+                }
+            }
+            mask[i * S + sl] = m;
+        }
+}
+
+/* The same membership test with the packet directions given ([n * S * 3], row per slot)
+   instead of formed from the held momenta: the masks of a transport whose direction
+   arithmetic differs from FP64 (the FP32 packets), evaluated with the exact test (Sec. 2.1:
+   the cone of solid angle 4 pi / N_TC about the packet direction). */
+void orc_cone_masks_dir(const orc_sim *s, const double *dirs, uint32_t *mask) {
+    int S = s->S, kn = s->cfg.n_ngb;
+    for (long long i = 0; i < s->n; ++i)
+        for (int sl = 0; sl < S; ++sl) {
+            uint32_t m = 0;
+            if (slot_active(s, i, sl, NULL)) {
+                const double *d = dirs + 3 * (i * S + sl);
                 for (int k = 0; k < kn; ++k) {
                     const int64_t *qj = s->q + 3 * (long long)s->nbr[i * kn + k];
                     const int64_t *qi = s->q + 3 * i;
@@ -1306,10 +1339,11 @@ void orc_get_budget(const orc_sim *s, double *out) {
     }
 }
 
-void orc_get_stats(const orc_sim *s, long long out[5]) {
+void orc_get_stats(const orc_sim *s, long long out[6]) {
     out[0] = s->st_hops;
     out[1] = s->st_virtual;
     out[2] = s->st_escaped_v;
     out[3] = s->st_sub;
     out[4] = s->st_sends;
+    out[5] = s->st_floor;
 }

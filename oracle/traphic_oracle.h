@@ -22,7 +22,7 @@
 extern "C" {
 #endif
 
-enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_HOP_LIMIT = 4 };
+enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_HOP_LIMIT = 4, ORC_ERR_SUBCYCLE_LIMIT = 9 };
 /* recombination radiation: transported through the reception cones (Sec. 2.2, the new
    implementation); on-the-spot case B; case A; transported through N_EC per-particle emission
    cones whose packets stay separate (Sec. 2.2, the original implementation) */
@@ -110,11 +110,12 @@ void orc_get_rotations(const orc_sim *s, double *R /* [n*9] */, double *Rs /* [n
 void orc_rebin(orc_sim *s);                        /* clock reset + re-bin (Sec. 2.1) */
 void orc_emit(orc_sim *s, long long step);         /* recombination + source emission */
 int orc_transport(orc_sim *s, long long step);     /* hop loop; returns status */
-void orc_chemistry(orc_sim *s);
+int orc_chemistry(orc_sim *s);     /* ORC_ERR_SUBCYCLE_LIMIT at the subcycle floor */
 int orc_step(orc_sim *s, long long step);
 /* masks of the current packets: bit k set when neighbour k of particle i lies in the
    transmission cone of slot sl; entries of inactive slots are 0 */
 void orc_cone_masks(const orc_sim *s, uint32_t *mask /* [n*S] */);
+void orc_cone_masks_dir(const orc_sim *s, const double *dirs, uint32_t *mask); /* given directions [n*S*3] */
 /* state access; slot fields are N, Mx, My, Mz, C (= N * clock), E (= N * eps) */
 void orc_get_slots(const orc_sim *s, double *f /* [6*n*S] */);
 void orc_set_slots(orc_sim *s, const double *f);
@@ -132,7 +133,7 @@ void orc_get_deposits(const orc_sim *s, double *abs_ /* [n*nf] */, double *absE 
 void orc_get_budget(const orc_sim *s, double *out /* [n_boxes*4] */);
 /* hops, virtual particles, escaped virtuals, chemistry subcycles, and packets sent (by gas
    particles, sources and virtual particles) of the last step */
-void orc_get_stats(const orc_sim *s, long long out[5]);
+void orc_get_stats(const orc_sim *s, long long out[6]);
 
 #ifdef __cplusplus
 }

@@ -823,10 +823,10 @@ extern "C" rt_status rt_transport(rt_ctx *c, long long step, void *stream) {
     return rt_run_step_parts(c, 4, step, (cudaStream_t)stream);
 }
 
-extern "C" rt_status rt_chemistry(rt_ctx *c, void *stream) {
-    rt_status s = need_built(c);
-    if (s) return s;
-    cudaStream_t st = (cudaStream_t)stream;
+// the chemistry and the end-of-step tally; RT_OK even when the subcycle floor was hit (the
+// floor hits are in c->stats[4] afterwards)
+static rt_status chemistry_run(rt_ctx *c, cudaStream_t st) {
+    rt_status s;
     if ((s = rt_chem_launch(c, st))) return s;
     if ((s = rt_budget_launch(c, 1, st))) return s;
     cudaMemcpyAsync(c->cnt_h, c->d.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
@@ -834,6 +834,20 @@ extern "C" rt_status rt_chemistry(rt_ctx *c, void *stream) {
     c->stats[3] = c->cnt_h[CNT_SUB];
     c->stats[4] = c->cnt_h[CNT_FLOOR];
     return s;
+}
+
+rt_status rt_subcycle_status(rt_ctx *c) {
+    if (c->stats[4] <= 0) return RT_OK;
+    return rt_fail(c, RT_ERR_SUBCYCLE_LIMIT,
+                   std::to_string(c->stats[4]) + " chemistry subcycles were held at the floor "
+                   "dt/sub_cap with a larger than 10% energy change (raise sub_cap)");
+}
+
+extern "C" rt_status rt_chemistry(rt_ctx *c, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    if ((s = chemistry_run(c, (cudaStream_t)stream))) return s;
+    return rt_subcycle_status(c);
 }
 
 extern "C" rt_status rt_step(rt_ctx *c, long long step, void *stream) {
@@ -851,8 +865,8 @@ extern "C" rt_status rt_step(rt_ctx *c, long long step, void *stream) {
     if ((s = rt_emit(c, step, stream))) return s;
     rt_status ts = rt_run_step_parts(c, 4, step, st);
     if (ts != RT_OK && ts != RT_ERR_HOP_LIMIT) return ts;
-    if ((s = rt_chemistry(c, stream))) return s;
-    return ts;
+    if ((s = chemistry_run(c, st))) return s;
+    return ts != RT_OK ? ts : rt_subcycle_status(c);
 }
 
 extern "C" rt_status rt_get_state(rt_ctx *c, double *x_HI, double *T, double *N_rec,
@@ -1056,13 +1070,14 @@ __global__ void k_masks(DevPtrs P, int cur, unsigned *out) {
 extern "C" rt_status rt_get_cone_masks(rt_ctx *c, unsigned *mask, int where, void *stream) {
     rt_status s = need_built(c);
     if (s) return s;
-    if (!mask) return RT_ERR_INVALID;
+    if (!mask || (where != RT_HOST && where != RT_DEVICE)) return RT_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     long long m = c->d.n * c->d.S;
     unsigned *t = dtmp<unsigned>(m);
     if (!t) return rt_fail(c, RT_ERR_OOM, "temp");
     k_masks<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->d, c->cur, t);
-    s = copy_out(c, mask, t, sizeof(unsigned) * m, where, st);
+    s = rt_cuda_check(c, cudaGetLastError(), "mask kernel");
+    if (s == RT_OK) s = copy_out(c, mask, t, sizeof(unsigned) * m, where, st);
     cudaStreamSynchronize(st);
     cudaFree(t);
     return s;
@@ -1228,7 +1243,9 @@ __global__ void k_deposits(DevPtrs P, double *a, double *e, double *ps) {
     if (key >= P.n * P.nf) return;
     long long i = key / P.nf;
     ps[key] = P.pass[key] + (double)P.passf[key] * P.norm[P.pbox[i]];
-    double NHI = P.xHI[i] * P.NH[i];
+    // the fixed-point words count in units of the neutral atoms at the start of the step (the
+    // n_HI frozen for the transport), not of the x_HI the chemistry has written since
+    double NHI = P.nH[i] > 0.0 ? P.nHI[i] / P.nH[i] * P.NH[i] : 0.0;
     a[key] = P.abs[key] + ((double)P.fx_abs[key] + (double)P.fx_lo[key] / FX_LO_SCALE) *
                               (NHI / FX_ABS_SCALE);
     e[key] = P.absE[key] + (double)P.fx_E[key] * (NHI * 1.602176634e-12 / FX_E_SCALE);

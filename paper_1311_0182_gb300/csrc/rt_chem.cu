@@ -4,7 +4,8 @@
 // Gamma = N_abs / (N_HI dt) and photoheating per neutral atom H = E_abs / (N_HI dt) from the
 // step's absorptions; subcycles with the electron density frozen inside each; inside a
 // subcycle the exact exponential solution of dx/dt = alpha n_e (1 - x) - (Gamma + beta n_e) x
-// and an explicit step of u = 1.5 k T n_H (1 + x_HII) limited to a 10% change (floor dt/sub_cap).
+// and an explicit step of u = 1.5 k T n_H (1 + x_HII) limited to a 10% change (floor dt/sub_cap;
+// a subcycle held at the floor is counted, and the step then reports RT_ERR_SUBCYCLE_LIMIT).
 // Rates: Hui & Gnedin (1997) recombination, recombination cooling and collisional ionisation;
 // Cen (1992) collisional-excitation cooling; free-free with g_ff = 1.3.  Case B with
 // on-the-spot, case A otherwise; with transport of recombination radiation the ground-level
@@ -97,7 +98,12 @@ __global__ void k_chem(DevPtrs P) {
                     double ht = 0.1 * u / fabs(dudt);
                     if (ht < h) h = ht;
                 }
-                if (h < dtmin) { h = dtmin; ++nfloor; }
+                // the floor binds only when the 10% limit, not the time left in the step,
+                // made the subcycle shorter than dt/sub_cap
+                if (h < dtmin) {
+                    if (h < dt - t) ++nfloor;
+                    h = dtmin;
+                }
             }
             if (h >= dt - t) { h = dt - t; last = true; }
             double xn, intII;

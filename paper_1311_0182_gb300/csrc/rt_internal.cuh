@@ -306,6 +306,8 @@ void rt_graph_destroy(rt_ctx *c);
 // the grid sizes (blocks) of the sender side, the virtual particles and the receiver side
 void rt_launch_grids(const rt_ctx *c, long long out[3]);
 rt_status rt_chem_launch(rt_ctx *c, cudaStream_t st);
+// RT_ERR_SUBCYCLE_LIMIT (with its message) when the last chemistry counted floor hits, else RT_OK
+rt_status rt_subcycle_status(rt_ctx *c);
 rt_status rt_budget_launch(rt_ctx *c, int phase, cudaStream_t st);
 void rt_host_axis_set(int n, double *out);
 void rt_upload_axes();

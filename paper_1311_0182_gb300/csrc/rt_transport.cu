@@ -214,15 +214,20 @@ __device__ __forceinline__ void packet_dir(double Mx, double My, double Mz, doub
     else { d0 = 1.0; d1 = 0.0; d2 = 0.0; }
 }
 
-// FP32: normalised photon counts can be small enough for |M|^2 to underflow, so scale first
+// FP32: normalised photon counts can be small enough for |M|^2 to underflow, so scale first.
+// Every operation is a correctly rounded IEEE single-precision operation in a fixed order
+// (reciprocal, products, (a^2 + b^2) + c^2, square root, reciprocal, products), so the FP32
+// direction is a reproducible function of the stored momentum: the exact cone test (FP64, on
+// this direction) then decides every membership the same way wherever it is evaluated.
 __device__ __forceinline__ void packet_dir(float Mx, float My, float Mz, float &d0, float &d1,
                                            float &d2) {
     float s = fmaxf(fabsf(Mx), fmaxf(fabsf(My), fabsf(Mz)));
     if (s > 0.0f) {
         float is = __frcp_rn(s);
-        float a = Mx * is, b = My * is, c = Mz * is;
-        float rn = rsqrtf(a * a + b * b + c * c);
-        d0 = a * rn; d1 = b * rn; d2 = c * rn;
+        float a = __fmul_rn(Mx, is), b = __fmul_rn(My, is), c = __fmul_rn(Mz, is);
+        float q = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+        float rn = __frcp_rn(__fsqrt_rn(q));
+        d0 = __fmul_rn(a, rn); d1 = __fmul_rn(b, rn); d2 = __fmul_rn(c, rn);
     } else {
         d0 = 1.0f; d1 = 0.0f; d2 = 0.0f;
     }
@@ -1894,7 +1899,8 @@ static rt_status step_graph(rt_ctx *c, long long step, cudaStream_t st) {
     c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], c->d.F_cap);
     c->stats[3] = c->cnt_h[CNT_SUB];
     c->stats[4] = c->cnt_h[CNT_FLOOR];
-    return transport_end(c, sizeof(Real) == 4);
+    rt_status ts = transport_end(c, sizeof(Real) == 4);
+    return ts != RT_OK ? ts : rt_subcycle_status(c);
 }
 
 rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st) {

@@ -15,7 +15,8 @@ from . import build as _build
 RT_HOST, RT_DEVICE = 0, 1
 STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID", 2: "RT_ERR_OOM", 3: "RT_ERR_CUDA",
           4: "RT_ERR_HOP_LIMIT", 5: "RT_ERR_KNN", 6: "RT_ERR_CAPACITY", 7: "RT_ERR_STATE",
-          8: "RT_ERR_RANGE"}
+          8: "RT_ERR_RANGE", 9: "RT_ERR_SUBCYCLE_LIMIT"}
+RT_ERR_HOP_LIMIT, RT_ERR_SUBCYCLE_LIMIT = 4, 9
 SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_build_neighbours",
            "rt_assign_cones", "rt_merge", "rt_emit", "rt_transport", "rt_chemistry", "rt_step",
            "rt_get_state", "rt_set_state", "rt_get_budget", "rt_get_neighbours", "rt_get_quantised",
@@ -240,12 +241,17 @@ class Context:
         self._check(st, "rt_transport")
         return st
 
-    def chemistry(self):
-        self._check(self.L.rt_chemistry(self.h, self._s()), "rt_chemistry")
+    def chemistry(self, allow_subcycle_limit=False):
+        st = self.L.rt_chemistry(self.h, self._s())
+        if st == RT_ERR_SUBCYCLE_LIMIT and allow_subcycle_limit:
+            return st
+        self._check(st, "rt_chemistry")
+        return st
 
-    def step(self, step, allow_hop_limit=False):
+    def step(self, step, allow_hop_limit=False, allow_subcycle_limit=False):
         st = self.L.rt_step(self.h, step, self._s())
-        if st == 4 and allow_hop_limit:
+        if (st == RT_ERR_HOP_LIMIT and allow_hop_limit) or \
+                (st == RT_ERR_SUBCYCLE_LIMIT and allow_subcycle_limit):
             return st
         self._check(st, "rt_step")
         return st

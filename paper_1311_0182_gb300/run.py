@@ -2,6 +2,7 @@
 
     python -m paper_1311_0182_gb300.run cfg2 --steps 20 [--n-side 32] [--fp64] [--profile-every 10]
                                         [--checkpoint-every 10 --checkpoint-dir DIR] [--resume FILE]
+                                        [--host-loop]
 
 Each line holds the step, the simulated time, the wall time of the step, the hop and virtual-
 particle counts, the photon budget (emitted, absorbed, escaped, in flight; Sec. 2.1: photon
@@ -9,6 +10,9 @@ conservation) with its closure, the ionised volume fraction and the I-front radi
 first source (Sec. 3 follows the front of the HII region), and every --profile-every steps the
 radial profiles of x_HI and T in shells of 1/32 of the box side.  Checkpoints go through
 rt_save_state; --resume restores one and continues from the step it was taken after.
+--host-loop drives the hop loop from the host (rt_set_graph off), so that every kernel of a step
+is a launch of its own (a profiler sees kernel nodes under the step graph's conditional node
+only as the graph launch).
 """
 from __future__ import annotations
 
@@ -115,10 +119,14 @@ def main(argv=None):
     ap.add_argument("--checkpoint-every", type=int, default=0)
     ap.add_argument("--checkpoint-dir", default=None)
     ap.add_argument("--resume", default=None, help="checkpoint file step<N>.ckpt to continue from")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the hop loop from the host: one launch per kernel and hop")
     args = ap.parse_args(argv)
     wl = _workload(args.workload, args)
     from . import rt
     ctx = rt.context_for(wl)
+    if args.host_loop:
+        ctx.set_graph(False)
     start = 0
     if args.resume:
         with open(args.resume, "rb") as f:

@@ -35,7 +35,7 @@ COOL_REC, COOL_CEX, COOL_CION, COOL_FF = 1, 2, 4, 8
 
 def default_params(**kw) -> dict:
     p = dict(n_ngb=32, n_ec=8, n_tc=8, n_rc=8, n_freq_src=1, dt=2.5 * MYR, dt_em=2.5 * MYR,
-             rec_mode=REC_TRANSPORT, evolve_T=0, seed=1001, hop_cap=4096, sub_cap=10000,
+             rec_mode=REC_TRANSPORT, evolve_T=0, seed=1001, hop_cap=4096, sub_cap=100000000,
              cool_flags=COOL_REC | COOL_CEX, T_floor=10.0, eps_rr_fixed=-1.0, sigma_rec=6.3e-18,
              transport_fp32=0, rec_shared_bin=0, tune_launch=0)
     p.update(kw)

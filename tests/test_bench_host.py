@@ -98,6 +98,9 @@ def test_reference_arm_prints_one_contract_line_on_rank_0_only():
     assert out["impl"] == "reference" and out["value"] > 0 and out["steps"] == 1
     assert out["metric"] == bench.METRIC and out["higher_is_better"] is True
     assert "workload" in out["config"]
+    # the config names the size the oracle actually timed, and what it samples
+    assert out["config"]["particles"] == 24 ** 3 and "24^3" in out["config"]["workload"]
+    assert out["config"]["sample_of"] == bench.workload_name(64)
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
     e2e = out["e2e"]
@@ -105,3 +108,33 @@ def test_reference_arm_prints_one_contract_line_on_rank_0_only():
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     r1 = _reference_arm({"RANK": "1"})
     assert r1.returncode == 0 and r1.stdout.strip() == ""
+
+
+def test_hop_loop_model_counts_the_per_particle_hop_bytes(monkeypatch):
+    """Per hop and active particle 2 S_act 20 B of slots, n_ngb (4 + 4) B of lists, 12 + 8 B of
+    position and density, 16 N_f B of tallies; 100 + 8 N_f B of chemistry per particle."""
+    monkeypatch.setattr(bench, "peaks", lambda: (8000.0, "measured"))
+    wl = {"params": {"n_ngb": 32, "n_freq_src": 8, "rec_shared_bin": 0}, "box_off": [0, 1000]}
+    st = {"moving_packets": 5000, "senders": 300}
+    m = bench.hop_loop_model(st, wl, 2.0)
+    B = 40 * 5000 + (256 + 20 + 144) * 300 + (100 + 72) * 1000
+    assert m["bytes_per_step"] == B
+    assert np.isclose(m["achieved"], B / 2e-3 / 1e9) and np.isclose(m["frac"], m["achieved"] / 8000)
+
+
+def test_accuracy_bars_and_routing_count():
+    from paper_1311_0182_gb300 import accuracy as A
+    ref = {"x_HI": np.array([0.5, 5e-5, 0.9, 0.2]), "T": np.array([1e4, 1e4, 100.0, 300.0])}
+    got = {"x_HI": np.array([0.5004, 5e-5 + 2e-7, 0.9, 0.2]), "T": np.array([1e4, 1e4, 100.2, 300.0])}
+    assert A.xhi_ok(got["x_HI"], ref["x_HI"]).tolist() == [True, False, True, True]
+    assert A.state_ok(got, ref).tolist() == [True, False, False, True]
+    NH = np.full(4, 1e55)                  # floors: 1e43 photons, 1e47 eV
+    Ao = np.array([1e50, 1e50, 1e50, 0.0])
+    Eo = Ao * 5 * A.EV
+    # photons 0.2% off; 0.01% off; nothing off; energy off by half the energy floor
+    Ag = np.array([1.002e50, 1e50 + 1e46, 1e50, 0.0])
+    Eg = Eo + np.array([0.0, 0.0, 0.0, 0.5e-8 * A.EV * 1e55])
+    aff = A.mark_routing_affected(Ag, Ao, Eg, Eo, NH, np.zeros(4, bool))
+    assert aff.tolist() == [True, False, False, False]
+    s = A.summary(got, ref, aff)
+    assert s["routing_affected"] == 1 and s["off_bars"] == 2 and s["off_bars_not_affected"] == 2

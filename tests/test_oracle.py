@@ -270,6 +270,46 @@ def test_chemistry_cooling_reaches_floor_and_subcycles_bounded():
     assert nsub <= p["sub_cap"] + 1
 
 
+def test_subcycle_floor_hits_are_the_subcycles_the_floor_lengthened():
+    """A floor hit is counted exactly when the floor dt/sub_cap made a subcycle longer than the
+    10% energy limit allowed: with no hit counted, a floor 1000 times lower gives the same
+    result bit for bit (the last, shortened subcycle of a step is not a hit); with a hit it
+    gives another result."""
+    rng = np.random.default_rng(5)
+    hits = quiet = 0
+    for _ in range(400):
+        sc = int(rng.choice([20, 200, 2000]))
+        p = _params(evolve_T=1, cool_flags=3, dt=0.5 * MYR, sub_cap=sc)
+        nH, NH = 10 ** rng.uniform(-4, -2), 1e60
+        x0, T0 = rng.uniform(0.01, 1.0), 10 ** rng.uniform(2, 4.5)
+        phot = 10 ** rng.uniform(-6, 0) * x0 * NH
+        heat = phot * 10 ** rng.uniform(0, 1.5) * EV
+        r1 = oracle.chem_particle(p, nH, NH, phot, heat, x0, T0)
+        r2 = oracle.chem_particle(dict(p, sub_cap=1000 * sc), nH, NH, phot, heat, x0, T0)
+        if r1[4] == 0:
+            quiet += 1
+            assert r1[:3] == r2[:3]
+        else:
+            hits += 1
+            assert r1[:3] != r2[:3]
+    assert hits >= 10 and quiet >= 10
+
+
+def test_subcycle_floor_is_an_error_status_of_the_step():
+    """Sec. 2.1 chemistry with a floor too high for the heating at the front: the step still
+    completes (state written, budget closed) and reports the floor (status 9)."""
+    wl = W.cfg2(n_side=12, sub_cap=4)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    assert s.step(0) == 9
+    assert s.stats()["floor_hits"] > 0
+    b = s.budget()[0]
+    assert abs(b[0] - b[1:].sum()) <= 1e-12 * b[0]
+    s2 = oracle.Sim(W.cfg2(n_side=12))
+    s2.build_neighbours()
+    assert s2.step(0) == 0 and s2.stats()["floor_hits"] == 0
+
+
 # --- transport ------------------------------------------------------------------------------------
 def test_grey_bins_of_1e5K_blackbody_match_paper():
     pv = paper_values()

@@ -30,6 +30,7 @@ CHAIN = [T.test_beer_lambert_chain]
 PHILOX = [T.test_philox_known_answers]
 BARRIER = [T.test_barrier_test_is_exact_against_rational_arithmetic]
 KNN = [lambda: T.test_knn_grid_equals_brute_force(k) for k in ("uniform", "clustered", "lattice")]
+FLOOR = [T.test_subcycle_floor_hits_are_the_subcycles_the_floor_lengthened]
 
 # name: (text in the oracle, its replacement, the pins expected to catch it)
 MUTATIONS = {
@@ -98,6 +99,10 @@ MUTATIONS = {
     "emission_split_by_n_ec_plus_1": (
         "p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em / (double)nec;",
         "p.N = s->ndot[j * nfs + nu] * s->cfg.dt_em / (double)(nec + 1);", EMISSION),
+    "floor_counted_on_the_last_subcycle": ("                if (h < dt - t) ++nfloor;",
+                                           "                ++nfloor;", FLOOR),
+    "floor_not_counted": ("                if (h < dt - t) ++nfloor;",
+                          "                if (h < 0.0) ++nfloor;", FLOOR),
     "single_emission_per_step": (
         "        for (int k = 0; k < s->K; ++k)\n            for (int nu = 0; nu < nfs; ++nu)",
         "        for (int k = 0; k < 1; ++k)\n            for (int nu = 0; nu < nfs; ++nu)", EMISSION),
