@@ -203,7 +203,10 @@ int orc_bin(const double R[9], const double *axes, int n_rc, const double d[3]) 
 /* cooling and collisional ionisation: the fits of Hui & Gnedin (1997) with        */
 /* lambda = 2 T_HI / T.  Collisional excitation cooling: Cen (1992).  Free-free:   */
 /* 1.42e-27 g_ff sqrt(T) with g_ff = 1.3.  Compton cooling off the CMB is left out  */
-/* (static, non-cosmological test fields).                                         */
+/* (static, non-cosmological test fields).  The coefficients, their values at 1e4,  */
+/* 2e4, 3e4 and 1e5 K and their sources are tabulated in docs/rates; the case-A and */
+/* case-B coefficients are checked against Osterbrock & Ferland (2006, Table 2.1)   */
+/* with the values in tests/golden/published_rates.txt.                            */
 /* ------------------------------------------------------------------------------ */
 void orc_rates(double T, double out[8]) {
     double lam = 2.0 * T_HI / T;

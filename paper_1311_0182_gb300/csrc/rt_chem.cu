@@ -7,7 +7,10 @@
 // and an explicit step of u = 1.5 k T n_H (1 + x_HII) limited to a 10% change (floor dt/sub_cap;
 // a subcycle held at the floor is counted, and the step then reports RT_ERR_SUBCYCLE_LIMIT).
 // Rates: Hui & Gnedin (1997) recombination, recombination cooling and collisional ionisation;
-// Cen (1992) collisional-excitation cooling; free-free with g_ff = 1.3.  Case B with
+// Cen (1992) collisional-excitation cooling; free-free with g_ff = 1.3.  The coefficients, their
+// values at 1e4, 2e4, 3e4 and 1e5 K and their sources are tabulated in docs/rates (the same table
+// as the CPU oracle's); the case-A and case-B coefficients are checked against Osterbrock &
+// Ferland (2006, Table 2.1), tests/golden/published_rates.txt.  Case B with
 // on-the-spot, case A otherwise; with transport of recombination radiation the ground-level
 // recombinations (alpha_A - alpha_B) are the photons emitted next step.
 //

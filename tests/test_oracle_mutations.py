@@ -31,6 +31,7 @@ PHILOX = [T.test_philox_known_answers]
 BARRIER = [T.test_barrier_test_is_exact_against_rational_arithmetic]
 KNN = [lambda: T.test_knn_grid_equals_brute_force(k) for k in ("uniform", "clustered", "lattice")]
 FLOOR = [T.test_subcycle_floor_hits_are_the_subcycles_the_floor_lengthened]
+FIELD = [T.test_interior_field_is_the_attenuated_point_source_field]
 
 # name: (text in the oracle, its replacement, the pins expected to catch it)
 MUTATIONS = {
@@ -56,6 +57,8 @@ MUTATIONS = {
                                                   "Gam = phot / (NH * dt);", CHEM),
     "optical_depth_with_total_density": ("double tau = (sig * s->nHI[j]) * l;",
                                          "double tau = (sig * s->nH[j]) * l;", CHAIN),
+    "optical_depth_over_half_the_hop": ("double tau = (sig * s->nHI[j]) * l;",
+                                        "double tau = (sig * s->nHI[j]) * (0.5 * l);", FIELD),
     "split_by_k_plus_1": ("double w = N / (double)m;", "double w = N / (double)(m + 1);", ONE_HOP),
     "first_member_only": ("for (int a = 0; a < m; ++a) deliver(",
                           "for (int a = 0; a < 1; ++a) deliver(", ONE_HOP),
