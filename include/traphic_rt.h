@@ -155,6 +155,16 @@ rt_status rt_set_sources(rt_ctx *ctx, const int *box, const double *x, const dou
 rt_status rt_set_source_options(rt_ctx *ctx, const double *dir, const int *gate, int where,
                                 void *stream);
 
+/* rt_set_identities -- the identities the random streams use (the reception and emission-cone
+   rotations and the packet identities that seed the virtual-particle draws; Sec. 2.1 rotates
+   cones at random): particle i of box b draws as particle box_first_id[b] + (i - box_off[b]),
+   and source j as source src_id[j] (host arrays of n_boxes and n_src entries; NULL keeps the
+   own indices, the default).  Boxes cut out of a larger workload with the identities they have
+   there repeat their results in it bit for bit (the boxes of a workload are independent), which
+   is how the boxes of one workload are split over several GPUs.  Identities must lie in
+   [0, 2^32).  Waits for the device.  Errors: RT_ERR_INVALID, RT_ERR_CUDA. */
+rt_status rt_set_identities(rt_ctx *ctx, const long long *box_first_id, const long long *src_id);
+
 /* rt_set_barrier -- an artificial photon barrier in box `box` (Sec. 4): the disk of radius
    `radius` (cm) centred at centre[3] (box coordinates, cm), perpendicular to coordinate axis
    `axis` (0, 1, 2), removes every packet whose straight path from sender to receiver (or to

@@ -91,6 +91,7 @@ def lib():
             L.orc_chemistry.argtypes = [vp]
             L.orc_step.argtypes = [vp, C.c_longlong]
             L.orc_cone_masks.argtypes = [vp, P(u32)]
+            L.orc_set_identities.argtypes = [vp, P(C.c_longlong), P(C.c_longlong)]
             L.orc_cone_masks_dir.argtypes = [vp, P(d), P(u32)]
             L.orc_get_slots.argtypes = [vp, P(d)]
             L.orc_set_slots.argtypes = [vp, P(d)]
@@ -251,6 +252,12 @@ class Sim:
         for (b, axis, centre, radius) in wl.get("barriers", []):
             c = arr(centre, np.float64)
             self.L.orc_set_barrier(self.h, int(b), int(axis), _p(c, d), float(radius))
+        # optional: the identities of boxes and sources cut out of a larger workload
+        if "box_first_id" in wl or "src_id" in wl:
+            bf = arr(wl["box_first_id"], np.int64) if "box_first_id" in wl else None
+            si = arr(wl["src_id"], np.int64) if "src_id" in wl else None
+            self.L.orc_set_identities(self.h, None if bf is None else _p(bf, C.c_longlong),
+                                      None if si is None else _p(si, C.c_longlong))
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -503,6 +503,11 @@ struct orc_sim {
     double *nH, *NH, *xHI, *T;
     int ns;
     int *sbox;
+    /* identities in the random streams: particle i of box b draws as particle
+       gid0[b] + (i - box_off[b]) and source j as source sid[j] (by default their own indices),
+       so that the boxes of a larger workload, run apart, repeat their draws */
+    long long *gid0;
+    long long *sid;
     int64_t *sq;
     double *ndot, *sigma, *eps;
     double *sdir;  /* [ns*3] fixed emission direction of a directed source, 0: isotropic */
@@ -548,6 +553,12 @@ static int64_t quantise(double x, double L) {
     if (!(fl >= 0.0)) q = 0;
     if (q > ORC_Q - 1) q = ORC_Q - 1;
     return q;
+}
+
+/* identity of particle i in the random streams */
+static uint64_t gid(const orc_sim *s, long long i) {
+    int b = s->box[i];
+    return (uint64_t)(s->gid0[b] + (i - s->box_off[b]));
 }
 
 orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off,
@@ -605,6 +616,10 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
         s->sq[3 * i + 2] = quantise(sz[i], L);
         for (int f = 0; f < nfs; ++f) s->ndot[i * nfs + f] = ndot[i * nfs + f];
     }
+    s->gid0 = (long long *)malloc(sizeof(long long) * (size_t)n_boxes);
+    for (int b = 0; b < n_boxes; ++b) s->gid0[b] = box_off[b];
+    s->sid = (long long *)malloc(sizeof(long long) * (size_t)(n_src + 1));
+    for (int j = 0; j < n_src; ++j) s->sid[j] = j;
     s->sdir = (double *)calloc((size_t)(3 * n_src + 3), sizeof(double));
     s->sgate = (int *)calloc((size_t)(n_src + 1), sizeof(int));
     s->bar = (barrier_t *)calloc((size_t)n_boxes, sizeof(barrier_t));
@@ -648,11 +663,17 @@ orc_sim *orc_create(const orc_config *cfg, int n_boxes, const long long *box_off
     return s;
 }
 
+int orc_set_identities(orc_sim *s, const long long *box_first_id, const long long *src_id) {
+    for (int b = 0; b < s->nb; ++b) s->gid0[b] = box_first_id ? box_first_id[b] : s->box_off[b];
+    for (int j = 0; j < s->ns; ++j) s->sid[j] = src_id ? src_id[j] : j;
+    return ORC_OK;
+}
+
 void orc_destroy(orc_sim *s) {
     if (!s) return;
     free(s->box_off); free(s->box_L); free(s->q); free(s->box); free(s->nH); free(s->NH);
     free(s->xHI); free(s->T); free(s->sbox); free(s->sq); free(s->ndot); free(s->sigma);
-    free(s->sdir); free(s->sgate); free(s->bar);
+    free(s->sdir); free(s->sgate); free(s->bar); free(s->gid0); free(s->sid);
     free(s->eps); free(s->nbr); free(s->h2); free(s->snbr); free(s->sh2);
     for (int b = 0; b < s->nb; ++b) grid_free(&s->grids[b]);
     free(s->grids); free(s->R); free(s->Rs);
@@ -763,11 +784,11 @@ void orc_get_quantised(const orc_sim *s, int64_t *q) {
 void orc_rotate(orc_sim *s, long long step) {
     for (long long i = 0; i < s->n; ++i)
         orc_rotation(s->cfg.seed, PURPOSE_RECEPTION, (uint32_t)step, (uint32_t)(step >> 32),
-                     (uint32_t)i, s->R + 9 * i);
+                     (uint32_t)gid(s, i), s->R + 9 * i);
     for (int j = 0; j < s->ns; ++j)
         for (int k = 0; k < s->K; ++k)
             orc_rotation(s->cfg.seed, PURPOSE_EMISSION, (uint32_t)step, (uint32_t)k,
-                         (uint32_t)j, s->Rs + 9 * ((long long)j * s->K + k));
+                         (uint32_t)s->sid[j], s->Rs + 9 * ((long long)j * s->K + k));
 }
 
 void orc_get_rotations(const orc_sim *s, double *R, double *Rs) {
@@ -886,7 +907,7 @@ void orc_emit(orc_sim *s, long long step) {
                     /* a directed source (a packet of the plane-parallel front of Sec. 4) sends
                        one packet per emission and frequency along its direction */
                     if (directed && e > 0) continue;
-                    uint64_t idx = (((uint64_t)j * s->K + k) * nfs + nu) * nec + e;
+                    uint64_t idx = (((uint64_t)s->sid[j] * s->K + k) * nfs + nu) * nec + e;
                     freep_t p;
                     memset(&p, 0, sizeof(p));
                     p.box = s->sbox[j];
@@ -924,7 +945,7 @@ void orc_emit(orc_sim *s, long long step) {
             for (int k = 0; k < s->K; ++k) {
                 double R[9];
                 orc_rotation(s->cfg.seed, PURPOSE_REC_EMISSION, (uint32_t)step, (uint32_t)k,
-                             (uint32_t)i, R);
+                             (uint32_t)gid(s, i), R);
                 for (int e = 0; e < nec; ++e) {
                     freep_t p;
                     memset(&p, 0, sizeof(p));
@@ -938,7 +959,7 @@ void orc_emit(orc_sim *s, long long step) {
                     p.eps = s->epsrec[i];
                     p.sig = s->cfg.sigma_rec;
                     p.nu = nrb;
-                    p.fid = (2ull << 62) | (uint64_t)((i * s->K + k) * nec + e);
+                    p.fid = (2ull << 62) | (uint64_t)((gid(s, i) * s->K + k) * nec + e);
                     tally_add(s, p.box, 0, p.N);
                     fl_push(&s->cur, &p);
                 }
@@ -1189,7 +1210,7 @@ int orc_transport(orc_sim *s, long long step) {
                 /* shared bin: the packet's mean cross-section; else its bin's */
                 double sig = (s->sg && sl < nrc) ? s->sg[i * nrc + sl] / N : s->sigma[sl / nrc];
                 send_packet(s, step, hop, s->box[i], s->q + 3 * i, s->nbr + i * kn, s->h2[i],
-                            N, d, clock, eps, sig, sl / nrc, (uint64_t)(i * S + sl) + 1);
+                            N, d, clock, eps, sig, sl / nrc, gid(s, i) * S + sl + 1);
             }
         /* then sources (first hop) and virtual particles, in creation order */
         for (long long f = 0; f < s->cur.n; ++f) {

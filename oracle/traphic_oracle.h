@@ -114,6 +114,11 @@ int orc_chemistry(orc_sim *s);     /* ORC_ERR_SUBCYCLE_LIMIT at the subcycle flo
 int orc_step(orc_sim *s, long long step);
 /* masks of the current packets: bit k set when neighbour k of particle i lies in the
    transmission cone of slot sl; entries of inactive slots are 0 */
+/* Identities in the random streams (rotations, packet identities): particle i of box b draws
+   as particle box_first_id[b] + (i - box_off[b]) and source j as source src_id[j]; NULL keeps
+   the own indices.  A box cut out of a larger workload with its identities repeats the draws
+   it makes there. */
+int orc_set_identities(orc_sim *s, const long long *box_first_id, const long long *src_id);
 void orc_cone_masks(const orc_sim *s, uint32_t *mask /* [n*S] */);
 void orc_cone_masks_dir(const orc_sim *s, const double *dirs, uint32_t *mask); /* given directions [n*S*3] */
 /* state access; slot fields are N, Mx, My, Mz, C (= N * clock), E (= N * eps) */

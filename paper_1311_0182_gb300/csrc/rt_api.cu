@@ -328,6 +328,8 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     P.dep_s = dalloc(c, R * n, &ok);
     P.depE_s = dalloc(c, R * n, &ok);
     A(P.sbox, int, n_src + 1);
+    A(P.gid0, long long, n_boxes);
+    A(P.sid, long long, n_src + 1);
     A(P.sqx, int, n_src + 1); A(P.sqy, int, n_src + 1); A(P.sqz, int, n_src + 1);
     A(P.ndot, double, (long long)n_src * P.nfs + 1);
     A(P.sigma, double, P.nfs + 1);
@@ -455,6 +457,10 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     }
     x->src_emit_h.assign(n_boxes, 0.0);
     x->box_NH_h.assign(n_boxes, 0.0);
+    if (rt_set_identities(c, nullptr, nullptr) != RT_OK) {
+        rt_destroy(c);
+        return RT_ERR_CUDA;
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         rt_destroy(c);
@@ -707,6 +713,30 @@ extern "C" rt_status rt_set_sources(rt_ctx *c, const int *box, const double *x, 
     c->built = false;
     set_norms(c);
     return rt_cuda_check(c, cudaStreamSynchronize(st), "set sources");
+}
+
+extern "C" rt_status rt_set_identities(rt_ctx *c, const long long *box_first_id,
+                                       const long long *src_id) {
+    if (!c) return RT_ERR_INVALID;
+    DevPtrs &P = c->d;
+    int nb = P.nb, ns = P.ns;
+    std::vector<long long> g(nb), sd(ns + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        long long cnt = c->box_off_h[b + 1] - c->box_off_h[b];
+        g[b] = box_first_id ? box_first_id[b] : c->box_off_h[b];
+        // the rotation counters take 32-bit identities
+        if (g[b] < 0 || g[b] + cnt > (1ll << 32))
+            return rt_fail(c, RT_ERR_INVALID, "rt_set_identities: box identities outside [0, 2^32)");
+    }
+    for (int j = 0; j < ns; ++j) {
+        sd[j] = src_id ? src_id[j] : j;
+        if (sd[j] < 0 || sd[j] >= (1ll << 32))
+            return rt_fail(c, RT_ERR_INVALID, "rt_set_identities: source identities outside [0, 2^32)");
+    }
+    cudaDeviceSynchronize();   // no kernel of this context may be reading the identities
+    cudaMemcpy(P.gid0, g.data(), sizeof(long long) * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(P.sid, sd.data(), sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice);
+    return rt_cuda_check(c, cudaGetLastError(), "identities");
 }
 
 extern "C" rt_status rt_set_source_options(rt_ctx *c, const double *dir, const int *gate,

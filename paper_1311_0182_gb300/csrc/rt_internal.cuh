@@ -158,6 +158,9 @@ struct DevPtrs {              // plain pointers handed to kernels (by value)
     void *dep_s;               // Real [n]: fixed-point scale of photon deposits
     // sources
     int *sbox, *sqx, *sqy, *sqz;
+    // identities in the random streams: particle i of box b draws as gid0[b] + (i - box_off[b]),
+    // source j as sid[j] (by default their own indices)
+    long long *gid0, *sid;
     double *ndot, *sigma, *eps;  // [ns*nfs], [nf], [nf]
     float *sigmaf, *box_uf, *escf;  // FP32 copies: sigma [nf], box unit [nb], escape scale [nb]
     float *passf;                // [n * nf] photons passing (FP32 path, slot units)
@@ -216,6 +219,11 @@ __device__ __forceinline__ unsigned cnt_word(const DevPtrs &P, int k) {
     unsigned v;
     asm volatile("ld.global.b32 %0, [%1];" : "=r"(v) : "l"(P.cnt + k));
     return v;
+}
+
+// identity of particle i (of box b) in the random streams
+__device__ __forceinline__ unsigned long long gid_of(const DevPtrs &P, long long i, int b) {
+    return (unsigned long long)(P.gid0[b] + (i - P.box_off[b]));
 }
 
 // kernel identities for the launch counter and the optional per-kernel timer

@@ -278,14 +278,15 @@ __global__ void k_rotate(DevPtrs P) {
     long long nsrc = (long long)P.ns * P.K;
     if (i < P.n) {
         double R[9];
-        random_rotation(P.seed, 1u, (unsigned)step, (unsigned)(step >> 32), (unsigned)i, R);
+        random_rotation(P.seed, 1u, (unsigned)step, (unsigned)(step >> 32),
+                        (unsigned)gid_of(P, i, P.pbox[i]), R);
 #pragma unroll
         for (int a = 0; a < 9; ++a) { P.R[i * 9 + a] = R[a]; P.Rf[i * 9 + a] = (float)R[a]; }
     } else if (i < P.n + nsrc) {
         long long t = i - P.n;
         int j = (int)((unsigned)t / (unsigned)P.K), k = (int)((unsigned)t % (unsigned)P.K);
         double R[9];
-        random_rotation(P.seed, 2u, (unsigned)step, (unsigned)k, (unsigned)j, R);
+        random_rotation(P.seed, 2u, (unsigned)step, (unsigned)k, (unsigned)P.sid[j], R);
 #pragma unroll
         for (int a = 0; a < 9; ++a) P.Rs[t * 9 + a] = R[a];
     }
@@ -432,7 +433,9 @@ __global__ void k_emit_src(DevPtrs P) {
     ((Real *)F.eps)[p] = (Real)(P.eps[nu] / P.eunit);
     if (P.shared) ((Real *)F.sig)[p] = sigma_units<Real>(P, nu);
     F.nu[p] = nu;
-    F.fid[p] = (1ull << 62) | (unsigned long long)p;
+    // identity (source, emission, frequency, cone), with the source's identity
+    F.fid[p] = (1ull << 62) |
+               ((((unsigned long long)P.sid[j] * P.K + k) * P.nfs + nu) * P.nec + e);
 }
 
 // The original implementation of recombination radiation (Sec. 2.2): particle i emits, K
@@ -455,7 +458,8 @@ __global__ void k_emit_rec_cones(DevPtrs P, long long base) {
     double Nr = P.Nrec[i];
     double N = Nr > 0.0 ? __ddiv_rn(Nr, (double)per) : 0.0;
     double R[9], d[3];
-    random_rotation(P.seed, 4u, (unsigned)step, (unsigned)k, (unsigned)i, R);
+    const unsigned long long gi = gid_of(P, i, b);
+    random_rotation(P.seed, 4u, (unsigned)step, (unsigned)k, (unsigned)gi, R);
     rot_apply(R, c_axd[P.ax_ec] + 3 * e, d);
     F.box[f] = b;
     F.qx[f] = P.qx[i]; F.qy[f] = P.qy[i]; F.qz[f] = P.qz[i];
@@ -469,7 +473,7 @@ __global__ void k_emit_rec_cones(DevPtrs P, long long base) {
     ((Real *)F.eps)[f] = (Real)(P.epsrec[i] / P.eunit);
     if (P.shared) ((Real *)F.sig)[f] = (Real)(P.sigma_rec / P.sunit);
     F.nu[f] = P.rbin;
-    F.fid[f] = (2ull << 62) | (unsigned long long)p;
+    F.fid[f] = (2ull << 62) | ((gi * P.K + k) * P.nec + e);   // (particle, emission, cone)
 }
 
 // ------------------------------------------------------------------------------------------
@@ -830,7 +834,7 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             clk = S.C[code] / N;
             eps = S.E[code] / N;
             if (SH && nu == 0) sg = ((Real *)P.slG[cur])[i * NRC + s] / N;
-            fid = code + 1ull;
+            fid = gid_of(P, i, box) * P.S + (code - (unsigned long long)i * P.S) + 1ull;
             snb = P.nbr + i * P.kn;
         } else {
             long long f = (long long)(code & ~RT_FREE_BIT);

@@ -1,7 +1,9 @@
 """One process per GPU for independent boxes.
 
 Boxes are independent problems: ranks split them (longest-processing-time greedy on particle
-count) and run with no collective on the data path.  The only cross-rank steps are the timing
+count) and run with no collective on the data path.  A sub-workload keeps the identities its
+particles and sources have in the full workload, so each box draws the same random numbers and
+gives the same results on whichever rank it runs.  The only cross-rank steps are the timing
 (maximum over ranks) and, when wanted, the photon budget (sum over ranks), both after the timed
 region.  A single box does not split without a per-hop exchange, so for one box every rank runs
 its own replica.
@@ -38,10 +40,16 @@ def local_workload(wl: dict, boxes) -> dict:
     nfs = wl["params"]["n_freq_src"]
     ndot = np.asarray(wl["src_ndot"]).reshape(len(wl["src_box"]), max(nfs, 1) if nfs else 0)
     out = dict(wl)
+    # the identities of the boxes' particles and sources in the full workload: the random
+    # streams of a box (rotations, packet identities) are then those it has there, and a rank
+    # running its boxes repeats their results in the unsplit run
+    first = np.asarray(wl.get("box_first_id", off[:-1]), dtype=np.int64)
+    sids = np.asarray(wl.get("src_id", np.arange(len(wl["src_box"]))), dtype=np.int64)
     out.update(
         box_off=new_off, box_L=np.asarray(wl["box_L"])[boxes],
         src_box=np.array([remap[int(b)] for b in np.asarray(wl["src_box"])[src_keep]], np.int32),
-        src_ndot=np.ascontiguousarray(ndot[src_keep]).reshape(-1))
+        src_ndot=np.ascontiguousarray(ndot[src_keep]).reshape(-1),
+        box_first_id=first[boxes], src_id=sids[src_keep])
     for k in ("x", "y", "z", "n_H", "N_H", "x_HI", "T"):
         out[k] = np.ascontiguousarray(np.asarray(wl[k])[idx])
     for k in ("src_x", "src_y", "src_z"):

@@ -25,6 +25,7 @@ SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
            "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier",
            "rt_set_graph", "rt_get_shared_sigma", "rt_set_shared_sigma", "rt_save_state",
+           "rt_set_identities",
            "rt_load_state"]
 
 
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = False):
     L.rt_axis_set.argtypes = [i, vp]
     L.rt_set_profiling.argtypes = [vp, i]
     L.rt_set_graph.argtypes = [vp, i]
+    L.rt_set_identities.argtypes = [vp, vp, vp]
     L.rt_get_profile.argtypes = [vp, vp, i, vp, vp, vp, vp]
     L.rt_last_error.argtypes = [vp]
     L.rt_last_error.restype = C.c_char_p
@@ -220,6 +222,17 @@ class Context:
                                     f("src_gate", np.int32) if "src_gate" in wl else None)
         for (b, axis, centre, radius) in wl.get("barriers", []):
             self.set_barrier(b, axis, centre, radius)
+        if "box_first_id" in wl or "src_id" in wl:
+            self.set_identities(wl.get("box_first_id"), wl.get("src_id"))
+
+    def set_identities(self, box_first_id=None, src_id=None):
+        """Random-stream identities of the boxes' particles and of the sources (None: their own
+        indices); a sub-workload with its identities repeats the full workload's results."""
+        bf = None if box_first_id is None else np.ascontiguousarray(box_first_id, np.int64)
+        si = None if src_id is None else np.ascontiguousarray(src_id, np.int64)
+        self._check(self.L.rt_set_identities(self.h, None if bf is None else bf.ctypes.data,
+                                             None if si is None else si.ctypes.data),
+                    "rt_set_identities")
 
     def build_neighbours(self):
         self._check(self.L.rt_build_neighbours(self.h, self._s()), "rt_build_neighbours")

@@ -381,6 +381,30 @@ def test_subcycle_floor_reports_its_status(fp32):
     assert q.step(0) == 0 and q.stats()["floor_hits"] == 0
 
 
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_boxes_cut_out_of_a_batch_repeat_their_results(fp32):
+    """The boxes of workload 4 split in two, each part run on its own context with the
+    identities its particles and sources have in the whole batch (rt_set_identities): every
+    box's particles end with the x_HI and T, and every box with the photon budget, of the
+    unsplit run, bit for bit.  This is how the boxes are shared among GPUs."""
+    from paper_1311_0182_gb300 import distributed as D, rt
+    wl = W.cfg4(n_boxes=24, n_min=300, n_max=3000, transport_fp32=fp32)
+    full = rt.context_for(wl)
+    for step in range(3):
+        full.step(step)
+    sf, bf = full.state(), full.budget()
+    for part in D.partition_boxes(np.diff(wl["box_off"]), 2):
+        sub = D.local_workload(wl, part)
+        g = rt.context_for(sub)
+        for step in range(3):
+            g.step(step)
+        idx = np.concatenate([np.arange(wl["box_off"][b], wl["box_off"][b + 1]) for b in part])
+        sg = g.state()
+        assert np.array_equal(sg["x_HI"], sf["x_HI"][idx])
+        assert np.array_equal(sg["T"], sf["T"][idx])
+        assert np.array_equal(g.budget(), bf[part])
+
+
 def test_multi_box_parity_and_conservation():
     wl = _clustered_boxes()
     g, o = _pair(wl, transport_fp32=0)
