@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--paper-workloads", action="store_true",
                     help="also time workload 3 (128^3 with a dense clump) and workload 5 (256^3 "
                          "clustered volume, 256 sources), FP32 transport")
+    ap.add_argument("--source-count", action="store_true",
+                    help="also time the same workload with its luminosity split over 1, 8 and 64 "
+                         "sources clustered where the one source sits (Sec. 2.1: the cost does "
+                         "not depend on the number of sources)")
     ap.add_argument("--on-the-spot", action="store_true",
                     help="also time the same workload without recombination transport (case B "
                          "on the spot), and with it in a shared bin against on the spot with one "
@@ -265,6 +269,8 @@ def run_ours(args):
         out["on_the_spot"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1)
         out["on_the_spot_shared_layout"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1,
                                                      rec_shared_bin=1)
+    if args.source_count:
+        out["source_count"] = source_count(args, stream)
     if args.batched:
         out["batched_boxes"] = batched(args, stream, world=world, rank=rank)
     if args.paper_workloads:
@@ -394,6 +400,47 @@ def fp64_path(args, stream, **over):
     return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
             "ms_per_step": ms / steps, "steps": steps, "packet_storage_bytes": slot_bytes,
             "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
+
+
+def source_count(args, stream, counts=(1, 8, 64), warmup=3, steps=3):
+    """Sec. 2.1: packets merge per reception cone at every particle, so the work of a step is
+    bounded by the particles and their cones, not by the number of sources.  The timed workload
+    with its luminosity split over 1, 8 and 64 sources clustered within 2% of the box side
+    around the centre: ms per step and the per-step work counters (particles sending, packets
+    moved, virtual particles, hops) of the last timed step, same precision and start state."""
+    import torch
+    from paper_1311_0182_gb300 import rt, workloads as W
+    out = {"spread_of_box": 0.02, "warmup": warmup, "steps": steps, "runs": {}}
+    for ns in counts:
+        wl = W.split_sources(W.cfg2(n_side=args.n_side,
+                                    transport_fp32=int(args.precision == "fp32")), ns)
+        ctx = rt.Context(wl, stream=stream)
+        with torch.cuda.stream(stream):
+            ctx.load_workload(wl)
+            ctx.build_neighbours()
+            for s in range(warmup):
+                ctx.step(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for s in range(warmup, warmup + steps):
+                ctx.step(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        st = ctx.stats()
+        b = ctx.budget()
+        out["runs"][str(ns)] = {"ms_per_step": ms, "senders": st["senders"],
+                                "moving_packets": st["moving_packets"], "virtual": st["virtual"],
+                                "hops": st["hops"],
+                                "budget_closure": float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])}
+        ctx.close()
+    r1 = out["runs"][str(counts[0])]
+    for ns in counts[1:]:
+        r = out["runs"][str(ns)]
+        r["ms_over_one_source"] = r["ms_per_step"] / r1["ms_per_step"]
+        r["moving_packets_over_one_source"] = r["moving_packets"] / r1["moving_packets"]
+    return out
 
 
 def batched(args, stream, warmup=2, steps=3, world=1, rank=0):

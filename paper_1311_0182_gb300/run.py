@@ -44,6 +44,53 @@ def radial_profile(r, values, r_max, n_shells=32):
     return edges, out
 
 
+def cylindrical_profiles(pos, axis_point, axis: int, height, r_max: float, n_shells: int,
+                         fields: dict) -> dict:
+    """Means of each field in `fields` (per-particle arrays) over concentric cylindrical shells
+    around the line through axis_point along coordinate `axis`, out to r_max, for particles
+    whose coordinate along the axis lies in height = (lo, hi): the shells in which Sec. 4
+    averages the intensities, neutral fractions and temperatures of the shadow region behind
+    the barrier.  Returns the shell edges, the particle counts and, per field, the shell means
+    (None for empty shells)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    c = np.asarray(axis_point, dtype=np.float64)
+    perp = [a for a in range(3) if a != axis]
+    rc = np.sqrt(((pos[:, perp] - c[perp]) ** 2).sum(1))
+    inside = (pos[:, axis] >= height[0]) & (pos[:, axis] < height[1])
+    edges = np.linspace(0.0, r_max, n_shells + 1)
+    idx = np.searchsorted(edges, rc, side="right") - 1
+    out = {"edges": edges.tolist(), "count": [], **{k: [] for k in fields}}
+    for k in range(n_shells):
+        m = inside & (idx == k)
+        out["count"].append(int(m.sum()))
+        for name, v in fields.items():
+            out[name].append(float(np.mean(np.asarray(v)[m])) if m.any() else None)
+    return out
+
+
+def shadow_profiles(wl: dict, state: dict, passing, dt: float, n_shells=10) -> dict:
+    """The diagnostic of Sec. 4 for the shadow workload: cylindrical shells around the shadow's
+    major axis (the line through the barrier's centre along x) out to half the box side, over
+    the part of the box behind the barrier from 0.35 to 0.75 of the side; per shell the mean
+    x_HI, T and intensity of the source photons (bin 0) and of the diffuse photons (every other
+    bin: the boundary emitters and the transported recombination photons), each intensity in
+    units of the source intensity of the outermost shell (photons passing a particle per
+    step, Sec. 3 and Sec. 4)."""
+    L = float(wl["box_L"][0])
+    b, axis, centre, radius = wl["barriers"][0]
+    pos = np.stack([wl["x"], wl["y"], wl["z"]], 1)
+    box0 = slice(int(wl["box_off"][0]), int(wl["box_off"][1]))
+    pas = np.asarray(passing)[box0] / dt
+    prof = cylindrical_profiles(pos[box0], centre, axis, (0.35 * L, 0.75 * L), 0.5 * L, n_shells,
+                                {"x_HI": state["x_HI"][box0], "T": state["T"][box0],
+                                 "I_source": pas[:, 0], "I_diffuse": pas[:, 1:].sum(1)})
+    ref = prof["I_source"][-1]
+    for k in ("I_source", "I_diffuse"):
+        prof[k] = [None if v is None or not ref else v / ref for v in prof[k]]
+    prof["barrier_radius"] = float(radius)
+    return prof
+
+
 def front_radius(r, x_HI, r_max, n_shells=32):
     """Radius where the shell-mean x_HI first crosses 0.5 going outwards (linear between shell
     centres); None when no shell crosses."""

@@ -340,6 +340,25 @@ def shadow(n_side=32, seed=1006, n_front=100, n_bnd=50, barrier=True, boundary=T
     return wl
 
 
+def split_sources(wl: dict, n_src: int, spread=0.02, seed=11) -> dict:
+    """The same workload with its first source's photons split equally over n_src sources
+    placed uniformly within +-spread of the box side around it (one cluster of sources where
+    one sat); the total luminosity per frequency bin is unchanged."""
+    if n_src <= 1:
+        return wl
+    rng = np.random.default_rng(seed)
+    b = int(wl["src_box"][0])
+    L = float(wl["box_L"][b])
+    c = np.array([wl["src_x"][0], wl["src_y"][0], wl["src_z"][0]])
+    pos = np.clip(c + rng.uniform(-spread, spread, (n_src, 3)) * L, 0.0, np.nextafter(L, 0.0))
+    nfs = wl["params"]["n_freq_src"]
+    ndot = np.asarray(wl["src_ndot"], dtype=np.float64).reshape(len(wl["src_box"]), nfs)[0]
+    out = dict(wl)
+    out.update(src_box=np.full(n_src, b, np.int32), src_x=pos[:, 0].copy(), src_y=pos[:, 1].copy(),
+               src_z=pos[:, 2].copy(), src_ndot=np.tile(ndot / n_src, n_src))
+    return out
+
+
 def tiny(n=200, seed=7, n_ngb=16, L=1.0 * KPC, **kw):
     """Small random box for brute-force and edge-case checks."""
     rng = np.random.default_rng(seed)

@@ -50,3 +50,31 @@ def test_logged_run_with_checkpoint_and_resume(tmp_path):
     for a, b in zip(again, lines[2:]):
         for k in ("hops", "virtual", "budget", "ionised_volume_fraction", "front_kpc"):
             assert a[k] == b[k], k
+
+
+def test_shadow_profiles_in_cylindrical_shells():
+    """Sec. 4 diagnostic on the oracle's shadow run (16^3, 14 steps: the front has passed the
+    barrier): in cylindrical shells around the shadow's axis, behind the barrier, no source
+    photons reach the shells inside the barrier's radius, where the gas stays neutral and cold,
+    while outside it the source intensity is that of the outer shell and the gas is ionised
+    and hot."""
+    import oracle
+    wl = W.shadow(n_side=16, n_front=20, n_bnd=10)
+    s = oracle.Sim(wl)
+    s.build_neighbours()
+    for k in range(14):
+        assert s.step(k) == 0
+    _, _, ps = s.deposits()
+    pr = R.shadow_profiles(wl, s.state(), ps, wl["params"]["dt"], n_shells=8)
+    e = np.array(pr["edges"])
+    rb = pr["barrier_radius"]
+    # shells more than a smoothing length (~0.1 of the side at 16^3) inside or outside the
+    # shadow's edge
+    shadow = e[1:] <= 0.65 * rb
+    lit = e[:-1] >= 1.2 * rb
+    assert shadow.sum() >= 2 and lit.sum() >= 3
+    Is, x, T = (np.array(pr[k], dtype=float) for k in ("I_source", "x_HI", "T"))
+    assert np.all(Is[shadow] < 0.05) and np.all(Is[lit] > 0.5)
+    assert np.all(x[shadow] > 0.9) and np.all(x[lit] < 0.5)
+    assert T[shadow].max() < 0.1 * T[lit].min()
+    assert sum(pr["count"]) > 0 and pr["I_source"][-1] == 1.0
