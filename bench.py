@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--paper-workloads", action="store_true",
                     help="also time workload 3 (128^3 with a dense clump) and workload 5 (256^3 "
                          "clustered volume, 256 sources), FP32 transport")
+    ap.add_argument("--tuned", action="store_true",
+                    help="also time the workload with the launch sizes of the hop kernels chosen "
+                         "by the step-graph tuner (tune_launch) after its tuning steps")
     ap.add_argument("--source-count", action="store_true",
                     help="also time the same workload with its luminosity split over 1, 8 and 64 "
                          "sources clustered where the one source sits (Sec. 2.1: the cost does "
@@ -269,6 +272,8 @@ def run_ours(args):
         out["on_the_spot"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1)
         out["on_the_spot_shared_layout"] = fp64_path(args, stream, transport_fp32=fp, rec_mode=1,
                                                      rec_shared_bin=1)
+    if args.tuned:
+        out["tuned_launch_sizes"] = tuned(args, stream)
     if args.source_count:
         out["source_count"] = source_count(args, stream)
     if args.batched:
@@ -400,6 +405,37 @@ def fp64_path(args, stream, **over):
     return {"value": n * steps / (ms / 1e3), "unit": "particle-sweeps/s",
             "ms_per_step": ms / steps, "steps": steps, "packet_storage_bytes": slot_bytes,
             "dtype": "f64" if not wl["params"]["transport_fp32"] else "f32 transport / f64 chemistry"}
+
+
+def tuned(args, stream, tuning_steps=18):
+    """The timed workload with tune_launch: 18 tuning steps (whole step-graph launches, each a
+    candidate triple of grid sizes or the best so far), then the main run's warm-up and timed
+    steps with the sizes it chose, against the same steps with the built-in sizes."""
+    import torch
+    from paper_1311_0182_gb300 import rt
+    wl = workload(args)
+    out = {}
+    for name, over in (("tuned", dict(tune_launch=1)), ("built_in", dict(tune_launch=0))):
+        ctx = rt.Context(wl, stream=stream, **over)
+        with torch.cuda.stream(stream):
+            ctx.load_workload(wl)
+            ctx.build_neighbours()
+            for s in range(tuning_steps + args.warmup):
+                ctx.step(s)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s0 = tuning_steps + args.warmup
+            for s in range(s0, s0 + args.steps):
+                ctx.step(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        st = ctx.stats()
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / args.steps,
+                     "grids": [st["grid_send"], st["grid_virtual"], st["grid_receive"]]}
+        ctx.close()
+    out["tuned_over_built_in"] = out["tuned"]["ms_per_step"] / out["built_in"]["ms_per_step"]
+    return out
 
 
 def source_count(args, stream, counts=(1, 8, 64), warmup=3, steps=3):

@@ -95,9 +95,13 @@ typedef struct {
                              neighbour search over 5, 7, 9, 12 and 16 in rt_build_neighbours */
     int tune_launch;      /* 1: the grid sizes of the three main hop kernels (sender side,
                              virtual particles, receiver side) are chosen by timing the first
-                             rt_step or rt_transport, which then runs hop by hop from the host
-                             whatever rt_set_graph says; 0: built-in sizes.  Results do not
-                             depend on the choice. */
+                             steps of rt_step as whole step-graph launches: coordinate search
+                             over 152 x {8, 16, 32, 64} blocks from the built-in sizes, each
+                             candidate step after a step of the best so far, per unit of work
+                             of the step (18 steps).  The winner is kept for the process per
+                             configuration and particle count, so a later context of the same
+                             kind starts with it.  0: built-in sizes.  Results do not depend on
+                             the choice. */
     int launch_grid[3];   /* grid sizes (blocks) of those three kernels; 0: built-in or tuned.
                              Any nonzero entry switches the tuning off (> 0 values are used,
                              zeros keep the built-in size). */

@@ -421,7 +421,7 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     for (int k = 0; k < 4; ++k)
         if (cudaEventCreateWithFlags(&c->hev[k], cudaEventDisableTiming) != cudaSuccess) ok = false;
     for (int k = 0; k < 6; ++k)
-        if (cudaEventCreate(&c->tev[k]) != cudaSuccess) ok = false;
+        if (k < 2 && cudaEventCreate(&c->tune_ev[k]) != cudaSuccess) ok = false;
     // the stream the step graph is captured on (it never runs work itself)
     if (cudaStreamCreateWithFlags(&c->st_cap, cudaStreamNonBlocking) != cudaSuccess) ok = false;
     if (!ok) {
@@ -486,7 +486,7 @@ extern "C" rt_status rt_destroy(rt_ctx *c) {
     for (int k = 0; k < 4; ++k)
         if (c->hev[k]) cudaEventDestroy(c->hev[k]);
     for (int k = 0; k < 6; ++k)
-        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+        if (k < 2 && c->tune_ev[k]) cudaEventDestroy(c->tune_ev[k]);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return RT_OK;
@@ -885,11 +885,12 @@ extern "C" rt_status rt_step(rt_ctx *c, long long step, void *stream) {
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
     // the captured step graph, unless kernels are being timed one by one (events cannot sit
-    // inside the graph's conditional hop loop) or the hop cap allows no hop
-    // (the first step that tunes the launch sizes runs hop by hop as well)
-    bool tune = c->cfg.tune_launch && !c->launch_tuned;
-    if (!tune && c->use_graph && c->prof == 0 && c->cfg.hop_cap > 0)
+    // inside the graph's conditional hop loop) or the hop cap allows no hop; while the launch
+    // sizes are being tuned (tune_launch), the graph steps are timed whole
+    if (c->use_graph && c->prof == 0 && c->cfg.hop_cap > 0) {
+        if (c->cfg.tune_launch && !c->launch_tuned) return rt_step_graph_tuned(c, step, st);
         return rt_step_graph(c, step, st);
+    }
     if ((s = rt_run_step_parts(c, 0, step, st))) return s;
     if ((s = rt_run_step_parts(c, 1, step, st))) return s;
     if ((s = rt_emit(c, step, stream))) return s;

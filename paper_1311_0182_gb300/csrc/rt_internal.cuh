@@ -238,6 +238,15 @@ struct KStat {
     long long launches = 0;
 };
 
+// state of the launch-size tuning on whole steps (tune_launch)
+struct TuneState {
+    int phase = 0;            // 0: not started; 1: next step runs the best; 2: the candidate; 3: done
+    int best[3] = {0, 0, 0};  // grid sizes of the sender side, virtual particles, receiver side
+    double best_cost = 0.0;   // ms per unit of work of the best's last step
+    std::vector<std::pair<int, int>> cand;   // (kernel, grid size) still to try
+    int steps = 0;
+};
+
 struct rt_ctx {
     rt_config cfg;
     DevPtrs d;
@@ -291,9 +300,8 @@ struct rt_ctx {
     // and the candidate with the least time per item wins
     int grid_hop[3] = {0, 0, 0};
     bool launch_tuned = false;
-    bool tuning = false;
-    double tune_ms[3][4] = {}, tune_items[3][4] = {};
-    cudaEvent_t tev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    TuneState tune;
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     double *src_emit = nullptr;   // device [nb]: source photons of one step per box
     std::vector<double> src_emit_h, box_NH_h;
 };
@@ -310,6 +318,7 @@ void rt_set_grid(rt_ctx *c, int occupancy);
 rt_status rt_run_step_parts(rt_ctx *c, int part, long long step, cudaStream_t st);
 // one whole step through the captured graph (captured again when its parameters changed)
 rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st);
+rt_status rt_step_graph_tuned(rt_ctx *c, long long step, cudaStream_t st);
 void rt_graph_destroy(rt_ctx *c);
 // the grid sizes (blocks) of the sender side, the virtual particles and the receiver side
 void rt_launch_grids(const rt_ctx *c, long long out[3]);

@@ -18,7 +18,11 @@
 //      No floating-point atomics: every sum has one fixed order.
 #include <algorithm>
 #include <climits>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "rt_knn.cuh"
 
@@ -1475,7 +1479,6 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     const int GA = c->grid_hop[0] ? c->grid_hop[0] : GRID_A;
     const int GV = c->grid_hop[1] ? c->grid_hop[1] : GRID_V;
     const int GB = c->grid_hop[2] ? c->grid_hop[2] : GRID_B;
-    const bool tm = c->tuning && !c->capturing;   // launch-size tuning: time the three kernels
     HopScratch &H = c->hop;
     const int tb = 256, gb = 152 * 64;
     long long n = P.n, nkey = n * P.nf;
@@ -1497,17 +1500,14 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
         LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, true, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
     else
         LAUNCH_ON(s2, KT_FREE_C, 1, (k_freeC<Real, NRC, false, false><<<rt_blocks(nfr * 32, tb, gb), tb, 0, s2>>>(P, fcur, H.lens, H.fmask, H.stoff)));
-    if (tm) cudaEventRecord(c->tev[0], st);
     if (P.shared)
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, true><<<rt_blocks(n * 32, tb, GA), tb, 0, st>>>(P, cur)));
     else
         LAUNCH(KT_PHASE_A, 1, (k_phaseA<Real, NRC, false><<<rt_blocks(n * 32, tb, GA), tb, 0, st>>>(P, cur)));
-    if (tm) cudaEventRecord(c->tev[1], st);
     cudaEventRecord(evA, st);
     cudaStreamWaitEvent(st, evFree, 0);
     LAUNCH(KT_SCAN, 2, (rt_scan_exclusive(c, P.reqcnt, P.reqoff, n + nfr, H.lens + 1, H.lens + 2, st)));
     LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
-    if (tm) cudaEventRecord(c->tev[2], st);
     const int IS = KNN_IB_SMALL, IL = KNN_IB_LARGE;
     if (P.kwide && P.shared)   // boxes above 2^22 particles: the general instance, 24-bit keys
         LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true, IL><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
@@ -1524,47 +1524,24 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     else
         LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
                                   P, cur, fcur, H.lens, H.esc_r, H.vstat)));
-    if (tm) cudaEventRecord(c->tev[3], st);
     LAUNCH_ON(s2, KT_SCAN, 2, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
     LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
     LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));
     cudaMemsetAsync(H.lens + 4, 0, sizeof(int), s2);
     cudaStreamWaitEvent(s2, evA, 0);
     LAUNCH_ON(s2, KT_WORKLIST, 1, (k_worklist<<<rt_blocks(nkey, tb, 152 * 16), tb, 0, s2>>>(P, cur, H.lens + 4)));
-    if (tm) cudaEventRecord(c->tev[4], s2);
     if (P.shared)
         LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, true><<<rt_blocks(nkey * NRC, tb, GB), tb, 0, s2>>>(P, cur, H.lens + 4)));
     else if (P.any_bar)
         LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, true, false><<<rt_blocks(nkey * NRC, tb, GB), tb, 0, s2>>>(P, cur, H.lens + 4)));
     else
         LAUNCH_ON(s2, KT_PHASE_B, 1, (k_phaseB<Real, NRC, false, false><<<rt_blocks(nkey * NRC, tb, GB), tb, 0, s2>>>(P, cur, H.lens + 4)));
-    if (tm) cudaEventRecord(c->tev[5], s2);
     cudaEventRecord(evB, s2);
     cudaStreamWaitEvent(st, evB, 0);
     LAUNCH(KT_HOP_COUNT, 1, (k_hop_counts<<<304, 256, 0, st>>>(P, cur ^ 1, fcur ^ 1, H.lens, H.esc_r, H.vstat)));
 }
 
-// After the tuning hop loop: per kernel the candidate with the least time per item (the
-// built-in size when a candidate saw no items); the step graph is captured again with them.
 static void graph_destroy(rt_ctx *c);
-static void finish_launch_tuning(rt_ctx *c) {
-    const int def[3] = {GRID_A, GRID_V, GRID_B};
-    for (int k = 0; k < 3; ++k) {
-        int best = -1;
-        double best_r = 0.0;
-        bool all = true;
-        for (int q = 0; q < 4; ++q) {
-            if (!(c->tune_items[k][q] > 0.0)) { all = false; continue; }
-            double r = c->tune_ms[k][q] / c->tune_items[k][q];
-            if (best < 0 || r < best_r) { best = q; best_r = r; }
-        }
-        c->grid_hop[k] = (all && best >= 0) ? 152 * (8 << best) : def[k];
-    }
-    c->tuning = false;
-    c->launch_tuned = true;
-    graph_destroy(c);
-}
-
 void rt_launch_grids(const rt_ctx *c, long long out[3]) {
     const int def[3] = {GRID_A, GRID_V, GRID_B};
     for (int k = 0; k < 3; ++k) out[k] = c->grid_hop[k] ? c->grid_hop[k] : def[k];
@@ -1673,25 +1650,11 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     // part 4: the hop loop, driven from the host (one synchronisation per hop)
     set_step(c, step, st);
     transport_begin(c, st);
-    c->tuning = c->cfg.tune_launch && !c->launch_tuned;
-    long long senders = -1, actp0 = 0, wls0 = 0;   // tuning: items of the hop's kernels
-    if (c->tuning) {
-        cudaMemcpyAsync(c->cnt_h, P.cnt, sizeof(long long) * CNT_N, cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
-        actp0 = c->cnt_h[CNT_ACTP];
-        wls0 = c->cnt_h[CNT_WLS];
-    }
     for (int hop = 0;; ++hop) {
         if (hop >= c->cfg.hop_cap) {
             LAUNCH(KT_DROP, 1, (k_drop_free<Real><<<rt_blocks(P.F_cap, tb, 152 * 64), tb, 0, st>>>(P, H.lens)));
             break;
         }
-        int pick[3];
-        if (c->tuning)   // each kernel cycles through the candidates, staggered
-            for (int k = 0; k < 3; ++k) {
-                pick[k] = (hop + k) % 4;
-                c->grid_hop[k] = 152 * (8 << pick[k]);
-            }
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_BEGIN, 0, 0, 0)));
         hop_core<Real, NRC>(c, st, c->nfree_h, c->cur, c->fcur);
         LAUNCH(KT_HOP_LENS, 1, (k_hop_lens<<<1, 1, 0, st>>>(P, H.lens, HL_END, c->cfg.hop_cap, 0, 0)));
@@ -1701,23 +1664,6 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
         rt_status hs = rt_cuda_check(c, cudaStreamSynchronize(st), "hop");
         if (hs != RT_OK) return hs;
         kt_resolve(c);
-        if (c->tuning) {
-            // items: particles with a packet to send (known from the previous hop's counts),
-            // virtual-particle requests, receiver work-list groups
-            long long items[3] = {senders, std::min<long long>(c->cnt_h[CNT_NREQ], P.F_cap),
-                                  c->cnt_h[CNT_WLS] - wls0};
-            wls0 = c->cnt_h[CNT_WLS];
-            senders = c->cnt_h[CNT_ACTP] - actp0;
-            actp0 = c->cnt_h[CNT_ACTP];
-            for (int k = 0; k < 3; ++k) {
-                float ms = 0.f;
-                if (items[k] > 0 &&
-                    cudaEventElapsedTime(&ms, c->tev[2 * k], c->tev[2 * k + 1]) == cudaSuccess) {
-                    c->tune_ms[k][pick[k]] += ms;
-                    c->tune_items[k][pick[k]] += (double)items[k];
-                }
-            }
-        }
         if (c->cnt_h[CNT_ERR]) break;
         c->nfree_h = std::min<long long>(c->cnt_h[CNT_NREQ], P.F_cap);
         if (c->cnt_h[CNT_ACTIVE] == 0 && c->cnt_h[CNT_LIVE] == 0) break;
@@ -1726,7 +1672,6 @@ static rt_status run_parts(rt_ctx *c, int part, long long step, cudaStream_t st)
     rt_status hs = rt_cuda_check(c, cudaStreamSynchronize(st), "hop loop");
     if (hs != RT_OK) return hs;
     kt_resolve(c);
-    if (c->tuning) finish_launch_tuning(c);
     return transport_end(c, sizeof(Real) == 4);
 }
 
@@ -1911,6 +1856,95 @@ rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st) {
     int nrc = c->d.nrc;
     if (c->d.fp32) return nrc == 8 ? step_graph<float, 8>(c, step, st) : step_graph<float, 32>(c, step, st);
     return nrc == 8 ? step_graph<double, 8>(c, step, st) : step_graph<double, 32>(c, step, st);
+}
+
+// ---- launch-size tuning on whole steps -------------------------------------------------------
+// With tune_launch the first steps run as the captured step graph, each with one triple of grid
+// sizes of the sender side, the virtual particles and the receiver side, and are timed with CUDA
+// events around the graph launch, so that the overlap of the two streams is in the objective.
+// The time of a step is divided by its work (packets moved, particles sending, virtual
+// particles: device counters of that step).  Coordinate search from the built-in sizes over
+// 152 x {8, 16, 32, 64} blocks, the virtual particles first, then the sender and the receiver
+// side; each candidate step follows a step of the current best, so that the pair sees nearly
+// the same work, and replaces it when it costs 1% less per unit of work.  The winner is kept
+// for the process per (configuration, particles, boxes): a later context of the same kind
+// starts with it and does not tune.  The steps run while tuning are ordinary steps: results do
+// not depend on the launch sizes.
+static std::mutex g_tune_mu;
+static std::map<std::string, std::array<int, 3>> g_tune_cache;
+
+static std::string tune_key(const rt_ctx *c) {
+    const DevPtrs &P = c->d;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%lld/%d/%d/%d/%d/%d/%d/%d/%d", P.n, P.nb, P.kn, P.ntc, P.nrc,
+             P.nf, P.fp32, P.rec_mode, P.shared);
+    return buf;
+}
+
+static void set_grids(rt_ctx *c, const int g[3]) {
+    bool same = true;
+    for (int k = 0; k < 3; ++k) same &= c->grid_hop[k] == g[k];
+    if (same) return;
+    for (int k = 0; k < 3; ++k) c->grid_hop[k] = g[k];
+    graph_destroy(c);     // the sizes are captured in the graph
+}
+
+rt_status rt_step_graph_tuned(rt_ctx *c, long long step, cudaStream_t st) {
+    TuneState &U = c->tune;
+    if (U.phase == 0) {   // start: a cached winner, or the candidates from the built-in sizes
+        const int def[3] = {GRID_A, GRID_V, GRID_B};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(tune_key(c));
+            if (it != g_tune_cache.end()) {
+                set_grids(c, it->second.data());
+                c->launch_tuned = true;
+                return rt_step_graph(c, step, st);
+            }
+        }
+        for (int k = 0; k < 3; ++k) U.best[k] = def[k];
+        U.cand.clear();
+        const int order[3] = {1, 0, 2};
+        for (int kk : order)
+            for (int q = 0; q < 4; ++q)
+                if (152 * (8 << q) != def[kk]) U.cand.push_back({kk, 152 * (8 << q)});
+        U.phase = 1;
+        U.steps = 0;
+    }
+    int g[3] = {U.best[0], U.best[1], U.best[2]};
+    if (U.phase == 2) g[U.cand.front().first] = U.cand.front().second;
+    set_grids(c, g);
+    cudaEventRecord(c->tune_ev[0], st);
+    rt_status s = rt_step_graph(c, step, st);
+    cudaEventRecord(c->tune_ev[1], st);
+    cudaError_t e = cudaEventSynchronize(c->tune_ev[1]);
+    if (s != RT_OK) return s;
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]);
+    if (e != cudaSuccess) return rt_cuda_check(c, e, "launch-size tuning");
+    double work = (double)(c->cnt_h[CNT_ACTS] + c->cnt_h[CNT_ACTP] + c->cnt_h[CNT_VIRT]);
+    double cost = (double)ms / (work > 0.0 ? work : 1.0);
+    ++U.steps;
+    if (U.phase == 1) {
+        U.best_cost = cost;
+        U.phase = 2;
+        return s;
+    }
+    if (cost < 0.99 * U.best_cost) {
+        for (int k = 0; k < 3; ++k) U.best[k] = g[k];
+    }
+    U.cand.erase(U.cand.begin());
+    // the next candidate of the same kernel is compared with the best found so far
+    if (U.cand.empty()) {
+        set_grids(c, U.best);
+        c->launch_tuned = true;
+        U.phase = 3;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[tune_key(c)] = {U.best[0], U.best[1], U.best[2]};
+    } else {
+        U.phase = 1;
+    }
+    return s;
 }
 
 void rt_graph_destroy(rt_ctx *c) { graph_destroy(c); }

@@ -673,22 +673,33 @@ def test_step_graph_at_the_hop_cap_and_after_a_barrier_change():
 
 
 def test_launch_size_tuning_changes_nothing_but_time():
-    """With tune_launch the first step times the sender side, the virtual particles and the
-    receiver side on grids of 152 x {8, 16, 32, 64} blocks, hop by hop, and keeps per kernel
-    the least time per item; sizes given in the configuration switch the tuning off.  The
-    results agree bit for bit whatever the sizes."""
+    """With tune_launch the first steps run as the step graph, each with one triple of grid
+    sizes (152 x {8, 16, 32, 64} blocks for the sender side, the virtual particles and the
+    receiver side; the candidate steps alternate with steps of the best so far), timed whole;
+    the winner is kept and reused by a later context of the same configuration and size, which
+    does not tune.  Sizes given in the configuration switch the tuning off.  The results agree
+    bit for bit whatever the sizes."""
     from paper_1311_0182_gb300 import rt
     wl = W.cfg2(n_side=20)
     a = rt.context_for(wl, tune_launch=1)
     b = rt.context_for(wl, tune_launch=0, launch_grid=(152, 304, 456))
-    for step in range(3):
+    seen = set()
+    for step in range(20):          # 9 candidates, each after a step of the best: 18 steps
         a.step(step)
         b.step(step)
         _same_results(a, b)
-    sa, sb = a.stats(), b.stats()
-    for k in ("grid_send", "grid_virtual", "grid_receive"):
-        assert sa[k] in (1216, 2432, 4864, 9728)
+        sa = a.stats()
+        seen.add((sa["grid_send"], sa["grid_virtual"], sa["grid_receive"]))
+    assert len(seen) >= 9            # every candidate ran
+    final = (sa["grid_send"], sa["grid_virtual"], sa["grid_receive"])
+    for k in final:
+        assert k in (1216, 2432, 4864, 9728)
+    sb = b.stats()
     assert (sb["grid_send"], sb["grid_virtual"], sb["grid_receive"]) == (152, 304, 456)
+    c = rt.context_for(wl, tune_launch=1)
+    c.step(0)
+    sc = c.stats()
+    assert (sc["grid_send"], sc["grid_virtual"], sc["grid_receive"]) == final
 
 
 @pytest.mark.parametrize("case", ["fp64", "fp32", "shared_clock_limited"])
