@@ -240,6 +240,7 @@ def run_ours(args):
                          "note": "host-driven hop loop, one synchronisation per hop; the "
                                  "dominant kernel bracketed with events"}
     out["roofline"]["hop_loop_model"] = hop_loop_model(st, wl, ms / args.steps)
+    out["roofline_issue"] = roofline_issue(out["roofline"], clocks_h)
     out["kernel_shares"] = shares
     out["stats_last_step"] = st
     out["floor_hits_last_step"] = st["floor_hits"]
@@ -310,26 +311,40 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str, n_side: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to this workload
-    by particle count, or None when the summary belongs to other source code."""
-    path = os.path.join(ROOT, "profiles", "traffic_per_launch.md")
+PER_UNIT_TABLE = ("profiles", "k_virtual_per_unit_hii_48cubed.md")
+
+
+def committed_per_unit(kernel: str):
+    """(DRAM bytes, warp instructions) per unit of work of `kernel` from the committed ncu
+    summary, or None when the summary belongs to other CUDA sources."""
+    path = os.path.join(ROOT, *PER_UNIT_TABLE)
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
     for line in lines:
-        parts = line.strip().strip("|").split("|")
-        parts = [p.strip() for p in parts]
-        if len(parts) >= 4 and parts[0] == kernel:
+        parts = [p.strip() for p in line.strip().strip("|").split("|")]
+        if len(parts) >= 6 and parts[0] == kernel:
             try:
-                nbytes, n_cap, src = float(parts[1]), int(parts[2]), parts[3]
+                dram, inst, src = float(parts[1]), float(parts[2]), parts[5]
             except ValueError:
                 continue
-            if src != source_hash():
-                return None
-            return nbytes * (n_side ** 3) / n_cap
+            return (dram, inst) if src == source_hash() else None
     return None
+
+
+def vp_model_bytes(params: dict) -> float:
+    """Algorithmic bytes per virtual particle of k_virtual (the library's model): request and
+    packet, per neighbour its position, four properties, two deposit words and the forwarded
+    list entry, and the forwarded packet."""
+    R = 4 if params["transport_fp32"] else 8
+    kn = params["n_ngb"]
+    return 8 + 6 * R + 40 + kn * (16 + 4 * R + 16 + 4) + 6 * R + 40
+
+
+def issue_peak(sm_mhz) -> float:
+    """Warp instructions per second the GPU can issue: 152 SMs x 4 schedulers x 1 per cycle."""
+    return 152 * 4 * (sm_mhz or 2070.0) * 1e6
 
 
 def roofline(ctx, kt, ms_step_total, args):
@@ -343,14 +358,38 @@ def roofline(ctx, kt, ms_step_total, args):
     ms = k["ms"] / max(k["launches"], 1)
     B = k["bytes"] / max(k["launches"], 1)
     ach = B / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    # DRAM traffic per launch: the committed per-virtual-particle figure times this launch's
+    # virtual particles (its algorithmic bytes over the model's bytes per virtual particle)
+    pu = committed_per_unit(name) if name == "virtual_particles" else None
+    units = B / vp_model_bytes(ctx.params) if pu else None
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "peak_kind": f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else kind,
-            "traffic": committed_traffic(name, args.n_side),
+            "traffic": pu[0] * units if pu else None,
+            "units_per_launch": units,
             "algorithmic_bytes_per_launch": B, "ms_per_launch": ms, "launches": k["launches"],
             "share_of_step": k["ms"] / ms_step_total if ms_step_total else None,
             "all_kernels": {n: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                 "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] and v["bytes"] else None}
                             for n, v in kt.items() if v["ms"] > 0}}
+
+
+def roofline_issue(rf: dict, clocks: dict):
+    """The bound the dominant kernel actually meets: instruction issue.  Warp instructions per
+    launch (the committed ncu count per virtual particle times the launch's virtual particles)
+    over the launch's event-timed duration, against 152 SMs x 4 schedulers x 1 instruction per
+    cycle at the SM clock sampled during those launches."""
+    if not rf or rf.get("kernel") != "virtual_particles":
+        return None
+    pu = committed_per_unit("virtual_particles")
+    if not pu or not rf.get("units_per_launch"):
+        return None
+    inst = pu[1] * rf["units_per_launch"]
+    ach = inst / (rf["ms_per_launch"] / 1e3)
+    peak = issue_peak(clocks.get("sm_mhz"))
+    return {"bound": "issue", "kernel": "virtual_particles", "achieved": ach, "peak": peak,
+            "unit": "warp-instructions/s", "frac": ach / peak,
+            "warp_instructions_per_launch": inst, "sm_mhz": clocks.get("sm_mhz"),
+            "peak_kind": "152 SMs x 4 schedulers x 1 warp instruction per cycle at the sampled SM clock"}
 
 
 def hop_loop_model(st: dict, wl: dict, ms_step: float) -> dict:

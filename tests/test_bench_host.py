@@ -14,11 +14,12 @@ import bench
 
 def test_roofline_is_algorithmic_bytes_over_event_time(monkeypatch):
     monkeypatch.setattr(bench, "peaks", lambda: (6684.1, "measured"))
-    monkeypatch.setattr(bench, "committed_traffic", lambda k, n: None)
+    monkeypatch.setattr(bench, "committed_per_unit", lambda k: None)
     kt = {"virtual_particles": {"ms": 10.0, "launches": 10, "bytes": 6.6841e9},
           "phase_a_send": {"ms": 2.0, "launches": 10, "bytes": 1e9},
           "hop_lens": {"ms": 20.0, "launches": 30, "bytes": 0.0}}
-    r = bench.roofline(None, kt, 50.0, types.SimpleNamespace(n_side=64))
+    r = bench.roofline(types.SimpleNamespace(params={"transport_fp32": 1, "n_ngb": 32}), kt, 50.0,
+                       types.SimpleNamespace(n_side=64))
     # the dominant modelled kernel, not the slowest kernel without a bytes model
     assert r["kernel"] == "virtual_particles"
     assert np.isclose(r["ms_per_launch"], 1.0)
@@ -34,25 +35,40 @@ def _fake_tree(tmp_path, table_hash):
     for fn in ("rt_transport.cu", "rt_internal.cuh", "rt_knn.cuh"):
         (csrc / fn).write_text("// " + fn + "\n")
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "profiles" / "traffic_per_launch.md").write_text(
-        "| kernel | DRAM bytes per launch | particles in capture | source hash |\n"
-        "|---|---|---|---|\n"
-        f"| virtual_particles | 200000000 | 262144 | {table_hash} |\n")
+    (tmp_path / "profiles" / bench.PER_UNIT_TABLE[1]).write_text(
+        "| kernel | DRAM bytes per unit | warp instructions per unit | unit | units in capture | source hash |\n"
+        "|---|---|---|---|---|---|\n"
+        f"| virtual_particles | 700.0 | 2500.0 | virtual particle | 1000 | {table_hash} |\n")
 
 
-def test_traffic_is_taken_only_for_the_profiled_sources(tmp_path, monkeypatch):
+def test_per_unit_figures_are_taken_only_for_the_profiled_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     _fake_tree(tmp_path, "0" * 16)
     h = bench.source_hash()
-    assert bench.committed_traffic("virtual_particles", 64) is None      # other sources
-    (tmp_path / "profiles" / "traffic_per_launch.md").unlink()
-    os.rmdir(tmp_path / "profiles")
+    assert bench.committed_per_unit("virtual_particles") is None        # other sources
     import shutil
+    shutil.rmtree(tmp_path / "profiles")
     shutil.rmtree(tmp_path / "paper_1311_0182_gb300")
     _fake_tree(tmp_path, h)
-    assert bench.committed_traffic("virtual_particles", 64) == 2e8
-    assert bench.committed_traffic("virtual_particles", 32) == 2e8 / 8   # scaled by particles
-    assert bench.committed_traffic("phase_b_merge", 64) is None
+    assert bench.committed_per_unit("virtual_particles") == (700.0, 2500.0)
+    assert bench.committed_per_unit("phase_b_merge") is None
+
+
+def test_traffic_and_issue_rooflines_scale_by_the_launch_units(tmp_path, monkeypatch):
+    """Traffic and instructions per launch: the committed per-virtual-particle figures times the
+    launch's virtual particles (its algorithmic bytes over the model's bytes per particle)."""
+    monkeypatch.setattr(bench, "peaks", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "committed_per_unit", lambda k: (700.0, 2500.0))
+    params = {"transport_fp32": 1, "n_ngb": 32}
+    per = bench.vp_model_bytes(params)
+    assert per == 8 + 24 + 40 + 32 * (16 + 16 + 16 + 4) + 24 + 40
+    kt = {"virtual_particles": {"ms": 2.0, "launches": 2, "bytes": 2 * 1000 * per}}
+    ctx = types.SimpleNamespace(params=params)
+    r = bench.roofline(ctx, kt, 10.0, types.SimpleNamespace(n_side=64))
+    assert np.isclose(r["units_per_launch"], 1000) and np.isclose(r["traffic"], 700.0 * 1000)
+    ri = bench.roofline_issue(r, {"sm_mhz": 2000.0})
+    assert np.isclose(ri["achieved"], 2500.0 * 1000 / 1e-3)
+    assert np.isclose(ri["peak"], 152 * 4 * 2000e6) and ri["bound"] == "issue"
 
 
 def test_kernel_shares_sum_to_one():
