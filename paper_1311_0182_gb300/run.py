@@ -147,6 +147,8 @@ def run(wl, steps, start=0, ctx=None, profile_every=0, checkpoint_every=0, check
             edges, px = radial_profile(r, x[box0], 0.5 * L)
             _, pT = radial_profile(r, st["T"][box0], 0.5 * L)
             line["profile"] = {"r_kpc": (edges / W.KPC).tolist(), "x_HI": px, "T": pT}
+            if wl.get("barriers"):
+                line["shadow"] = shadow_profiles(wl, st, ctx.deposits()[2], wl["params"]["dt"])
         if checkpoint_every and checkpoint_dir and (s + 1) % checkpoint_every == 0:
             path = os.path.join(checkpoint_dir, f"step{s:06d}.ckpt")
             with open(path, "wb") as f:
