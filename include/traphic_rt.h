@@ -261,6 +261,18 @@ rt_status rt_get_neighbours(rt_ctx *ctx, int *nbr, long long *h2, int *src_nbr,
                             long long *src_h2, int where, void *stream);
 /* quantised positions [n * 3] */
 rt_status rt_get_quantised(rt_ctx *ctx, long long *q, int where, void *stream);
+/* rt_query_neighbours -- the exact n_ngb nearest particles of m points of box `box`, by the
+   search the virtual particles use (Sec. 2.1: a virtual particle's neighbours are the n_ngb
+   particles nearest to it), from the per-cell candidate lists that rt_build_neighbours builds.
+   q[m * 3]: quantised positions (int, each in [0, 2^20), the units of rt_get_quantised).
+   nbr[m * n_ngb]: global particle indices, nearest first, equal distances to the lower index;
+   d2[m * n_ngb]: their squared quantised distances; NULL skips.  A point whose search fails
+   gets -1 entries.  Allocates temporary device buffers for host arrays and synchronises
+   `stream`.  Errors: RT_ERR_STATE (before rt_build_neighbours), RT_ERR_INVALID (a bad box or
+   count, or a coordinate out of range: no output is valid then), RT_ERR_KNN (some search
+   failed, as for the particles' own), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_query_neighbours(rt_ctx *ctx, int box, long long m, const int *q, int *nbr,
+                              long long *d2, int where, void *stream);
 /* rotation matrices (row-major): reception [n * 9], emission [n_src * K * 9], K = dt/dt_em */
 rt_status rt_get_rotations(rt_ctx *ctx, double *R, double *Rs, int where, void *stream);
 /* transmission masks of the held packets [n * S], S = n_rc * (n_freq_src + 1): bit k set
@@ -319,8 +331,9 @@ rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass,
    transport: gas-to-gas contributions, particles with a packet able to move, packets able to
    move, staged free-packet contributions, receiver work-list entries, occupied slots written
    by the receiver side; then the cell occupancy of the kNN grids in use; then the grid sizes
-   (blocks) of the sender side, the virtual particles and the receiver side in use;
-   out[17..19] are 0 */
+   (blocks) of the sender side, the virtual particles and the receiver side in use; then the
+   entries of the per-cell candidate lists of the virtual particles' kNN (4 bytes each, built
+   by rt_build_neighbours); out[18..19] are 0 */
 #define RT_NSTATS 20
 rt_status rt_get_stats(rt_ctx *ctx, long long *out);
 /* the isotropic cone direction set with n directions (8 or 32), [n * 3] host */

@@ -352,6 +352,9 @@ extern "C" rt_status rt_create(const rt_config *cfg, int n_boxes, const long lon
     A(P.grid.cs, int, n_boxes);
     A(P.grid.coff, long long, n_boxes);
     A(P.grid.start, int, ncell + 1);
+    A(P.grid.cand_off, long long, ncell + 1);
+    P.grid.cand = nullptr;       // sized and filled by the neighbour build
+    P.grid.cand_cap = 0;
     c->grid_cap = ncell;
     A(P.grid.items, int4, n);
     A(P.grid.tab, int, KNN_TAB_N);
@@ -476,6 +479,7 @@ extern "C" rt_status rt_destroy(rt_ctx *c) {
     rt_graph_destroy(c);
     if (c->st_cap) cudaStreamDestroy(c->st_cap);
     for (size_t k = 0; k < c->allocs.size(); ++k) cudaFree(c->allocs[k]);
+    if (c->d.grid.cand) cudaFree(c->d.grid.cand);
     if (c->scan_tmp) cudaFree(c->scan_tmp);
     if (c->scan_tmp2) cudaFree(c->scan_tmp2);
     if (c->cnt_h) cudaFreeHost(c->cnt_h);
@@ -485,8 +489,8 @@ extern "C" rt_status rt_destroy(rt_ctx *c) {
     }
     for (int k = 0; k < 4; ++k)
         if (c->hev[k]) cudaEventDestroy(c->hev[k]);
-    for (int k = 0; k < 6; ++k)
-        if (k < 2 && c->tune_ev[k]) cudaEventDestroy(c->tune_ev[k]);
+    for (int k = 0; k < 2; ++k)
+        if (c->tune_ev[k]) cudaEventDestroy(c->tune_ev[k]);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return RT_OK;
@@ -1060,6 +1064,60 @@ template <typename T> static T *dtmp(size_t n) {
     return p;
 }
 
+void rt_launch_query(rt_ctx *c, int b, long long m, const int *q, int *nbr, long long *d2,
+                     int *fail, cudaStream_t st);
+
+extern "C" rt_status rt_query_neighbours(rt_ctx *c, int box, long long m, const int *q, int *nbr,
+                                         long long *d2, int where, void *stream) {
+    rt_status s = need_built(c);
+    if (s) return s;
+    if (box < 0 || box >= c->d.nb || m < 0 || (m > 0 && !q) ||
+        (where != RT_HOST && where != RT_DEVICE))
+        return rt_fail(c, RT_ERR_INVALID, "rt_query_neighbours: bad box, count or pointer");
+    if (m == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t kn = (size_t)c->d.kn;
+    int *qd = (int *)q, *nd = nbr, *fd = dtmp<int>(1);
+    long long *dd = d2;
+    bool host = where == RT_HOST;
+    if (host) {
+        qd = dtmp<int>(3 * (size_t)m);
+        nd = nbr ? dtmp<int>(kn * m) : nullptr;
+        dd = d2 ? dtmp<long long>(kn * m) : nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!fd || !qd || (nbr && !nd) || (d2 && !dd)) {
+        s = rt_fail(c, RT_ERR_OOM, "temp");
+    } else {
+        cudaMemsetAsync(fd, 0, sizeof(int), st);
+        if (host) e = cudaMemcpyAsync(qd, q, sizeof(int) * 3 * m, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            rt_launch_query(c, box, m, qd, nd, dd, fd, st);
+            e = cudaGetLastError();
+        }
+        int fail = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&fail, fd, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && host && nbr)
+            e = cudaMemcpyAsync(nbr, nd, sizeof(int) * kn * m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && host && d2)
+            e = cudaMemcpyAsync(d2, dd, sizeof(long long) * kn * m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        s = rt_cuda_check(c, e, "rt_query_neighbours");
+        if (s == RT_OK && (fail & 1))
+            s = rt_fail(c, RT_ERR_INVALID, "rt_query_neighbours: a coordinate out of [0, 2^20)");
+        else if (s == RT_OK && (fail & 2))
+            s = rt_fail(c, RT_ERR_KNN, "rt_query_neighbours: a search found too few particles");
+    }
+    cudaStreamSynchronize(st);
+    if (fd) cudaFree(fd);
+    if (host) {
+        if (qd) cudaFree(qd);
+        if (nd) cudaFree(nd);
+        if (dd) cudaFree(dd);
+    }
+    return s;
+}
+
 extern "C" rt_status rt_get_quantised(rt_ctx *c, long long *q, int where, void *stream) {
     if (!c || !q || !c->have_particles) return RT_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1307,6 +1365,7 @@ extern "C" rt_status rt_get_stats(rt_ctx *c, long long *out) {
     for (int k = 0; k < RT_NSTATS; ++k) out[k] = c->stats[k];
     out[13] = c->cell_occ;
     rt_launch_grids(c, out + 14);
+    out[17] = c->cand_entries;
     return RT_OK;
 }
 

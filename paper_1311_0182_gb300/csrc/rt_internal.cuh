@@ -17,7 +17,7 @@
 
 #define RT_Q 1048576          // 2^20 quantisation cells per box side
 #define RT_BUDGET_CHUNK 4096
-#define RT_OCC_MIN 2           // finest kNN grid the occupancy search tries
+#define RT_OCC_MIN 1           // finest kNN grid the occupancy search tries
 #define RT_MAXK 32            // maximum neighbours per particle
 #define RT_FREE_BIT (1ull << 63)
 #define RT_SCAN_NB 608         // blocks of every prefix-sum launch (4 per SM)
@@ -83,6 +83,11 @@ struct Grid {                 // per-box uniform cell lists (device arrays)
     int4 *items;              // (qx, qy, qz, local index) sorted by cell
     long long ncells;
     int *tab;                 // cell offsets of the kNN search, nearest first (rt_knn.cuh)
+    // per-cell candidate lists of the virtual particles' kNN (rt_knn.cuh): cand_off[ncells + 1]
+    // offsets into cand; an entry is ring << 24 | the item's position among the box's items
+    long long *cand_off;
+    unsigned *cand;
+    long long cand_cap;       // entries allocated
 };
 
 struct HopScratch {           // per-hop scratch: [0] free packets, [1] n + free, [2] requests, [3] staged
@@ -257,6 +262,7 @@ struct rt_ctx {
     int cell_occ = 9;              // particles per cell of the kNN grids in use
     long long grid_cap = 0;        // cells allocated (the finest grid that can be chosen)
     bool grid_tuned = false;       // occupancy chosen (or fixed by the configuration)
+    long long cand_entries = 0;    // entries of the candidate lists in use
     long long *cnt_h = nullptr;   // pinned
     std::vector<void *> allocs;
     bool have_particles = false, have_sources = false, built = false;
@@ -311,6 +317,8 @@ rt_status rt_fail(rt_ctx *c, rt_status s, const std::string &msg);
 rt_status rt_cuda_check(rt_ctx *c, cudaError_t e, const char *what);
 void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const int *d_len,
                        int *d_total, cudaStream_t st, int *tmp = nullptr);
+void rt_scan_exclusive64(const int *in, long long *out, long long n, long long *tmp,
+                         cudaStream_t st);
 rt_status rt_knn_build(rt_ctx *c, cudaStream_t st);
 // per-box cell grids for a target occupancy; host-synchronous copies: no kernel that reads
 // the grids may be in flight

@@ -189,11 +189,10 @@ __global__ void k_rev_sort(DevPtrs P) {
 }
 
 // Timing probe of the occupancy search: the kNN search of virtual-particle-like points, one
-// per fourth particle, up to 0.44 smoothing lengths from it in a hashed direction, bounded
-// (by 1.5 h, which holds its n_ngb neighbours) like the virtual particles' search.  Writes one
-// word no one reads, so that the search is not dropped.
+// per fourth particle, up to 0.44 smoothing lengths from it in a hashed direction, from the
+// candidate list of its cell like the virtual particles' search.  Writes one word no one reads,
+// so that the search is not dropped.
 __global__ void __launch_bounds__(256) k_knn_probe(DevPtrs P, unsigned long long *sink) {
-    __shared__ int sdelta[8][32];
     int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -211,18 +210,169 @@ __global__ void __launch_bounds__(256) k_knn_probe(DevPtrs P, unsigned long long
         int qx = min(max(P.qx[i] + o[0], 0), RT_Q - 1);
         int qy = min(max(P.qy[i] + o[1], 0), RT_Q - 1);
         int qz = min(max(P.qz[i] + o[2], 0), RT_Q - 1);
-        long long bd = 3 * H / 2 + 2;
+        CandQuery Q = cand_query(P.grid, b, qx, qy, qz);
         long long d2;
         int idx;
         if (knn_wide_box(P.box_off[b + 1] - P.box_off[b]))
-            warp_knn<KNN_IB_LARGE>(box_grid(P, b), qx, qy, qz, -1, P.kn, d2, idx,
-                                   sdelta[threadIdx.x >> 5], bd * bd);
+            cand_knn<KNN_IB_LARGE>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w, P.kn,
+                                   d2, idx);
         else
-            warp_knn<KNN_IB_SMALL>(box_grid(P, b), qx, qy, qz, -1, P.kn, d2, idx,
-                                   sdelta[threadIdx.x >> 5], bd * bd);
+            cand_knn<KNN_IB_SMALL>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w, P.kn,
+                                   d2, idx);
         acc += (unsigned long long)idx;
     }
     if (lane == 0 && acc == 0xffffffffffffffffull) *sink = acc;
+}
+
+// ---- per-cell candidate lists (rt_knn.cuh) ----------------------------------------------------
+// the box and coordinates of global cell index c
+__device__ __forceinline__ int cell_box(const DevPtrs &P, long long c) {
+    int lo = 0, hi = P.nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.grid.coff[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Calls f(position of the item among the box's items, item) for every particle of box b whose
+// squared distance to the cell box [lo, lo + cs - 1]^3 is at most u2 (lane = grid column; a
+// column's cells are consecutive, so its candidate cells are one range of items).
+template <typename F>
+__device__ __forceinline__ void cand_walk(const DevPtrs &P, int b, int cx, int cy, int cz,
+                                          long long u2, F f) {
+    int lane = threadIdx.x & 31;
+    int G = P.grid.G[b], cs = P.grid.cs[b];
+    long long coff = P.grid.coff[b];
+    int ibase = P.grid.start[coff];
+    // a cell at Chebyshev offset o >= 2 is at least (o - 1) cs + 1 from the cell
+    int R = G;
+    if (u2 < KNN_INF) {
+        long long u = (long long)sqrt((double)u2) + 1;
+        if (u / cs + 1 < G) R = (int)(u / cs + 1);
+    }
+    int lx = cx * cs, ly = cy * cs, lz = cz * cs;
+    int hx = lx + cs - 1, hy = ly + cs - 1, hz = lz + cs - 1;
+    int side = 2 * R + 1;
+    long long ncol = (long long)side * side;
+    int z0 = max(cz - R, 0), z1 = min(cz + R, G - 1);
+    for (long long cb = 0; cb < ncol; cb += 32) {
+        long long col = cb + lane;
+        if (col >= ncol) continue;
+        int ix = cx - R + (int)(col / side), iy = cy - R + (int)(col % side);
+        if (ix < 0 || iy < 0 || ix >= G || iy >= G) continue;
+        long long gx = ix < cx ? lx - (ix * cs + cs - 1) : (ix > cx ? ix * cs - hx : 0);
+        long long gy = iy < cy ? ly - (iy * cs + cs - 1) : (iy > cy ? iy * cs - hy : 0);
+        if (gx * gx + gy * gy > u2) continue;
+        long long colbase = coff + ((long long)ix * G + iy) * G;
+        int p0 = P.grid.start[colbase + z0], p1 = P.grid.start[colbase + z1 + 1];
+        for (int pos = p0; pos < p1; ++pos) {
+            int4 it = P.grid.items[pos];
+            if (box_d2(it.x, it.y, it.z, lx, ly, lz, hx, hy, hz) <= u2) f(pos - ibase, it);
+        }
+    }
+}
+
+// one warp per cell: U^2 (the kn nearest of the cell's centre point, each at its distance to
+// the farthest corner of the cell) and the number of candidates
+__global__ void __launch_bounds__(256) k_cand_count(DevPtrs P, long long *u2out, int *cnt) {
+    __shared__ int sdelta[8][32];
+    int lane = threadIdx.x & 31;
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = w0; c < P.grid.ncells; c += nw) {
+        int b = cell_box(P, c);
+        int G = P.grid.G[b], cs = P.grid.cs[b];
+        long long lc = c - P.grid.coff[b];
+        int cx = (int)(lc / ((long long)G * G)), cy = (int)((lc / G) % G), cz = (int)(lc % G);
+        int lx = cx * cs, ly = cy * cs, lz = cz * cs;
+        int mx = cand_centre(lx, cs), my = cand_centre(ly, cs), mz = cand_centre(lz, cs);
+        long long d2;
+        int idx;
+        bool ok = knn_wide_box(P.box_off[b + 1] - P.box_off[b])
+                      ? warp_knn<KNN_IB_LARGE>(box_grid(P, b), mx, my, mz, -1, P.kn, d2, idx,
+                                               sdelta[threadIdx.x >> 5])
+                      : warp_knn<KNN_IB_SMALL>(box_grid(P, b), mx, my, mz, -1, P.kn, d2, idx,
+                                               sdelta[threadIdx.x >> 5]);
+        long long u2 = 0;
+        if (ok && lane < P.kn) {
+            long long j = P.box_off[b] + idx;
+            long long ex = max(P.qx[j] - lx, lx + cs - 1 - P.qx[j]);
+            long long ey = max(P.qy[j] - ly, ly + cs - 1 - P.qy[j]);
+            long long ez = max(P.qz[j] - lz, lz + cs - 1 - P.qz[j]);
+            u2 = ex * ex + ey * ey + ez * ez;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            long long v = __shfl_xor_sync(FULLMASK, u2, o);
+            u2 = v > u2 ? v : u2;
+        }
+        // no kn nearest (a box of fewer particles, or a k-th distance beyond the key range):
+        // the whole box
+        if (!ok) u2 = KNN_INF;
+        int n = 0;
+        cand_walk(P, b, cx, cy, cz, u2, [&](int, const int4 &) { ++n; });
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(FULLMASK, n, o);
+        if (lane == 0) {
+            u2out[c] = u2;
+            cnt[c] = n;
+        }
+    }
+}
+
+// one warp per cell: the entries, by ring (a counting sort in shared memory)
+__global__ void __launch_bounds__(256) k_cand_fill(DevPtrs P, const long long *u2in) {
+    __shared__ int bins[8][256];
+    int lane = threadIdx.x & 31;
+    int *bin = bins[threadIdx.x >> 5];
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = w0; c < P.grid.ncells; c += nw) {
+        int b = cell_box(P, c);
+        int G = P.grid.G[b], cs = P.grid.cs[b];
+        long long lc = c - P.grid.coff[b];
+        int cx = (int)(lc / ((long long)G * G)), cy = (int)((lc / G) % G), cz = (int)(lc % G);
+        int mx = cand_centre(cx * cs, cs), my = cand_centre(cy * cs, cs), mz = cand_centre(cz * cs, cs);
+        int w = cand_ring_width(cs);
+        long long u2 = u2in[c];
+        long long a = P.grid.cand_off[c], e = P.grid.cand_off[c + 1];
+        auto ring_of = [&](const int4 &it) {
+            long long dx = it.x - mx, dy = it.y - my, dz = it.z - mz;
+            long long d2 = dx * dx + dy * dy + dz * dz;
+            long long r = (long long)(sqrt((double)d2) / (double)w);
+            if (r > 255) r = 255;
+            while (r > 0 && (r * w) * (r * w) > d2) --r;   // r w <= |p - m|
+            return (int)r;
+        };
+        for (int k = lane; k < 256; k += 32) bin[k] = 0;
+        __syncwarp();
+        cand_walk(P, b, cx, cy, cz, u2, [&](int, const int4 &it) { atomicAdd(&bin[ring_of(it)], 1); });
+        __syncwarp();
+        // exclusive scan of the 256 bins: 8 per lane
+        int loc[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { loc[k] = s; s += bin[lane * 8 + k]; }
+        int incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(FULLMASK, incl, o);
+            if (lane >= o) incl += v;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) bin[lane * 8 + k] = incl - s + loc[k];
+        __syncwarp();
+        bool over = false;
+        cand_walk(P, b, cx, cy, cz, u2, [&](int ipos, const int4 &it) {
+            int r = ring_of(it);
+            long long pos = a + atomicAdd(&bin[r], 1);
+            if (pos < e) P.grid.cand[pos] = ((unsigned)r << 24) | (unsigned)ipos;
+            else over = true;
+        });
+        if (over) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_KNN);
+        __syncwarp();
+    }
 }
 
 static void cell_lists(rt_ctx *c, cudaStream_t st) {
@@ -237,13 +387,48 @@ static void cell_lists(rt_ctx *c, cudaStream_t st) {
     k_cell_fill<<<nbk, tb, 0, st>>>(P, fill);
 }
 
-// The occupancy of the kNN cell grids (the tile of candidates each search walks) is picked
-// on the particle set itself: after the first neighbour build, the search of points placed
-// like virtual particles (the hot use of the grids) is timed on each candidate grid and the
-// fastest wins.  Done once per context; any grid gives the same exact neighbours, so only the
-// time depends on the choice.
-static void tune_grid(rt_ctx *c, cudaStream_t st) {
-    static const int cand[] = {2, 3, 4, 5, 7, 9};
+// The candidate lists of the current grid: counts and U^2 per cell, 64-bit offsets, storage
+// (grown when needed), entries.  Setup work: it synchronises the stream to size the storage.
+static rt_status cand_lists(rt_ctx *c, cudaStream_t st) {
+    DevPtrs &P = c->d;
+    long long nc = P.grid.ncells;
+    int tb = 256;
+    int *cnt = P.seg_cnt;   // scratch, sized >= ncells + 1
+    long long *tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, sizeof(long long) * (size_t)(nc + RT_SCAN_NB));
+    if (e != cudaSuccess) return rt_cuda_check(c, e, "candidate lists");
+    long long *u2 = tmp + RT_SCAN_NB;
+    cudaMemsetAsync(cnt + nc, 0, sizeof(int), st);
+    k_cand_count<<<rt_blocks(nc * 32, tb, 152 * 64), tb, 0, st>>>(P, u2, cnt);
+    rt_scan_exclusive64(cnt, P.grid.cand_off, nc + 1, tmp, st);
+    long long total = 0;
+    cudaMemcpyAsync(&total, P.grid.cand_off + nc, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && total > P.grid.cand_cap) {
+        if (P.grid.cand) cudaFree(P.grid.cand);
+        P.grid.cand = nullptr;
+        P.grid.cand_cap = 0;
+        e = cudaMalloc(&P.grid.cand, sizeof(unsigned) * (size_t)(total > 0 ? total : 1));
+        if (e == cudaSuccess) P.grid.cand_cap = total;
+        else P.grid.cand = nullptr;
+    }
+    if (e == cudaSuccess)
+        k_cand_fill<<<rt_blocks(nc * 32, tb, 152 * 64), tb, 0, st>>>(P, u2);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    c->cand_entries = total;
+    return rt_cuda_check(c, e, "candidate lists");
+}
+
+// The occupancy of the kNN cell grids (the cells whose candidate lists the virtual particles'
+// search takes) is picked on the particle set itself: after the first neighbour build, the
+// search of points placed like virtual particles (the hot use of the grids) is timed on each
+// candidate grid, with its candidate lists, and the fastest wins.  Done once per context; any
+// grid gives the same exact neighbours, so only the time depends on the choice.
+static rt_status tune_grid(rt_ctx *c, cudaStream_t st) {
+    static const int cand[] = {1, 2, 3, 4, 6};
     DevPtrs &P = c->d;
     int tb = 256;
     // rt_set_grid rewrites the grid description with plain copies, which do not wait for
@@ -254,9 +439,11 @@ static void tune_grid(rt_ctx *c, cudaStream_t st) {
     cudaEventCreate(&e1);
     float best_ms = 0.f;
     int best = c->cell_occ;
+    rt_status s = RT_OK;
     for (int occ : cand) {
         rt_set_grid(c, occ);
         cell_lists(c, st);
+        if ((s = cand_lists(c, st)) != RT_OK) break;
         cudaEventRecord(e0, st);
         k_knn_probe<<<rt_blocks((P.n / 4 + 1) * 32, tb, 152 * 64), tb, 0, st>>>(
             P, (unsigned long long *)&P.cnt[CNT_N - 1]);   // an unused counter as the sink
@@ -268,9 +455,12 @@ static void tune_grid(rt_ctx *c, cudaStream_t st) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (s != RT_OK) return s;
     rt_set_grid(c, best);
     cell_lists(c, st);
+    if ((s = cand_lists(c, st)) != RT_OK) return s;
     c->grid_tuned = true;
+    return RT_OK;
 }
 
 rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
@@ -293,8 +483,48 @@ rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
     rt_scan_exclusive(c, cnt, P.rev_off, n + 1, nullptr, nullptr, st);
     k_rev_fill<<<nbe, tb, 0, st>>>(P, fill);
     k_rev_sort<<<nbk, tb, 0, st>>>(P);
-    if (!c->grid_tuned) tune_grid(c, st);   // needs the smoothing lengths just computed
-    return rt_cuda_check(c, cudaGetLastError(), "neighbour build");
+    rt_status s = rt_cuda_check(c, cudaGetLastError(), "neighbour build");
+    if (s != RT_OK) return s;
+    // the virtual particles' candidate lists, on the grid the occupancy search picks (it needs
+    // the smoothing lengths just computed)
+    s = c->grid_tuned ? cand_lists(c, st) : tune_grid(c, st);
+    // the step graph holds the grid description by value
+    rt_graph_destroy(c);
+    return s;
+}
+
+// rt_query_neighbours: one warp per point; fail bit 1: a coordinate out of range, bit 2: a
+// failed search
+__global__ void __launch_bounds__(256) k_query(DevPtrs P, int b, long long m, const int *q,
+                                               int *nbr, long long *d2out, int *fail) {
+    int lane = threadIdx.x & 31;
+    long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    bool wide = knn_wide_box(P.box_off[b + 1] - P.box_off[b]);
+    for (long long w = w0; w < m; w += nw) {
+        int qx = q[3 * w], qy = q[3 * w + 1], qz = q[3 * w + 2];
+        bool ok = qx >= 0 && qy >= 0 && qz >= 0 && qx < RT_Q && qy < RT_Q && qz < RT_Q;
+        if (!ok && lane == 0) atomicOr(fail, 1);
+        long long d2 = -1;
+        int idx = 0;
+        if (ok) {
+            CandQuery Q = cand_query(P.grid, b, qx, qy, qz);
+            ok = wide ? cand_knn<KNN_IB_LARGE>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up,
+                                               Q.w, P.kn, d2, idx)
+                      : cand_knn<KNN_IB_SMALL>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up,
+                                               Q.w, P.kn, d2, idx);
+            if (!ok && lane == 0) atomicOr(fail, 2);
+        }
+        if (lane < P.kn) {
+            if (nbr) nbr[w * P.kn + lane] = ok ? (int)(P.box_off[b] + idx) : -1;
+            if (d2out) d2out[w * P.kn + lane] = ok ? d2 : -1;
+        }
+    }
+}
+
+void rt_launch_query(rt_ctx *c, int b, long long m, const int *q, int *nbr, long long *d2,
+                     int *fail, cudaStream_t st) {
+    if (m > 0) k_query<<<rt_blocks(m * 32, 256, 152 * 64), 256, 0, st>>>(c->d, b, m, q, nbr, d2, fail);
 }
 
 // launchers used by the API for particle/source upload

@@ -73,6 +73,30 @@ __device__ __forceinline__ void warp_insert(unsigned long long &t, unsigned long
     if (t > c) t = (lane == 0 || p < c) ? c : p;
 }
 
+// Merge one batch of candidate keys (one per lane, KNN_KEY_NONE for none; pass: the lane's key
+// is below the current k-th key) into the sorted top list t, and update kth (the key held by lane
+// kn - 1).  Few passing candidates are inserted one by one (one that no longer beats the list's
+// last entry falls off its end); more are sorted and merged.
+__device__ __forceinline__ void knn_merge_batch(unsigned long long ck, bool pass, int kn,
+                                                unsigned long long &t, unsigned long long &kth) {
+    unsigned m = __ballot_sync(FULLMASK, pass);
+    if (!m) return;
+    if (__popc(m) <= KNN_INSERT_MAX) {
+        while (m) {
+            int src = __ffs(m) - 1;
+            m &= m - 1u;
+            warp_insert(t, __shfl_sync(FULLMASK, ck, src));
+        }
+    } else if (__shfl_sync(FULLMASK, t, 0) == KNN_KEY_NONE) {
+        // first candidates: the sorted batch is the list
+        t = pass ? ck : KNN_KEY_NONE;
+        warp_sort(t);
+    } else {
+        warp_merge(t, pass ? ck : KNN_KEY_NONE);
+    }
+    kth = __shfl_sync(FULLMASK, t, kn - 1);
+}
+
 // the table of cell offsets: all of [-KNN_TAB_R, KNN_TAB_R]^3, each entry
 // (ox + 4) | (oy + 4) << 4 | (oz + 4) << 8 | dmin << 12, sorted by dmin, then by |o|^2, where
 // dmin = sum_a max(|o_a| - 1, 0)^2: a point in the query's cell is at least dmin * cs^2 from
@@ -160,25 +184,7 @@ __device__ inline void knn_visit(const BoxGrid &g, int qx, int qy, int qz, int e
             long long dx = it.x - qx, dy = it.y - qy, dz = it.z - qz;
             ck = knn_key<IB>(dx * dx + dy * dy + dz * dz, it.w);
         }
-        bool pass = ck < kth && ck <= bkey;
-        unsigned m = __ballot_sync(FULLMASK, pass);
-        if (!m) continue;
-        if (__popc(m) <= KNN_INSERT_MAX) {
-            // few candidates: insert them one by one (one that no longer beats the list's last
-            // entry falls off its end)
-            while (m) {
-                int src = __ffs(m) - 1;
-                m &= m - 1u;
-                warp_insert(t, __shfl_sync(FULLMASK, ck, src));
-            }
-        } else if (__shfl_sync(FULLMASK, t, 0) == KNN_KEY_NONE) {
-            // first candidates: the sorted batch is the list
-            t = pass ? ck : KNN_KEY_NONE;
-            warp_sort(t);
-        } else {
-            warp_merge(t, pass ? ck : KNN_KEY_NONE);
-        }
-        kth = __shfl_sync(FULLMASK, t, kn - 1);
+        knn_merge_batch(ck, ck < kth && ck <= bkey, kn, t, kth);
     }
 }
 
@@ -318,4 +324,102 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
         out_idx = (int)(t & ((1ull << IB) - 1ull));
     }
     return kth != KNN_KEY_NONE && (IB == KNN_IB_SMALL || (long long)(kth >> IB) < knn_d2max<IB>());
+}
+
+// ---- per-cell candidate lists (the virtual particles' search) ---------------------------------
+// Gas particles do not move, so for every cell of a box's grid the particles that can be among
+// the kn nearest of some point of the cell are listed once, after the neighbour build.  With
+// lo and hi = lo + cs - 1 the cell's corners and U the largest distance from any point of the
+// cell to any of the kn nearest particles of the cell's centre point (computed per particle as
+// its distance to the farthest corner), every point of the cell has kn particles within U, so
+// its kn nearest lie within U of it, and hence within U of the cell: the list holds every
+// particle whose distance to the cell is at most U.  Entries are ordered by ring, the distance
+// from the centre point m in units of w, rounded down (ring * w <= |p - m|, capped at 255).  A
+// query q in the cell takes the list 32 entries at a time; a particle p of ring r is at least
+// r * w - |q - m| from q, so once the first entry of a batch has r * w - |q - m| above the
+// current k-th distance, no later entry can enter the result, which is the exact kn nearest
+// either way.
+
+// ring width of a box's lists: an eighth of the cell side
+__device__ __forceinline__ int cand_ring_width(int cs) { return cs >= 16 ? cs >> 3 : 1; }
+
+// the centre point of the cell starting at lo (inside the quantised range)
+__device__ __forceinline__ int cand_centre(int lo, int cs) {
+    int m = lo + (cs >> 1);
+    return m < RT_Q - 1 ? m : RT_Q - 1;
+}
+
+// an upper bound on sqrt(x) for 0 <= x < 2^42, from 32-bit operations with upward rounding
+__device__ __forceinline__ float sqrt_up(long long x) {
+    float hi = __uint2float_rn((unsigned)(x >> 21));           // < 2^21: exact
+    float lo = __uint2float_rn((unsigned)(x & 0x1fffffll));    // < 2^21: exact
+    return __fsqrt_ru(__fmaf_ru(hi, 2097152.0f, lo));
+}
+
+// Exact kNN of q (quantised) from the candidate list [a, e) of its cell: the result and the
+// return value are those of warp_knn over the whole box.  items: the box's grid items (an entry's
+// low 24 bits index them); w: the box's ring width; rq_up: an upper bound on |q - m|.
+template <int IB>
+__device__ inline bool cand_knn(const int4 *items, const unsigned *cand, long long a, long long e,
+                                int qx, int qy, int qz, float rq_up, int w, int kn,
+                                long long &out_d2, int &out_idx) {
+    int lane = threadIdx.x & 31;
+    unsigned long long t = KNN_KEY_NONE, kth = KNN_KEY_NONE;
+    // entries and items of the next batch are loaded before the current batch is merged
+    unsigned ent = a + lane < e ? __ldg(cand + a + lane) : 0xffffffffu;
+    int4 nxt = make_int4(0, 0, 0, -1);
+    if (a + lane < e) nxt = __ldg(items + (ent & 0xffffffu));
+    for (long long base = a; base < e; base += 32) {
+        unsigned cur = ent;
+        int4 it = nxt;
+        bool have = base + lane < e;
+        if (kth != KNN_KEY_NONE) {
+            // the batch's first entry has the smallest ring of what is left
+            int r0 = (int)(__shfl_sync(FULLMASK, cur, 0) >> 24);
+            float reach = __fadd_ru(sqrt_up((long long)(kth >> IB)), rq_up);
+            if (__int2float_rd(r0 * w) > reach) break;
+        }
+        if (base + 32 + lane < e) {
+            ent = __ldg(cand + base + 32 + lane);
+            nxt = __ldg(items + (ent & 0xffffffu));
+        }
+        unsigned long long ck = KNN_KEY_NONE;
+        if (have) {
+            long long dx = it.x - qx, dy = it.y - qy, dz = it.z - qz;
+            ck = knn_key<IB>(dx * dx + dy * dy + dz * dz, it.w);
+        }
+        knn_merge_batch(ck, ck < kth, kn, t, kth);
+    }
+    if (t == KNN_KEY_NONE) {
+        out_d2 = KNN_INF;
+        out_idx = 0x7fffffff;
+    } else {
+        out_d2 = (long long)(t >> IB);
+        out_idx = (int)(t & ((1ull << IB) - 1ull));
+    }
+    return kth != KNN_KEY_NONE && (IB == KNN_IB_SMALL || (long long)(kth >> IB) < knn_d2max<IB>());
+}
+
+// The query of a virtual particle at (qx, qy, qz) in box b: its cell's list, ring width and
+// the bound on its distance to the cell's centre point.
+struct CandQuery {
+    const int4 *items;
+    long long a, e;
+    int w;
+    float rq_up;
+};
+__device__ __forceinline__ CandQuery cand_query(const Grid &gr, int b, int qx, int qy, int qz) {
+    CandQuery Q;
+    int G = gr.G[b], cs = gr.cs[b];
+    long long coff = gr.coff[b];
+    int cx = cell_coord(qx, cs, G), cy = cell_coord(qy, cs, G), cz = cell_coord(qz, cs, G);
+    long long cell = coff + ((long long)cx * G + cy) * G + cz;
+    Q.a = gr.cand_off[cell];
+    Q.e = gr.cand_off[cell + 1];
+    Q.items = gr.items + gr.start[coff];
+    Q.w = cand_ring_width(cs);
+    long long mx = cand_centre(cx * cs, cs) - qx, my = cand_centre(cy * cs, cs) - qy,
+              mz = cand_centre(cz * cs, cs) - qz;
+    Q.rq_up = sqrt_up(mx * mx + my * my + mz * mz);
+    return Q;
 }

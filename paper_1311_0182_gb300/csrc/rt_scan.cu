@@ -6,29 +6,30 @@
 
 #define SCAN_BLOCK 1024
 
-__device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *sh, T *total) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = v;
+    T incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(FULLMASK, incl, o);
+        T t = __shfl_up_sync(FULLMASK, incl, o);
         if (lane >= o) incl += t;
     }
     if (lane == 31) sh[w] = incl;
     __syncthreads();
     if (w == 0) {
-        int s = lane < (blockDim.x >> 5) ? sh[lane] : 0;
-        int si = s;
+        T s = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+        T si = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(FULLMASK, si, o);
+            T t = __shfl_up_sync(FULLMASK, si, o);
             if (lane >= o) si += t;
         }
         sh[lane] = si - s;
         if (lane == 31) sh[32] = si;
     }
     __syncthreads();
-    int r = incl - v + sh[w];
+    T r = incl - v + sh[w];
     *total = sh[32];
     __syncthreads();
     return r;
@@ -98,4 +99,45 @@ void rt_scan_exclusive(rt_ctx *c, const int *in, int *out, long long n, const in
     if (!tmp) tmp = c->scan_tmp;
     k_scan_sum<<<SCAN_NB, SCAN_BLOCK, 0, st>>>(in, n, d_len, tmp);
     k_scan_fin<<<SCAN_NB, SCAN_BLOCK, 0, st>>>(in, out, n, d_len, tmp, d_total);
+}
+
+// The same scan into 64-bit offsets (the per-cell candidate lists, whose total can pass 2^31):
+// counts are int32, sums and offsets int64; no device-side length.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan64_sum(const int *in, long long n,
+                                                           long long *btot) {
+    __shared__ long long sh[33];
+    long long b0, b1;
+    scan_range(n, b0, b1);
+    long long v = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += SCAN_BLOCK) v += in[i];
+    long long tot;
+    block_excl_scan(v, sh, &tot);
+    if (threadIdx.x == 0) btot[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan64_fin(const int *in, long long *out,
+                                                           long long n, const long long *btot) {
+    __shared__ long long sh[33];
+    long long b0, b1;
+    scan_range(n, b0, b1);
+    long long before = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCAN_BLOCK) before += btot[k];
+    long long tb;
+    block_excl_scan(before, sh, &tb);
+    long long carry = tb;
+    for (long long base = b0; base < b1; base += SCAN_BLOCK) {
+        long long i = base + threadIdx.x;
+        long long v = i < b1 ? (long long)in[i] : 0;
+        long long tot;
+        long long r = block_excl_scan(v, sh, &tot);
+        if (i < b1) out[i] = carry + r;
+        carry += tot;
+    }
+}
+
+// tmp: SCAN_NB 64-bit block totals (device)
+void rt_scan_exclusive64(const int *in, long long *out, long long n, long long *tmp,
+                         cudaStream_t st) {
+    k_scan64_sum<<<SCAN_NB, SCAN_BLOCK, 0, st>>>(in, n, tmp);
+    k_scan64_fin<<<SCAN_NB, SCAN_BLOCK, 0, st>>>(in, out, n, tmp);
 }

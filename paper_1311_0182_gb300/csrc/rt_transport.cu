@@ -787,7 +787,6 @@ template <typename Real, int NRC, bool BAR, bool SH, int IB>
 __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
                                                  const int *lens, unsigned long long *esc_r,
                                                  unsigned char *vstat) {
-    __shared__ int sdelta[8][32];   // kNN batch bookkeeping, one row per warp
     int lane = threadIdx.x & 31;
     long long nreq = lens[2];
     if (nreq > P.F_cap) nreq = P.F_cap;
@@ -795,9 +794,10 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     Slots<Real> S(P, cur);
     uint2 key = philox_key(P.seed, 3u);
     // Latency: the next request's code is loaded one request ahead; per-box and per-frequency
-    // values and the sender's neighbour positions are loaded before the position draws; the
-    // four per-neighbour inputs of the interpolation and deposit are gathered together; the
-    // values returned by the deposit atomics are checked one request later.
+    // values are loaded before the position draws; the kNN search loads each batch of its
+    // cell's candidates before merging the previous one; the four per-neighbour inputs of the
+    // interpolation and deposit are gathered together; the values returned by the deposit
+    // atomics are checked one request later.
     // Each block takes one contiguous chunk of the requests, and its warps pull requests from
     // the chunk through a shared counter, one ahead: the warps of a block finish together
     // (request costs vary), and blocks still retire one by one, which lets the receiver side
@@ -825,7 +825,6 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
         Real N, d0, d1, d2, clk, eps;
         unsigned long long fid;
         Real sg = Real(0);          // shared bin: the packet's mean cross-section (sunit)
-        const int *snb;             // the sender's neighbour list (bounds the kNN search)
         if (!(code & RT_FREE_BIT)) {
             long long i = (unsigned)code / (unsigned)P.S;   // slot codes < 2^31
             int s = (int)((unsigned)code % (unsigned)P.S);
@@ -839,7 +838,6 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             eps = S.E[code] / N;
             if (SH && nu == 0) sg = ((Real *)P.slG[cur])[i * NRC + s] / N;
             fid = gid_of(P, i, box) * P.S + (code - (unsigned long long)i * P.S) + 1ull;
-            snb = P.nbr + i * P.kn;
         } else {
             long long f = (long long)(code & ~RT_FREE_BIT);
             box = Fi.box[f]; qx = Fi.qx[f]; qy = Fi.qy[f]; qz = Fi.qz[f];
@@ -851,16 +849,10 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             nu = Fi.nu[f];
             if (SH && nu == 0) sg = ((Real *)Fi.sig)[f];
             fid = Fi.fid[f];
-            snb = Fi.nbr + f * P.kn;
         }
         long long boff = P.box_off[box];
         bool sgs = SH && nu == 0;
         Real sig = sgs ? sg * (Real)P.sunit : sigma_of<Real>(P, nu), bu = box_unit<Real>(P, box);
-        int sqx = 0, sqy = 0, sqz = 0;
-        if (lane < P.kn) {
-            int q = snb[lane];
-            sqx = P.qx[q]; sqy = P.qy[q]; sqz = P.qz[q];
-        }
         // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
         long long H = isqrt64(h2);   // = floor(sqrt(h2)) exactly (h2 < 3 * 2^40)
         unsigned span = (unsigned)(2 * H + 1);   // < 2^22
@@ -906,25 +898,13 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
             }
             continue;
         }
-        // the sender's kn neighbours are kn points of the box: the farthest of them from the
-        // virtual particle bounds its kn-th neighbour distance
         bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
-        long long sb2 = 0;
-        if (lane < P.kn) {
-            long long ex = sqx - vx, ey = sqy - vy, ez = sqz - vz;
-            sb2 = ex * ex + ey * ey + ez * ez;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            long long t = __shfl_xor_sync(FULLMASK, sb2, o);
-            sb2 = t > sb2 ? t : sb2;
-        }
+        // exact kNN from the candidate list of the virtual particle's cell
         long long kd2;
         int kidx;
-        BoxGrid g;
-        g.G = P.grid.G[box]; g.cs = P.grid.cs[box]; g.coff = P.grid.coff[box];
-        g.start = P.grid.start; g.items = P.grid.items; g.tab = P.grid.tab;
-        if (!warp_knn<IB>(g, vx, vy, vz, -1, P.kn, kd2, kidx, sdelta[threadIdx.x >> 5], sb2)) {
+        CandQuery Q = cand_query(P.grid, box, vx, vy, vz);
+        if (!cand_knn<IB>(Q.items, P.grid.cand, Q.a, Q.e, vx, vy, vz, Q.rq_up, Q.w, P.kn, kd2,
+                          kidx)) {
             // a k-th neighbour beyond the key range: reported; indices kept inside the box
             bad_knn = true;
             long long nbx = P.box_off[box + 1] - boff;

@@ -25,7 +25,7 @@ SYMBOLS = ["rt_create", "rt_destroy", "rt_set_particles", "rt_set_sources", "rt_
            "rt_get_deposits", "rt_get_stats", "rt_axis_set", "rt_set_profiling",
            "rt_get_profile", "rt_last_error", "rt_set_source_options", "rt_set_barrier",
            "rt_set_graph", "rt_get_shared_sigma", "rt_set_shared_sigma", "rt_save_state",
-           "rt_set_identities",
+           "rt_set_identities", "rt_query_neighbours",
            "rt_load_state"]
 
 
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
     L.rt_set_profiling.argtypes = [vp, i]
     L.rt_set_graph.argtypes = [vp, i]
     L.rt_set_identities.argtypes = [vp, vp, vp]
+    L.rt_query_neighbours.argtypes = [vp, i, ll, vp, vp, vp, i, vp]
     L.rt_get_profile.argtypes = [vp, vp, i, vp, vp, vp, vp]
     L.rt_last_error.argtypes = [vp]
     L.rt_last_error.restype = C.c_char_p
@@ -312,6 +313,18 @@ class Context:
                     "rt_get_quantised")
         return q
 
+    def query_neighbours(self, box: int, q):
+        """The exact n_ngb nearest particles (global indices) and their squared quantised
+        distances for quantised points q [m, 3] of box `box`, by the virtual particles' search."""
+        k = self.params["n_ngb"]
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.int32).reshape(-1, 3))
+        nbr = np.zeros((len(q), k), np.int32)
+        d2 = np.zeros((len(q), k), np.int64)
+        self._check(self.L.rt_query_neighbours(self.h, box, len(q), q.ctypes.data,
+                                               nbr.ctypes.data, d2.ctypes.data, RT_HOST,
+                                               self._s()), "rt_query_neighbours")
+        return nbr, d2
+
     def rotations(self):
         R = np.zeros((self.n, 9))
         Rs = np.zeros((max(self.ns * self.K, 1), 9))
@@ -424,7 +437,7 @@ class Context:
         keys = ["hops", "virtual", "escaped_virtual", "subcycles", "floor_hits", "peak_free",
                 "peak_active", "gas_contrib", "senders", "moving_packets", "staged_contrib",
                 "receiver_groups", "receiver_outputs", "cell_occupancy", "grid_send",
-                "grid_virtual", "grid_receive"]
+                "grid_virtual", "grid_receive", "candidate_entries"]
         return dict(zip(keys, list(out)))
 
 

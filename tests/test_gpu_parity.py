@@ -106,6 +106,65 @@ def test_quantisation_and_neighbours_bit_exact(name):
         assert np.array_equal(a, b)
 
 
+def _lattice_box(n_side=12):
+    """One box of particles on a cubic lattice: many exactly equal distances."""
+    L = W.KPC
+    g = (np.arange(n_side) + 0.5) * L / n_side
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    n = len(pos)
+    params = W.default_params(seed=5, dt=0.05 * W.MYR, dt_em=0.05 * W.MYR)
+    return W._pack(params, [L], [0, n], pos, np.full(n, 1e-3), np.full(n, 1e-3 * L ** 3 / n),
+                   np.full(n, 0.3), np.full(n, 1e4), [0], np.array([[0.5 * L] * 3]),
+                   np.full((1, 1), 1e48), [6.3e-18], [0.0])
+
+
+@pytest.mark.parametrize("name,occ", [("cfg2_small", 0), ("cfg2_small", 1), ("cfg2_small", 6),
+                                      ("lattice", 0), ("lattice", 2), ("clustered", 0),
+                                      ("clustered", 1)])
+def test_virtual_particle_search_against_brute_force(name, occ):
+    """The virtual particles' exact kNN from the per-cell candidate lists (Sec. 2.1: a virtual
+    particle's neighbours are the n_ngb particles nearest to it) equals a brute-force search,
+    ties to the lower index, for points like virtual particles (within a smoothing length of a
+    particle), points on particles, cell corners and the edges and corners of the box, on
+    uniform, lattice (exact ties) and clustered boxes with duplicate positions, at several
+    grid occupancies."""
+    from paper_1311_0182_gb300 import rt
+    wl = {"cfg2_small": lambda: W.cfg2(n_side=20), "lattice": _lattice_box,
+          "clustered": _clustered_boxes}[name]()
+    g = rt.context_for(dict(wl, params=dict(wl["params"], cell_occupancy=occ)))
+    q = g.quantised()
+    nbr, h2 = g.neighbours()[:2]
+    k = wl["params"]["n_ngb"]
+    rng = np.random.default_rng(3)
+    off = wl["box_off"]
+    Q = 1 << 20
+    for b in range(len(off) - 1):
+        lo, hi = int(off[b]), int(off[b + 1])
+        qb = q[lo:hi]
+        m = 200
+        pi = rng.integers(0, hi - lo, m)
+        d = rng.normal(size=(m, 3))
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        r = np.sqrt(h2[lo + pi]) * rng.uniform(0, 1, m) ** (1 / 3)
+        pts = [np.clip(np.rint(qb[pi] + d * r[:, None]), 0, Q - 1).astype(np.int64),
+               qb[rng.integers(0, hi - lo, 20)],
+               np.array([[x, y, z] for x in (0, Q - 1) for y in (0, Q - 1) for z in (0, Q - 1)]),
+               np.stack([rng.integers(0, Q, 20), np.zeros(20, np.int64),
+                         np.full(20, Q - 1)], 1),
+               (rng.integers(0, 8, (20, 3)) * (Q // 8)).astype(np.int64)]
+        pts = np.concatenate(pts)
+        got, gd2 = g.query_neighbours(b, pts)
+        idx = np.arange(lo, hi)
+        for p, nb, dd in zip(pts, got, gd2):
+            d2 = ((qb - p) ** 2).sum(1)
+            order = np.lexsort((idx, d2))[:k]
+            assert np.array_equal(nb, idx[order]), (name, occ, b, p)
+            assert np.array_equal(dd, d2[order])
+    with pytest.raises(rt.RTError):
+        g.query_neighbours(0, np.array([[0, 0, Q]]))
+    g.close()
+
+
 def test_neighbours_full_size_sampled():
     """The timed 64^3 workload: sampled particles against a brute-force search."""
     wl = W.cfg2()
@@ -614,10 +673,10 @@ def _same_results(a, b):
     assert np.array_equal(a.budget(), b.budget())
     for x, y in zip(a.deposits(), b.deposits()):
         assert np.array_equal(x, y)
-    # (the kNN grid occupancy and the launch sizes are chosen by timing and may differ; results
-    # do not depend on them)
+    # (the kNN grid occupancy, with the size of its candidate lists, and the launch sizes are
+    # chosen by timing and may differ; results do not depend on them)
     sta, stb = a.stats(), b.stats()
-    for k in ("cell_occupancy", "grid_send", "grid_virtual", "grid_receive"):
+    for k in ("cell_occupancy", "grid_send", "grid_virtual", "grid_receive", "candidate_entries"):
         sta.pop(k)
         stb.pop(k)
     assert sta == stb
@@ -840,16 +899,18 @@ def test_full_size_batched_and_clump_workloads_conserve_photons():
 
 
 def test_grid_occupancy_search_changes_nothing_but_time():
-    """The kNN grid occupancy is picked by timing the neighbour search (cell_occupancy 0); any
-    grid gives the same exact neighbours, and the steps agree bit for bit."""
+    """The kNN grid occupancy is picked by timing the virtual particles' search from the
+    per-cell candidate lists (cell_occupancy 0); any grid gives the same exact neighbours, and
+    the steps agree bit for bit."""
     from paper_1311_0182_gb300 import rt
     wl = W.cfg2(n_side=20)
     ctxs = {occ: rt.context_for(dict(wl, params=dict(wl["params"], cell_occupancy=occ)))
-            for occ in (0, 2, 5, 16)}
-    assert ctxs[0].stats()["cell_occupancy"] in (2, 3, 4, 5, 7, 9)
+            for occ in (0, 1, 2, 5, 16)}
+    assert ctxs[0].stats()["cell_occupancy"] in (1, 2, 3, 4, 6)
     assert ctxs[5].stats()["cell_occupancy"] == 5
+    assert all(g.stats()["candidate_entries"] > 0 for g in ctxs.values())
     ref = ctxs[5].neighbours()
-    for occ in (0, 2, 16):
+    for occ in (0, 1, 2, 16):
         for a, b in zip(ctxs[occ].neighbours(), ref):
             assert np.array_equal(a, b)
     for g in ctxs.values():
