@@ -23,7 +23,9 @@
 #define KNN_IB_LARGE 24        // index bits of a larger box (up to 2^24 particles)
 #define KNN_KEY_NONE 0xffffffffffffffffull
 // merge by insertion when at most this many candidates of a batch pass the k-th key
+#ifndef KNN_INSERT_MAX
 #define KNN_INSERT_MAX 16
+#endif
 
 // the largest d2 a key with IB index bits holds
 template <int IB> __device__ __forceinline__ long long knn_d2max() { return (1ll << (64 - IB)) - 2; }
@@ -340,8 +342,13 @@ __device__ inline bool warp_knn(const BoxGrid &g, int qx, int qy, int qz, int ex
 // current k-th distance, no later entry can enter the result, which is the exact kn nearest
 // either way.
 
-// ring width of a box's lists: an eighth of the cell side
-__device__ __forceinline__ int cand_ring_width(int cs) { return cs >= 16 ? cs >> 3 : 1; }
+// ring width of a box's lists: a sixteenth of the cell side
+#ifndef CAND_RING_SHIFT
+#define CAND_RING_SHIFT 4
+#endif
+__device__ __forceinline__ int cand_ring_width(int cs) {
+    return cs >= (1 << (CAND_RING_SHIFT + 1)) ? cs >> CAND_RING_SHIFT : 1;
+}
 
 // the centre point of the cell starting at lo (inside the quantised range)
 __device__ __forceinline__ int cand_centre(int lo, int cs) {

@@ -145,8 +145,14 @@ void rt_upload_axes() {
 }
 
 // Resident 256-thread blocks per SM asked of the hop kernels: four (64 registers a thread)
-// for FP32 packets; three for FP64, whose wider values would otherwise spill.
+// for FP32 packets; three for FP64, whose wider values would otherwise spill.  The virtual
+// particles take five with FP32 packets (48 registers, some spilled): the extra warps hide
+// more latency than the spills cost (measured on the 64^3 step graph).
 #define HOP_MINB(Real) (sizeof(Real) == 4 ? 4 : 3)
+#ifndef VIRT_MINB_F32
+#define VIRT_MINB_F32 5
+#endif
+#define VIRT_MINB(Real) (sizeof(Real) == 4 ? VIRT_MINB_F32 : 3)
 // Largest grids (blocks) of the sender side, the virtual particles and the receiver side;
 // each block takes a contiguous chunk of the live items.  Set by a measured sweep on the 64^3
 // HII-region step: fewer, longer-lived blocks than one per 32 items, while still several
@@ -776,6 +782,19 @@ __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long l
     Dz = __float2int_rn(__fmul_rn(d2, fh));
 }
 
+// A virtual-particle request decoded: the packet, its sender's position and smoothing length,
+// and the per-box and per-frequency values the request needs.
+template <typename Real> struct VDec {
+    long long h2, boff;
+    unsigned long long fid;
+    Real N, d0, d1, d2, clk, eps, sg, sig, bu;
+    int box, qx, qy, qz, nu, H;
+};
+// requests a warp takes together: one lane decodes each, into shared memory
+#ifndef VREQ_GROUP
+#define VREQ_GROUP 4
+#endif
+
 // Virtual particles (Sec. 2.1): one warp per request.
 // BAR: some box has a barrier (a separate instance keeps the test out of the common case);
 // SH: the shared frequency bin (likewise); IB: index bits of the kNN keys (24 when a box holds
@@ -784,7 +803,7 @@ __device__ __forceinline__ void axis_offset(float d0, float d1, float d2, long l
 // pointers are re-read from the parameter space instead of being held in registers); the
 // step and hop of the random draws are read from the device counters where they are used.
 template <typename Real, int NRC, bool BAR, bool SH, int IB>
-__global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
+__global__ void __launch_bounds__(256, VIRT_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
                                                  const int *lens, unsigned long long *esc_r,
                                                  unsigned char *vstat) {
     int lane = threadIdx.x & 31;
@@ -793,189 +812,204 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_virtual(DevPtrs P, int 
     FreeBuf Fi = P.fr[fcur], Fo = P.fr[fcur ^ 1];
     Slots<Real> S(P, cur);
     uint2 key = philox_key(P.seed, 3u);
-    // Latency: the next request's code is loaded one request ahead; per-box and per-frequency
-    // values are loaded before the position draws; the kNN search loads each batch of its
-    // cell's candidates before merging the previous one; the four per-neighbour inputs of the
-    // interpolation and deposit are gathered together; the values returned by the deposit
-    // atomics are checked one request later.
-    // Each block takes one contiguous chunk of the requests, and its warps pull requests from
-    // the chunk through a shared counter, one ahead: the warps of a block finish together
-    // (request costs vary), and blocks still retire one by one, which lets the receiver side
-    // on the other stream in.  Results do not depend on which warp takes a request.
+    // A warp takes VREQ_GROUP consecutive requests at a time; lane v decodes request v of the
+    // group (slot or free packet, direction, clock, identity, per-box and per-frequency values)
+    // into shared memory, so that the group's loads and divisions run side by side instead of
+    // once per request on every lane.  Then the warp serves the requests one after the other.
+    // Latency: the kNN search loads each batch of its cell's candidates before merging the
+    // previous one; the four per-neighbour inputs of the interpolation and deposit are gathered
+    // together; the values returned by the deposit atomics are checked one request later.
+    // Each block takes one contiguous chunk of the requests, and its warps pull groups from the
+    // chunk through a shared counter: the warps of a block finish close together (request costs
+    // vary), and blocks still retire one by one, which lets the receiver side on the other
+    // stream in.  Results do not depend on which warp takes a request.
+    __shared__ VDec<Real> sdec[8][VREQ_GROUP];
     __shared__ int snext;
+    VDec<Real> *mine = sdec[threadIdx.x >> 5];
     long long chunk = (nreq + gridDim.x - 1) / gridDim.x;
     long long rb0 = (long long)blockIdx.x * chunk;
     long long rb1 = rb0 + chunk < nreq ? rb0 + chunk : nreq;
     if (threadIdx.x == 0) snext = 0;
     __syncthreads();
-    long long r_first = 0;
-    if (lane == 0) r_first = rb0 + atomicAdd(&snext, 1);
-    r_first = __shfl_sync(FULLMASK, r_first, 0);
-    unsigned long long code_next = r_first < rb1 ? P.req[r_first] : 0ull;
+    const float cf = 1.0f - 2.0f / (float)P.ntc;
     unsigned long long pend_a = 0ull, pend_e = 0ull;   // words before this lane's last adds
     bool bad = false, bad_knn = false;
-    for (long long r = r_first, rn; r < rb1; r = rn) {
-        unsigned long long code = code_next;
-        rn = 0;
-        if (lane == 0) rn = rb0 + atomicAdd(&snext, 1);
-        rn = __shfl_sync(FULLMASK, rn, 0);
-        if (rn < rb1) code_next = P.req[rn];
-        int box, qx, qy, qz, nu;
-        long long h2;
-        Real N, d0, d1, d2, clk, eps;
-        unsigned long long fid;
-        Real sg = Real(0);          // shared bin: the packet's mean cross-section (sunit)
-        if (!(code & RT_FREE_BIT)) {
-            long long i = (unsigned)code / (unsigned)P.S;   // slot codes < 2^31
-            int s = (int)((unsigned)code % (unsigned)P.S);
-            nu = s / NRC;
-            box = P.pbox[i];
-            qx = P.qx[i]; qy = P.qy[i]; qz = P.qz[i];
-            h2 = P.h2[i];
-            N = S.N[code];
-            packet_dir(S.X[code], S.Y[code], S.Z[code], d0, d1, d2);
-            clk = S.C[code] / N;
-            eps = S.E[code] / N;
-            if (SH && nu == 0) sg = ((Real *)P.slG[cur])[i * NRC + s] / N;
-            fid = gid_of(P, i, box) * P.S + (code - (unsigned long long)i * P.S) + 1ull;
-        } else {
-            long long f = (long long)(code & ~RT_FREE_BIT);
-            box = Fi.box[f]; qx = Fi.qx[f]; qy = Fi.qy[f]; qz = Fi.qz[f];
-            h2 = Fi.h2[f];
-            N = ((Real *)Fi.N)[f];
-            d0 = ((Real *)Fi.dx)[f]; d1 = ((Real *)Fi.dy)[f]; d2 = ((Real *)Fi.dz)[f];
-            clk = ((Real *)Fi.clock)[f];
-            eps = ((Real *)Fi.eps)[f];
-            nu = Fi.nu[f];
-            if (SH && nu == 0) sg = ((Real *)Fi.sig)[f];
-            fid = Fi.fid[f];
-        }
-        long long boff = P.box_off[box];
-        bool sgs = SH && nu == 0;
-        Real sig = sgs ? sg * (Real)P.sunit : sigma_of<Real>(P, nu), bu = box_unit<Real>(P, box);
-        // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
-        long long H = isqrt64(h2);   // = floor(sqrt(h2)) exactly (h2 < 3 * 2^40)
-        unsigned span = (unsigned)(2 * H + 1);   // < 2^22
-        float cf = 1.0f - 2.0f / (float)P.ntc;
-        int Dx = 0, Dy = 0, Dz = 0;   // |D| <= H < 2^21
-        bool found = false;
-        for (int a0 = 0; a0 < 64 && !found; a0 += 32) {
-            unsigned a = (unsigned)(a0 + lane);
-            // counter: (step, hop << 8 | draw, packet id); step and hop from the device counters
-            uint4 u = philox4x32_10(make_uint4(cnt_word(P, CNT_STEP), (cnt_word(P, CNT_HOP) << 8) | a,
-                                               (unsigned)fid, (unsigned)(fid >> 32)), key);
-            // floor(u * span / 2^32) - H, |e| <= H < 2^21: 32-bit integers (a 64-bit integer to
-            // float conversion would run on the FP64 pipe)
-            int ix = (int)__umulhi(u.x, span) - (int)H;
-            int iy = (int)__umulhi(u.y, span) - (int)H;
-            int iz = (int)__umulhi(u.z, span) - (int)H;
-            long long ex = ix, ey = iy, ez = iz;
-            long long r2 = ex * ex + ey * ey + ez * ez;
-            bool ok = r2 > 0 && r2 <= h2 &&
-                      cone_test<Real>(ix, iy, iz, (float)ix, (float)iy, (float)iz, d0, d1, d2, cf,
-                                      P.ntc);
-            unsigned m = __ballot_sync(FULLMASK, ok);
-            if (m) {
-                int src = __ffs(m) - 1;
-                Dx = __shfl_sync(FULLMASK, ix, src);
-                Dy = __shfl_sync(FULLMASK, iy, src);
-                Dz = __shfl_sync(FULLMASK, iz, src);
-                found = true;
+    for (;;) {
+        long long g0 = 0;
+        if (lane == 0) g0 = rb0 + atomicAdd(&snext, VREQ_GROUP);
+        g0 = __shfl_sync(FULLMASK, g0, 0);
+        if (g0 >= rb1) break;
+        const int gn = (int)(rb1 - g0 < VREQ_GROUP ? rb1 - g0 : VREQ_GROUP);
+        if (lane < gn) {
+            unsigned long long code = P.req[g0 + lane];
+            VDec<Real> D;
+            D.sg = Real(0);          // shared bin: the packet's mean cross-section (sunit)
+            if (!(code & RT_FREE_BIT)) {
+                long long i = (unsigned)code / (unsigned)P.S;   // slot codes < 2^31
+                int s = (int)((unsigned)code % (unsigned)P.S);
+                D.nu = s / NRC;
+                D.box = P.pbox[i];
+                D.qx = P.qx[i]; D.qy = P.qy[i]; D.qz = P.qz[i];
+                D.h2 = P.h2[i];
+                D.N = S.N[code];
+                packet_dir(S.X[code], S.Y[code], S.Z[code], D.d0, D.d1, D.d2);
+                D.clk = S.C[code] / D.N;
+                D.eps = S.E[code] / D.N;
+                if (SH && D.nu == 0) D.sg = ((Real *)P.slG[cur])[i * NRC + s] / D.N;
+                D.fid = gid_of(P, i, D.box) * P.S + (code - (unsigned long long)i * P.S) + 1ull;
+            } else {
+                long long f = (long long)(code & ~RT_FREE_BIT);
+                D.box = Fi.box[f]; D.qx = Fi.qx[f]; D.qy = Fi.qy[f]; D.qz = Fi.qz[f];
+                D.h2 = Fi.h2[f];
+                D.N = ((Real *)Fi.N)[f];
+                D.d0 = ((Real *)Fi.dx)[f]; D.d1 = ((Real *)Fi.dy)[f]; D.d2 = ((Real *)Fi.dz)[f];
+                D.clk = ((Real *)Fi.clock)[f];
+                D.eps = ((Real *)Fi.eps)[f];
+                D.nu = Fi.nu[f];
+                if (SH && D.nu == 0) D.sg = ((Real *)Fi.sig)[f];
+                D.fid = Fi.fid[f];
             }
+            D.boff = P.box_off[D.box];
+            D.sig = (SH && D.nu == 0) ? D.sg * (Real)P.sunit : sigma_of<Real>(P, D.nu);
+            D.bu = box_unit<Real>(P, D.box);
+            D.H = (int)isqrt64(D.h2);   // = floor(sqrt(h2)) exactly (h2 < 3 * 2^40), < 2^21
+            mine[lane] = D;
         }
-        if (!found) axis_offset(d0, d1, d2, H, Dx, Dy, Dz);
-        int vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
-        // outside the box: the photons escape (vstat 1); on a path through the barrier they
-        // are removed, counted with the escapes (vstat 3)
-        int gone = (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) ? 1
-                 : (BAR && barrier_crosses_call(P.bar[box], qx, qy, qz, vx, vy, vz)) ? 3 : 0;
-        if (gone) {
-            if (lane == 0) {
-                esc_r[r] = esc_fixed(N, P, box);
-                vstat[r] = (unsigned char)gone;
-                Fo.box[r] = box;
-                ((Real *)Fo.N)[r] = Real(0);
+        __syncwarp();
+        for (int v = 0; v < gn; ++v) {
+            const long long r = g0 + v;
+            const int box = mine[v].box, qx = mine[v].qx, qy = mine[v].qy, qz = mine[v].qz,
+                      nu = mine[v].nu;
+            const long long h2 = mine[v].h2, boff = mine[v].boff;
+            const Real N = mine[v].N, d0 = mine[v].d0, d1 = mine[v].d1, d2 = mine[v].d2,
+                       clk = mine[v].clk, eps = mine[v].eps, sg = mine[v].sg, sig = mine[v].sig,
+                       bu = mine[v].bu;
+            const unsigned long long fid = mine[v].fid;
+            const bool sgs = SH && nu == 0;
+            // position: first accepted of 64 counter-based draws in [-H, H]^3, else on the axis
+            const long long H = mine[v].H;
+            unsigned span = (unsigned)(2 * H + 1);   // < 2^22
+            int Dx = 0, Dy = 0, Dz = 0;   // |D| <= H < 2^21
+            bool found = false;
+            for (int a0 = 0; a0 < 64 && !found; a0 += 32) {
+                unsigned a = (unsigned)(a0 + lane);
+                // counter: (step, hop << 8 | draw, packet id); step and hop from the device counters
+                uint4 u = philox4x32_10(make_uint4(cnt_word(P, CNT_STEP), (cnt_word(P, CNT_HOP) << 8) | a,
+                                                   (unsigned)fid, (unsigned)(fid >> 32)), key);
+                // floor(u * span / 2^32) - H, |e| <= H < 2^21: 32-bit integers (a 64-bit integer to
+                // float conversion would run on the FP64 pipe)
+                int ix = (int)__umulhi(u.x, span) - (int)H;
+                int iy = (int)__umulhi(u.y, span) - (int)H;
+                int iz = (int)__umulhi(u.z, span) - (int)H;
+                long long ex = ix, ey = iy, ez = iz;
+                long long r2 = ex * ex + ey * ey + ez * ez;
+                bool ok = r2 > 0 && r2 <= h2 &&
+                          cone_test<Real>(ix, iy, iz, (float)ix, (float)iy, (float)iz, d0, d1, d2, cf,
+                                          P.ntc);
+                unsigned m = __ballot_sync(FULLMASK, ok);
+                if (m) {
+                    int src = __ffs(m) - 1;
+                    Dx = __shfl_sync(FULLMASK, ix, src);
+                    Dy = __shfl_sync(FULLMASK, iy, src);
+                    Dz = __shfl_sync(FULLMASK, iz, src);
+                    found = true;
+                }
             }
-            continue;
-        }
-        bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
-        // exact kNN from the candidate list of the virtual particle's cell
-        long long kd2;
-        int kidx;
-        CandQuery Q = cand_query(P.grid, box, vx, vy, vz);
-        if (!cand_knn<IB>(Q.items, P.grid.cand, Q.a, Q.e, vx, vy, vz, Q.rq_up, Q.w, P.kn, kd2,
-                          kidx)) {
-            // a k-th neighbour beyond the key range: reported; indices kept inside the box
-            bad_knn = true;
-            long long nbx = P.box_off[box + 1] - boff;
-            if (kidx < 0 || kidx >= nbx) { kidx = 0; kd2 = 0; }
-        }
-        long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
-        bool valid = lane < P.kn;
-        long long j = valid ? boff + kidx : 0;
-        Real om = Real(0), nhj = Real(0), Vj = Real(0), dsj = Real(0), dej = Real(0);
-        if (valid) {
-            Vj = ((Real *)P.Vr)[j];
-            nhj = ((Real *)P.nHIr)[j];
-            dsj = ((Real *)P.dep_s)[j];
-            dej = ((Real *)P.depE_s)[j];
-            Real q = h2v > 0 ? rt_sqrt<Real>(to_real<Real>(kd2) / to_real<Real>(h2v)) : Real(0);
-            om = Vj * kernel_w<Real>(q);
-        }
-        Real sw = om;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULLMASK, sw, o);
-        if (!(sw > Real(0))) {
-            om = Vj;
-            sw = om;
-#pragma unroll
+            if (!found) axis_offset(d0, d1, d2, H, Dx, Dy, Dz);
+            int vx = qx + Dx, vy = qy + Dy, vz = qz + Dz;
+            // outside the box: the photons escape (vstat 1); on a path through the barrier they
+            // are removed, counted with the escapes (vstat 3)
+            int gone = (vx < 0 || vy < 0 || vz < 0 || vx >= RT_Q || vy >= RT_Q || vz >= RT_Q) ? 1
+                     : (BAR && barrier_crosses_call(P.bar[box], qx, qy, qz, vx, vy, vz)) ? 3 : 0;
+            if (gone) {
+                if (lane == 0) {
+                    esc_r[r] = esc_fixed(N, P, box);
+                    vstat[r] = (unsigned char)gone;
+                    Fo.box[r] = box;
+                    ((Real *)Fo.N)[r] = Real(0);
+                }
+                continue;
+            }
+            bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
+            // exact kNN from the candidate list of the virtual particle's cell
+            long long kd2;
+            int kidx;
+            CandQuery Q = cand_query(P.grid, box, vx, vy, vz);
+            if (!cand_knn<IB>(Q.items, P.grid.cand, Q.a, Q.e, vx, vy, vz, Q.rq_up, Q.w, P.kn, kd2,
+                              kidx)) {
+                // a k-th neighbour beyond the key range: reported; indices kept inside the box
+                bad_knn = true;
+                long long nbx = P.box_off[box + 1] - boff;
+                if (kidx < 0 || kidx >= nbx) { kidx = 0; kd2 = 0; }
+            }
+            long long h2v = __shfl_sync(FULLMASK, kd2, P.kn - 1);
+            bool valid = lane < P.kn;
+            long long j = valid ? boff + kidx : 0;
+            Real om = Real(0), nhj = Real(0), Vj = Real(0), dsj = Real(0), dej = Real(0);
+            if (valid) {
+                Vj = ((Real *)P.Vr)[j];
+                nhj = ((Real *)P.nHIr)[j];
+                dsj = ((Real *)P.dep_s)[j];
+                dej = ((Real *)P.depE_s)[j];
+                Real q = h2v > 0 ? rt_sqrt<Real>(to_real<Real>(kd2) / to_real<Real>(h2v)) : Real(0);
+                om = Vj * kernel_w<Real>(q);
+            }
+            Real sw = om;
+    #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULLMASK, sw, o);
-        }
-        Real wn = om * nhj;
-        Real swn = wn;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) swn += __shfl_xor_sync(FULLMASK, swn, o);
-        Real nHIv = swn / sw;
-        Real t = (Real)Dx * d0 + (Real)Dy * d1 + (Real)Dz * d2;
-        Real l = t * bu;
-        Real tau = (sig * nHIv) * l;
-        Real A, T;
-        split_absorbed<Real>(N, tau, A, T);
-        if (valid && swn > Real(0) && wn > Real(0)) {
-            Real Ak = A * (wn / swn);
-            long long key2 = j * P.nf + nu;
-            // two fixed-point words: units of 2^-40 N_HI and 2^-72 N_HI (integer sums do not
-            // depend on their order)
-            Real fa = Ak * dsj;
-            Real fe = Ak * eps * dej;
-            pend_a = 0ull;
-            pend_e = 0ull;
-            if (fa > Real(0)) {
-                unsigned long long qh = 0, ql = 0;
-                bad |= !fx_split(fa, qh, ql);
-                if (qh) pend_a = atomicAdd(&P.fx_abs[key2], qh);
-                if (ql) atomicAdd(&P.fx_lo[key2], ql);
+            if (!(sw > Real(0))) {
+                om = Vj;
+                sw = om;
+    #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(FULLMASK, sw, o);
             }
-            if (fe > Real(0)) {
-                bad |= fe > Real(4.0e18);
-                pend_e = atomicAdd(&P.fx_E[key2], to_fixed(fe));
+            Real wn = om * nhj;
+            Real swn = wn;
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) swn += __shfl_xor_sync(FULLMASK, swn, o);
+            Real nHIv = swn / sw;
+            Real t = (Real)Dx * d0 + (Real)Dy * d1 + (Real)Dz * d2;
+            Real l = t * bu;
+            Real tau = (sig * nHIv) * l;
+            Real A, T;
+            split_absorbed<Real>(N, tau, A, T);
+            if (valid && swn > Real(0) && wn > Real(0)) {
+                Real Ak = A * (wn / swn);
+                long long key2 = j * P.nf + nu;
+                // two fixed-point words: units of 2^-40 N_HI and 2^-72 N_HI (integer sums do not
+                // depend on their order)
+                Real fa = Ak * dsj;
+                Real fe = Ak * eps * dej;
+                pend_a = 0ull;
+                pend_e = 0ull;
+                if (fa > Real(0)) {
+                    unsigned long long qh = 0, ql = 0;
+                    bad |= !fx_split(fa, qh, ql);
+                    if (qh) pend_a = atomicAdd(&P.fx_abs[key2], qh);
+                    if (ql) atomicAdd(&P.fx_lo[key2], ql);
+                }
+                if (fe > Real(0)) {
+                    bad |= fe > Real(4.0e18);
+                    pend_e = atomicAdd(&P.fx_E[key2], to_fixed(fe));
+                }
+            }
+            if (valid) Fo.nbr[r * P.kn + lane] = (int)j;
+            if (lane == 0) {
+                esc_r[r] = 0ull;
+                vstat[r] = T > Real(0) ? 0 : 2;
+                Fo.box[r] = box;
+                Fo.qx[r] = vx; Fo.qy[r] = vy; Fo.qz[r] = vz;
+                Fo.h2[r] = h2v;
+                ((Real *)Fo.N)[r] = T;
+                ((Real *)Fo.dx)[r] = d0; ((Real *)Fo.dy)[r] = d1; ((Real *)Fo.dz)[r] = d2;
+                ((Real *)Fo.clock)[r] = clk + l / (Real)C_LIGHT;
+                ((Real *)Fo.eps)[r] = eps;
+                if (sgs) ((Real *)Fo.sig)[r] = sg;
+                Fo.nu[r] = nu;
+                Fo.fid[r] = mix64(fid);
             }
         }
-        if (valid) Fo.nbr[r * P.kn + lane] = (int)j;
-        if (lane == 0) {
-            esc_r[r] = 0ull;
-            vstat[r] = T > Real(0) ? 0 : 2;
-            Fo.box[r] = box;
-            Fo.qx[r] = vx; Fo.qy[r] = vy; Fo.qz[r] = vz;
-            Fo.h2[r] = h2v;
-            ((Real *)Fo.N)[r] = T;
-            ((Real *)Fo.dx)[r] = d0; ((Real *)Fo.dy)[r] = d1; ((Real *)Fo.dz)[r] = d2;
-            ((Real *)Fo.clock)[r] = clk + l / (Real)C_LIGHT;
-            ((Real *)Fo.eps)[r] = eps;
-            if (sgs) ((Real *)Fo.sig)[r] = sg;
-            Fo.nu[r] = nu;
-            Fo.fid[r] = mix64(fid);
-        }
+        __syncwarp();   // the group's decoded requests are read before the next group's decode
     }
     bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
     if (bad) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
