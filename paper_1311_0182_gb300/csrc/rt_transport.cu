@@ -574,28 +574,18 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
             }
             int nb_chunk = min(32, total - cb);
             int my_cm = 0;
-            unsigned my_mask = 0u;
+            // the chunk's packets one after the other (lane = neighbour k): cone membership; the
+            // bitmap word of lane k collects, frequency by frequency, the bins whose cone holds
+            // k (a word continues across chunks while the frequency does); a cone with no member
+            // adds its bin to the empty-cone word of its frequency, held on lane nu
             for (int u = 0; u < nb_chunk; ++u) {
                 Real e0 = __shfl_sync(FULLMASK, d0, u), e1 = __shfl_sync(FULLMASK, d1, u),
                      e2 = __shfl_sync(FULLMASK, d2, u);
-                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, e0, e1, e2, cf, P.ntc);
-                unsigned m = __ballot_sync(FULLMASK, in);
-                if (lane == u) { my_mask = m; my_cm = __popc(m); }
-            }
-            ncon += (lane < nb_chunk) ? my_cm : 0;
-            if (has && my_cm > 0)
-                rec_store(P.rec, s, rdiv<Real>(N, (Real)my_cm), d0, d1, d2, rdiv<Real>(C, N),
-                          rdiv<Real>(E, N), sgs, sgr);
-            // empty cones of this chunk, folded into the per-frequency words
-            bool empty = has && my_cm == 0;
-            unsigned emb = __ballot_sync(FULLMASK, empty);
-            nreq += __popc(emb);
-            // bitmap words: lane k collects, frequency by frequency, the bins whose cone holds k
-            // (a word continues across chunks while the frequency does)
-            for (int u = 0; u < nb_chunk; ++u) {
                 int unu = __shfl_sync(FULLMASK, onu, u);
                 int ub = __shfl_sync(FULLMASK, ob, u);
-                unsigned um = __shfl_sync(FULLMASK, my_mask, u);
+                bool in = valid && cone_test<Real>(dx, dy, dz, fx, fy, fz, e0, e1, e2, cf, P.ntc);
+                unsigned m = __ballot_sync(FULLMASK, in);
+                if (lane == u) my_cm = __popc(m);
                 if (unu != cur_nu) {
                     if (valid && word) {
                         P.bm[(long long)cur_nu * nrev + rp] = word;
@@ -604,13 +594,14 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseA(DevPtrs P, int c
                     word = 0u;
                     cur_nu = unu;
                 }
-                if ((um >> lane) & 1u) word |= 1u << ub;
+                if (in) word |= 1u << ub;
+                if (m == 0u && lane == unu) emp_acc |= 1u << ub;
             }
-            // empty-cone bins per frequency, gathered on lane nu
-            for (int q = 0; q < P.nf; ++q) {
-                unsigned red = __reduce_or_sync(FULLMASK, (empty && onu == q) ? (1u << ob) : 0u);
-                if (lane == q) emp_acc |= red;
-            }
+            ncon += (lane < nb_chunk) ? my_cm : 0;
+            if (has && my_cm > 0)
+                rec_store(P.rec, s, rdiv<Real>(N, (Real)my_cm), d0, d1, d2, rdiv<Real>(C, N),
+                          rdiv<Real>(E, N), sgs, sgr);
+            nreq += __popc(__ballot_sync(FULLMASK, has && my_cm == 0));
         }
         // every word starts the hop at zero (the receiver side clears the words it reads), and
         // each (frequency, neighbour) word is written once: a plain store
