@@ -18,7 +18,8 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
  *    queued on it asynchronously unless noted.  A context is not thread-safe.
  *  - The library owns every internal buffer: rt_create allocates them on the current device
- *    and rt_destroy frees them.
+ *    (rt_build_neighbours adds the candidate lists of the neighbour search, whose size it
+ *    counts first) and rt_destroy frees them.
  *  - Every entry point returns an rt_status; nothing is thrown across the ABI.  After a
  *    non-OK status rt_last_error() holds a one-line description.  Device-side limits (hop
  *    cap, packet capacity, deposit range) set a sticky error word that rt_step/rt_transport
@@ -91,8 +92,9 @@ typedef struct {
     double eps_rr_fixed;  /* excess energy of recombination photons, erg; < 0: kT of emitter */
     double sigma_rec;     /* grey cross-section of the recombination photons, cm^2 */
     long long free_cap;   /* capacity of free packets per hop (0: library default) */
-    int cell_occupancy;   /* particles per cell of the kNN grids; 0: chosen by timing the
-                             neighbour search over 5, 7, 9, 12 and 16 in rt_build_neighbours */
+    int cell_occupancy;   /* particles per cell of the kNN grids; 0: chosen in
+                             rt_build_neighbours by timing the virtual particles' search over
+                             1, 2, 3, 4 and 6 */
     int tune_launch;      /* 1: the grid sizes of the three main hop kernels (sender side,
                              virtual particles, receiver side) are chosen by timing the first
                              steps of rt_step as whole step-graph launches: coordinate search
@@ -181,8 +183,12 @@ rt_status rt_set_barrier(rt_ctx *ctx, int box, int axis, const double *centre, d
 /* rt_build_neighbours -- exact n_ngb nearest neighbours of every particle and source within
    its box, ordered by (squared quantised distance, index); smoothing length h = distance of
    the n_ngb-th; and the receiver-sorted reverse lists (Sec. 2.1: packets search the
-   neighbours within the smoothing volume of the particle they are attached to).  Static
-   density fields: call once after rt_set_particles.  Errors: RT_ERR_KNN, RT_ERR_CUDA. */
+   neighbours within the smoothing volume of the particle they are attached to).  Also builds
+   the per-cell candidate lists the virtual particles' neighbour search takes: for each kNN
+   cell, every particle that can be among the n_ngb nearest of a point in the cell (about 100
+   to 200 four-byte entries per particle, allocated here).  Static density fields: call once
+   after rt_set_particles; a later call rebuilds everything.  Synchronises `stream`.  Errors:
+   RT_ERR_KNN, RT_ERR_CUDA (also when the candidate lists cannot be allocated). */
 rt_status rt_build_neighbours(rt_ctx *ctx, void *stream);
 
 /* rt_assign_cones -- the rotations of step `step` (reception cones of every particle, once
