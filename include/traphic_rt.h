@@ -339,7 +339,8 @@ rt_status rt_get_deposits(rt_ctx *ctx, double *abs_, double *absE, double *pass,
    by the receiver side; then the cell occupancy of the kNN grids in use; then the grid sizes
    (blocks) of the sender side, the virtual particles and the receiver side in use; then the
    entries of the per-cell candidate lists of the virtual particles' kNN (4 bytes each, built
-   by rt_build_neighbours); out[18..19] are 0 */
+   by rt_build_neighbours), and the cells without a list, deep in voids, whose queries take the
+   grid walk instead; out[19] is 0 */
 #define RT_NSTATS 20
 rt_status rt_get_stats(rt_ctx *ctx, long long *out);
 /* the isotropic cone direction set with n directions (8 or 32), [n * 3] host */

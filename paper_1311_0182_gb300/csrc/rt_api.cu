@@ -1366,6 +1366,7 @@ extern "C" rt_status rt_get_stats(rt_ctx *c, long long *out) {
     out[13] = c->cell_occ;
     rt_launch_grids(c, out + 14);
     out[17] = c->cand_entries;
+    out[18] = c->cand_fallback;
     return RT_OK;
 }
 

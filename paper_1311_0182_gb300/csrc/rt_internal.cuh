@@ -263,6 +263,7 @@ struct rt_ctx {
     long long grid_cap = 0;        // cells allocated (the finest grid that can be chosen)
     bool grid_tuned = false;       // occupancy chosen (or fixed by the configuration)
     long long cand_entries = 0;    // entries of the candidate lists in use
+    long long cand_fallback = 0;   // cells without a list (their queries take the grid walk)
     long long *cnt_h = nullptr;   // pinned
     std::vector<void *> allocs;
     bool have_particles = false, have_sources = false, built = false;

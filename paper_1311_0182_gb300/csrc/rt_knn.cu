@@ -190,9 +190,12 @@ __global__ void k_rev_sort(DevPtrs P) {
 
 // Timing probe of the occupancy search: the kNN search of virtual-particle-like points, one
 // per fourth particle, up to 0.44 smoothing lengths from it in a hashed direction, from the
-// candidate list of its cell like the virtual particles' search.  Writes one word no one reads,
+// candidate list of its cell (or the grid walk where it has none) like the virtual particles'
+// search.  Writes one word no one reads,
 // so that the search is not dropped.
+template <bool FB>
 __global__ void __launch_bounds__(256) k_knn_probe(DevPtrs P, unsigned long long *sink) {
+    __shared__ int sdelta[FB ? 8 : 1][32];
     int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -210,15 +213,22 @@ __global__ void __launch_bounds__(256) k_knn_probe(DevPtrs P, unsigned long long
         int qx = min(max(P.qx[i] + o[0], 0), RT_Q - 1);
         int qy = min(max(P.qy[i] + o[1], 0), RT_Q - 1);
         int qz = min(max(P.qz[i] + o[2], 0), RT_Q - 1);
-        CandQuery Q = cand_query(P.grid, b, qx, qy, qz);
         long long d2;
         int idx;
-        if (knn_wide_box(P.box_off[b + 1] - P.box_off[b]))
-            cand_knn<KNN_IB_LARGE>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w, P.kn,
-                                   d2, idx);
-        else
-            cand_knn<KNN_IB_SMALL>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w, P.kn,
-                                   d2, idx);
+        int *sd = sdelta[FB ? threadIdx.x >> 5 : 0];
+        bool wide = knn_wide_box(P.box_off[b + 1] - P.box_off[b]);
+        if (FB) {
+            if (wide) vp_knn<KNN_IB_LARGE>(P.grid, b, qx, qy, qz, P.kn, d2, idx, sd);
+            else vp_knn<KNN_IB_SMALL>(P.grid, b, qx, qy, qz, P.kn, d2, idx, sd);
+        } else {
+            CandQuery Q = cand_query(P.grid, b, qx, qy, qz);
+            if (wide)
+                cand_knn<KNN_IB_LARGE>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w,
+                                       P.kn, d2, idx);
+            else
+                cand_knn<KNN_IB_SMALL>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w,
+                                       P.kn, d2, idx);
+        }
         acc += (unsigned long long)idx;
     }
     if (lane == 0 && acc == 0xffffffffffffffffull) *sink = acc;
@@ -235,6 +245,15 @@ __device__ __forceinline__ int cell_box(const DevPtrs &P, long long c) {
     return lo;
 }
 
+// Chebyshev radius (in cells) of the cells that can hold a particle within sqrt(u2) of a
+// cell: a cell at offset o >= 2 is at least (o - 1) cs + 1 from it
+__device__ __forceinline__ int cand_radius(long long u2, int cs, int G) {
+    if (u2 >= KNN_INF) return G;
+    long long u = (long long)sqrt((double)u2) + 1;
+    long long r = u / cs + 1;
+    return r < G ? (int)r : G;
+}
+
 // Calls f(position of the item among the box's items, item) for every particle of box b whose
 // squared distance to the cell box [lo, lo + cs - 1]^3 is at most u2 (lane = grid column; a
 // column's cells are consecutive, so its candidate cells are one range of items).
@@ -245,12 +264,7 @@ __device__ __forceinline__ void cand_walk(const DevPtrs &P, int b, int cx, int c
     int G = P.grid.G[b], cs = P.grid.cs[b];
     long long coff = P.grid.coff[b];
     int ibase = P.grid.start[coff];
-    // a cell at Chebyshev offset o >= 2 is at least (o - 1) cs + 1 from the cell
-    int R = G;
-    if (u2 < KNN_INF) {
-        long long u = (long long)sqrt((double)u2) + 1;
-        if (u / cs + 1 < G) R = (int)(u / cs + 1);
-    }
+    int R = cand_radius(u2, cs, G);
     int lx = cx * cs, ly = cy * cs, lz = cz * cs;
     int hx = lx + cs - 1, hy = ly + cs - 1, hz = lz + cs - 1;
     int side = 2 * R + 1;
@@ -274,8 +288,10 @@ __device__ __forceinline__ void cand_walk(const DevPtrs &P, int b, int cx, int c
 }
 
 // one warp per cell: U^2 (the kn nearest of the cell's centre point, each at its distance to
-// the farthest corner of the cell) and the number of candidates
-__global__ void __launch_bounds__(256) k_cand_count(DevPtrs P, long long *u2out, int *cnt) {
+// the farthest corner of the cell) and the number of candidates, 0 for a cell without a list
+// (counted in *nfall)
+__global__ void __launch_bounds__(256) k_cand_count(DevPtrs P, long long *u2out, int *cnt,
+                                                    unsigned long long *nfall) {
     __shared__ int sdelta[8][32];
     int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -289,11 +305,15 @@ __global__ void __launch_bounds__(256) k_cand_count(DevPtrs P, long long *u2out,
         int mx = cand_centre(lx, cs), my = cand_centre(ly, cs), mz = cand_centre(lz, cs);
         long long d2;
         int idx;
-        bool ok = knn_wide_box(P.box_off[b + 1] - P.box_off[b])
-                      ? warp_knn<KNN_IB_LARGE>(box_grid(P, b), mx, my, mz, -1, P.kn, d2, idx,
-                                               sdelta[threadIdx.x >> 5])
-                      : warp_knn<KNN_IB_SMALL>(box_grid(P, b), mx, my, mz, -1, P.kn, d2, idx,
-                                               sdelta[threadIdx.x >> 5]);
+        if (knn_wide_box(P.box_off[b + 1] - P.box_off[b]))
+            warp_knn<KNN_IB_LARGE>(box_grid(P, b), mx, my, mz, -1, P.kn, d2, idx,
+                                   sdelta[threadIdx.x >> 5]);
+        else
+            warp_knn<KNN_IB_SMALL>(box_grid(P, b), mx, my, mz, -1, P.kn, d2, idx,
+                                   sdelta[threadIdx.x >> 5]);
+        // any kn particles bound U, so a search whose keys saturated (a k-th distance beyond
+        // their range) still gives one; only a box of fewer than kn particles has none
+        bool ok = __all_sync(FULLMASK, lane >= P.kn || idx != 0x7fffffff);
         long long u2 = 0;
         if (ok && lane < P.kn) {
             long long j = P.box_off[b] + idx;
@@ -307,16 +327,20 @@ __global__ void __launch_bounds__(256) k_cand_count(DevPtrs P, long long *u2out,
             long long v = __shfl_xor_sync(FULLMASK, u2, o);
             u2 = v > u2 ? v : u2;
         }
-        // no kn nearest (a box of fewer particles, or a k-th distance beyond the key range):
-        // the whole box
+        // fewer than kn particles in the box: the whole box
         if (!ok) u2 = KNN_INF;
         int n = 0;
-        cand_walk(P, b, cx, cy, cz, u2, [&](int, const int4 &) { ++n; });
+        bool keep = cand_radius(u2, cs, G) <= CAND_R_MAX;   // (always in a box of G <= 8)
+        if (keep) {
+            cand_walk(P, b, cx, cy, cz, u2, [&](int, const int4 &) { ++n; });
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(FULLMASK, n, o);
+            for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(FULLMASK, n, o);
+            keep = n <= CAND_MAX;
+        }
         if (lane == 0) {
             u2out[c] = u2;
-            cnt[c] = n;
+            cnt[c] = keep ? n : 0;
+            if (!keep) atomicAdd(nfall, 1ull);
         }
     }
 }
@@ -337,6 +361,7 @@ __global__ void __launch_bounds__(256) k_cand_fill(DevPtrs P, const long long *u
         int w = cand_ring_width(cs);
         long long u2 = u2in[c];
         long long a = P.grid.cand_off[c], e = P.grid.cand_off[c + 1];
+        if (e == a) continue;   // no list: its queries take the grid walk
         auto ring_of = [&](const int4 &it) {
             long long dx = it.x - mx, dy = it.y - my, dz = it.z - mz;
             long long d2 = dx * dx + dy * dy + dz * dz;
@@ -395,14 +420,17 @@ static rt_status cand_lists(rt_ctx *c, cudaStream_t st) {
     int tb = 256;
     int *cnt = P.seg_cnt;   // scratch, sized >= ncells + 1
     long long *tmp = nullptr;
-    cudaError_t e = cudaMalloc(&tmp, sizeof(long long) * (size_t)(nc + RT_SCAN_NB));
+    cudaError_t e = cudaMalloc(&tmp, sizeof(long long) * (size_t)(nc + RT_SCAN_NB + 1));
     if (e != cudaSuccess) return rt_cuda_check(c, e, "candidate lists");
     long long *u2 = tmp + RT_SCAN_NB;
+    unsigned long long *nfall = (unsigned long long *)(tmp + RT_SCAN_NB + nc);
     cudaMemsetAsync(cnt + nc, 0, sizeof(int), st);
-    k_cand_count<<<rt_blocks(nc * 32, tb, 152 * 64), tb, 0, st>>>(P, u2, cnt);
+    cudaMemsetAsync(nfall, 0, sizeof(unsigned long long), st);
+    k_cand_count<<<rt_blocks(nc * 32, tb, 152 * 64), tb, 0, st>>>(P, u2, cnt, nfall);
     rt_scan_exclusive64(cnt, P.grid.cand_off, nc + 1, tmp, st);
-    long long total = 0;
+    long long total = 0, fall = 0;
     cudaMemcpyAsync(&total, P.grid.cand_off + nc, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&fall, nfall, sizeof(long long), cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && total > P.grid.cand_cap) {
         if (P.grid.cand) cudaFree(P.grid.cand);
@@ -419,6 +447,7 @@ static rt_status cand_lists(rt_ctx *c, cudaStream_t st) {
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGetLastError();
     c->cand_entries = total;
+    c->cand_fallback = fall;
     return rt_cuda_check(c, e, "candidate lists");
 }
 
@@ -445,8 +474,12 @@ static rt_status tune_grid(rt_ctx *c, cudaStream_t st) {
         cell_lists(c, st);
         if ((s = cand_lists(c, st)) != RT_OK) break;
         cudaEventRecord(e0, st);
-        k_knn_probe<<<rt_blocks((P.n / 4 + 1) * 32, tb, 152 * 64), tb, 0, st>>>(
-            P, (unsigned long long *)&P.cnt[CNT_N - 1]);   // an unused counter as the sink
+        // the probe takes the instance the virtual particles will (with the grid-walk
+        // fallback only when some cell has no list)
+        unsigned long long *sink = (unsigned long long *)&P.cnt[CNT_N - 1];   // an unused counter
+        int pb = rt_blocks((P.n / 4 + 1) * 32, tb, 152 * 64);
+        if (c->cand_fallback > 0) k_knn_probe<true><<<pb, tb, 0, st>>>(P, sink);
+        else k_knn_probe<false><<<pb, tb, 0, st>>>(P, sink);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -497,6 +530,7 @@ rt_status rt_knn_build(rt_ctx *c, cudaStream_t st) {
 // failed search
 __global__ void __launch_bounds__(256) k_query(DevPtrs P, int b, long long m, const int *q,
                                                int *nbr, long long *d2out, int *fail) {
+    __shared__ int sdelta[8][32];
     int lane = threadIdx.x & 31;
     long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -508,11 +542,9 @@ __global__ void __launch_bounds__(256) k_query(DevPtrs P, int b, long long m, co
         long long d2 = -1;
         int idx = 0;
         if (ok) {
-            CandQuery Q = cand_query(P.grid, b, qx, qy, qz);
-            ok = wide ? cand_knn<KNN_IB_LARGE>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up,
-                                               Q.w, P.kn, d2, idx)
-                      : cand_knn<KNN_IB_SMALL>(Q.items, P.grid.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up,
-                                               Q.w, P.kn, d2, idx);
+            int *sd = sdelta[threadIdx.x >> 5];
+            ok = wide ? vp_knn<KNN_IB_LARGE>(P.grid, b, qx, qy, qz, P.kn, d2, idx, sd)
+                      : vp_knn<KNN_IB_SMALL>(P.grid, b, qx, qy, qz, P.kn, d2, idx, sd);
             if (!ok && lane == 0) atomicOr(fail, 2);
         }
         if (lane < P.kn) {

@@ -407,6 +407,14 @@ __device__ inline bool cand_knn(const int4 *items, const unsigned *cand, long lo
     return kth != KNN_KEY_NONE && (IB == KNN_IB_SMALL || (long long)(kth >> IB) < knn_d2max<IB>());
 }
 
+// A cell keeps a candidate list when its walk radius (in cells, from U) is at most CAND_R_MAX
+// and the list holds at most CAND_MAX entries.  Other cells (deep in a void, where the n_ngb
+// nearest lie far away and U takes in a large part of a distant cluster) get an empty list; a
+// query there takes the grid walk.  A kept list is never empty: it holds the centre point's
+// n_ngb nearest.
+#define CAND_R_MAX 8
+#define CAND_MAX 4096
+
 // The query of a virtual particle at (qx, qy, qz) in box b: its cell's list, ring width and
 // the bound on its distance to the cell's centre point.
 struct CandQuery {
@@ -429,4 +437,47 @@ __device__ __forceinline__ CandQuery cand_query(const Grid &gr, int b, int qx, i
               mz = cand_centre(cz * cs, cs) - qz;
     Q.rq_up = sqrt_up(mx * mx + my * my + mz * mz);
     return Q;
+}
+
+// the grid description of box b, for the grid walk
+__device__ __forceinline__ BoxGrid grid_of_box(const Grid &gr, int b) {
+    BoxGrid g;
+    g.G = gr.G[b];
+    g.cs = gr.cs[b];
+    g.coff = gr.coff[b];
+    g.start = gr.start;
+    g.items = gr.items;
+    g.tab = gr.tab;
+    return g;
+}
+
+struct KnnOut {
+    long long d2;
+    int idx;
+    bool ok;
+};
+
+// The grid walk for a query in a cell without a candidate list, kept out of line: it is rare,
+// and inlined it would take registers from the common path.  Called by the whole warp.
+template <int IB>
+__device__ __noinline__ KnnOut knn_walk_query(BoxGrid g, int qx, int qy, int qz, int kn,
+                                              int *sdelta) {
+    KnnOut o;
+    o.ok = warp_knn<IB>(g, qx, qy, qz, -1, kn, o.d2, o.idx, sdelta);
+    return o;
+}
+
+// The virtual particles' exact kNN of (qx, qy, qz) in box b: from the cell's candidate list,
+// or by the grid walk where the cell has none.  Both give warp_knn's result.  sdelta: 32 ints
+// of shared memory owned by the calling warp (the grid walk's).
+template <int IB>
+__device__ __forceinline__ bool vp_knn(const Grid &gr, int b, int qx, int qy, int qz, int kn,
+                                       long long &d2, int &idx, int *sdelta) {
+    CandQuery Q = cand_query(gr, b, qx, qy, qz);
+    if (Q.e > Q.a)
+        return cand_knn<IB>(Q.items, gr.cand, Q.a, Q.e, qx, qy, qz, Q.rq_up, Q.w, kn, d2, idx);
+    KnnOut o = knn_walk_query<IB>(grid_of_box(gr, b), qx, qy, qz, kn, sdelta);
+    d2 = o.d2;
+    idx = o.idx;
+    return o.ok;
 }

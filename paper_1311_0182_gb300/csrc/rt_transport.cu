@@ -789,11 +789,13 @@ template <typename Real> struct VDec {
 // Virtual particles (Sec. 2.1): one warp per request.
 // BAR: some box has a barrier (a separate instance keeps the test out of the common case);
 // SH: the shared frequency bin (likewise); IB: index bits of the kNN keys (24 when a box holds
-// more than 2^22 particles)
+// more than 2^22 particles); FB: some cell has no candidate list, and queries there take the
+// grid walk (a separate instance keeps that call, and the registers it costs, out of the
+// common case)
 // cur, fcur: the hop's slot and free-packet buffers (launch parameters, so that buffer
 // pointers are re-read from the parameter space instead of being held in registers); the
 // step and hop of the random draws are read from the device counters where they are used.
-template <typename Real, int NRC, bool BAR, bool SH, int IB>
+template <typename Real, int NRC, bool BAR, bool SH, int IB, bool FB>
 __global__ void __launch_bounds__(256, VIRT_MINB(Real)) k_virtual(DevPtrs P, int cur, int fcur,
                                                  const int *lens, unsigned long long *esc_r,
                                                  unsigned char *vstat) {
@@ -815,6 +817,7 @@ __global__ void __launch_bounds__(256, VIRT_MINB(Real)) k_virtual(DevPtrs P, int
     // vary), and blocks still retire one by one, which lets the receiver side on the other
     // stream in.  Results do not depend on which warp takes a request.
     __shared__ VDec<Real> sdec[8][VREQ_GROUP];
+    __shared__ int sdelta[FB ? 8 : 1][32];   // the grid walk of cells without a candidate list
     __shared__ int snext;
     VDec<Real> *mine = sdec[threadIdx.x >> 5];
     long long chunk = (nreq + gridDim.x - 1) / gridDim.x;
@@ -922,12 +925,20 @@ __global__ void __launch_bounds__(256, VIRT_MINB(Real)) k_virtual(DevPtrs P, int
                 continue;
             }
             bad |= pend_a > (1ull << 62) || pend_e > (1ull << 62);
-            // exact kNN from the candidate list of the virtual particle's cell
+            // exact kNN from the candidate list of the virtual particle's cell (the grid walk
+            // in a cell without one)
             long long kd2;
             int kidx;
-            CandQuery Q = cand_query(P.grid, box, vx, vy, vz);
-            if (!cand_knn<IB>(Q.items, P.grid.cand, Q.a, Q.e, vx, vy, vz, Q.rq_up, Q.w, P.kn, kd2,
-                              kidx)) {
+            bool kok;
+            if (FB) {
+                kok = vp_knn<IB>(P.grid, box, vx, vy, vz, P.kn, kd2, kidx,
+                                 sdelta[FB ? threadIdx.x >> 5 : 0]);
+            } else {
+                CandQuery Q = cand_query(P.grid, box, vx, vy, vz);
+                kok = cand_knn<IB>(Q.items, P.grid.cand, Q.a, Q.e, vx, vy, vz, Q.rq_up, Q.w, P.kn,
+                                   kd2, kidx);
+            }
+            if (!kok) {
                 // a k-th neighbour beyond the key range: reported; indices kept inside the box
                 bad_knn = true;
                 long long nbx = P.box_off[box + 1] - boff;
@@ -1471,6 +1482,22 @@ static void set_step(rt_ctx *c, long long step, cudaStream_t st) {
     c->step_dev = step;
 }
 
+// The virtual-particle kernel of the hop: the instance with the grid-walk fallback only when
+// some cell of the context has no candidate list.
+template <typename Real, int NRC, bool BAR, bool SH, int IB>
+static void launch_virtual(rt_ctx *c, cudaStream_t st, int GV, int cur, int fcur) {
+    DevPtrs &P = c->d;
+    HopScratch &H = c->hop;
+    const int tb = 256;
+    int nb = rt_blocks(P.F_cap * 32, tb, GV);
+    if (c->cand_fallback > 0)
+        k_virtual<Real, NRC, BAR, SH, IB, true><<<nb, tb, 0, st>>>(P, cur, fcur, H.lens, H.esc_r,
+                                                                   H.vstat);
+    else
+        k_virtual<Real, NRC, BAR, SH, IB, false><<<nb, tb, 0, st>>>(P, cur, fcur, H.lens, H.esc_r,
+                                                                    H.vstat);
+}
+
 // One hop.  Two streams: st: gas senders, the request list, virtual particles, the hop counts.
 // s2: free-packet senders and staging, receiver segments, work list, receiver side.  s2 starts
 // after everything before this hop on st; the work list waits for the gas senders (touched
@@ -1515,20 +1542,15 @@ static void hop_core(rt_ctx *c, cudaStream_t st, long long nfr, int cur, int fcu
     LAUNCH(KT_EXPAND, 1, (k_expand<<<rt_blocks(n + nfr, tb, gb), tb, 0, st>>>(P, H.lens)));
     const int IS = KNN_IB_SMALL, IL = KNN_IB_LARGE;
     if (P.kwide && P.shared)   // boxes above 2^22 particles: the general instance, 24-bit keys
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true, IL><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
-                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+        LAUNCH(KT_VIRTUAL, 1, (launch_virtual<Real, NRC, true, true, IL>(c, st, GV, cur, fcur)));
     else if (P.kwide)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false, IL><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
-                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+        LAUNCH(KT_VIRTUAL, 1, (launch_virtual<Real, NRC, true, false, IL>(c, st, GV, cur, fcur)));
     else if (P.shared)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, true, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
-                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+        LAUNCH(KT_VIRTUAL, 1, (launch_virtual<Real, NRC, true, true, IS>(c, st, GV, cur, fcur)));
     else if (P.any_bar)
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, true, false, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
-                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+        LAUNCH(KT_VIRTUAL, 1, (launch_virtual<Real, NRC, true, false, IS>(c, st, GV, cur, fcur)));
     else
-        LAUNCH(KT_VIRTUAL, 1, (k_virtual<Real, NRC, false, false, IS><<<rt_blocks(P.F_cap * 32, tb, GV), tb, 0, st>>>(
-                                  P, cur, fcur, H.lens, H.esc_r, H.vstat)));
+        LAUNCH(KT_VIRTUAL, 1, (launch_virtual<Real, NRC, false, false, IS>(c, st, GV, cur, fcur)));
     LAUNCH_ON(s2, KT_SCAN, 2, (rt_scan_exclusive(c, P.seg_cnt, P.seg_off, nkey, nullptr, nullptr, s2, c->scan_tmp2)));
     LAUNCH_ON(s2, KT_SEG_FILL, 1, (k_seg_fill<<<rt_blocks(P.ST_cap, tb, 152 * 16), tb, 0, s2>>>(P, H.lens)));
     LAUNCH_ON(s2, KT_SEG_SORT, 1, (k_seg_sort<<<(unsigned)((nkey + tb - 1) / tb), tb, 0, s2>>>(P)));

@@ -437,7 +437,7 @@ class Context:
         keys = ["hops", "virtual", "escaped_virtual", "subcycles", "floor_hits", "peak_free",
                 "peak_active", "gas_contrib", "senders", "moving_packets", "staged_contrib",
                 "receiver_groups", "receiver_outputs", "cell_occupancy", "grid_send",
-                "grid_virtual", "grid_receive", "candidate_entries"]
+                "grid_virtual", "grid_receive", "candidate_entries", "candidate_fallback_cells"]
         return dict(zip(keys, list(out)))
 
 

@@ -118,20 +118,40 @@ def _lattice_box(n_side=12):
                    np.full((1, 1), 1e48), [6.3e-18], [0.0])
 
 
+def _void_box(n_dense=20000, n_sparse=24, seed=13):
+    """One box whose particles fill a corner cube of 0.3 of the side, with a few scattered over
+    the rest: cells far from the cube have no candidate list (their n_ngb nearest lie far
+    away), and queries there take the grid walk."""
+    rng = np.random.default_rng(seed)
+    L = W.KPC
+    pos = np.concatenate([rng.uniform(0.0, 0.3 * L, size=(n_dense, 3)),
+                          rng.uniform(0.0, np.nextafter(L, 0.0), size=(n_sparse, 3))])
+    n = len(pos)
+    params = W.default_params(seed=seed, dt=0.05 * W.MYR, dt_em=0.05 * W.MYR)
+    return W._pack(params, [L], [0, n], pos, np.full(n, 1e-3), np.full(n, 1e-3 * L ** 3 / n),
+                   np.full(n, 0.3), np.full(n, 1e4), [0], np.array([[0.15 * L] * 3]),
+                   np.full((1, 1), 1e48), [6.3e-18], [0.0])
+
+
 @pytest.mark.parametrize("name,occ", [("cfg2_small", 0), ("cfg2_small", 1), ("cfg2_small", 6),
                                       ("lattice", 0), ("lattice", 2), ("clustered", 0),
-                                      ("clustered", 1)])
+                                      ("clustered", 1), ("void", 0), ("void", 1)])
 def test_virtual_particle_search_against_brute_force(name, occ):
     """The virtual particles' exact kNN from the per-cell candidate lists (Sec. 2.1: a virtual
     particle's neighbours are the n_ngb particles nearest to it) equals a brute-force search,
     ties to the lower index, for points like virtual particles (within a smoothing length of a
     particle), points on particles, cell corners and the edges and corners of the box, on
     uniform, lattice (exact ties) and clustered boxes with duplicate positions, at several
-    grid occupancies."""
+    grid occupancies; in a box that is mostly void, the cells without a list answer by the
+    grid walk, with the same result."""
     from paper_1311_0182_gb300 import rt
     wl = {"cfg2_small": lambda: W.cfg2(n_side=20), "lattice": _lattice_box,
-          "clustered": _clustered_boxes}[name]()
+          "clustered": _clustered_boxes, "void": _void_box}[name]()
     g = rt.context_for(dict(wl, params=dict(wl["params"], cell_occupancy=occ)))
+    if name == "void":
+        assert g.stats()["candidate_fallback_cells"] > 0
+    elif name in ("cfg2_small", "lattice"):
+        assert g.stats()["candidate_fallback_cells"] == 0
     q = g.quantised()
     nbr, h2 = g.neighbours()[:2]
     k = wl["params"]["n_ngb"]
@@ -1147,6 +1167,14 @@ def test_box_above_2_22_particles_uses_24_bit_keys():
         order = cand[np.lexsort((cand, d2[cand]))][:32]
         assert np.array_equal(nbr[i], order)
         assert h2[i] == d2[order[-1]]
+    # the virtual particles' search with 24-bit keys, at points near particles
+    pts = np.clip(q[rng.choice(n, 6, replace=False)] + rng.integers(-2000, 2000, (6, 3)), 0,
+                  (1 << 20) - 1)
+    got, gd2 = g.query_neighbours(0, pts)
+    for p_, nb_ in zip(pts, got):
+        d2 = ((q - p_) ** 2).sum(1)
+        cand = np.nonzero(d2 <= np.partition(d2, 31)[31])[0]
+        assert np.array_equal(nb_, cand[np.lexsort((cand, d2[cand]))][:32])
     g.step(0)
     b = g.budget()[0]
     assert g.stats()["virtual"] > 0 and abs(b[0] - b[1:].sum()) <= 1e-6 * b[0]
