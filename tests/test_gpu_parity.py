@@ -118,10 +118,11 @@ def _lattice_box(n_side=12):
                    np.full((1, 1), 1e48), [6.3e-18], [0.0])
 
 
-def _void_box(n_dense=20000, n_sparse=24, seed=13):
+def _void_box(n_dense=20000, n_sparse=24, seed=13, src_at=0.15):
     """One box whose particles fill a corner cube of 0.3 of the side, with a few scattered over
     the rest: cells far from the cube have no candidate list (their n_ngb nearest lie far
-    away), and queries there take the grid walk."""
+    away), and queries there take the grid walk.  The source sits at src_at of the side on the
+    diagonal."""
     rng = np.random.default_rng(seed)
     L = W.KPC
     pos = np.concatenate([rng.uniform(0.0, 0.3 * L, size=(n_dense, 3)),
@@ -129,7 +130,7 @@ def _void_box(n_dense=20000, n_sparse=24, seed=13):
     n = len(pos)
     params = W.default_params(seed=seed, dt=0.05 * W.MYR, dt_em=0.05 * W.MYR)
     return W._pack(params, [L], [0, n], pos, np.full(n, 1e-3), np.full(n, 1e-3 * L ** 3 / n),
-                   np.full(n, 0.3), np.full(n, 1e4), [0], np.array([[0.15 * L] * 3]),
+                   np.full(n, 0.3), np.full(n, 1e4), [0], np.array([[src_at * L] * 3]),
                    np.full((1, 1), 1e48), [6.3e-18], [0.0])
 
 
@@ -182,6 +183,39 @@ def test_virtual_particle_search_against_brute_force(name, occ):
             assert np.array_equal(dd, d2[order])
     with pytest.raises(rt.RTError):
         g.query_neighbours(0, np.array([[0, 0, Q]]))
+    g.close()
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_steps_with_virtual_particles_in_cells_without_a_list(fp32):
+    """Virtual particles placed in cells without a candidate list take the grid walk inside the
+    step (the virtual-particle kernel's instance with the fallback).  The source sits deep in
+    the void of a box whose particles fill a corner cube, so its empty cones place virtual
+    particles far from the cube.  Three steps against the oracle: FP64 within 1e-7 in the
+    absorptions and the state (a wrong neighbour set would move them by order one); FP32
+    conserves photons and stays within the bars, with the routing-flip allowance of the other
+    FP32 tests."""
+    wl = _void_box(n_dense=6000, n_sparse=16, src_at=0.8)
+    g, o = _pair(wl, transport_fp32=fp32, cell_occupancy=1)
+    assert g.stats()["candidate_fallback_cells"] > 0
+    affected = np.zeros(g.n, dtype=bool)
+    for step in range(3):
+        g.step(step)
+        assert o.step(step) == 0
+        if fp32:
+            _route_affected(g, o, wl["N_H"], affected)
+    assert g.stats()["virtual"] > 0
+    if fp32 == 0:
+        ag, eg, pg = g.deposits()
+        ao, eo, po = o.deposits()
+        assert np.allclose(ag, ao, rtol=1e-7, atol=1e-12 * max(ao.max(), 1e-300))
+        sg, so = g.state(), o.state()
+        assert np.allclose(sg["x_HI"], so["x_HI"], rtol=1e-7, atol=1e-15)
+        assert np.allclose(sg["T"], so["T"], rtol=1e-7)
+    else:
+        _assert_fp32_bars(g.state(), o.state(), affected, 3, "void box")
+    b = g.budget()[0]
+    assert abs(b[0] - b[1:].sum()) <= (1e-9 if fp32 == 0 else 1e-6) * b[0]
     g.close()
 
 
