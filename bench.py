@@ -249,7 +249,7 @@ def run_ours(args):
     out["budget_closure"] = float(abs(b[0, 0] - b[0, 1:].sum()) / b[0, 0])
     ctx_h.close()
     if not args.no_e2e:
-        out["e2e"] = e2e(args, ctx, wl, stream, step)
+        out["e2e"] = e2e(args, wl, stream, step - args.steps, st0, ctx.state()["x_HI"])
     ctx.close()
     if not args.no_fp64 and args.precision == "fp32":
         out["fp64_path"] = fp64_path(args, stream)
@@ -653,15 +653,26 @@ def precision_check(args, stream, steps=10):
     return out
 
 
-def e2e(args, ctx, wl, stream, step):
+def e2e(args, wl, stream, first, st0, x_ref):
     """Same metric through the C ABI with host buffers: per step the state arrays go host ->
-    device, the step runs, and the state and photon budget come back."""
+    device, the step runs, and the state and photon budget come back.  A fresh context with
+    the main run's grid and launch sizes is brought to the first timed step untimed, so the
+    timed steps are the same steps, with the same work, as `value`'s; its state after them is
+    compared with the main run's."""
     import torch
+    from paper_1311_0182_gb300 import rt
+    ctx = rt.Context(wl, stream=stream, cell_occupancy=st0["cell_occupancy"], tune_launch=0,
+                     launch_grid=(st0["grid_send"], st0["grid_virtual"], st0["grid_receive"]))
+    with torch.cuda.stream(stream):
+        ctx.load_workload(wl)
+        ctx.build_neighbours()
+    _advance(ctx, stream, first)
     n = ctx.n
     hx = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
     hT = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
-    ctx.get_state_into(x_HI=hx, T=hT)      # continue the run from where the device stands
-    steps = max(2, args.steps)
+    ctx.get_state_into(x_HI=hx, T=hT)      # the host holds the state of the first timed step
+    steps = args.steps
+    step = first
     with torch.cuda.stream(stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -673,8 +684,12 @@ def e2e(args, ctx, wl, stream, step):
             ctx.budget()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": "particle-sweeps/s", "h2d_bytes_per_step": 16 * n,
-            "d2h_bytes_per_step": 16 * n + 32 * ctx.nb, "steps": steps}
+    out = {"value": n * steps / dt, "unit": "particle-sweeps/s", "h2d_bytes_per_step": 16 * n,
+           "d2h_bytes_per_step": 16 * n + 32 * ctx.nb, "steps": steps,
+           "timed_steps": [first, first + steps - 1],
+           "same_result_bits": bool(np.array_equal(hx, x_ref))}
+    ctx.close()
+    return out
 
 
 def _oracle_sample(n_side, steps):
