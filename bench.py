@@ -210,8 +210,10 @@ def run_ours(args):
         clk_h.start()
         torch.cuda.synchronize()
         e0.record(stream)
+        hops = []                       # per timed step (the same steps as the graph's)
         for s in range(step, step + args.steps):
             ctx_h.step(s)
+            hops.append(ctx_h.stats()["hops"])     # a host-side read after the step's own sync
         e1.record(stream)
         torch.cuda.synchronize()
         ms_h = e0.elapsed_time(e1)
@@ -229,7 +231,10 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 transport / f64 chemistry" if args.precision == "fp32" else "f64",
            "data": "synthetic", "config": workload_config(args, wl), "gpu_launches": launches,
-           "clocks": clocks}
+           "clocks": clocks,
+           # a particle-hop is one gas particle taking part in one hop
+           "hops_per_step": sum(hops) / len(hops),
+           "particle_hops_per_s": world * n * sum(hops) / (ms / 1e3)}
     # roofline of the dominant kernel, timed over the same steps run hop by hop
     out["roofline"] = roofline(ctx_h, kt, ms_h, args)
     out["roofline"]["timing"] = ("CUDA events on the launching stream around every launch of "

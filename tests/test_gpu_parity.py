@@ -873,6 +873,31 @@ def test_state_round_trip_host_and_device():
     assert np.array_equal(g.state()["x_HI"], s["x_HI"])
 
 
+def test_query_neighbours_with_device_buffers():
+    """rt_query_neighbours with device pointers gives what it gives with host arrays."""
+    import ctypes
+    import torch
+    from paper_1311_0182_gb300 import rt
+    g = rt.context_for(W.cfg2(n_side=16))
+    q = g.quantised()
+    rng = np.random.default_rng(4)
+    pts = np.clip(q[rng.integers(0, g.n, 64)] + rng.integers(-5000, 5000, (64, 3)), 0,
+                  (1 << 20) - 1).astype(np.int32)
+    nh, dh = g.query_neighbours(0, pts)
+    k = nh.shape[1]
+    qd = torch.tensor(pts, device="cuda")
+    nd = torch.empty((64, k), dtype=torch.int32, device="cuda")
+    dd = torch.empty((64, k), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    st = g.L.rt_query_neighbours(g.h, 0, 64, ctypes.c_void_p(qd.data_ptr()),
+                                 ctypes.c_void_p(nd.data_ptr()), ctypes.c_void_p(dd.data_ptr()),
+                                 rt.RT_DEVICE, None)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert np.array_equal(nd.cpu().numpy(), nh) and np.array_equal(dd.cpu().numpy(), dh)
+    g.close()
+
+
 def test_profiling_mask_times_only_the_chosen_kernels():
     """Kernels outside the mask are counted but not timed; the mask leaves results unchanged."""
     from paper_1311_0182_gb300 import rt
