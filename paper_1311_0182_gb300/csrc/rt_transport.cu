@@ -1086,30 +1086,37 @@ __global__ void __launch_bounds__(256) k_worklist(DevPtrs P, int cur, int *wl_n)
 
 // absorptions of one receiver group in one hop.  FP64 path: FP64 sums.  FP32 path: the
 // group's (fixed-order) sums go into the particle's fixed-point words, like the virtual-particle
-// deposits, so no FP64 instruction runs in the hop loop; pass counts stay in FP32.
+// deposits, so no FP64 instruction runs in the hop loop; pass counts stay in FP32.  Returns the
+// high absorption word before the add (0 on the FP64 path), which the caller range-checks one
+// group later, so that the group does not wait for the atomic's round trip.
 template <typename Real>
-__device__ __forceinline__ void deposit_group(const DevPtrs &P, long long key, long long j, int box,
-                                              Real a, Real ae, Real w);
+__device__ __forceinline__ unsigned long long deposit_group(const DevPtrs &P, long long key,
+                                                            long long j, int box, Real a, Real ae,
+                                                            Real w);
 template <>
-__device__ __forceinline__ void deposit_group<double>(const DevPtrs &P, long long key, long long j,
-                                                      int box, double a, double ae, double w) {
+__device__ __forceinline__ unsigned long long deposit_group<double>(const DevPtrs &P,
+                                                                    long long key, long long j,
+                                                                    int box, double a, double ae,
+                                                                    double w) {
     double nm = P.norm[box];
     P.abs[key] += a * nm;
     P.absE[key] += ae * nm * P.eunit;
     P.pass[key] += w * nm;
+    return 0ull;
 }
 template <>
-__device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long key, long long j,
-                                                     int box, float a, float ae, float w) {
+__device__ __forceinline__ unsigned long long deposit_group<float>(const DevPtrs &P,
+                                                                   long long key, long long j,
+                                                                   int box, float a, float ae,
+                                                                   float w) {
     // atomics: virtual-particle deposits into the same words may run at the same time
+    unsigned long long old = 0ull;
     float fa = a * ((float *)P.dep_s)[j];
     if (fa > 0.0f) {
         unsigned long long qh, ql;
         if (fx_split(fa, qh, ql)) {
-            unsigned long long old = atomicAdd(&P.fx_abs[key], qh);
+            old = atomicAdd(&P.fx_abs[key], qh);
             atomicAdd(&P.fx_lo[key], ql);
-            if (old > (1ull << 62))
-                atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
         } else {
             atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
         }
@@ -1117,6 +1124,7 @@ __device__ __forceinline__ void deposit_group<float>(const DevPtrs &P, long long
     float fe = ae * ((float *)P.depE_s)[j];
     if (fe > 0.0f) atomicAdd(&P.fx_E[key], f2u64_rz(fe + 0.5f));
     P.passf[key] += w;
+    return old;
 }
 
 // Receiver side.  Group of G = n_rc lanes per (particle j, frequency nu); lane = reception
@@ -1155,6 +1163,8 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
         if (gl == 0) v = gb0 + atomicAdd(&snext, 1);
         return __shfl_sync(gmask, v, 0, G);
     };
+    unsigned long long pend = 0ull;   // the high absorption word before the last deposit
+    bool bad = false;
     for (long long gi = next_group(); gi < gb1; gi = next_group()) {
         unsigned wv = (unsigned)P.worklist[gi];
         long long key = wv & 0x7fffffffu;
@@ -1327,9 +1337,14 @@ __global__ void __launch_bounds__(256, HOP_MINB(Real)) k_phaseB(DevPtrs P, int c
         if (gl == 0) {
             P.occ[nxt][key] = bo;
             P.act[nxt][key] = ba;
-            if (touched || fc > 0) deposit_group<Real>(P, key, j, box, a, ae, w);
+            if (touched || fc > 0) {
+                bad |= pend > (1ull << 62);
+                pend = deposit_group<Real>(P, key, j, box, a, ae, w);
+            }
         }
     }
+    bad |= pend > (1ull << 62);
+    if (bad) atomicOr((unsigned long long *)&P.cnt[CNT_ERR], (unsigned long long)ERRB_RANGE);
 }
 
 // After a hop: active slots, live free packets, escaped photons per box (fixed point).
