@@ -98,9 +98,11 @@ typedef struct {
     int tune_launch;      /* 1: the grid sizes of the three main hop kernels (sender side,
                              virtual particles, receiver side) are chosen by timing the first
                              steps of rt_step as whole step-graph launches: coordinate search
-                             over 152 x {8, 16, 32, 64} blocks from the built-in sizes, each
-                             candidate step after a step of the best so far, per unit of work
-                             of the step (18 steps).  The winner is kept for the process per
+                             from the built-in sizes over 152 x {2, 3, 4, 5} blocks for the
+                             virtual particles (one wave at most: they pull work from a queue)
+                             and 152 x {8, 16, 32, 64} for the two others, each candidate step
+                             after a step of the best so far, per unit of work of the step (18
+                             steps).  The winner is kept for the process per
                              configuration and particle count, so a later context of the same
                              kind starts with it.  0: built-in sizes.  Results do not depend on
                              the choice. */

@@ -53,6 +53,7 @@ enum {
     CNT_DROP = 22,      // 1: the hop cap stopped the loop with packets still moving
     CNT_PKFREE = 23,    // largest request count of a hop in this step
     CNT_PKACT = 24,     // largest active-slot count after a hop in this step
+    CNT_VQ = 25,        // the virtual particles' work queue: requests taken in this hop
     CNT_N = 32
 };
 

@@ -153,15 +153,15 @@ void rt_upload_axes() {
 #define VIRT_MINB_F32 5
 #endif
 #define VIRT_MINB(Real) (sizeof(Real) == 4 ? VIRT_MINB_F32 : 3)
-// Largest grids (blocks) of the sender side, the virtual particles and the receiver side;
-// each block takes a contiguous chunk of the live items.  Set by a measured sweep on the 64^3
-// HII-region step: fewer, longer-lived blocks than one per 32 items, while still several
-// blocks per SM turn over during a launch.
+// Largest grids (blocks) of the sender side, the virtual particles and the receiver side.  On
+// the sender and receiver sides each block takes a contiguous chunk of the live items; the
+// sizes were set by a measured sweep on the 64^3 HII-region step: fewer, longer-lived blocks
+// than one per 32 items, while still several blocks per SM turn over during a launch.
 #ifndef GRID_A
 #define GRID_A (152 * 16)
 #endif
 #ifndef GRID_V
-#define GRID_V (152 * 32)
+#define GRID_V (152 * VIRT_MINB_F32)   // one wave: the virtual particles pull from a work queue
 #endif
 #ifndef GRID_B
 #define GRID_B (152 * 8)
@@ -812,28 +812,24 @@ __global__ void __launch_bounds__(256, VIRT_MINB(Real)) k_virtual(DevPtrs P, int
     // Latency: the kNN search loads each batch of its cell's candidates before merging the
     // previous one; the four per-neighbour inputs of the interpolation and deposit are gathered
     // together; the values returned by the deposit atomics are checked one request later.
-    // Each block takes one contiguous chunk of the requests, and its warps pull groups from the
-    // chunk through a shared counter: the warps of a block finish close together (request costs
-    // vary), and blocks still retire one by one, which lets the receiver side on the other
-    // stream in.  Results do not depend on which warp takes a request.
+    // Work queue: every warp of the launch takes its next group from one device counter
+    // (CNT_VQ, set to zero before the hop), so all resident warps stay busy until the requests
+    // run out, whatever each request costs; the grid is one wave of resident blocks.  (Blocks
+    // that own a fixed chunk each leave most of their warps idle while the slowest finishes:
+    // 25 of 40 warps per SM were active.)  Results do not depend on which warp takes a request.
     __shared__ VDec<Real> sdec[8][VREQ_GROUP];
     __shared__ int sdelta[FB ? 8 : 1][32];   // the grid walk of cells without a candidate list
-    __shared__ int snext;
     VDec<Real> *mine = sdec[threadIdx.x >> 5];
-    long long chunk = (nreq + gridDim.x - 1) / gridDim.x;
-    long long rb0 = (long long)blockIdx.x * chunk;
-    long long rb1 = rb0 + chunk < nreq ? rb0 + chunk : nreq;
-    if (threadIdx.x == 0) snext = 0;
-    __syncthreads();
+    unsigned long long *queue = (unsigned long long *)&P.cnt[CNT_VQ];
     const float cf = 1.0f - 2.0f / (float)P.ntc;
     unsigned long long pend_a = 0ull, pend_e = 0ull;   // words before this lane's last adds
     bool bad = false, bad_knn = false;
     for (;;) {
         long long g0 = 0;
-        if (lane == 0) g0 = rb0 + atomicAdd(&snext, VREQ_GROUP);
+        if (lane == 0) g0 = (long long)atomicAdd(queue, (unsigned long long)VREQ_GROUP);
         g0 = __shfl_sync(FULLMASK, g0, 0);
-        if (g0 >= rb1) break;
-        const int gn = (int)(rb1 - g0 < VREQ_GROUP ? rb1 - g0 : VREQ_GROUP);
+        if (g0 >= nreq) break;
+        const int gn = (int)(nreq - g0 < VREQ_GROUP ? nreq - g0 : VREQ_GROUP);
         if (lane < gn) {
             unsigned long long code = P.req[g0 + lane];
             VDec<Real> D;
@@ -1422,6 +1418,7 @@ __global__ void k_hop_lens(DevPtrs P, int *lens, int phase, long long arg, int i
     if (phase == HL_BEGIN) {            // before the hop: counters, scan length
         cnt[CNT_ACTIVE] = 0;
         cnt[CNT_LIVE] = 0;
+        cnt[CNT_VQ] = 0;                // the virtual particles' work queue
         lens[1] = (int)(P.n + lens[0]);
         // in the graph: which of the four copies of the hop (slot and free-packet buffers) runs
         if (in_graph) cudaGraphSetConditional(handle, (unsigned)(cnt[CNT_CUR] | (cnt[CNT_FCUR] << 1)));
@@ -1905,10 +1902,12 @@ rt_status rt_step_graph(rt_ctx *c, long long step, cudaStream_t st) {
 // sizes of the sender side, the virtual particles and the receiver side, and are timed with CUDA
 // events around the graph launch, so that the overlap of the two streams is in the objective.
 // The time of a step is divided by its work (packets moved, particles sending, virtual
-// particles: device counters of that step).  Coordinate search from the built-in sizes over
-// 152 x {8, 16, 32, 64} blocks, the virtual particles first, then the sender and the receiver
-// side; each candidate step follows a step of the current best, so that the pair sees nearly
-// the same work, and replaces it when it costs 1% less per unit of work.  The winner is kept
+// particles: device counters of that step).  Coordinate search from the built-in sizes, the
+// virtual particles first (152 x {2, 3, 4, 5} blocks: at most one wave, since its warps pull
+// from a work queue; fewer blocks leave room for the receiver side beside it), then the sender
+// and the receiver side (152 x {8, 16, 32, 64} blocks); each candidate step follows a step of
+// the current best, so that the pair sees nearly the same work, and replaces it when it costs
+// 1% less per unit of work.  The winner is kept
 // for the process per (configuration, particles, boxes): a later context of the same kind
 // starts with it and does not tune.  The steps run while tuning are ordinary steps: results do
 // not depend on the launch sizes.
@@ -1948,8 +1947,10 @@ rt_status rt_step_graph_tuned(rt_ctx *c, long long step, cudaStream_t st) {
         U.cand.clear();
         const int order[3] = {1, 0, 2};
         for (int kk : order)
-            for (int q = 0; q < 4; ++q)
-                if (152 * (8 << q) != def[kk]) U.cand.push_back({kk, 152 * (8 << q)});
+            for (int q = 0; q < 4; ++q) {
+                int g = kk == 1 ? 152 * (2 + q) : 152 * (8 << q);
+                if (g != def[kk]) U.cand.push_back({kk, g});
+            }
         U.phase = 1;
         U.steps = 0;
     }

@@ -787,8 +787,9 @@ def test_step_graph_at_the_hop_cap_and_after_a_barrier_change():
 
 def test_launch_size_tuning_changes_nothing_but_time():
     """With tune_launch the first steps run as the step graph, each with one triple of grid
-    sizes (152 x {8, 16, 32, 64} blocks for the sender side, the virtual particles and the
-    receiver side; the candidate steps alternate with steps of the best so far), timed whole;
+    sizes (152 x {8, 16, 32, 64} blocks for the sender and the receiver side, 152 x {2, 3, 4, 5}
+    for the virtual particles; the candidate steps alternate with steps of the best so far),
+    timed whole;
     the winner is kept and reused by a later context of the same configuration and size, which
     does not tune.  Sizes given in the configuration switch the tuning off.  The results agree
     bit for bit whatever the sizes."""
@@ -805,8 +806,8 @@ def test_launch_size_tuning_changes_nothing_but_time():
         seen.add((sa["grid_send"], sa["grid_virtual"], sa["grid_receive"]))
     assert len(seen) >= 9            # every candidate ran
     final = (sa["grid_send"], sa["grid_virtual"], sa["grid_receive"])
-    for k in final:
-        assert k in (1216, 2432, 4864, 9728)
+    assert final[0] in (1216, 2432, 4864, 9728) and final[2] in (1216, 2432, 4864, 9728)
+    assert final[1] in (304, 456, 608, 760)
     sb = b.stats()
     assert (sb["grid_send"], sb["grid_virtual"], sb["grid_receive"]) == (152, 304, 456)
     c = rt.context_for(wl, tune_launch=1)
