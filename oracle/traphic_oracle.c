@@ -11,9 +11,9 @@
  * 2011), the reading taken is stated at the function that implements it.
  *
  * Parity unpinned (no printed number or closed form fixes them; checked only through
- * the physical limits): the values of the collisional ionisation, collisional excitation
- * and free-free fits (the ionisation cooling's tie to the ionisation energy and the
- * free-free sqrt(T) scaling are pinned).  Where a virtual particle lands is checked statistically against the
+ * the physical limits): the normalisations of the collisional ionisation and collisional
+ * excitation fits (their activation energies, the ionisation cooling's tie to the
+ * ionisation energy, and the free-free normalisation and sqrt(T) scaling are pinned).  Where a virtual particle lands is checked statistically against the
  * uniform law of its reading; the rest of its step (its interpolated n_HI, projected length,
  * clock and the sharing of its absorptions) by invariants of a uniform medium and by brute
  * force of whole chains on tiny boxes.  The equal split among cone members and the

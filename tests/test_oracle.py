@@ -217,6 +217,38 @@ def test_collisional_ionisation_cooling_removes_the_ionisation_energy():
         assert abs(oracle.rates(4 * T)["L_ff"] / r["L_ff"] - 2) < 1e-12
 
 
+def _activation_temperature(name, T, h=1e-3):
+    """-d ln(rate) / d(1/T) at T, by a central difference in 1/T."""
+    u = 1.0 / T
+    a = oracle.rates(1.0 / (u * (1 + h)))[name]
+    b = oracle.rates(1.0 / (u * (1 - h)))[name]
+    return -(math.log(a) - math.log(b)) / (2 * h * u)
+
+
+def test_collisional_rates_have_the_atomic_activation_energies():
+    """A collisional rate of H I is a Boltzmann factor exp(-E/kT) times a slowly varying
+    function of T, with E the energy the collision must supply.  So -d ln(rate)/d(1/T) tends to
+    E/k as T falls, with corrections of order T:
+    - collisional ionisation (beta): the ionisation energy of hydrogen, 13.598 eV;
+    - collisional excitation cooling: the excitation of the n = 2 level, 3/4 of 13.598 eV
+      (the Lyman-alpha energy, 10.2 eV).
+    A fit with the wrong level, the wrong energy or a mistyped exponent fails."""
+    E_ion = 13.598 * EV / K_B
+    E_12 = 0.75 * E_ion
+    for T, tol in ((1000.0, 0.005), (2000.0, 0.01)):
+        assert abs(_activation_temperature("beta", T) / E_ion - 1) < tol
+        assert abs(_activation_temperature("L_cex", T) / E_12 - 1) < tol / 2
+
+
+def test_free_free_cooling_has_the_textbook_normalisation():
+    """Thermal bremsstrahlung of a hydrogen plasma emits 1.4e-27 T^(1/2) n_e n_p g_B erg cm^-3
+    s^-1, with the frequency-averaged Gaunt factor g_B between 1.1 and 1.5 (Rybicki & Lightman
+    1979, Eq. 5.15b and the text after it)."""
+    for T in (1e4, 3e4, 1e5, 1e6):
+        g = oracle.rates(T)["L_ff"] / (1.4e-27 * math.sqrt(T))
+        assert 1.1 <= g <= 1.5, (T, g)
+
+
 def test_recombination_heating_energy():
     v, tol = paper_values()["kT_27000K_eV"]
     assert abs(K_B * 27000 / EV / v - 1) < tol

@@ -25,6 +25,8 @@ CONE = [T.test_transmission_cone_solid_angle]
 BIN = [T.test_reception_bin_is_nearest_rotated_axis]
 RATES = [T.test_recombination_coefficients_match_paper,
          T.test_collisional_ionisation_cooling_removes_the_ionisation_energy]
+COLLISIONAL = [T.test_collisional_rates_have_the_atomic_activation_energies,
+               T.test_free_free_cooling_has_the_textbook_normalisation]
 CHEM = [T.test_chemistry_photon_accounting_and_recombination_photons]
 CHAIN = [T.test_beer_lambert_chain]
 PHILOX = [T.test_philox_known_answers]
@@ -53,6 +55,12 @@ MUTATIONS = {
                                        "double Lci = 0.5 * K_B * T_HI * beta;", RATES),
     "free_free_wrong_power": ("double Lff = 1.42e-27 * 1.3 * sqrt(T);",
                               "double Lff = 1.42e-27 * 1.3 * pow(T, 0.45);", RATES),
+    "free_free_gaunt_factor_doubled": ("double Lff = 1.42e-27 * 1.3 * sqrt(T);",
+                                       "double Lff = 1.42e-27 * 2.6 * sqrt(T);", COLLISIONAL),
+    "excitation_to_the_n3_level": ("double Lce = 7.5e-19 * exp(-118348.0 / T)",
+                                   "double Lce = 7.5e-19 * exp(-140265.0 / T)", COLLISIONAL),
+    "ionisation_boltzmann_factor_halved": ("pow(T, -1.5) * exp(-lam / 2.0)",
+                                           "pow(T, -1.5) * exp(-lam / 4.0)", COLLISIONAL),
     "photoionisation_rate_per_atom_not_neutral": ("Gam = phot / (NHI * dt);",
                                                   "Gam = phot / (NH * dt);", CHEM),
     "optical_depth_with_total_density": ("double tau = (sig * s->nHI[j]) * l;",
